@@ -1,0 +1,176 @@
+/*
+ * gc.h -- exact per-edge 3/4-node graphlet counting on one GB300 GPU (sm_103a).
+ *
+ * C ABI of libgc.so. Implements the data-parallel hot path of Rossi & Zhou,
+ * "Hybrid CPU-GPU Framework for Network Motifs" (arXiv 1608.05138):
+ *   Problem 1 (global graphlet counting): for the 17 graphlets H_1..H_17 of
+ *   Table 1 (all connected and disconnected induced subgraphs on 2, 3 and 4
+ *   vertices) count their induced embeddings in G;
+ *   the edge-centric method of Sec. 4: per edge e = (u, v) the triangle set T
+ *   and star sets S_u, S_v (Fig. 2, Alg. 1/2), the 4-cliques over T
+ *   (Alg. 3/5) and the induced 4-cycles over S_u x S_v (Alg. 4/6), the
+ *   per-edge 3-graphlet equations and unrestricted counts C_3..C_16
+ *   (Sec. 4.5), and the global counts X_1..X_17 (Sec. 4.6).
+ *
+ * General conventions
+ *   - No C++ exception crosses this boundary; every call returns a gc_status.
+ *     On failure gc_last_error() returns a thread-local message.
+ *   - Inputs are owned by the caller and are copied during the call; the
+ *     library keeps no pointer to them. Outputs are caller-owned. Handles are
+ *     library-owned until gc_graph_free / gc_batch_destroy.
+ *   - A handle must not be used from two threads at the same time.
+ *   - Graphs are CSR with int32 indices: row_ptr[n + 1] with row_ptr[0] = 0,
+ *     col_idx[row_ptr[n]]; each row sorted strictly ascending, the graph
+ *     undirected (symmetric), without self-loops. n counts every vertex,
+ *     isolated ones included (they change X_2, X_5, X_6, X_13..X_17).
+ *     2m = row_ptr[n] must be below 2^31.
+ *   - Edge ids: edge e is the e-th pair (u, v), u < v, met in row-major order
+ *     of the upper triangle of the CSR.
+ *   - Counts are exact integers. Global counts are 128-bit: global_out[i-1]
+ *     holds the low 64 bits of X_i, global_hi[i-1] the high 64 bits.
+ */
+#ifndef GC_H
+#define GC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gc_graph_s* gc_graph;
+typedef struct gc_batch_s* gc_batch;
+typedef int gc_status;
+
+enum {
+  GC_OK = 0,
+  GC_PENDING = 1,          /* gc_batch_poll: not finished yet */
+  GC_ERR_ARG = -1,         /* NULL handle/pointer, negative size, bad flag */
+  GC_ERR_UNSORTED = -2,    /* a row of col_idx is not ascending, or row_ptr decreases */
+  GC_ERR_DUPLICATE = -3,   /* a neighbour appears twice in one row */
+  GC_ERR_SELF_LOOP = -4,   /* col_idx of row x contains x */
+  GC_ERR_ASYMMETRIC = -5,  /* (x, y) present without (y, x) */
+  GC_ERR_RANGE = -6,       /* column index outside [0, n), row_ptr[0] != 0 */
+  GC_ERR_NOMEM = -7,       /* device or host allocation failed */
+  GC_ERR_CUDA = -8,        /* a CUDA call failed (message has the CUDA error) */
+  GC_ERR_OVERFLOW = -9,    /* 2m >= 2^31, or a high word is needed but global_hi is NULL */
+  GC_ERR_TIMEOUT = -10,    /* a bounded device wait gave up (device status word set) */
+  GC_ERR_BUSY = -11        /* gc_batch_submit: the device-memory budget is full */
+};
+
+#define GC_EDGE_COLS 13      /* per-edge columns, see gc_count_edge_graphlets */
+#define GC_NUM_GRAPHLETS 17  /* X_1 .. X_17 */
+#define GC_NUM_CSUMS 13      /* C_3 C_4 C_5 C_7 .. C_16 */
+
+/* gc_graph_upload flags */
+#define GC_NO_VALIDATE 0x1u  /* skip the host-side CSR checks (caller guarantees them) */
+
+/* Thread-local message describing the last failed call of this thread. */
+const char* gc_last_error(void);
+
+/*
+ * Validate a CSR graph on the host, copy it to the device and prepare it
+ * (Problem 1 input; preprocessing P3 of Sec. 4.3; edge ordering Pi of Sec. 4.4).
+ *   n        number of vertices, 0 <= n < 2^31
+ *   row_ptr  host pointer, n + 1 int32
+ *   col_idx  host pointer, row_ptr[n] int32
+ *   flags    0 or GC_NO_VALIDATE
+ *   stream   cudaStream_t (as void*) on which all work of this graph runs;
+ *            NULL = the legacy default stream
+ *   out      receives the new handle
+ * Errors: GC_ERR_ARG, GC_ERR_RANGE, GC_ERR_UNSORTED, GC_ERR_DUPLICATE,
+ * GC_ERR_SELF_LOOP, GC_ERR_ASYMMETRIC, GC_ERR_OVERFLOW (2m >= 2^31),
+ * GC_ERR_NOMEM, GC_ERR_CUDA. On error *out is NULL and nothing is leaked.
+ * The call returns after the device data is ready.
+ */
+gc_status gc_graph_upload(int32_t n, const int32_t* row_ptr, const int32_t* col_idx,
+                          uint32_t flags, void* stream, gc_graph* out);
+
+/* n and the number of undirected edges m = row_ptr[n] / 2. Either pointer may be NULL. */
+gc_status gc_graph_info(gc_graph g, int64_t* n, int64_t* m);
+
+/* Edge list in edge-id order: uv[2e] = u, uv[2e+1] = v, u < v. uv is a host
+ * pointer to 2m int32. */
+gc_status gc_graph_edges(gc_graph g, int32_t* uv);
+
+/*
+ * Count every 2/3/4-node graphlet (Problem 1) by the per-edge method.
+ *   per_edge_out  NULL (skip), or a host or device pointer (detected with
+ *                 cudaPointerGetAttributes) to m x GC_EDGE_COLS uint64, row e
+ *                 for edge id e, columns (T, S_u, S_v of Fig. 2; D_e as in
+ *                 Sec. 4.5):
+ *                   0 x3  = |T|                     (triangles on e)
+ *                   1 x4  = |S_u| + |S_v|           (2-stars on e)
+ *                   2 x5  = D_e = n-2-|T|-|S_u|-|S_v| (3-node-1-edge on e)
+ *                   3 x7  = 4-cliques containing e
+ *                   4 x10 = induced 4-cycles containing e
+ *                   5 C(|T|,2)        6 |T|(|S_u|+|S_v|)
+ *                   7 C(|S_u|,2)+C(|S_v|,2)            8 |S_u||S_v|
+ *                   9 |T| D_e        10 m - d_u - d_v + 1
+ *                  11 (|S_u|+|S_v|) D_e               12 C(D_e,2)
+ *                 (columns 5..12 are the per-edge summands of C_8, C_9,
+ *                 C_11..C_16; all columns are symmetric in u and v).
+ *   global_out    host pointer, 17 uint64: low 64 bits of X_1..X_17 (Table 1
+ *                 numbering, Sec. 4.6); must not be NULL.
+ *   global_hi     host pointer, 17 uint64 for the high 64 bits, or NULL. If
+ *                 NULL and some X_i >= 2^64 the call writes the low words and
+ *                 returns GC_ERR_OVERFLOW.
+ * Runs on the graph's stream and returns when the results are written.
+ * Errors: GC_ERR_ARG, GC_ERR_CUDA, GC_ERR_NOMEM, GC_ERR_OVERFLOW.
+ */
+gc_status gc_count_edge_graphlets(gc_graph g, uint64_t* per_edge_out, uint64_t* global_out,
+                                  uint64_t* global_hi);
+
+/* The 13 unrestricted counts C_3, C_4, C_5, C_7, C_8, ..., C_16 (Sec. 4.5) of
+ * the last gc_count_edge_graphlets on g, as low/high 64-bit words (host
+ * pointers, 13 each; hi may be NULL). GC_ERR_ARG if g was never counted. */
+gc_status gc_graph_csums(gc_graph g, uint64_t* lo, uint64_t* hi);
+
+/* Device time of each phase of the last gc_count_edge_graphlets, measured
+ * with CUDA events on the graph's stream. ms: host array of
+ * gc_phase_count() doubles. */
+int gc_phase_count(void);
+const char* gc_phase_name(int i);
+gc_status gc_graph_phase_ms(gc_graph g, double* ms);
+
+/* Release the graph and all its device memory. NULL is accepted. */
+gc_status gc_graph_free(gc_graph g);
+
+/*
+ * Batched and served counting of many graphs (global counts only).
+ *
+ * gc_batch_create: a runtime with its own CUDA stream that keeps admitted
+ *   graphs resident on the device and counts them in shared launches (one
+ *   persistent kernel per pass over all graphs of a launch, with work
+ *   stealing over the graphs' vertex groups). device_mem_budget_bytes bounds
+ *   the device memory the admitted graphs may hold at once (> 0).
+ *   flags: 0, or GC_BATCH_MANUAL (launch only on gc_batch_flush; otherwise a
+ *   dispatcher thread launches pending graphs as soon as the device is free:
+ *   continuous batching).
+ * gc_batch_submit: validates and copies one CSR graph (same rules as
+ *   gc_graph_upload), admits it if it fits in the budget, and returns a
+ *   ticket. GC_ERR_BUSY if it does not fit now (retry after polling), or
+ *   GC_ERR_NOMEM if it could never fit.
+ * gc_batch_flush: launch everything pending now (returns without waiting).
+ * gc_batch_poll: waits up to timeout_us microseconds (0 = just test, < 0 =
+ *   forever) for the ticket. GC_OK: global_out/global_hi (17 words each, hi
+ *   may be NULL as above) hold X_1..X_17 and the ticket is retired; GC_PENDING:
+ *   not finished; GC_ERR_ARG: unknown or already retired ticket;
+ *   GC_ERR_TIMEOUT: the device reported a bounded wait that gave up.
+ * gc_batch_destroy: waits for outstanding work and frees everything.
+ */
+#define GC_BATCH_MANUAL 0x1u
+gc_status gc_batch_create(int64_t device_mem_budget_bytes, uint32_t flags, gc_batch* out);
+gc_status gc_batch_submit(gc_batch b, int32_t n, const int32_t* row_ptr, const int32_t* col_idx,
+                          uint64_t* ticket_out);
+gc_status gc_batch_flush(gc_batch b);
+gc_status gc_batch_poll(gc_batch b, uint64_t ticket, uint64_t* global_out, uint64_t* global_hi,
+                        int32_t timeout_us);
+gc_status gc_batch_destroy(gc_batch b);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GC_H */

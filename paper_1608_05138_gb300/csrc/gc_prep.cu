@@ -1,0 +1,355 @@
+// gc_prep.cu -- one-time device preparation of an uploaded graph.
+//
+//   * degrees d_x and the P3 orientation of every edge (Sec. 4.3): the "low"
+//     endpoint u has the smaller (degree, id) pair, the "high" endpoint v the
+//     larger, so d_v >= d_u;
+//   * edge ids (rank of (u, v), u < v, in row-major upper-triangle order) and
+//     the slot -> edge id map of both CSR directions;
+//   * degree-oriented out-lists: out(x) = neighbours of higher (degree, id)
+//     rank, ascending ids. Each pair {a, b} of adjacent vertices appears in
+//     exactly one out-list; the 4-clique step uses this to count each pair
+//     of T once (the role of the Psi reset in Alg. 5);
+//   * the work units of the counting passes: every vertex v that is the high
+//     endpoint of at least one edge forms one "v-group" (its low neighbours);
+//     groups are binned by floor(log2(estimated work)) and listed heaviest
+//     bin first -- the difficulty-ordered edge queue Pi of Sec. 4.4 at group
+//     granularity, with d_v + sum_{r in Gamma(v)} d_r as the work estimate
+//     (a vertex analogue of the vol ordering of Table 4).
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "gc_internal.h"
+
+namespace gc {
+namespace {
+
+constexpr int kScanTile = 2048;  // elements per scan tile (256 threads x 8)
+
+__device__ __forceinline__ bool rank_less(const int32_t* deg, int32_t a, int32_t b) {
+  int32_t da = deg[a], db = deg[b];
+  return da < db || (da == db && a < b);
+}
+
+// first index in [lo, hi) with a[i] >= key
+__device__ __forceinline__ int32_t lower_bound_i32(const int32_t* a, int32_t lo, int32_t hi,
+                                                   int32_t key) {
+  while (lo < hi) {
+    int32_t mid = lo + ((hi - lo) >> 1);
+    if (a[mid] < key) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void k_deg_up(int32_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                         int32_t* __restrict__ deg, int32_t* __restrict__ up) {
+  for (int32_t x = blockIdx.x * blockDim.x + threadIdx.x; x < n; x += gridDim.x * blockDim.x) {
+    int32_t b = rp[x], e = rp[x + 1];
+    deg[x] = e - b;
+    up[x] = e - lower_bound_i32(ci, b, e, x + 1);
+  }
+}
+
+// Warp per vertex: number of higher-rank neighbours, sum of neighbour degrees,
+// maximum degree.
+__global__ void k_out_cnt(int32_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                          const int32_t* __restrict__ deg, int32_t* __restrict__ out_cnt,
+                          long long* __restrict__ S, int32_t* __restrict__ dmax) {
+  const int lane = threadIdx.x & 31;
+  const int warps = (gridDim.x * blockDim.x) >> 5;
+  for (int32_t x = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < n; x += warps) {
+    int32_t b = rp[x], e = rp[x + 1];
+    int32_t c = 0;
+    long long s = 0;
+    for (int32_t p = b + lane; p < e; p += 32) {
+      int32_t y = ci[p];
+      c += rank_less(deg, x, y) ? 1 : 0;
+      s += deg[y];
+    }
+    for (int o = 16; o; o >>= 1) {
+      c += __shfl_xor_sync(0xffffffffu, c, o);
+      s += __shfl_xor_sync(0xffffffffu, s, o);
+    }
+    if (lane == 0) {
+      out_cnt[x] = c;
+      S[x] = s;
+      if (e - b > 0) atomicMax(dmax, e - b);
+    }
+  }
+}
+
+// Warp per vertex: edge ids of every slot, edge list, out-lists.
+__global__ void k_edges(int32_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                        const int32_t* __restrict__ deg, const int32_t* __restrict__ up,
+                        const int32_t* __restrict__ upoff, const int32_t* __restrict__ out_ptr,
+                        int32_t* __restrict__ eid, int32_t* __restrict__ uv,
+                        int32_t* __restrict__ out_idx) {
+  const int lane = threadIdx.x & 31;
+  const int warps = (gridDim.x * blockDim.x) >> 5;
+  for (int32_t x = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < n; x += warps) {
+    const int32_t b = rp[x], e = rp[x + 1];
+    const int32_t first_up = e - up[x];
+    int32_t o = out_ptr[x];
+    for (int32_t base = b; base < e; base += 32) {
+      int32_t p = base + lane;
+      bool valid = p < e;
+      int32_t y = valid ? ci[p] : 0;
+      bool is_out = valid && rank_less(deg, x, y);
+      if (valid) {
+        int32_t id;
+        if (y > x) {
+          id = upoff[x] + (p - first_up);
+          uv[2 * (int64_t)id] = x;
+          uv[2 * (int64_t)id + 1] = y;
+        } else {
+          int32_t yb = rp[y], ye = rp[y + 1];
+          int32_t q = lower_bound_i32(ci, yb, ye, x);  // x is in row y (symmetry)
+          id = (q < ye && ci[q] == x) ? upoff[y] + (q - (ye - up[y])) : 0;  // 0 only for invalid input
+        }
+        eid[p] = id;
+      }
+      unsigned mask = __ballot_sync(0xffffffffu, is_out);
+      if (is_out) out_idx[o + __popc(mask & ((1u << lane) - 1u))] = y;
+      o += __popc(mask);
+    }
+  }
+}
+
+__device__ __forceinline__ int bin_of(long long cost) {
+  return cost <= 1 ? 0 : 63 - __clzll(cost);
+}
+
+__global__ void k_bin_hist(int32_t n, const int32_t* __restrict__ deg,
+                           const int32_t* __restrict__ out_cnt, const long long* __restrict__ S,
+                           int32_t* __restrict__ hist) {
+  __shared__ int32_t h[64];
+  if (threadIdx.x < 64) h[threadIdx.x] = 0;
+  __syncthreads();
+  for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+    if (deg[v] - out_cnt[v] > 0) atomicAdd(&h[bin_of(S[v] + deg[v])], 1);
+  }
+  __syncthreads();
+  if (threadIdx.x < 64 && h[threadIdx.x]) atomicAdd(&hist[threadIdx.x], h[threadIdx.x]);
+}
+
+__global__ void k_bin_scatter(int32_t n, const int32_t* __restrict__ deg,
+                              const int32_t* __restrict__ out_cnt,
+                              const long long* __restrict__ S, int32_t* __restrict__ cursor,
+                              int32_t* __restrict__ units) {
+  for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+    if (deg[v] - out_cnt[v] > 0) {
+      int32_t pos = atomicAdd(&cursor[bin_of(S[v] + deg[v])], 1);
+      units[pos] = v;
+    }
+  }
+}
+
+// ---- exclusive scan of int32 (totals fit int32) ----
+__global__ void k_scan_tile_sums(int32_t n, const int32_t* __restrict__ in, int32_t* __restrict__ sums) {
+  __shared__ int32_t ws[8];
+  int32_t base = blockIdx.x * kScanTile;
+  int32_t s = 0;
+  for (int i = threadIdx.x; i < kScanTile; i += blockDim.x) {
+    int32_t k = base + i;
+    if (k < n) s += in[k];
+  }
+  for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int32_t t = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += ws[w];
+    sums[blockIdx.x] = t;
+  }
+}
+
+// single block: exclusive scan of the tile sums in place
+__global__ void k_scan_sums(int32_t nb, int32_t* __restrict__ sums) {
+  __shared__ int32_t ws[32];
+  __shared__ int32_t carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int32_t base = 0; base < nb; base += blockDim.x) {
+    int32_t k = base + threadIdx.x;
+    int32_t v = k < nb ? sums[k] : 0;
+    int32_t x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) ws[w] = x;
+    __syncthreads();
+    if (w == 0) {
+      int32_t t = lane < (int)(blockDim.x >> 5) ? ws[lane] : 0;
+      for (int o = 1; o < 32; o <<= 1) {
+        int32_t y = __shfl_up_sync(0xffffffffu, t, o);
+        if (lane >= o) t += y;
+      }
+      ws[lane] = t;
+    }
+    __syncthreads();
+    int32_t pre = (w > 0 ? ws[w - 1] : 0) + x - v + carry;
+    if (k < nb) sums[k] = pre;
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) carry = pre + v;
+    __syncthreads();
+  }
+}
+
+// out[k] = exclusive prefix, out[n] = total
+__global__ void k_scan_tiles(int32_t n, const int32_t* __restrict__ in,
+                             const int32_t* __restrict__ sums, int32_t* __restrict__ out) {
+  __shared__ int32_t ws[8];
+  const int per = kScanTile / 256;  // 8 consecutive elements per thread
+  int32_t base = blockIdx.x * kScanTile + threadIdx.x * per;
+  int32_t v[per];
+  int32_t t = 0;
+  for (int i = 0; i < per; ++i) {
+    int32_t k = base + i;
+    v[i] = k < n ? in[k] : 0;
+    t += v[i];
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int32_t x = t;
+  for (int o = 1; o < 32; o <<= 1) {
+    int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) ws[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    int32_t s = lane < 8 ? ws[lane] : 0;
+    for (int o = 1; o < 8; o <<= 1) {
+      int32_t y = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += y;
+    }
+    if (lane < 8) ws[lane] = s;
+  }
+  __syncthreads();
+  int32_t run = sums[blockIdx.x] + (w > 0 ? ws[w - 1] : 0) + x - t;
+  for (int i = 0; i < per; ++i) {
+    int32_t k = base + i;
+    if (k < n) out[k] = run;
+    run += v[i];
+    if (k == n - 1) out[n] = run;
+  }
+}
+
+gc_status exclusive_scan(int32_t n, const int32_t* in, int32_t* out, cudaStream_t s) {
+  if (n == 0) {
+    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(int32_t), s);
+    return e == cudaSuccess ? GC_OK : cuda_fail(e, "scan memset");
+  }
+  int32_t nb = (n + kScanTile - 1) / kScanTile;
+  int32_t* sums = nullptr;
+  cudaError_t e = cudaMallocAsync(&sums, sizeof(int32_t) * nb, s);
+  if (e != cudaSuccess) return cuda_fail(e, "scan alloc");
+  k_scan_tile_sums<<<nb, 256, 0, s>>>(n, in, sums);
+  k_scan_sums<<<1, 1024, 0, s>>>(nb, sums);
+  k_scan_tiles<<<nb, 256, 0, s>>>(n, in, sums, out);
+  e = cudaGetLastError();
+  cudaFreeAsync(sums, s);
+  return e == cudaSuccess ? GC_OK : cuda_fail(e, "scan launch");
+}
+
+int grid_for(int64_t work, int block) {
+  int64_t g = (work + block - 1) / block;
+  if (g < 1) g = 1;
+  if (g > 65535LL * 16) g = 65535LL * 16;
+  return (int)g;
+}
+
+}  // namespace
+
+void free_prep(PrepBuffers* p, cudaStream_t s) {
+  if (p->deg) cudaFreeAsync(p->deg, s);
+  if (p->eid) cudaFreeAsync(p->eid, s);
+  if (p->uv) cudaFreeAsync(p->uv, s);
+  if (p->out_ptr) cudaFreeAsync(p->out_ptr, s);
+  if (p->out_idx) cudaFreeAsync(p->out_idx, s);
+  if (p->units) cudaFreeAsync(p->units, s);
+  *p = PrepBuffers();
+}
+
+gc_status prepare_graph(int32_t n, int32_t m, const int32_t* d_rp, const int32_t* d_ci,
+                        const int32_t* d_vgid, PrepBuffers* out, cudaStream_t s) {
+  (void)d_vgid;
+  PrepBuffers P;
+  int32_t *up = nullptr, *upoff = nullptr, *out_cnt = nullptr, *dmax = nullptr, *hist = nullptr;
+  long long* S = nullptr;
+  gc_status st = GC_OK;
+  cudaError_t e = cudaSuccess;
+  const int64_t nnz = 2 * (int64_t)m;
+#define GC_TRY(call, what)                 \
+  do {                                     \
+    e = (call);                            \
+    if (e != cudaSuccess) {                \
+      st = cuda_fail(e, what);             \
+      goto fail;                           \
+    }                                      \
+  } while (0)
+  GC_TRY(cudaMallocAsync(&P.deg, sizeof(int32_t) * (n > 0 ? n : 1), s), "alloc deg");
+  GC_TRY(cudaMallocAsync(&P.eid, sizeof(int32_t) * (nnz > 0 ? nnz : 1), s), "alloc eid");
+  GC_TRY(cudaMallocAsync(&P.uv, sizeof(int32_t) * (nnz > 0 ? nnz : 1), s), "alloc uv");
+  GC_TRY(cudaMallocAsync(&P.out_ptr, sizeof(int32_t) * ((int64_t)n + 1), s), "alloc out_ptr");
+  GC_TRY(cudaMallocAsync(&P.out_idx, sizeof(int32_t) * (m > 0 ? m : 1), s), "alloc out_idx");
+  GC_TRY(cudaMallocAsync(&P.units, sizeof(int32_t) * (n > 0 ? n : 1), s), "alloc units");
+  GC_TRY(cudaMallocAsync(&up, sizeof(int32_t) * (n > 0 ? n : 1), s), "alloc up");
+  GC_TRY(cudaMallocAsync(&upoff, sizeof(int32_t) * ((int64_t)n + 1), s), "alloc upoff");
+  GC_TRY(cudaMallocAsync(&out_cnt, sizeof(int32_t) * (n > 0 ? n : 1), s), "alloc out_cnt");
+  GC_TRY(cudaMallocAsync(&S, sizeof(long long) * (n > 0 ? n : 1), s), "alloc S");
+  GC_TRY(cudaMallocAsync(&dmax, sizeof(int32_t) * 65, s), "alloc dmax");
+  hist = dmax + 1;
+  GC_TRY(cudaMemsetAsync(dmax, 0, sizeof(int32_t) * 65, s), "memset");
+  if (n > 0) {
+    k_deg_up<<<grid_for(n, 256), 256, 0, s>>>(n, d_rp, d_ci, P.deg, up);
+    GC_TRY(cudaGetLastError(), "k_deg_up");
+    if ((st = exclusive_scan(n, up, upoff, s)) != GC_OK) goto fail;
+    k_out_cnt<<<grid_for((int64_t)n * 32, 256), 256, 0, s>>>(n, d_rp, d_ci, P.deg, out_cnt, S, dmax);
+    GC_TRY(cudaGetLastError(), "k_out_cnt");
+    if ((st = exclusive_scan(n, out_cnt, P.out_ptr, s)) != GC_OK) goto fail;
+    k_edges<<<grid_for((int64_t)n * 32, 256), 256, 0, s>>>(n, d_rp, d_ci, P.deg, up, upoff,
+                                                            P.out_ptr, P.eid, P.uv, P.out_idx);
+    GC_TRY(cudaGetLastError(), "k_edges");
+    k_bin_hist<<<grid_for(n, 256), 256, 0, s>>>(n, P.deg, out_cnt, S, hist);
+    GC_TRY(cudaGetLastError(), "k_bin_hist");
+    {
+      int32_t h[65];
+      GC_TRY(cudaMemcpyAsync(h, dmax, sizeof(h), cudaMemcpyDeviceToHost, s), "copy hist");
+      GC_TRY(cudaStreamSynchronize(s), "sync hist");
+      P.dmax = h[0];
+      int32_t cur[64];
+      int32_t acc = 0;
+      for (int b = 63; b >= 0; --b) {  // heaviest bin first
+        cur[b] = acc;
+        acc += h[1 + b];
+      }
+      P.n_units = acc;
+      GC_TRY(cudaMemcpyAsync(hist, cur, sizeof(cur), cudaMemcpyHostToDevice, s), "copy cursors");
+      k_bin_scatter<<<grid_for(n, 256), 256, 0, s>>>(n, P.deg, out_cnt, S, hist, P.units);
+      GC_TRY(cudaGetLastError(), "k_bin_scatter");
+    }
+  } else {
+    GC_TRY(cudaMemsetAsync(P.out_ptr, 0, sizeof(int32_t), s), "memset out_ptr");
+  }
+    cudaFreeAsync(up, s);
+  cudaFreeAsync(upoff, s);
+  cudaFreeAsync(out_cnt, s);
+  cudaFreeAsync(S, s);
+  cudaFreeAsync(dmax, s);
+  *out = P;
+  return GC_OK;
+fail:
+  cudaStreamSynchronize(s);
+  if (up) cudaFreeAsync(up, s);
+  if (upoff) cudaFreeAsync(upoff, s);
+  if (out_cnt) cudaFreeAsync(out_cnt, s);
+  if (S) cudaFreeAsync(S, s);
+  if (dmax) cudaFreeAsync(dmax, s);
+  free_prep(&P, s);
+  return st;
+#undef GC_TRY
+}
+
+}  // namespace gc

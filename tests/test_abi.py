@@ -1,0 +1,84 @@
+"""The C-ABI library builds, loads and exports every entry point that
+include/gc.h declares; host-side CSR validation returns the documented error
+codes before any device work (no GPU needed)."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_1608_05138_gb300 as gcb
+from tests import graphs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "gc.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(gc_[a-z_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1608_05138_gb300 import build
+    build.build()
+    return gcb.lib()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 15
+    for name in names:
+        assert hasattr(lib, name), name
+    assert sorted(gcb.EXPORTED) == names
+
+
+def test_library_is_built_for_sm103a(lib):
+    import subprocess
+    out = subprocess.run(["cuobjdump", "--list-elf", gcb.library_path()], capture_output=True, text=True)
+    if out.returncode != 0:
+        pytest.skip("cuobjdump unavailable")
+    assert "sm_103a" in out.stdout
+
+
+def _err(rp, ci):
+    with pytest.raises(gcb.GcError) as ei:
+        gcb.gc_graph_upload(np.asarray(rp, np.int32), np.asarray(ci, np.int32))
+    return ei.value.status
+
+
+def test_validation_error_codes(lib):
+    # unsorted row
+    assert _err([0, 2, 3, 4], [2, 1, 0, 0]) == -2
+    # duplicate neighbour
+    assert _err([0, 2, 4], [1, 1, 0, 0]) == -3
+    # self-loop
+    assert _err([0, 2, 4], [0, 1, 0, 1]) == -4
+    # asymmetric: 0-1 present, 1-0 missing, 1-2 / 2-1 present
+    assert _err([0, 1, 2, 3], [1, 2, 1]) == -5
+    # out of range
+    assert _err([0, 1, 2], [5, 0]) == -6
+    # row_ptr[0] != 0
+    assert _err([1, 2, 3], [1, 0]) == -6
+    # decreasing row_ptr
+    assert _err([0, 2, 1, 4], [1, 2, 0, 0]) == -2
+
+
+def test_valid_graph_passes_host_validation_first(lib):
+    # a valid graph gets past validation; without a GPU the next step fails
+    # with a CUDA error, never a validation code.
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("GPU present: covered by the GPU tests")
+    rp, ci = graphs.complete(4)
+    with pytest.raises(gcb.GcError) as ei:
+        gcb.gc_graph_upload(rp, ci)
+    assert ei.value.status in (-7, -8)
+
+
+def test_no_fallback_when_library_missing(monkeypatch, tmp_path):
+    monkeypatch.setattr(gcb, "_SO", str(tmp_path / "missing.so"))
+    monkeypatch.setattr(gcb, "_lib", None)
+    with pytest.raises(RuntimeError):
+        gcb.lib()

@@ -1,0 +1,254 @@
+"""GPU path (libgc.so through the C ABI) against the CPU oracle, bit-exact.
+
+Counts are integers, so the tolerance is zero: every per-edge column and
+every global count must be equal. Small and medium graphs are compared in
+full; the full-size power-law graphs are compared on sampled edges computed
+one by one by the oracle, plus the exact relation between the GPU's own
+per-edge rows and its global counts.
+"""
+import numpy as np
+import pytest
+
+import graphgen
+import oracle
+import paper_1608_05138_gb300 as gcb
+from tests import graphs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1608_05138_gb300 import build
+    build.build()
+
+
+def gpu_count(rp, ci, per_edge=True):
+    with gcb.Graph(rp, ci) as g:
+        pe = np.zeros((g.m, 13), np.uint64) if per_edge else None
+        X = g.count(pe)
+        return X, pe, g.csums(), g.edges()
+
+
+def assert_parity(rp, ci):
+    X, pe, cs, uv = gpu_count(rp, ci)
+    o = oracle.count(rp, ci)
+    np.testing.assert_array_equal(uv, oracle.edges(rp, ci))
+    np.testing.assert_array_equal(pe, o["per_edge"])
+    assert cs == o["csum"]
+    assert X == o["X"]
+    return X, pe
+
+
+def test_er2000_config_bit_exact():
+    rp, ci = graphgen.config_er2000()
+    X, pe = assert_parity(rp, ci)
+    assert X[0] == len(ci) // 2
+
+
+@pytest.mark.parametrize("seed", range(1, 13))
+def test_random_graphs(seed):
+    for n, p in ((7, 0.5), (40, 0.3), (150, 0.08), (300, 0.02), (64, 0.9)):
+        assert_parity(*graphgen.er(n, p, seed * 100 + n))
+
+
+@pytest.mark.parametrize("seed", range(1, 5))
+def test_power_law_graphs(seed):
+    assert_parity(*graphgen.chung_lu(3000, 15000, 2.1, 30000.0, 800.0, seed))
+    assert_parity(*graphgen.rmat(11, 16, 0.57, 0.19, 0.19, seed))
+
+
+def test_closed_form_families():
+    for rp, ci in (graphs.complete(30), graphs.cycle(17), graphs.complete_bipartite(7, 9),
+                   graphs.star(3000), graphs.petersen(), graphs.cube(), graphs.wheel(12)):
+        assert_parity(rp, ci)
+
+
+def test_degenerate_graphs():
+    for n in (0, 1, 2, 5):
+        X, pe, _, _ = gpu_count(*graphs.empty(n))
+        assert X == oracle.count(*graphs.empty(n))["X"] and pe.shape == (0, 13)
+    assert_parity(*graphs.csr(2, [(0, 1)]))
+    assert_parity(*graphs.csr(9, [(3, 7)]))          # single edge, 7 isolated vertices
+    assert_parity(*graphs.csr(40, [(0, 1), (1, 2), (0, 2), (30, 31)]))
+
+
+def test_wide_counts_need_high_words():
+    n = 70000  # C(n, 4) > 2^64
+    rp, ci = graphs.csr(n, [(0, 1), (1, 2)])
+    with gcb.Graph(rp, ci) as g:
+        X = g.count()
+        assert X == oracle.count(rp, ci, per_edge=False)["X"] and X[16] >= 2**64
+        with pytest.raises(gcb.GcError) as ei:
+            g.count(wide=False)
+        assert ei.value.status == -9
+
+
+def test_triangle_list_beyond_shared_buffer():
+    # book graph: two adjacent hubs sharing 1500 neighbours (|T| = 1500), with
+    # a matching and a few triangles among the shared neighbours.
+    k = 1500
+    edges = [(0, 1)] + [(0, 2 + i) for i in range(k)] + [(1, 2 + i) for i in range(k)]
+    edges += [(2 + i, 3 + i) for i in range(0, k - 1, 2)]
+    edges += [(2 + i, 4 + i) for i in range(0, 60, 3)]
+    edges += [(2 + k + j, 2 + j) for j in range(50)]
+    assert_parity(*graphs.csr(2 + k + 50, edges))
+
+
+def test_global_psi_tables():
+    # more vertices than the shared-memory table holds
+    assert_parity(*graphgen.chung_lu(60000, 300000, 2.1, 600000.0, 3000.0, 21))
+
+
+def test_relabelling_is_metamorphic():
+    rp, ci = graphgen.chung_lu(2000, 12000, 2.1, 24000.0, 500.0, 22)
+    n = len(rp) - 1
+    perm = np.random.default_rng(5).permutation(n)
+    E = graphs.edges_of(rp, ci)
+    rp2, ci2 = graphs.csr(n, [(int(perm[a]), int(perm[b])) for a, b in E])
+    X1, pe1, _, uv1 = gpu_count(rp, ci)
+    X2, pe2, _, uv2 = gpu_count(rp2, ci2)
+    assert X1 == X2
+    pos = {(int(a), int(b)): i for i, (a, b) in enumerate(uv2)}
+    for i, (a, b) in enumerate(uv1):
+        pa, pb = int(perm[a]), int(perm[b])
+        j = pos[(min(pa, pb), max(pa, pb))]
+        np.testing.assert_array_equal(pe1[i], pe2[j])
+
+
+def test_device_output_and_repeat():
+    import torch
+    rp, ci = graphgen.rmat(12, 16, 0.57, 0.19, 0.19, 23)
+    with gcb.Graph(rp, ci) as g:
+        host = np.zeros((g.m, 13), np.uint64)
+        X1 = g.count(host)
+        dev = torch.zeros((g.m, 13), dtype=torch.int64, device="cuda")
+        X2 = g.count(dev)
+        X3 = g.count()
+        assert X1 == X2 == X3
+        np.testing.assert_array_equal(dev.cpu().numpy().view(np.uint64), host)
+        ms = g.phase_ms()
+        assert set(ms) == set(gcb.gc_phase_names()) and all(v >= 0 for v in ms.values())
+
+
+def _sampled_check(rp, ci, k=1500, seed=0):
+    """Full-size graph: sampled rows against the oracle one by one, and the
+    GPU's global counts against the derivation from its own per-edge rows."""
+    import torch
+    with gcb.Graph(rp, ci) as g:
+        dev = torch.zeros((g.m, 13), dtype=torch.int64, device="cuda")
+        X = g.count(dev)
+        cs = g.csums()
+        m = g.m
+        rng = np.random.default_rng(seed)
+        deg = np.diff(rp)
+        uv = g.edges()
+        heavy = np.argsort(-(deg[uv[:, 0]].astype(np.int64) * deg[uv[:, 1]]))[:20]
+        ids = np.unique(np.concatenate([rng.integers(0, m, k), heavy, [0, m - 1]])).astype(np.int64)
+        rows = dev[torch.from_numpy(ids).cuda()].cpu().numpy().view(np.uint64)
+        np.testing.assert_array_equal(rows, oracle.count_sample(rp, ci, ids))
+        # column sums of the GPU's per-edge rows (exact, in Python ints) equal
+        # its unrestricted counts, and the derivation reproduces its globals
+        colsum = [int(dev[:, c].sum(dtype=torch.int64).item()) for c in range(13)]
+        order = [0, 1, 2, 3, 5, 6, 4, 7, 8, 9, 10, 11, 12]
+        for kk, c in enumerate(order):
+            assert colsum[c] % (1 << 64) == cs[kk] % (1 << 64) or colsum[c] == cs[kk]
+        rc, Xd = oracle.derive(len(rp) - 1, m, cs)
+        assert rc == 0 and Xd == X
+        n = len(rp) - 1
+        from math import comb
+        assert sum(X[6:17]) == comb(n, 4) and sum(X[2:6]) == comb(n, 3)
+        assert X[3] == int(sum(comb(int(d), 2) for d in deg)) - 3 * X[2]
+
+
+def test_chung_lu_1m_config_sampled():
+    rp, ci = graphgen.config_chung_lu()
+    _sampled_check(rp, ci, k=1000, seed=1)
+
+
+def test_rmat22_config_sampled():
+    rp, ci = graphgen.config_rmat(22)
+    _sampled_check(rp, ci, k=300, seed=2)
+
+
+# ---------------- batched / served form ----------------
+
+def _oracle_X(rp, ci):
+    return oracle.count(rp, ci, per_edge=False, threads=4)["X"]
+
+
+@pytest.mark.parametrize("manual", [True, False])
+def test_batch_matches_plain_and_oracle(manual):
+    B = graphgen.batch(300, n_lo=20, n_hi=200, seed=31)
+    b = gcb.gc_batch_create(8 << 30, gcb.GC_BATCH_MANUAL if manual else 0)
+    try:
+        tickets = [gcb.gc_batch_submit(b, *B.graph(i)) for i in range(len(B))]
+        gcb.gc_batch_flush(b)
+        res = [gcb.gc_batch_poll(b, t, timeout_us=60_000_000) for t in tickets]
+    finally:
+        gcb.gc_batch_destroy(b)
+    for i in range(len(B)):
+        assert res[i] == _oracle_X(*B.graph(i)), i
+
+
+def test_batch_large_graphs_in_one_launch():
+    gs = [graphgen.chung_lu(30000, 150000, 2.2, 300000.0, 2000.0, 40 + i) for i in range(3)]
+    gs.append(graphgen.er(500, 0.3, 44))
+    b = gcb.gc_batch_create(16 << 30, gcb.GC_BATCH_MANUAL)
+    try:
+        ts = [gcb.gc_batch_submit(b, *g) for g in gs]
+        gcb.gc_batch_flush(b)
+        res = [gcb.gc_batch_poll(b, t, timeout_us=120_000_000) for t in ts]
+    finally:
+        gcb.gc_batch_destroy(b)
+    for g, r in zip(gs, res):
+        assert r == _oracle_X(*g)
+
+
+def test_batch_budget_and_tickets():
+    rp, ci = graphgen.er(300, 0.2, 50)
+    b = gcb.gc_batch_create(1 << 20, gcb.GC_BATCH_MANUAL)  # 1 MiB: a few small graphs
+    try:
+        t1 = gcb.gc_batch_submit(b, rp, ci)
+        busy = None
+        for _ in range(100):
+            busy = gcb.gc_batch_try_submit(b, rp, ci)
+            if busy is None:
+                break
+        assert busy is None, "budget never filled"
+        big = graphgen.er(3000, 0.5, 51)
+        with pytest.raises(gcb.GcError) as ei:
+            gcb.gc_batch_submit(b, *big)
+        assert ei.value.status == -7
+        assert gcb.gc_batch_poll(b, t1, timeout_us=0) is None  # nothing launched yet
+        gcb.gc_batch_flush(b)
+        assert gcb.gc_batch_poll(b, t1, timeout_us=120_000_000) == _oracle_X(rp, ci)
+        with pytest.raises(gcb.GcError):
+            gcb.gc_batch_poll(b, t1, timeout_us=0)  # retired
+        t2 = gcb.gc_batch_try_submit(b, rp, ci)     # budget freed after retirement
+        assert t2 is not None
+        gcb.gc_batch_flush(b)
+        assert gcb.gc_batch_poll(b, t2, timeout_us=120_000_000) == _oracle_X(rp, ci)
+    finally:
+        gcb.gc_batch_destroy(b)
+
+
+def test_served_result_same_alone_and_in_mix():
+    params = graphgen.serving_params(12, m_lo=1000, m_hi=60000, seed=7)
+    gs = [graphgen.serving_graph(params, r) for r in range(12)]
+    alone = []
+    for g in gs:
+        b = gcb.gc_batch_create(4 << 30, 0)
+        try:
+            alone.append(gcb.gc_batch_poll(b, gcb.gc_batch_submit(b, *g), timeout_us=120_000_000))
+        finally:
+            gcb.gc_batch_destroy(b)
+    b = gcb.gc_batch_create(4 << 30, 0)
+    try:
+        ts = [gcb.gc_batch_submit(b, *g) for g in gs]
+        mix = [gcb.gc_batch_poll(b, t, timeout_us=120_000_000) for t in ts]
+    finally:
+        gcb.gc_batch_destroy(b)
+    assert mix == alone
+    for g, r in zip(gs[:4], mix[:4]):
+        assert r == _oracle_X(*g)
