@@ -31,6 +31,8 @@
 #include <stdlib.h>
 #include <string.h>
 #include <math.h>
+#include <pthread.h>
+#include <unistd.h>
 
 #define GG_GAMMA 0x9E3779B97F4A7C15ULL
 
@@ -54,23 +56,61 @@ uint64_t gg_splitmix_at(uint64_t seed, uint64_t stream, uint64_t i) {
 
 void gg_free(void* p) { free(p); }
 
-/* ---------- LSD radix sort of uint64 keys (16-bit digits) ---------- */
+/* ---------- parallel LSD radix sort of uint64 keys (16-bit digits) ---------- */
+static int gg_threads(void) {
+  long p = sysconf(_SC_NPROCESSORS_ONLN);
+  if (p < 1) p = 1;
+  if (p > 32) p = 32;
+  return (int)p;
+}
+
+typedef struct {
+  const uint64_t* src; uint64_t* dst; int64_t lo, hi; int shift; int64_t* cnt;
+} gg_rs_job_t;
+
+static void* gg_rs_hist(void* a) {
+  gg_rs_job_t* j = (gg_rs_job_t*)a;
+  memset(j->cnt, 0, 65536 * sizeof(int64_t));
+  for (int64_t i = j->lo; i < j->hi; ++i) j->cnt[(j->src[i] >> j->shift) & 0xFFFF]++;
+  return NULL;
+}
+static void* gg_rs_scatter(void* a) {
+  gg_rs_job_t* j = (gg_rs_job_t*)a;
+  for (int64_t i = j->lo; i < j->hi; ++i) {
+    uint64_t x = j->src[i];
+    j->dst[j->cnt[(x >> j->shift) & 0xFFFF]++] = x;
+  }
+  return NULL;
+}
+
 static int gg_radix_sort_u64(uint64_t* a, int64_t n, int key_bits) {
   if (n <= 1) return 0;
+  int T = gg_threads();
+  if (n < (1 << 20)) T = 1;
   uint64_t* tmp = (uint64_t*)malloc((size_t)n * sizeof(uint64_t));
-  int64_t* cnt = (int64_t*)malloc(65536 * sizeof(int64_t));
-  if (!tmp || !cnt) { free(tmp); free(cnt); return -1; }
+  int64_t* cnt = (int64_t*)malloc((size_t)T * 65536 * sizeof(int64_t));
+  gg_rs_job_t* jobs = (gg_rs_job_t*)malloc((size_t)T * sizeof(gg_rs_job_t));
+  pthread_t* th = (pthread_t*)malloc((size_t)T * sizeof(pthread_t));
+  if (!tmp || !cnt || !jobs || !th) { free(tmp); free(cnt); free(jobs); free(th); return -1; }
   uint64_t* src = a; uint64_t* dst = tmp;
   for (int shift = 0; shift < key_bits; shift += 16) {
-    memset(cnt, 0, 65536 * sizeof(int64_t));
-    for (int64_t i = 0; i < n; ++i) cnt[(src[i] >> shift) & 0xFFFF]++;
+    for (int t = 0; t < T; ++t) {
+      jobs[t].src = src; jobs[t].dst = dst; jobs[t].shift = shift;
+      jobs[t].lo = n * t / T; jobs[t].hi = n * (t + 1) / T; jobs[t].cnt = cnt + (size_t)t * 65536;
+    }
+    for (int t = 1; t < T; ++t) pthread_create(&th[t], NULL, gg_rs_hist, &jobs[t]);
+    gg_rs_hist(&jobs[0]);
+    for (int t = 1; t < T; ++t) pthread_join(th[t], NULL);
     int64_t s = 0;
-    for (int d = 0; d < 65536; ++d) { int64_t c = cnt[d]; cnt[d] = s; s += c; }
-    for (int64_t i = 0; i < n; ++i) dst[cnt[(src[i] >> shift) & 0xFFFF]++] = src[i];
-    uint64_t* t = src; src = dst; dst = t;
+    for (int d = 0; d < 65536; ++d)
+      for (int t = 0; t < T; ++t) { int64_t c = cnt[(size_t)t * 65536 + d]; cnt[(size_t)t * 65536 + d] = s; s += c; }
+    for (int t = 1; t < T; ++t) pthread_create(&th[t], NULL, gg_rs_scatter, &jobs[t]);
+    gg_rs_scatter(&jobs[0]);
+    for (int t = 1; t < T; ++t) pthread_join(th[t], NULL);
+    uint64_t* x = src; src = dst; dst = x;
   }
   if (src != a) memcpy(a, src, (size_t)n * sizeof(uint64_t));
-  free(tmp); free(cnt);
+  free(tmp); free(cnt); free(jobs); free(th);
   return 0;
 }
 
@@ -120,6 +160,7 @@ static int gg_finish(int32_t n, uint64_t* keys, int64_t k, int64_t* m_out,
   int bits = 32 + gg_bits((uint64_t)(n > 0 ? n - 1 : 0));
   if (gg_radix_sort_u64(keys, k, bits) != 0) return -1;
   int64_t m = gg_unique_sorted(keys, k);
+  while (m > 0 && keys[m - 1] == 0xFFFFFFFFFFFFFFFFULL) --m;  /* dropped self-loops sort last */
   int rc = gg_csr_from_pairs(n, keys, m, rp, ci);
   if (rc == 0) *m_out = m;
   return rc;
@@ -263,31 +304,50 @@ int gg_chung_lu(int32_t n, int64_t m_target, double gamma, double sum_w, double 
 }
 
 /* ---------------- R-MAT ---------------- */
+typedef struct {
+  uint64_t key; int scale; double a, ab, abc; int64_t lo, hi; uint64_t* keys;
+} gg_rmat_job_t;
+
+#define GG_NONE 0xFFFFFFFFFFFFFFFFULL  /* self-loop marker: sorts after every pair */
+
+static void* gg_rmat_draw(void* p) {
+  gg_rmat_job_t* j = (gg_rmat_job_t*)p;
+  for (int64_t i = j->lo; i < j->hi; ++i) {
+    uint64_t u = 0, v = 0;
+    for (int l = 0; l < j->scale; ++l) {
+      double r = gg_u01(gg_at(j->key, (uint64_t)i * (uint64_t)j->scale + (uint64_t)l));
+      uint64_t rb, cb;
+      if (r < j->a) { rb = 0; cb = 0; }
+      else if (r < j->ab) { rb = 0; cb = 1; }
+      else if (r < j->abc) { rb = 1; cb = 0; }
+      else { rb = 1; cb = 1; }
+      u = (u << 1) | rb; v = (v << 1) | cb;
+    }
+    j->keys[i] = u == v ? GG_NONE : (u < v ? ((u << 32) | v) : ((v << 32) | u));
+  }
+  return NULL;
+}
+
 int gg_rmat(int scale, int64_t edge_factor, double a, double b, double c, uint64_t seed,
             int32_t* n_out, int64_t* m_out, int32_t** rp, int32_t** ci) {
   if (scale < 1 || scale > 30 || edge_factor < 0) return -3;
   int64_t draws = edge_factor << scale;
   uint64_t* keys = (uint64_t*)malloc((size_t)(draws > 0 ? draws : 1) * sizeof(uint64_t));
   if (!keys) return -1;
-  uint64_t key = gg_key(seed, 3);
-  double ab = a + b, abc = a + b + c;
-  int64_t k = 0;
-  for (int64_t i = 0; i < draws; ++i) {
-    uint64_t u = 0, v = 0;
-    for (int l = 0; l < scale; ++l) {
-      double r = gg_u01(gg_at(key, (uint64_t)i * (uint64_t)scale + (uint64_t)l));
-      uint64_t rb, cb;
-      if (r < a) { rb = 0; cb = 0; }
-      else if (r < ab) { rb = 0; cb = 1; }
-      else if (r < abc) { rb = 1; cb = 0; }
-      else { rb = 1; cb = 1; }
-      u = (u << 1) | rb; v = (v << 1) | cb;
-    }
-    if (u == v) continue;
-    keys[k++] = u < v ? ((u << 32) | v) : ((v << 32) | u);
+  int T = gg_threads();
+  if (draws < (1 << 18)) T = 1;
+  gg_rmat_job_t jobs[32];
+  pthread_t th[32];
+  for (int t = 0; t < T; ++t) {
+    jobs[t].key = gg_key(seed, 3); jobs[t].scale = scale;
+    jobs[t].a = a; jobs[t].ab = a + b; jobs[t].abc = a + b + c;
+    jobs[t].lo = draws * t / T; jobs[t].hi = draws * (t + 1) / T; jobs[t].keys = keys;
   }
+  for (int t = 1; t < T; ++t) pthread_create(&th[t], NULL, gg_rmat_draw, &jobs[t]);
+  gg_rmat_draw(&jobs[0]);
+  for (int t = 1; t < T; ++t) pthread_join(th[t], NULL);
   int32_t n = (int32_t)(1 << scale);
-  int rc = gg_finish(n, keys, k, m_out, rp, ci);
+  int rc = gg_finish(n, keys, draws, m_out, rp, ci);
   free(keys);
   if (rc == 0) *n_out = n;
   return rc;

@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <string>
 #include <thread>
 #include <vector>
@@ -87,6 +88,92 @@ gc_status validate_csr(int32_t n, const int32_t* rp, const int32_t* ci) {
   return GC_OK;
 }
 
+// Preprocessing P1 (Sec. 4.3): relabel vertices by ascending degree (ties by
+// id), so that internal ids are the (degree, id) ranks used by P3 and by the
+// degree-ordered passes. Rows are re-sorted in the new ids. Edge ids stay
+// those of the caller's graph: eid[slot] of every internal slot is the
+// caller's edge id, and perm maps internal -> caller vertex ids.
+struct Relabeled {
+  std::vector<int32_t> rp, ci, eid, perm;
+};
+
+static void parallel_for(int64_t n, int nt, const std::function<void(int64_t, int64_t)>& f) {
+  if (nt <= 1 || n < 4096) {
+    f(0, n);
+    return;
+  }
+  std::vector<std::thread> th;
+  for (int t = 1; t < nt; ++t) th.emplace_back(f, n * t / nt, n * (t + 1) / nt);
+  f(0, n / nt);
+  for (auto& x : th) x.join();
+}
+
+Relabeled relabel_by_degree(int32_t n, const int32_t* rp, const int32_t* ci) {
+  Relabeled R;
+  const int64_t nnz = rp[n];
+  unsigned hw = std::thread::hardware_concurrency();
+  const int nt = (int)std::min<unsigned>(hw ? hw : 1, 16);
+  int32_t dmax = 0;
+  for (int32_t x = 0; x < n; ++x) dmax = std::max(dmax, rp[x + 1] - rp[x]);
+  // stable counting sort by degree
+  std::vector<int32_t> cnt((size_t)dmax + 2, 0);
+  for (int32_t x = 0; x < n; ++x) cnt[rp[x + 1] - rp[x] + 1]++;
+  for (int32_t d = 0; d <= dmax; ++d) cnt[d + 1] += cnt[d];
+  R.perm.resize((size_t)n);
+  std::vector<int32_t> newid((size_t)n);
+  for (int32_t x = 0; x < n; ++x) {
+    int32_t i = cnt[rp[x + 1] - rp[x]]++;
+    R.perm[i] = x;
+    newid[x] = i;
+  }
+  // caller's edge id of every caller slot
+  std::vector<int32_t> up((size_t)n + 1, 0);
+  parallel_for(n, nt, [&](int64_t a, int64_t b) {
+    for (int64_t x = a; x < b; ++x)
+      up[x + 1] = (int32_t)(rp[x + 1] - (std::upper_bound(ci + rp[x], ci + rp[x + 1], (int32_t)x) - ci));
+  });
+  for (int32_t x = 0; x < n; ++x) up[x + 1] += up[x];  // up[x] = first edge id of row x
+  std::vector<int32_t> eid_in((size_t)(nnz > 0 ? nnz : 1));
+  parallel_for(n, nt, [&](int64_t a, int64_t b) {
+    for (int64_t x = a; x < b; ++x) {
+      const int32_t* row = ci + rp[x];
+      const int32_t first_up = (int32_t)(std::upper_bound(row, ci + rp[x + 1], (int32_t)x) - ci);
+      for (int32_t p = rp[x]; p < rp[x + 1]; ++p) {
+        int32_t y = ci[p];
+        if (y > x) {
+          eid_in[p] = up[x] + (p - first_up);
+        } else {
+          const int32_t* q = std::lower_bound(ci + rp[y], ci + rp[y + 1], (int32_t)x);
+          const int32_t fu = (int32_t)(std::upper_bound(ci + rp[y], ci + rp[y + 1], y) - ci);
+          eid_in[p] = up[y] + (int32_t)(q - ci) - fu;
+        }
+      }
+    }
+  });
+  R.rp.resize((size_t)n + 1);
+  R.rp[0] = 0;
+  for (int32_t i = 0; i < n; ++i) R.rp[i + 1] = R.rp[i] + (rp[R.perm[i] + 1] - rp[R.perm[i]]);
+  R.ci.resize((size_t)(nnz > 0 ? nnz : 1));
+  R.eid.resize((size_t)(nnz > 0 ? nnz : 1));
+  parallel_for(n, nt, [&](int64_t a, int64_t b) {
+    std::vector<uint64_t> tmp;
+    for (int64_t i = a; i < b; ++i) {
+      const int32_t x = R.perm[i];
+      tmp.clear();
+      for (int32_t p = rp[x]; p < rp[x + 1]; ++p)
+        tmp.push_back(((uint64_t)(uint32_t)newid[ci[p]] << 32) | (uint32_t)eid_in[p]);
+      std::sort(tmp.begin(), tmp.end());
+      int32_t o = R.rp[i];
+      for (uint64_t k : tmp) {
+        R.ci[o] = (int32_t)(k >> 32);
+        R.eid[o] = (int32_t)(k & 0xffffffffu);
+        ++o;
+      }
+    }
+  });
+  return R;
+}
+
 }  // namespace gc
 
 using namespace gc;
@@ -103,13 +190,9 @@ struct gc_graph_s {
   int32_t* d_gn = nullptr;     // [1] n
   int64_t* d_gm = nullptr;     // [1] m
   // counting scratch
-  int32_t* d_tri = nullptr;
-  uint32_t* d_tables = nullptr;
-  int32_t* d_spill = nullptr;
-  int32_t spill_len = 0;
+  Scratch sc;
   unsigned long long* d_csum = nullptr;  // [13][2]
   unsigned long long* d_x = nullptr;     // [17][2]
-  int32_t* d_misc = nullptr;             // [0] cursor, [1] status, [2] max |T|
   uint64_t* d_pe_tmp = nullptr;          // device staging for a host per-edge buffer
   cudaEvent_t ev[kNumPhases + 1] = {};
   bool counted = false;
@@ -128,11 +211,9 @@ static void graph_release(gc_graph g) {
   free_prep(&g->prep, g->stream);
   cudaStreamSynchronize(g->stream);
   cudaFree(g->d_gbase);
-  cudaFree(g->d_tri);
-  cudaFree(g->d_tables);
-  cudaFree(g->d_spill);
+  scratch_free(&g->sc, g->stream);
+  cudaStreamSynchronize(g->stream);
   cudaFree(g->d_csum);
-  cudaFree(g->d_misc);
   cudaFree(g->d_pe_tmp);
   for (auto& e : g->ev)
     if (e) cudaEventDestroy(e);
@@ -171,15 +252,28 @@ gc_status gc_graph_upload(int32_t n, const int32_t* row_ptr, const int32_t* col_
       return st;                        \
     }                                   \
   } while (0)
+  Relabeled R = relabel_by_degree(n, row_ptr, col_idx);
+  int32_t* d_eid = nullptr;
+  int32_t* d_perm = nullptr;
   GC_CHECK(cudaMalloc(&g->d_rp, sizeof(int32_t) * ((size_t)n + 1)), "alloc row_ptr");
   GC_CHECK(cudaMalloc(&g->d_ci, sizeof(int32_t) * (size_t)(nnz > 0 ? nnz : 1)), "alloc col_idx");
-  GC_CHECK(cudaMemcpyAsync(g->d_rp, row_ptr, sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyHostToDevice, s),
+  GC_CHECK(cudaMallocAsync(&d_eid, sizeof(int32_t) * (size_t)(nnz > 0 ? nnz : 1), s), "alloc eid");
+  GC_CHECK(cudaMallocAsync(&d_perm, sizeof(int32_t) * (size_t)(n > 0 ? n : 1), s), "alloc perm");
+  GC_CHECK(cudaMemcpyAsync(g->d_rp, R.rp.data(), sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyHostToDevice, s),
            "copy row_ptr");
-  if (nnz > 0)
-    GC_CHECK(cudaMemcpyAsync(g->d_ci, col_idx, sizeof(int32_t) * (size_t)nnz, cudaMemcpyHostToDevice, s),
+  if (nnz > 0) {
+    GC_CHECK(cudaMemcpyAsync(g->d_ci, R.ci.data(), sizeof(int32_t) * (size_t)nnz, cudaMemcpyHostToDevice, s),
              "copy col_idx");
-  st = prepare_graph(n, g->m, g->d_rp, g->d_ci, nullptr, &g->prep, s);
+    GC_CHECK(cudaMemcpyAsync(d_eid, R.eid.data(), sizeof(int32_t) * (size_t)nnz, cudaMemcpyHostToDevice, s),
+             "copy edge ids");
+  }
+  if (n > 0)
+    GC_CHECK(cudaMemcpyAsync(d_perm, R.perm.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice, s),
+             "copy perm");
+  st = prepare_graph(n, g->m, g->d_rp, g->d_ci, nullptr, d_eid, d_perm, &g->prep, s);
+  cudaFreeAsync(d_perm, s);
   if (st != GC_OK) { graph_release(g); return st; }
+  cudaStreamSynchronize(s);  // host copies of R are released on return
   // single-graph descriptor block: gbase | gn | gm (gm 8-byte aligned)
   GC_CHECK(cudaMalloc(&g->d_gbase, 32), "alloc descriptors");
   {
@@ -193,12 +287,9 @@ gc_status gc_graph_upload(int32_t n, const int32_t* row_ptr, const int32_t* col_
   }
   GC_CHECK(cudaMalloc(&g->d_csum, sizeof(unsigned long long) * (13 * 2 + 17 * 2)), "alloc sums");
   g->d_x = g->d_csum + 13 * 2;
-  GC_CHECK(cudaMalloc(&g->d_misc, sizeof(int32_t) * 4), "alloc misc");
-  GC_CHECK(cudaMalloc(&g->d_tri, sizeof(int32_t) * (size_t)(g->m > 0 ? g->m : 1)), "alloc tri");
-  if (n > kSmemTableMax) {
-    size_t words = (size_t)count_grid_size() * (size_t)n;
-    GC_CHECK(cudaMalloc(&g->d_tables, sizeof(uint32_t) * words), "alloc Psi tables");
-    GC_CHECK(cudaMemsetAsync(g->d_tables, 0, sizeof(uint32_t) * words, s), "zero Psi tables");
+  {
+    gc_status st2 = scratch_init(&g->sc, g->m, g->prep.n_units, n, s);
+    if (st2 != GC_OK) { graph_release(g); return st2; }
   }
   for (auto& ev : g->ev) GC_CHECK(cudaEventCreate(&ev), "event create");
   GC_CHECK(cudaStreamSynchronize(s), "sync upload");
@@ -269,53 +360,15 @@ gc_status gc_count_edge_graphlets(gc_graph g, uint64_t* per_edge_out, uint64_t* 
   dg.gn = g->d_gn;
   dg.gm = g->d_gm;
   dg.table_n = g->n;
-  CountArgs a;
-  a.units = g->prep.units;
-  a.n_units = g->prep.n_units;
-  a.cursor = g->d_misc;
-  a.tables = g->d_tables;
-  a.tri = g->d_tri;
-  a.spill = nullptr;
-  a.spill_len = 0;
-  a.per_edge = pe_dev;
-  a.csum = g->d_csum;
-  a.status = g->d_misc + 1;
-  GC_CHECK(cudaMemsetAsync(g->d_misc, 0, sizeof(int32_t) * 4, s), "memset misc");
-  GC_CHECK(cudaMemsetAsync(g->d_csum, 0, sizeof(unsigned long long) * 13 * 2, s), "memset sums");
-  GC_CHECK(cudaEventRecord(g->ev[kPhasePassA], s), "event");
-  if (a.n_units > 0) {
-    if ((st = run_pass_a(dg, a, s)) != GC_OK) return st;
-    // |T| beyond the shared-memory buffer needs a per-warp spill area.
-    if ((st = run_max_tri(g->d_tri, g->m, g->d_misc + 2, s)) != GC_OK) return st;
-    int32_t tmax = 0;
-    GC_CHECK(cudaMemcpyAsync(&tmax, g->d_misc + 2, sizeof(int32_t), cudaMemcpyDeviceToHost, s), "copy max T");
-    GC_CHECK(cudaStreamSynchronize(s), "sync max T");
-    if (tmax > kTcap) {
-      if (tmax > g->spill_len) {
-        cudaFree(g->d_spill);
-        g->d_spill = nullptr;
-        g->spill_len = 0;
-        size_t len = (size_t)count_grid_size() * kWarps * (size_t)tmax;
-        GC_CHECK(cudaMalloc(&g->d_spill, sizeof(int32_t) * len), "alloc T spill");
-        g->spill_len = tmax;
-      }
-      a.spill = g->d_spill;
-      a.spill_len = g->spill_len;
-    }
-    GC_CHECK(cudaMemsetAsync(g->d_misc, 0, sizeof(int32_t), s), "reset cursor");
-  }
-  GC_CHECK(cudaEventRecord(g->ev[kPhasePassB], s), "event");
-  if (a.n_units > 0)
-    if ((st = run_pass_b(dg, a, s)) != GC_OK) return st;
-  GC_CHECK(cudaEventRecord(g->ev[kPhaseDerive], s), "event");
-  if ((st = run_derive(dg, g->d_csum, g->d_x, a.status, s)) != GC_OK) return st;
-  GC_CHECK(cudaEventRecord(g->ev[kPhaseCopy], s), "event");
+  dg.ranked = true;
+  if ((st = run_count(dg, g->prep.units, g->prep.n_units, pe_dev, g->d_csum, g->d_x, &g->sc, s, g->ev)) != GC_OK)
+    return st;
   unsigned long long hx[17 * 2 + 13 * 2];
   int32_t hstatus = 0;
   GC_CHECK(cudaMemcpyAsync(hx, g->d_x, sizeof(unsigned long long) * 17 * 2, cudaMemcpyDeviceToHost, s), "copy X");
   GC_CHECK(cudaMemcpyAsync(hx + 34, g->d_csum, sizeof(unsigned long long) * 13 * 2, cudaMemcpyDeviceToHost, s),
            "copy C");
-  GC_CHECK(cudaMemcpyAsync(&hstatus, a.status, sizeof(int32_t), cudaMemcpyDeviceToHost, s), "copy status");
+  GC_CHECK(cudaMemcpyAsync(&hstatus, g->sc.misc + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, s), "copy status");
   if (want_pe && pe_dev != per_edge_out)
     GC_CHECK(cudaMemcpyAsync(per_edge_out, pe_dev, sizeof(uint64_t) * 13 * (size_t)g->m, cudaMemcpyDeviceToHost, s),
              "copy per-edge");
@@ -361,8 +414,8 @@ gc_status gc_graph_csums(gc_graph g, uint64_t* lo, uint64_t* hi) {
 int gc_phase_count(void) { return kNumPhases; }
 
 const char* gc_phase_name(int i) {
-  static const char* names[kNumPhases] = {"pass_a_triangles", "pass_b_cliques_cycles", "derive",
-                                          "copy_out"};
+  static const char* names[kNumPhases] = {"pass_a_triangles", "pass_c_cycles", "pass_b_cliques_finish",
+                                          "pass_b_large_T", "derive", "copy_out"};
   return (i >= 0 && i < kNumPhases) ? names[i] : "";
 }
 

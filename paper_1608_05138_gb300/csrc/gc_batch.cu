@@ -133,12 +133,11 @@ void run_launch(std::vector<PendingGraph>& graphs, cudaStream_t s, Launch* L) {
     }
     h_rp[n] = (int32_t)eo;
   }
-  int32_t *d_rp = nullptr, *d_ci = nullptr, *d_vgid = nullptr, *d_desc = nullptr, *d_tri = nullptr,
-          *d_misc = nullptr, *d_spill = nullptr;
+  int32_t *d_rp = nullptr, *d_ci = nullptr, *d_vgid = nullptr, *d_desc = nullptr;
   int64_t* d_gm = nullptr;
-  uint32_t* d_tables = nullptr;
   unsigned long long *d_csum = nullptr, *d_x = nullptr;
   PrepBuffers prep;
+  Scratch sc;
   cudaError_t e = cudaSuccess;
   gc_status st = GC_OK;
   auto fail = [&](cudaError_t err, const char* what) {
@@ -158,8 +157,6 @@ void run_launch(std::vector<PendingGraph>& graphs, cudaStream_t s, Launch* L) {
   GB_TRY(cudaMallocAsync(&d_vgid, sizeof(int32_t) * h_vgid.size(), s), "batch alloc");
   GB_TRY(cudaMallocAsync(&d_desc, sizeof(int32_t) * h_desc.size(), s), "batch alloc");
   GB_TRY(cudaMallocAsync(&d_gm, sizeof(int64_t) * G, s), "batch alloc");
-  GB_TRY(cudaMallocAsync(&d_tri, sizeof(int32_t) * (size_t)(m > 0 ? m : 1), s), "batch alloc");
-  GB_TRY(cudaMallocAsync(&d_misc, sizeof(int32_t) * 4, s), "batch alloc");
   GB_TRY(cudaMallocAsync(&d_csum, sizeof(unsigned long long) * (size_t)G * 26, s), "batch alloc");
   GB_TRY(cudaMallocAsync(&d_x, sizeof(unsigned long long) * (size_t)G * 34, s), "batch alloc");
   GB_TRY(cudaMemcpyAsync(d_rp, h_rp.data(), sizeof(int32_t) * h_rp.size(), cudaMemcpyHostToDevice, s), "batch copy");
@@ -167,14 +164,16 @@ void run_launch(std::vector<PendingGraph>& graphs, cudaStream_t s, Launch* L) {
   GB_TRY(cudaMemcpyAsync(d_vgid, h_vgid.data(), sizeof(int32_t) * h_vgid.size(), cudaMemcpyHostToDevice, s), "batch copy");
   GB_TRY(cudaMemcpyAsync(d_desc, h_desc.data(), sizeof(int32_t) * h_desc.size(), cudaMemcpyHostToDevice, s), "batch copy");
   GB_TRY(cudaMemcpyAsync(d_gm, h_gm.data(), sizeof(int64_t) * G, cudaMemcpyHostToDevice, s), "batch copy");
-  GB_TRY(cudaMemsetAsync(d_misc, 0, sizeof(int32_t) * 4, s), "batch memset");
-  GB_TRY(cudaMemsetAsync(d_csum, 0, sizeof(unsigned long long) * (size_t)G * 26, s), "batch memset");
   if (n > 0) {
     int blocks = (int)std::min<int64_t>(((int64_t)n * 32 + 255) / 256, 65535LL * 8);
     k_globalize<<<blocks, 256, 0, s>>>(n, d_rp, d_vgid, d_desc, d_ci);
     GB_TRY(cudaGetLastError(), "k_globalize");
   }
-  if ((st = prepare_graph(n, m, d_rp, d_ci, d_vgid, &prep, s)) != GC_OK) {
+  if ((st = prepare_graph(n, m, d_rp, d_ci, d_vgid, nullptr, nullptr, &prep, s)) != GC_OK) {
+    L->error = gc_last_error();
+    goto out;
+  }
+  if ((st = scratch_init(&sc, m, prep.n_units, table_n, s)) != GC_OK) {
     L->error = gc_last_error();
     goto out;
   }
@@ -194,48 +193,20 @@ void run_launch(std::vector<PendingGraph>& graphs, cudaStream_t s, Launch* L) {
     dg.gn = d_desc + G;
     dg.gm = d_gm;
     dg.table_n = table_n;
-    CountArgs a;
-    a.units = prep.units;
-    a.n_units = prep.n_units;
-    a.cursor = d_misc;
-    a.tables = nullptr;
-    a.tri = d_tri;
-    a.spill = nullptr;
-    a.spill_len = 0;
-    a.per_edge = nullptr;
-    a.csum = d_csum;
-    a.status = d_misc + 1;
-    if (table_n > kSmemTableMax) {
-      size_t words = (size_t)count_grid_size() * (size_t)table_n;
-      GB_TRY(cudaMallocAsync(&d_tables, sizeof(uint32_t) * words, s), "batch alloc tables");
-      GB_TRY(cudaMemsetAsync(d_tables, 0, sizeof(uint32_t) * words, s), "batch memset tables");
-      a.tables = d_tables;
+    dg.ranked = false;
+    if ((st = run_count(dg, prep.units, prep.n_units, nullptr, d_csum, d_x, &sc, s, nullptr)) != GC_OK) {
+      L->error = gc_last_error();
+      goto out;
     }
-    if (a.n_units > 0) {
-      if ((st = run_pass_a(dg, a, s)) != GC_OK) { L->error = gc_last_error(); goto out; }
-      if ((st = run_max_tri(d_tri, m, d_misc + 2, s)) != GC_OK) { L->error = gc_last_error(); goto out; }
-      int32_t tmax = 0;
-      GB_TRY(cudaMemcpyAsync(&tmax, d_misc + 2, sizeof(int32_t), cudaMemcpyDeviceToHost, s), "batch copy");
-      GB_TRY(cudaStreamSynchronize(s), "batch sync");
-      if (tmax > kTcap) {
-        GB_TRY(cudaMallocAsync(&d_spill, sizeof(int32_t) * (size_t)count_grid_size() * kWarps * tmax, s),
-               "batch alloc spill");
-        a.spill = d_spill;
-        a.spill_len = tmax;
-      }
-      GB_TRY(cudaMemsetAsync(d_misc, 0, sizeof(int32_t), s), "batch memset");
-      if ((st = run_pass_b(dg, a, s)) != GC_OK) { L->error = gc_last_error(); goto out; }
-    }
-    if ((st = run_derive(dg, d_csum, d_x, a.status, s)) != GC_OK) { L->error = gc_last_error(); goto out; }
     GB_TRY(cudaMemcpyAsync(L->h_x, d_x, sizeof(unsigned long long) * (size_t)G * 34, cudaMemcpyDeviceToHost, s),
            "batch copy out");
-    GB_TRY(cudaMemcpyAsync(L->h_status, d_misc + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, s), "batch copy out");
+    GB_TRY(cudaMemcpyAsync(L->h_status, sc.misc + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, s), "batch copy out");
   }
 out:
 #undef GB_TRY
   free_prep(&prep, s);
-  for (void* p : {(void*)d_rp, (void*)d_ci, (void*)d_vgid, (void*)d_desc, (void*)d_gm, (void*)d_tri,
-                  (void*)d_misc, (void*)d_spill, (void*)d_tables, (void*)d_csum, (void*)d_x})
+  scratch_free(&sc, s);
+  for (void* p : {(void*)d_rp, (void*)d_ci, (void*)d_vgid, (void*)d_desc, (void*)d_gm, (void*)d_csum, (void*)d_x})
     if (p) cudaFreeAsync(p, s);
   L->launch_status = st;
   if (st == GC_OK) {

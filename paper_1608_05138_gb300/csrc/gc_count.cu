@@ -9,14 +9,15 @@
 // Pass A -- triangle step (Alg. 1): Psi(r) = lambda1 for r in Gamma(v); for
 //   every low neighbour u, |T| = #{w in Gamma(u) : Psi(w) = lambda1}.
 //
-// Pass B -- 4-clique and 4-cycle steps (Alg. 5 / Alg. 6), with Psi extended
-//   from a type tag to a count: for the whole v-group
-//       Psi(w) = [w in Gamma(v)] * 2^31 + |Gamma(w) ∩ Gamma(v)|,
-//   built once by scanning Gamma(r) for every r in Gamma(v). This memoises the
-//   Gamma(w) scans that Alg. 6 repeats for every edge sharing v. Per edge:
-//     T       = {w in Gamma(u) \ {v} : Psi(w) has the lambda1 bit}  (Alg. 1)
-//     P(e)    = sum_{w in Gamma(u)\{v}} (|Gamma(w) ∩ Gamma(v)| - 1)
-//               (walks u-w-r-v with w != v, r != u: 4-cycles through e)
+// Pass C -- 4-cycle step (Alg. 4/6) reorganised: P(e), the number of
+//   4-cycles (as subgraphs) through e = #{(w, r) : w in Gamma(u)\{v},
+//   r in Gamma(v)\{u}, w != r, w ~ r}, for all edges at once by counting
+//   wedges from the highest-rank vertex of each cycle (see k_pass_c).
+//
+// Pass B -- 4-clique step (Alg. 5) and the per-edge finish. Psi for the
+//   v-group holds 1 + the position of r in Gamma(v) for r in Gamma(v). Per
+//   edge:
+//     T       = {w in Gamma(u) \ {v} : Psi(w) != 0}          (Alg. 1)
 //     cross   = sum_{a in T} (|T_(a,u)| + |T_(a,v)| - 2)
 //     x7      = sum_{a in T} |out(a) ∩ T|        (Alg. 5; out(a) = higher-rank
 //               neighbours, so every adjacent pair of T is counted once --
@@ -61,6 +62,66 @@ __device__ __forceinline__ int contains(const int32_t* a, int32_t len, int32_t k
     if (x < key) lo = mid + 1; else hi = mid;
   }
   return (lo < len && a[lo] == key) ? 1 : 0;
+}
+
+
+// 4-clique count of one edge: sum over members a of T (ascending, t of them)
+// of |out(a) ∩ T|, for one warp. Members are taken 32 at a time; the entries
+// of their out-lists are flattened over the lanes (coalesced, no idle lanes)
+// and each lane keeps kMLP loads in flight before probing. in_T(r) answers
+// membership; a member whose out-list is longer than T (when long_ok) has
+// T's members searched in its out-list instead.
+template <int kMLP, class InT>
+__device__ __forceinline__ long long warp_clique_count(const DevGraph& g, const int32_t* T, int32_t t,
+                                                       int32_t i_begin, int32_t i_stride, int lane,
+                                                       bool long_ok, InT in_T) {
+  long long x7 = 0;
+  for (int32_t i0 = i_begin; i0 < t; i0 += i_stride) {
+    const int32_t i = i0 + lane;
+    int32_t ob = 0, len = 0;
+    if (i < t) {
+      const int32_t aa = T[i];
+      ob = g.out_ptr[aa];
+      len = g.out_ptr[aa + 1] - ob;
+    }
+    const bool longer = long_ok && len > t;
+    const int32_t L = longer ? 0 : len;
+    int32_t incl = L;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const int32_t excl = incl - L;
+    const int32_t total = __shfl_sync(0xffffffffu, incl, 31);
+    for (int32_t k0 = 0; k0 < total; k0 += 32 * kMLP) {
+      int32_t r[kMLP];
+#pragma unroll
+      for (int j = 0; j < kMLP; ++j) {
+        const int32_t kk = k0 + 32 * j + lane;
+        int32_t lo = 0, hi = 31;  // owner: last lane whose range starts at or before kk
+#pragma unroll
+        for (int it = 0; it < 5; ++it) {
+          const int32_t mid = (lo + hi + 1) >> 1;
+          if (__shfl_sync(0xffffffffu, excl, mid) <= kk) lo = mid; else hi = mid - 1;
+        }
+        const int32_t oj = __shfl_sync(0xffffffffu, ob, lo);
+        const int32_t ej = __shfl_sync(0xffffffffu, excl, lo);
+        r[j] = kk < total ? g.out_idx[oj + (kk - ej)] : -1;
+      }
+#pragma unroll
+      for (int j = 0; j < kMLP; ++j)
+        if (r[j] >= 0) x7 += in_T(r[j]);
+    }
+    unsigned lm = __ballot_sync(0xffffffffu, longer);
+    while (lm) {
+      const int src = __ffs(lm) - 1;
+      lm &= lm - 1;
+      const int32_t oj = __shfl_sync(0xffffffffu, ob, src);
+      const int32_t lj = __shfl_sync(0xffffffffu, len, src);
+      for (int32_t j = lane; j < t; j += 32) x7 += contains(g.out_idx + oj, lj, T[j]);
+    }
+  }
+  return x7;
 }
 
 __device__ __forceinline__ void atomic_add_u128(unsigned long long* p, u128 v) {
@@ -109,7 +170,7 @@ __device__ __forceinline__ uint32_t* table_of(const DevGraph& g, const CountArgs
 template <bool kSmemTable>
 __global__ void __launch_bounds__(kBlock) k_pass_a(DevGraph g, CountArgs a) {
   extern __shared__ uint32_t smem[];
-  __shared__ int32_t s_unit;
+  __shared__ int32_t s_unit, s_next;
   uint32_t* tab = table_of<kSmemTable>(g, a, smem);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (kSmemTable)
@@ -124,8 +185,13 @@ __global__ void __launch_bounds__(kBlock) k_pass_a(DevGraph g, CountArgs a) {
     const int32_t base = g.gbase[g.vgid ? g.vgid[v] : 0];
     const int32_t vb = g.rp[v], ve = g.rp[v + 1];
     for (int32_t p = vb + threadIdx.x; p < ve; p += kBlock) tab[g.ci[p] - base] = 1u;
+    if (threadIdx.x == 0) s_next = vb;
     __syncthreads();
-    for (int32_t p = vb + warp; p < ve; p += kWarps) {
+    for (;;) {  // edges of the group handed to warps one at a time
+      int32_t p = 0;
+      if (lane == 0) p = atomicAdd(&s_next, 1);
+      p = __shfl_sync(0xffffffffu, p, 0);
+      if (p >= ve) break;
       const int32_t u = g.ci[p];
       if (!rank_less(g.deg, u, v)) continue;
       const int32_t ub = g.rp[u], ue = g.rp[u + 1];
@@ -141,20 +207,19 @@ __global__ void __launch_bounds__(kBlock) k_pass_a(DevGraph g, CountArgs a) {
 
 // ---------------- pass B: cliques, cycles, columns, sums ----------------
 template <bool kSmemTable>
-__global__ void __launch_bounds__(kBlock) k_pass_b(DevGraph g, CountArgs a) {
+__global__ void __launch_bounds__(kBlock, kCtasPerSm) k_pass_b(DevGraph g, CountArgs a) {
   extern __shared__ uint32_t smem[];
-  __shared__ int32_t s_unit;
+  __shared__ int32_t s_unit, s_next;
   uint32_t* tab = table_of<kSmemTable>(g, a, smem);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  int32_t* tbuf_smem =
+  int32_t* buf =
       reinterpret_cast<int32_t*>(smem + (kSmemTable ? ((g.table_n + 3) & ~3) : 0)) + warp * kTcap;
-  int32_t* tbuf_spill =
-      a.spill ? a.spill + ((size_t)blockIdx.x * kWarps + warp) * (size_t)a.spill_len : nullptr;
   const bool zero_all = kSmemTable && g.table_n <= 4096;
 
   u128 acc = 0;  // lane k < 13: running sum of C-sum k for graph cur_g
   int32_t cur_g = -1;
 
+  const int32_t n_chunks = *a.n_chunks;
   if (kSmemTable)
     for (int32_t i = threadIdx.x; i < g.table_n; i += kBlock) tab[i] = 0;
   for (;;) {
@@ -162,8 +227,10 @@ __global__ void __launch_bounds__(kBlock) k_pass_b(DevGraph g, CountArgs a) {
     if (threadIdx.x == 0) s_unit = atomicAdd(a.cursor, 1);
     __syncthreads();
     const int32_t k = s_unit;
-    if (k >= a.n_units) break;
-    const int32_t v = a.units[k];
+    if (k >= n_chunks) break;
+    const int32_t v = a.chunks[3 * k];
+    const int32_t cb = a.chunks[3 * k + 1], ce = a.chunks[3 * k + 2];
+    if (cb >= ce) continue;
     const int32_t gid = g.vgid ? g.vgid[v] : 0;
     const int32_t base = g.gbase[gid];
     const int64_t n_g = g.gn[gid], m_g = g.gm[gid];
@@ -176,67 +243,61 @@ __global__ void __launch_bounds__(kBlock) k_pass_b(DevGraph g, CountArgs a) {
       cur_g = gid;
     }
 
-    // Build Psi for the group: lambda1 bit for Gamma(v), counts |Gamma(w) ∩ Gamma(v)|.
-    for (int32_t p = vb + warp; p < ve; p += kWarps) {
-      const int32_t r = g.ci[p];
-      if (lane == 0) atomicOr(&tab[r - base], kFlag);
-      const int32_t rb = g.rp[r], re = g.rp[r + 1];
-      for (int32_t q = rb + lane; q < re; q += 32) {
-        const int32_t w = g.ci[q];
-        if (w != v) atomicAdd(&tab[w - base], 1u);
-      }
-    }
+    // Psi for the group: Psi(r) = 1 + position of r in Gamma(v) (non-zero =
+    // lambda1, "neighbour of v"); the position gives the edge (r, v).
+    for (int32_t p = vb + threadIdx.x; p < ve; p += kBlock) tab[g.ci[p] - base] = (uint32_t)(p - vb + 1);
+    if (threadIdx.x == 0) s_next = cb;
     __syncthreads();
 
-    // One warp per edge (u, v) of the group.
-    for (int32_t p = vb + warp; p < ve; p += kWarps) {
+    // One warp per edge (u, v) of the chunk's slots of Gamma(v), handed out
+    // one at a time so that heavy edges do not leave warps idle at the barrier.
+    for (;;) {
+      int32_t p = 0;
+      if (lane == 0) p = atomicAdd(&s_next, 1);
+      p = __shfl_sync(0xffffffffu, p, 0);
+      if (p >= ce) break;
       const int32_t u = g.ci[p];
       if (!rank_less(g.deg, u, v)) continue;
       const int32_t e = g.eid[p];
       const int32_t t_expect = a.tri[e];
-      int32_t* buf = t_expect <= kTcap ? tbuf_smem : tbuf_spill;
-      if (buf == nullptr || (buf == tbuf_spill && t_expect > a.spill_len)) {
-        if (lane == 0) atomicOr(a.status, (int32_t)kSpillOverflow);
+      if (t_expect > kTcap) {  // |T| beyond the warp's buffer: a whole CTA takes it later
+        if (lane == 0) {
+          const int32_t i = atomicAdd(a.n_deferred, 1);
+          if (i < a.deferred_cap) {
+            a.deferred[2 * i] = v;
+            a.deferred[2 * i + 1] = p;
+          } else {
+            atomicOr(a.status, (int32_t)kSpillOverflow);
+          }
+        }
         continue;
       }
       const int32_t ub = g.rp[u], ue = g.rp[u + 1];
-      long long P = 0, cross = 0;
+      long long cross = 0;
       int32_t t = 0;
       for (int32_t q0 = ub; q0 < ue; q0 += 32) {
         const int32_t q = q0 + lane;
         const bool valid = q < ue;
         const int32_t w = valid ? g.ci[q] : v;
-        const bool use = valid && w != v;
-        const uint32_t ent = use ? tab[w - base] : 0u;
-        const long long W = (long long)(ent & kCount);
-        const bool inT = (ent & kFlag) != 0u;
-        if (use) P += W - 1;
-        if (inT) cross += (long long)a.tri[g.eid[q]] + W - 2;
+        const uint32_t ent = (valid && w != v) ? tab[w - base] : 0u;
+        const bool inT = ent != 0u;
+        if (inT) cross += (long long)a.tri[g.eid[q]] + (long long)a.tri[g.eid[vb + (int32_t)ent - 1]] - 2;
         const unsigned mask = __ballot_sync(0xffffffffu, inT);
         if (inT && t + __popc(mask & ((1u << lane) - 1u)) < t_expect)
           buf[t + __popc(mask & ((1u << lane) - 1u))] = w;
         t += __popc(mask);
       }
-      P = warp_sum_ll(P);
       cross = warp_sum_ll(cross);
+      const long long P = (long long)a.P[e];
       if (t != t_expect) {  // cannot happen on a valid graph
         if (lane == 0) atomicOr(a.status, (int32_t)kSpillOverflow);
         continue;
       }
       __syncwarp();
-      // 4-cliques: each adjacent pair of T counted once via the out-list of its
-      // lower-rank member; per member the shorter side drives the search.
-      long long x7 = 0;
-      for (int32_t i = 0; i < t; ++i) {
-        const int32_t aa = buf[i];
-        const int32_t ob = g.out_ptr[aa], oe = g.out_ptr[aa + 1];
-        const int32_t len = oe - ob;
-        if (len <= t) {
-          for (int32_t j = ob + lane; j < oe; j += 32) x7 += contains(buf, t, g.out_idx[j]);
-        } else {
-          for (int32_t j = lane; j < t; j += 32) x7 += contains(g.out_idx + ob, len, buf[j]);
-        }
-      }
+      // 4-cliques: each adjacent pair of T is counted once, through the
+      // out-list of its lower-rank member; membership by binary search in T.
+      long long x7 = warp_clique_count<4>(g, buf, t, 0, 32, lane, true,
+                                          [&](int32_t r) { return contains(buf, t, r); });
       x7 = warp_sum_ll(x7);
       __syncwarp();
       const long long x10 = P - cross + 2 * x7;
@@ -256,15 +317,201 @@ __global__ void __launch_bounds__(kBlock) k_pass_b(DevGraph g, CountArgs a) {
     if (zero_all) {
       for (int32_t i = threadIdx.x; i < g.table_n; i += kBlock) tab[i] = 0;
     } else {
-      for (int32_t p = vb + warp; p < ve; p += kWarps) {
-        const int32_t r = g.ci[p];
-        if (lane == 0) tab[r - base] = 0u;
-        const int32_t rb = g.rp[r], re = g.rp[r + 1];
-        for (int32_t q = rb + lane; q < re; q += 32) tab[g.ci[q] - base] = 0u;
-      }
+      for (int32_t p = vb + threadIdx.x; p < ve; p += kBlock) tab[g.ci[p] - base] = 0u;
     }
   }
   if (cur_g >= 0 && lane < 13) atomic_add_u128(a.csum + ((size_t)cur_g * 13 + lane) * 2, acc);
+}
+
+// ---------------- pass B for edges with a large T ----------------
+// One CTA per edge whose T exceeds a warp's shared buffer. T is written in
+// order to a per-CTA global buffer; when its id range fits, a shared-memory
+// bitmap over [min T, max T] answers "r in T" with one load in the 4-clique
+// step, otherwise a binary search in the buffer does.
+__global__ void __launch_bounds__(kBigBlock, 1) k_pass_big(DevGraph g, CountArgs a) {
+  extern __shared__ uint32_t bm[];  // kBigWords words
+  __shared__ int32_t s_k, s_wcnt[kBigWarps], s_woff[kBigWarps + 1];
+  __shared__ long long s_red[kBigWarps];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint32_t* tab = a.tables + (size_t)blockIdx.x * (size_t)g.table_n;
+  int32_t* T = a.tbuf + (size_t)blockIdx.x * (size_t)a.tbuf_len;
+  const int32_t n_def = min(*a.n_deferred, a.deferred_cap);
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_k = atomicAdd(a.cursor, 1);
+    __syncthreads();
+    const int32_t k = s_k;
+    if (k >= n_def) break;
+    const int32_t v = a.deferred[2 * k], p = a.deferred[2 * k + 1];
+    const int32_t u = g.ci[p], e = g.eid[p];
+    const int32_t gid = g.vgid ? g.vgid[v] : 0;
+    const int32_t base = g.gbase[gid];
+    const int64_t n_g = g.gn[gid], m_g = g.gm[gid];
+    const int32_t vb = g.rp[v], ve = g.rp[v + 1];
+    const int32_t ub = g.rp[u], ue = g.rp[u + 1];
+    const int32_t t_expect = a.tri[e];
+    if (t_expect > a.tbuf_len) {
+      if (threadIdx.x == 0) atomicOr(a.status, (int32_t)kSpillOverflow);
+      continue;
+    }
+    for (int32_t q = vb + threadIdx.x; q < ve; q += kBigBlock) tab[g.ci[q] - base] = (uint32_t)(q - vb + 1);
+    __syncthreads();
+    // T in order, and the cross term
+    long long cross = 0;
+    int32_t t = 0;
+    for (int32_t q0 = ub; q0 < ue; q0 += kBigBlock) {
+      const int32_t q = q0 + threadIdx.x;
+      const int32_t w = q < ue ? g.ci[q] : v;
+      const uint32_t ent = w != v ? tab[w - base] : 0u;
+      const bool inT = ent != 0u;
+      if (inT) cross += (long long)a.tri[g.eid[q]] + (long long)a.tri[g.eid[vb + (int32_t)ent - 1]] - 2;
+      const unsigned mask = __ballot_sync(0xffffffffu, inT);
+      if (lane == 0) s_wcnt[warp] = __popc(mask);
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        int32_t acc = 0;
+        for (int i = 0; i < kBigWarps; ++i) { s_woff[i] = acc; acc += s_wcnt[i]; }
+        s_woff[kBigWarps] = acc;
+      }
+      __syncthreads();
+      const int32_t pos = t + s_woff[warp] + __popc(mask & ((1u << lane) - 1u));
+      if (inT && pos < t_expect) T[pos] = w;
+      t += s_woff[kBigWarps];
+      __syncthreads();
+    }
+    // reduce cross over the CTA
+    cross = warp_sum_ll(cross);
+    if (lane == 0) s_red[warp] = cross;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      long long c = 0;
+      for (int i = 0; i < kBigWarps; ++i) c += s_red[i];
+      s_red[0] = c;
+    }
+    __syncthreads();
+    cross = s_red[0];
+    if (t != t_expect) {  // cannot happen on a valid graph
+      if (threadIdx.x == 0) atomicOr(a.status, (int32_t)kSpillOverflow);
+      for (int32_t q = vb + threadIdx.x; q < ve; q += kBigBlock) tab[g.ci[q] - base] = 0u;
+      continue;
+    }
+    const int32_t lo = T[0], hi = T[t - 1];
+    const bool use_bm = (int64_t)hi - lo + 1 <= (int64_t)kBigWords * 32;
+    if (use_bm) {
+      const int32_t words = (hi - lo) / 32 + 1;
+      for (int32_t i = threadIdx.x; i < words; i += kBigBlock) bm[i] = 0u;
+      __syncthreads();
+      for (int32_t i = threadIdx.x; i < t; i += kBigBlock) {
+        const int32_t d = T[i] - lo;
+        atomicOr(&bm[d >> 5], 1u << (d & 31));
+      }
+    }
+    __syncthreads();
+    long long x7;
+    if (use_bm) {
+      x7 = warp_clique_count<4>(g, T, t, warp * 32, kBigBlock, lane, false, [&](int32_t r) {
+        const int32_t d = r - lo;
+        return (r >= lo && r <= hi) ? (int)((bm[d >> 5] >> (d & 31)) & 1u) : 0;
+      });
+    } else {
+      x7 = warp_clique_count<4>(g, T, t, warp * 32, kBigBlock, lane, true,
+                                [&](int32_t r) { return contains(T, t, r); });
+    }
+    x7 = warp_sum_ll(x7);
+    __syncthreads();
+    if (lane == 0) s_red[warp] = x7;
+    __syncthreads();
+    if (threadIdx.x < 13) {
+      long long xs = 0;
+      for (int i = 0; i < kBigWarps; ++i) xs += s_red[i];
+      const long long x10 = (long long)a.P[e] - cross + 2 * xs;
+      const int64_t du = ue - ub, dv = ve - vb;
+      const int64_t su = du - t - 1, sv = dv - t - 1;
+      const int64_t D = n_g - 2 - t - su - sv;
+      const int c = threadIdx.x;
+      const uint64_t col = edge_column(c, t, su, sv, D, xs, x10, m_g, du, dv);
+      if (a.per_edge) a.per_edge[(size_t)e * 13 + c] = col;
+      const uint64_t cs = edge_column(csum_column(c), t, su, sv, D, xs, x10, m_g, du, dv);
+      atomic_add_u128(a.csum + ((size_t)gid * 13 + c) * 2, (u128)cs);
+    }
+    for (int32_t q = vb + threadIdx.x; q < ve; q += kBigBlock) tab[g.ci[q] - base] = 0u;
+  }
+}
+
+// ---------------- pass C: 4-cycles through every edge ----------------
+// P(e) = number of 4-cycles (as subgraphs) containing e. Each 4-cycle is
+// counted from its highest-rank vertex h: with cnt_h(o) = #{x in Gamma(h) :
+// x < h, o in Gamma(x), o < h}, the wedge h-x-o closes cnt_h(o) - 1 cycles
+// through h, each of which contains the edges (h, x) and (x, o) once. Ranks
+// are the (degree, id) order of preprocessing P1/P3, so every wedge is met
+// from one h only.
+template <bool kSmemTable>
+__global__ void __launch_bounds__(kBlock) k_pass_c(DevGraph g, CountArgs a) {
+  extern __shared__ uint32_t smem[];
+  __shared__ int32_t s_unit, s_next[3];
+  uint32_t* tab = table_of<kSmemTable>(g, a, smem);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const bool zero_all = kSmemTable && g.table_n <= 4096;
+  if (kSmemTable)
+    for (int32_t i = threadIdx.x; i < g.table_n; i += kBlock) tab[i] = 0;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_unit = atomicAdd(a.cursor, 1);
+    __syncthreads();
+    const int32_t k = s_unit;
+    if (k >= a.n_units) break;
+    const int32_t h = a.units[k];
+    const int32_t base = g.gbase[g.vgid ? g.vgid[h] : 0];
+    const int32_t hb = g.rp[h], he = g.rp[h + 1];
+    if (threadIdx.x < 3) s_next[threadIdx.x] = hb;
+    __syncthreads();
+    // x runs over the lower-rank neighbours of h; o over those of x's
+    // neighbours that rank below h (a prefix of Gamma(x) when ids are ranks).
+    for (int pass = 0; pass < (zero_all ? 2 : 3); ++pass) {
+      for (;;) {
+        int32_t p = 0;
+        if (lane == 0) p = atomicAdd(&s_next[pass], 1);
+        p = __shfl_sync(0xffffffffu, p, 0);
+        if (p >= he) break;
+        const int32_t x = g.ci[p];
+        if (!rank_less(g.deg, x, h)) continue;
+        const int32_t xb = g.rp[x];
+        int32_t xe = g.rp[x + 1];
+        if (g.ranked) {
+          int32_t lo = xb, hi = xe;
+          while (lo < hi) {
+            const int32_t mid = (lo + hi) >> 1;
+            if (g.ci[mid] < h) lo = mid + 1; else hi = mid;
+          }
+          xe = lo;
+        }
+        unsigned long long s = 0;
+        for (int32_t q = xb + lane; q < xe; q += 32) {
+          const int32_t o = g.ci[q];
+          if (!g.ranked && !rank_less(g.deg, o, h)) continue;
+          if (pass == 0) {
+            atomicAdd(&tab[o - base], 1u);
+          } else if (pass == 1) {
+            const uint32_t c = tab[o - base] - 1u;
+            if (c) {
+              atomicAdd(&a.P[g.eid[q]], (unsigned long long)c);
+              s += c;
+            }
+          } else {
+            tab[o - base] = 0u;
+          }
+        }
+        if (pass == 1) {
+          for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+          if (lane == 0 && s) atomicAdd(&a.P[g.eid[p]], s);
+        }
+      }
+      __syncthreads();
+    }
+    if (zero_all) {
+      for (int32_t i = threadIdx.x; i < g.table_n; i += kBlock) tab[i] = 0;
+    }
+  }
 }
 
 // ---------------- derive X_1..X_17 per graph ----------------
@@ -348,16 +595,19 @@ gc_status launch(K kernel, size_t smem, const DevGraph& g, const CountArgs& a, c
 
 }  // namespace
 
-// Persistent grid: two CTAs of kBlock threads per SM.
+// Persistent grid: kCtasPerSm CTAs of kBlock threads per SM.
 int count_grid_size() {
   if (g_grid == 0) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    g_grid = (sms > 0 ? sms : 1) * 2;
+    g_grid = (sms > 0 ? sms : 1) * kCtasPerSm;
   }
   return g_grid;
 }
+
+// One CTA of kBigBlock threads per SM for the large-T edges.
+int big_grid_size() { return count_grid_size() / kCtasPerSm > 0 ? count_grid_size() / kCtasPerSm : 1; }
 
 gc_status run_pass_a(const DevGraph& g, const CountArgs& a, cudaStream_t s) {
   const bool sm = a.tables == nullptr;
@@ -369,6 +619,23 @@ gc_status run_pass_b(const DevGraph& g, const CountArgs& a, cudaStream_t s) {
   const bool sm = a.tables == nullptr;
   if (sm) return launch(k_pass_b<true>, smem_bytes(true, g.table_n, true), g, a, s, "k_pass_b");
   return launch(k_pass_b<false>, smem_bytes(false, g.table_n, true), g, a, s, "k_pass_b");
+}
+
+gc_status run_pass_c(const DevGraph& g, const CountArgs& a, cudaStream_t s) {
+  const bool sm = a.tables == nullptr;
+  if (sm) return launch(k_pass_c<true>, smem_bytes(true, g.table_n, false), g, a, s, "k_pass_c");
+  return launch(k_pass_c<false>, smem_bytes(false, g.table_n, false), g, a, s, "k_pass_c");
+}
+
+gc_status run_pass_big(const DevGraph& g, const CountArgs& a, int32_t n_deferred, cudaStream_t s) {
+  const size_t smem = sizeof(uint32_t) * kBigWords;
+  cudaError_t e = cudaFuncSetAttribute(k_pass_big, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return cuda_fail(e, "k_pass_big");
+  int grid = big_grid_size();
+  if (n_deferred < grid) grid = n_deferred > 0 ? n_deferred : 1;
+  k_pass_big<<<grid, kBigBlock, smem, s>>>(g, a);
+  e = cudaGetLastError();
+  return e == cudaSuccess ? GC_OK : cuda_fail(e, "k_pass_big");
 }
 
 gc_status run_derive(const DevGraph& g, const unsigned long long* csum, unsigned long long* x,

@@ -83,7 +83,7 @@ __global__ void k_edges(int32_t n, const int32_t* __restrict__ rp, const int32_t
                         const int32_t* __restrict__ deg, const int32_t* __restrict__ up,
                         const int32_t* __restrict__ upoff, const int32_t* __restrict__ out_ptr,
                         int32_t* __restrict__ eid, int32_t* __restrict__ uv,
-                        int32_t* __restrict__ out_idx) {
+                        int32_t* __restrict__ out_idx, bool write_ids) {
   const int lane = threadIdx.x & 31;
   const int warps = (gridDim.x * blockDim.x) >> 5;
   for (int32_t x = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < n; x += warps) {
@@ -95,7 +95,7 @@ __global__ void k_edges(int32_t n, const int32_t* __restrict__ rp, const int32_t
       bool valid = p < e;
       int32_t y = valid ? ci[p] : 0;
       bool is_out = valid && rank_less(deg, x, y);
-      if (valid) {
+      if (valid && write_ids) {
         int32_t id;
         if (y > x) {
           id = upoff[x] + (p - first_up);
@@ -111,6 +111,25 @@ __global__ void k_edges(int32_t n, const int32_t* __restrict__ rp, const int32_t
       unsigned mask = __ballot_sync(0xffffffffu, is_out);
       if (is_out) out_idx[o + __popc(mask & ((1u << lane) - 1u))] = y;
       o += __popc(mask);
+    }
+  }
+}
+
+// Edge list in the caller's labels when the graph was relabelled.
+__global__ void k_uv_perm(int32_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                          const int32_t* __restrict__ eid, const int32_t* __restrict__ perm,
+                          int32_t* __restrict__ uv) {
+  const int lane = threadIdx.x & 31;
+  const int warps = (gridDim.x * blockDim.x) >> 5;
+  for (int32_t x = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < n; x += warps) {
+    const int32_t px = perm[x];
+    for (int32_t p = rp[x] + lane; p < rp[x + 1]; p += 32) {
+      const int32_t y = ci[p];
+      if (y < x) continue;
+      const int32_t py = perm[y];
+      const int64_t e = eid[p];
+      uv[2 * e] = px < py ? px : py;
+      uv[2 * e + 1] = px < py ? py : px;
     }
   }
 }
@@ -236,6 +255,15 @@ __global__ void k_scan_tiles(int32_t n, const int32_t* __restrict__ in,
   }
 }
 
+int grid_for(int64_t work, int block) {
+  int64_t g = (work + block - 1) / block;
+  if (g < 1) g = 1;
+  if (g > 65535LL * 16) g = 65535LL * 16;
+  return (int)g;
+}
+
+}  // namespace
+
 gc_status exclusive_scan(int32_t n, const int32_t* in, int32_t* out, cudaStream_t s) {
   if (n == 0) {
     cudaError_t e = cudaMemsetAsync(out, 0, sizeof(int32_t), s);
@@ -253,15 +281,6 @@ gc_status exclusive_scan(int32_t n, const int32_t* in, int32_t* out, cudaStream_
   return e == cudaSuccess ? GC_OK : cuda_fail(e, "scan launch");
 }
 
-int grid_for(int64_t work, int block) {
-  int64_t g = (work + block - 1) / block;
-  if (g < 1) g = 1;
-  if (g > 65535LL * 16) g = 65535LL * 16;
-  return (int)g;
-}
-
-}  // namespace
-
 void free_prep(PrepBuffers* p, cudaStream_t s) {
   if (p->deg) cudaFreeAsync(p->deg, s);
   if (p->eid) cudaFreeAsync(p->eid, s);
@@ -269,13 +288,16 @@ void free_prep(PrepBuffers* p, cudaStream_t s) {
   if (p->out_ptr) cudaFreeAsync(p->out_ptr, s);
   if (p->out_idx) cudaFreeAsync(p->out_idx, s);
   if (p->units) cudaFreeAsync(p->units, s);
+  if (p->S) cudaFreeAsync(p->S, s);
   *p = PrepBuffers();
 }
 
 gc_status prepare_graph(int32_t n, int32_t m, const int32_t* d_rp, const int32_t* d_ci,
-                        const int32_t* d_vgid, PrepBuffers* out, cudaStream_t s) {
+                        const int32_t* d_vgid, int32_t* d_eid_given, const int32_t* d_perm,
+                        PrepBuffers* out, cudaStream_t s) {
   (void)d_vgid;
   PrepBuffers P;
+  P.eid = d_eid_given;
   int32_t *up = nullptr, *upoff = nullptr, *out_cnt = nullptr, *dmax = nullptr, *hist = nullptr;
   long long* S = nullptr;
   gc_status st = GC_OK;
@@ -290,7 +312,7 @@ gc_status prepare_graph(int32_t n, int32_t m, const int32_t* d_rp, const int32_t
     }                                      \
   } while (0)
   GC_TRY(cudaMallocAsync(&P.deg, sizeof(int32_t) * (n > 0 ? n : 1), s), "alloc deg");
-  GC_TRY(cudaMallocAsync(&P.eid, sizeof(int32_t) * (nnz > 0 ? nnz : 1), s), "alloc eid");
+  if (!P.eid) GC_TRY(cudaMallocAsync(&P.eid, sizeof(int32_t) * (nnz > 0 ? nnz : 1), s), "alloc eid");
   GC_TRY(cudaMallocAsync(&P.uv, sizeof(int32_t) * (nnz > 0 ? nnz : 1), s), "alloc uv");
   GC_TRY(cudaMallocAsync(&P.out_ptr, sizeof(int32_t) * ((int64_t)n + 1), s), "alloc out_ptr");
   GC_TRY(cudaMallocAsync(&P.out_idx, sizeof(int32_t) * (m > 0 ? m : 1), s), "alloc out_idx");
@@ -298,7 +320,8 @@ gc_status prepare_graph(int32_t n, int32_t m, const int32_t* d_rp, const int32_t
   GC_TRY(cudaMallocAsync(&up, sizeof(int32_t) * (n > 0 ? n : 1), s), "alloc up");
   GC_TRY(cudaMallocAsync(&upoff, sizeof(int32_t) * ((int64_t)n + 1), s), "alloc upoff");
   GC_TRY(cudaMallocAsync(&out_cnt, sizeof(int32_t) * (n > 0 ? n : 1), s), "alloc out_cnt");
-  GC_TRY(cudaMallocAsync(&S, sizeof(long long) * (n > 0 ? n : 1), s), "alloc S");
+  GC_TRY(cudaMallocAsync(&P.S, sizeof(long long) * (n > 0 ? n : 1), s), "alloc S");
+  S = P.S;
   GC_TRY(cudaMallocAsync(&dmax, sizeof(int32_t) * 65, s), "alloc dmax");
   hist = dmax + 1;
   GC_TRY(cudaMemsetAsync(dmax, 0, sizeof(int32_t) * 65, s), "memset");
@@ -310,8 +333,13 @@ gc_status prepare_graph(int32_t n, int32_t m, const int32_t* d_rp, const int32_t
     GC_TRY(cudaGetLastError(), "k_out_cnt");
     if ((st = exclusive_scan(n, out_cnt, P.out_ptr, s)) != GC_OK) goto fail;
     k_edges<<<grid_for((int64_t)n * 32, 256), 256, 0, s>>>(n, d_rp, d_ci, P.deg, up, upoff,
-                                                            P.out_ptr, P.eid, P.uv, P.out_idx);
+                                                            P.out_ptr, P.eid, P.uv, P.out_idx,
+                                                            d_eid_given == nullptr);
     GC_TRY(cudaGetLastError(), "k_edges");
+    if (d_eid_given) {
+      k_uv_perm<<<grid_for((int64_t)n * 32, 256), 256, 0, s>>>(n, d_rp, d_ci, P.eid, d_perm, P.uv);
+      GC_TRY(cudaGetLastError(), "k_uv_perm");
+    }
     k_bin_hist<<<grid_for(n, 256), 256, 0, s>>>(n, P.deg, out_cnt, S, hist);
     GC_TRY(cudaGetLastError(), "k_bin_hist");
     {
@@ -336,7 +364,6 @@ gc_status prepare_graph(int32_t n, int32_t m, const int32_t* d_rp, const int32_t
     cudaFreeAsync(up, s);
   cudaFreeAsync(upoff, s);
   cudaFreeAsync(out_cnt, s);
-  cudaFreeAsync(S, s);
   cudaFreeAsync(dmax, s);
   *out = P;
   return GC_OK;
@@ -345,7 +372,6 @@ fail:
   if (up) cudaFreeAsync(up, s);
   if (upoff) cudaFreeAsync(upoff, s);
   if (out_cnt) cudaFreeAsync(out_cnt, s);
-  if (S) cudaFreeAsync(S, s);
   if (dmax) cudaFreeAsync(dmax, s);
   free_prep(&P, s);
   return st;

@@ -74,7 +74,7 @@ def test_degenerate_graphs():
 
 
 def test_wide_counts_need_high_words():
-    n = 70000  # C(n, 4) > 2^64
+    n = 200000  # C(n, 4) > 2^64
     rp, ci = graphs.csr(n, [(0, 1), (1, 2)])
     with gcb.Graph(rp, ci) as g:
         X = g.count()
