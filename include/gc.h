@@ -169,6 +169,32 @@ gc_status gc_batch_poll(gc_batch b, uint64_t ticket, uint64_t* global_out, uint6
                         int32_t timeout_us);
 gc_status gc_batch_destroy(gc_batch b);
 
+/*
+ * Triangle counts per CSR slot without any memory allocation.
+ *
+ * For callers that cannot allocate device memory (a fixed arena, a stream
+ * under capture, an allocator callback, a budget that forbids growth). The
+ * paper has no counterpart: it is a variant of the triangle step that reads
+ * the caller's device CSR in place and uses, as its only scratch, a 32 MiB
+ * file-scope device array (256 bitmaps of 2^20 bits) that every GPU loading
+ * libgc.so holds until the process exits.
+ *   n        vertices, 0 <= n <= 1,048,576; larger n returns GC_ERR_OVERFLOW
+ *   row_ptr  device pointer, n + 1 int32 (same CSR rules as gc_graph_upload;
+ *            not validated here)
+ *   col_idx  device pointer, row_ptr[n] int32
+ *   tri_out  device pointer, row_ptr[n] int32: tri_out[p] = |Gamma(x) ∩ Gamma(y)|
+ *            for the slot p = (x, y) (both directions of an edge get its |T|)
+ *   stream   cudaStream_t (as void*), NULL = legacy default stream
+ * Asynchronous on `stream`; calls no cudaMalloc/cudaFree. The first call on a
+ * device, with that device current, looks up the array's device address
+ * (cudaGetSymbolAddress) -- make that first call before any stream capture.
+ * All calls share the array and each call clears it first: calls whose
+ * kernels overlap on the GPU (other streams, other threads) race and give
+ * wrong results.
+ */
+gc_status gc_edge_triangles_noalloc(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int32_t* tri_out,
+                                    void* stream);
+
 #ifdef __cplusplus
 }
 #endif

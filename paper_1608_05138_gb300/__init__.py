@@ -35,7 +35,7 @@ GC_BATCH_MANUAL = 0x1
 EXPORTED = ["gc_last_error", "gc_graph_upload", "gc_graph_info", "gc_graph_edges",
             "gc_count_edge_graphlets", "gc_graph_csums", "gc_phase_count", "gc_phase_name",
             "gc_graph_phase_ms", "gc_graph_free", "gc_batch_create", "gc_batch_submit",
-            "gc_batch_flush", "gc_batch_poll", "gc_batch_destroy"]
+            "gc_batch_flush", "gc_batch_poll", "gc_batch_destroy", "gc_edge_triangles_noalloc"]
 
 
 class GcError(RuntimeError):
@@ -72,9 +72,11 @@ def lib():
             L.gc_batch_flush.argtypes = [vp]
             L.gc_batch_poll.argtypes = [vp, C.c_uint64, vp, vp, i32]
             L.gc_batch_destroy.argtypes = [vp]
+            L.gc_edge_triangles_noalloc.argtypes = [i32, vp, vp, vp, vp]
             for name in ("gc_graph_upload", "gc_graph_info", "gc_graph_edges", "gc_count_edge_graphlets",
                          "gc_graph_csums", "gc_graph_phase_ms", "gc_graph_free", "gc_batch_create",
-                         "gc_batch_submit", "gc_batch_flush", "gc_batch_poll", "gc_batch_destroy"):
+                         "gc_batch_submit", "gc_batch_flush", "gc_batch_poll", "gc_batch_destroy",
+                         "gc_edge_triangles_noalloc"):
                 getattr(L, name).restype = C.c_int
             _lib = L
     return _lib
@@ -261,3 +263,14 @@ def gc_batch_poll(b, ticket: int, timeout_us: int = -1):
 def gc_batch_destroy(b):
     if b is not None:
         _check(lib().gc_batch_destroy(b), "gc_batch_destroy")
+
+
+# ---------------- allocation-free triangle step ----------------
+
+def gc_edge_triangles_noalloc(row_ptr, col_idx, tri_out, stream=None):
+    """Per-slot triangle counts from a device CSR into a device int32 buffer,
+    with no memory allocation (see include/gc.h). row_ptr, col_idx and
+    tri_out are contiguous int32 CUDA tensors; runs asynchronously."""
+    n = row_ptr.numel() - 1
+    _check(lib().gc_edge_triangles_noalloc(n, _ptr(row_ptr), _ptr(col_idx), _ptr(tri_out),
+                                           _stream_handle(stream)), "gc_edge_triangles_noalloc")
