@@ -53,32 +53,37 @@ def load_workload(name: str, scale: int):
     return rp, ci, desc
 
 
-def algorithmic_bytes(rp, ci, tri_per_edge=None):
-    """Bytes the implemented passes must move per launch:
-    pass A: 8 d_v per v-group (mark + clear) + 8 d_u + 8 per edge;
-    pass B: per v-group 4 d_v + sum_{r in Gamma(v)} (8 + 20 d_r), per edge
-    8 d_u + 12 |T| + 104 (13-column row). Also the paper-method logical bytes
-    B_e = 4 (d_u + d_v + sum_{w in Gamma(u)\\{v}} d_w) + 120."""
+def algorithmic_bytes(work: dict) -> dict:
+    """Algorithmic bytes per launch of each counting kernel, from the units the
+    kernels report (gc_graph_work_counts); per-unit figures are in the design doc §7:
+      pass A: 8 per entry of Gamma(v) and of the Gamma(u) scans (read + Psi)
+      pass C: 48 per wedge h-x-o (entry read, count RMW, attribution read,
+              edge id, P atomic, clear)
+      pass B: 16 per d_v of a chunk (Psi set and clear), 8 per d_u (Gamma(u)
+              read + Psi lookup), 28 per member of T (edge ids, triangle
+              counts, out-list bounds, T store), 4 per out-list entry tested,
+              120 per edge (13-column row, P, |T|, edge id)
+      large-T pass: 16 per d_u + d_v, 28 per member of T, 4 per entry tested."""
+    return {
+        "k_pass_a": 8 * work["a_units"],
+        "k_pass_c": 48 * work["c_wedges"],
+        "k_pass_b": 16 * work["b_group_deg"] + 8 * work["b_deg"] + 28 * work["b_T"] + 4 * work["b_probes"]
+        + 120 * work["b_edges"],
+        "k_pass_big": 16 * work["big_deg"] + 28 * work["big_T"] + 4 * work["big_probes"],
+    }
+
+
+def paper_method_bytes(rp, ci):
+    """Logical bytes of the paper's literal per-edge scans (Alg. 1/5/6):
+    B_e = 4 (d_u + d_v + sum_{w in Gamma(u)\\{v}} d_w) + 120 per edge."""
     n = len(rp) - 1
     deg = np.diff(rp).astype(np.int64)
     rows = np.repeat(np.arange(n, dtype=np.int64), deg)
     cols = ci.astype(np.int64)
-    S = np.zeros(n, np.int64)
-    if len(cols):
-        S = np.bincount(rows, weights=deg[cols], minlength=n).astype(np.int64)
-    # low endpoint of each directed slot (row, col) where row is low
-    low_is_row = (deg[rows] < deg[cols]) | ((deg[rows] == deg[cols]) & (rows < cols))
-    du = deg[rows[low_is_row]]
-    dv = deg[cols[low_is_row]]
-    high = cols[low_is_row]
-    groups = np.unique(high)
-    t_sum = int(tri_per_edge.sum()) if tri_per_edge is not None else 0
-    m = len(du)
-    pass_a = int(8 * deg[groups].sum() + 8 * du.sum() + 8 * m)
-    pass_b = int(4 * deg[groups].sum() + 8 * deg[groups].sum() + 20 * S[groups].sum()
-                 + 8 * du.sum() + 12 * t_sum + 104 * m)
-    logical = int(4 * (du.sum() + dv.sum() + (S[rows[low_is_row]] - dv).sum()) + 120 * m)
-    return {"pass_a": pass_a, "pass_b": pass_b, "logical_paper_method": logical}
+    S = np.bincount(rows, weights=deg[cols], minlength=n).astype(np.int64) if len(cols) else np.zeros(n, np.int64)
+    low = (deg[rows] < deg[cols]) | ((deg[rows] == deg[cols]) & (rows < cols))
+    du, dv = deg[rows[low]], deg[cols[low]]
+    return int(4 * (du.sum() + dv.sum() + (S[rows[low]] - dv).sum()) + 120 * len(du))
 
 
 class ClockSampler:
@@ -219,8 +224,6 @@ def main():
     for _ in range(args.warmup):
         X = g.count(per_edge)
     torch.cuda.synchronize()
-    tri = per_edge[:, 0].cpu().numpy()
-    ab = algorithmic_bytes(rp, ci, tri)
 
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
@@ -233,6 +236,7 @@ def main():
         for _ in range(args.steps):
             X = g.count(per_edge)
             phases.append(g.phase_ms())
+        work = g.work_counts()
         ev1.record(stream)
         torch.cuda.synchronize()
     step_ms = ev0.elapsed_time(ev1) / args.steps
@@ -273,18 +277,24 @@ def main():
         except Exception:
             peak, peak_src = 6800.0, "fallback"
     ph_ms = {k: statistics.mean(p[k] for p in phases) for k in phases[0]}
-    pb = ph_ms["pass_b_cliques_finish"]
-    achieved = ab["pass_b"] / (pb / 1000.0) / 1e9
+    kernel_ms = {"k_pass_a": ph_ms["pass_a_triangles"], "k_pass_c": ph_ms["pass_c_cycles"],
+                 "k_pass_b": ph_ms["pass_b_cliques_finish"], "k_pass_big": ph_ms["pass_b_large_T"]}
+    ab = algorithmic_bytes(work)
+    kernels = {k: {"ms": kernel_ms[k], "algorithmic_bytes": ab[k],
+                   "gbs": ab[k] / (kernel_ms[k] / 1000.0) / 1e9 if kernel_ms[k] > 0 else None,
+                   "share": kernel_ms[k] / sum(kernel_ms.values())} for k in kernel_ms}
+    dom = max(kernel_ms, key=kernel_ms.get)
+    achieved = kernels[dom]["gbs"]
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "peak_source": peak_src, "kernel": "k_pass_b", "kernel_ms": pb,
-            "algorithmic_bytes": ab["pass_b"], "traffic": None,
-            "logical_paper_method_gbs": ab["logical_paper_method"] / (pb / 1000.0) / 1e9}
+            "peak_source": peak_src, "kernel": dom, "kernel_ms": kernel_ms[dom],
+            "algorithmic_bytes": ab[dom], "traffic": None, "kernels": kernels,
+            "logical_paper_method_gbs": paper_method_bytes(rp, ci) / (step_ms / 1000.0) / 1e9}
     line = {"metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int64", "data": "synthetic",
             "config": {"workload": desc, "n": len(rp) - 1, "m": m, "per_edge_rows": "device",
                        "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas{world}"},
-            "phases_ms": ph_ms,
+            "phases_ms": ph_ms, "work": work,
             "roofline": roof, "clocks": clk.summary(), "gpu_launches": 4 * args.steps,
             "e2e": e2e}
     if not args.no_cpu:

@@ -134,6 +134,17 @@ int gc_phase_count(void);
 const char* gc_phase_name(int i);
 gc_status gc_graph_phase_ms(gc_graph g, double* ms);
 
+/* Units of work the kernels processed in the last gc_count_edge_graphlets on
+ * g (host pointer, GC_NUM_WORK uint64), in this order:
+ *   0 pass B sum of d_v over its chunks   1 pass B sum of d_u over its edges
+ *   2 pass B sum of |T|                    3 pass B out-list entries tested (4-cliques)
+ *   4 pass B edges                         5 large-T pass sum of d_u + d_v
+ *   6 large-T pass sum of |T|              7 large-T pass entries tested
+ *   8 pass C wedges h-x-o                  9 pass A sum of d_v + d_u
+ * Used to turn kernel times into algorithmic bytes per second. */
+#define GC_NUM_WORK 10
+gc_status gc_graph_work_counts(gc_graph g, uint64_t* out);
+
 /* Release the graph and all its device memory. NULL is accepted. */
 gc_status gc_graph_free(gc_graph g);
 

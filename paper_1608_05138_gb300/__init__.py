@@ -35,7 +35,10 @@ GC_BATCH_MANUAL = 0x1
 EXPORTED = ["gc_last_error", "gc_graph_upload", "gc_graph_info", "gc_graph_edges",
             "gc_count_edge_graphlets", "gc_graph_csums", "gc_phase_count", "gc_phase_name",
             "gc_graph_phase_ms", "gc_graph_free", "gc_batch_create", "gc_batch_submit",
-            "gc_batch_flush", "gc_batch_poll", "gc_batch_destroy", "gc_edge_triangles_noalloc"]
+            "gc_batch_flush", "gc_batch_poll", "gc_batch_destroy", "gc_edge_triangles_noalloc",
+            "gc_graph_work_counts"]
+WORK_NAMES = ["b_group_deg", "b_deg", "b_T", "b_probes", "b_edges", "big_deg", "big_T", "big_probes",
+              "c_wedges", "a_units"]
 
 
 class GcError(RuntimeError):
@@ -73,10 +76,11 @@ def lib():
             L.gc_batch_poll.argtypes = [vp, C.c_uint64, vp, vp, i32]
             L.gc_batch_destroy.argtypes = [vp]
             L.gc_edge_triangles_noalloc.argtypes = [i32, vp, vp, vp, vp]
+            L.gc_graph_work_counts.argtypes = [vp, vp]
             for name in ("gc_graph_upload", "gc_graph_info", "gc_graph_edges", "gc_count_edge_graphlets",
                          "gc_graph_csums", "gc_graph_phase_ms", "gc_graph_free", "gc_batch_create",
                          "gc_batch_submit", "gc_batch_flush", "gc_batch_poll", "gc_batch_destroy",
-                         "gc_edge_triangles_noalloc"):
+                         "gc_edge_triangles_noalloc", "gc_graph_work_counts"):
                 getattr(L, name).restype = C.c_int
             _lib = L
     return _lib
@@ -176,6 +180,12 @@ def gc_graph_phase_ms(g):
     return dict(zip(gc_phase_names(), ms.tolist()))
 
 
+def gc_graph_work_counts(g):
+    out = np.zeros(len(WORK_NAMES), np.uint64)
+    _check(lib().gc_graph_work_counts(g, _ptr(out)), "gc_graph_work_counts")
+    return dict(zip(WORK_NAMES, (int(x) for x in out)))
+
+
 def gc_graph_free(g):
     if g is not None:
         _check(lib().gc_graph_free(g), "gc_graph_free")
@@ -199,6 +209,9 @@ class Graph:
 
     def phase_ms(self):
         return gc_graph_phase_ms(self.handle)
+
+    def work_counts(self):
+        return gc_graph_work_counts(self.handle)
 
     def close(self):
         if self.handle is not None:

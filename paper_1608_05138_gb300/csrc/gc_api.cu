@@ -197,6 +197,7 @@ struct gc_graph_s {
   cudaEvent_t ev[kNumPhases + 1] = {};
   bool counted = false;
   uint64_t csum_lo[13] = {0}, csum_hi[13] = {0};
+  uint64_t work[kNumWork] = {0};
 };
 
 extern "C" {
@@ -369,6 +370,7 @@ gc_status gc_count_edge_graphlets(gc_graph g, uint64_t* per_edge_out, uint64_t* 
   GC_CHECK(cudaMemcpyAsync(hx + 34, g->d_csum, sizeof(unsigned long long) * 13 * 2, cudaMemcpyDeviceToHost, s),
            "copy C");
   GC_CHECK(cudaMemcpyAsync(&hstatus, g->sc.misc + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, s), "copy status");
+  GC_CHECK(cudaMemcpyAsync(g->work, g->sc.work, sizeof(g->work), cudaMemcpyDeviceToHost, s), "copy work");
   if (want_pe && pe_dev != per_edge_out)
     GC_CHECK(cudaMemcpyAsync(per_edge_out, pe_dev, sizeof(uint64_t) * 13 * (size_t)g->m, cudaMemcpyDeviceToHost, s),
              "copy per-edge");
@@ -408,6 +410,14 @@ gc_status gc_graph_csums(gc_graph g, uint64_t* lo, uint64_t* hi) {
     lo[k] = g->csum_lo[k];
     if (hi) hi[k] = g->csum_hi[k];
   }
+  return GC_OK;
+}
+
+gc_status gc_graph_work_counts(gc_graph g, uint64_t* out) {
+  if (!g || !out) { set_error("NULL argument"); return GC_ERR_ARG; }
+  if (!g->counted) { set_error("graph not counted yet"); return GC_ERR_ARG; }
+  static_assert(kNumWork == GC_NUM_WORK, "work counter count");
+  for (int i = 0; i < kNumWork; ++i) out[i] = g->work[i];
   return GC_OK;
 }
 

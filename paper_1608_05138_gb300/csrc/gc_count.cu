@@ -34,6 +34,8 @@
 //   C_9 = sum |T|(|S_u| + |S_v|)), exact 128-bit division checked.
 #include <cuda_runtime.h>
 
+#include <cstdlib>
+
 #include "gc_internal.h"
 
 namespace gc {
@@ -67,14 +69,14 @@ __device__ __forceinline__ int contains(const int32_t* a, int32_t len, int32_t k
 
 // 4-clique count of one edge: sum over members a of T (ascending, t of them)
 // of |out(a) ∩ T|, for one warp. Members are taken 32 at a time; the entries
-// of their out-lists are flattened over the lanes (coalesced, no idle lanes)
-// and each lane keeps kMLP loads in flight before probing. in_T(r) answers
-// membership; a member whose out-list is longer than T (when long_ok) has
-// T's members searched in its out-list instead.
+// of their out-lists are flattened over the lanes (coalesced loads, no idle
+// lanes) and each lane keeps kMLP loads in flight before probing. in_T(r)
+// answers membership; a member whose out-list is longer than T (when
+// long_ok) has T's members searched in its out-list instead.
 template <int kMLP, class InT>
 __device__ __forceinline__ long long warp_clique_count(const DevGraph& g, const int32_t* T, int32_t t,
                                                        int32_t i_begin, int32_t i_stride, int lane,
-                                                       bool long_ok, InT in_T) {
+                                                       bool long_ok, InT in_T, long long& probes) {
   long long x7 = 0;
   for (int32_t i0 = i_begin; i0 < t; i0 += i_stride) {
     const int32_t i = i0 + lane;
@@ -93,6 +95,7 @@ __device__ __forceinline__ long long warp_clique_count(const DevGraph& g, const 
     }
     const int32_t excl = incl - L;
     const int32_t total = __shfl_sync(0xffffffffu, incl, 31);
+    probes += total;
     for (int32_t k0 = 0; k0 < total; k0 += 32 * kMLP) {
       int32_t r[kMLP];
 #pragma unroll
@@ -118,6 +121,7 @@ __device__ __forceinline__ long long warp_clique_count(const DevGraph& g, const 
       lm &= lm - 1;
       const int32_t oj = __shfl_sync(0xffffffffu, ob, src);
       const int32_t lj = __shfl_sync(0xffffffffu, len, src);
+      probes += t;
       for (int32_t j = lane; j < t; j += 32) x7 += contains(g.out_idx + oj, lj, T[j]);
     }
   }
@@ -173,6 +177,7 @@ __global__ void __launch_bounds__(kBlock) k_pass_a(DevGraph g, CountArgs a) {
   __shared__ int32_t s_unit, s_next;
   uint32_t* tab = table_of<kSmemTable>(g, a, smem);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  long long w_units = 0;
   if (kSmemTable)
     for (int32_t i = threadIdx.x; i < g.table_n; i += kBlock) tab[i] = 0;
   for (;;) {
@@ -180,11 +185,15 @@ __global__ void __launch_bounds__(kBlock) k_pass_a(DevGraph g, CountArgs a) {
     if (threadIdx.x == 0) s_unit = atomicAdd(a.cursor, 1);
     __syncthreads();
     const int32_t k = s_unit;
-    if (k >= a.n_units) break;
+    if (k >= a.n_units) {
+      if (lane == 0 && w_units) atomicAdd(a.work + kWorkAUnits, (unsigned long long)w_units);
+      break;
+    }
     const int32_t v = a.units[k];
     const int32_t base = g.gbase[g.vgid ? g.vgid[v] : 0];
     const int32_t vb = g.rp[v], ve = g.rp[v + 1];
     for (int32_t p = vb + threadIdx.x; p < ve; p += kBlock) tab[g.ci[p] - base] = 1u;
+    if (threadIdx.x == 0) w_units += ve - vb;
     if (threadIdx.x == 0) s_next = vb;
     __syncthreads();
     for (;;) {  // edges of the group handed to warps one at a time
@@ -198,7 +207,10 @@ __global__ void __launch_bounds__(kBlock) k_pass_a(DevGraph g, CountArgs a) {
       int c = 0;
       for (int32_t q = ub + lane; q < ue; q += 32) c += tab[g.ci[q] - base] != 0u;
       c = warp_sum_i(c);
-      if (lane == 0) a.tri[g.eid[p]] = c;
+      if (lane == 0) {
+        a.tri[g.eid[p]] = c;
+        w_units += ue - ub;
+      }
     }
     __syncthreads();
     for (int32_t p = vb + threadIdx.x; p < ve; p += kBlock) tab[g.ci[p] - base] = 0u;
@@ -218,6 +230,7 @@ __global__ void __launch_bounds__(kBlock, kCtasPerSm) k_pass_b(DevGraph g, Count
 
   u128 acc = 0;  // lane k < 13: running sum of C-sum k for graph cur_g
   int32_t cur_g = -1;
+  long long w_gdeg = 0, w_deg = 0, w_t = 0, w_probe = 0, w_edges = 0;  // warp-uniform work tallies
 
   const int32_t n_chunks = *a.n_chunks;
   if (kSmemTable)
@@ -246,6 +259,7 @@ __global__ void __launch_bounds__(kBlock, kCtasPerSm) k_pass_b(DevGraph g, Count
     // Psi for the group: Psi(r) = 1 + position of r in Gamma(v) (non-zero =
     // lambda1, "neighbour of v"); the position gives the edge (r, v).
     for (int32_t p = vb + threadIdx.x; p < ve; p += kBlock) tab[g.ci[p] - base] = (uint32_t)(p - vb + 1);
+    if (warp == 0) w_gdeg += dv;
     if (threadIdx.x == 0) s_next = cb;
     __syncthreads();
 
@@ -260,7 +274,7 @@ __global__ void __launch_bounds__(kBlock, kCtasPerSm) k_pass_b(DevGraph g, Count
       if (!rank_less(g.deg, u, v)) continue;
       const int32_t e = g.eid[p];
       const int32_t t_expect = a.tri[e];
-      if (t_expect > kTcap) {  // |T| beyond the warp's buffer: a whole CTA takes it later
+      if (t_expect > a.big_t) {  // large T: a whole CTA takes this edge later
         if (lane == 0) {
           const int32_t i = atomicAdd(a.n_deferred, 1);
           if (i < a.deferred_cap) {
@@ -297,11 +311,14 @@ __global__ void __launch_bounds__(kBlock, kCtasPerSm) k_pass_b(DevGraph g, Count
       // 4-cliques: each adjacent pair of T is counted once, through the
       // out-list of its lower-rank member; membership by binary search in T.
       long long x7 = warp_clique_count<4>(g, buf, t, 0, 32, lane, true,
-                                          [&](int32_t r) { return contains(buf, t, r); });
+                                          [&](int32_t r) { return contains(buf, t, r); }, w_probe);
       x7 = warp_sum_ll(x7);
       __syncwarp();
       const long long x10 = P - cross + 2 * x7;
       const int64_t du = ue - ub;
+      w_deg += du;
+      w_t += t;
+      w_edges += 1;
       const int64_t su = du - t - 1, sv = dv - t - 1;
       const int64_t D = n_g - 2 - t - su - sv;
       if (lane < 13) {
@@ -321,21 +338,31 @@ __global__ void __launch_bounds__(kBlock, kCtasPerSm) k_pass_b(DevGraph g, Count
     }
   }
   if (cur_g >= 0 && lane < 13) atomic_add_u128(a.csum + ((size_t)cur_g * 13 + lane) * 2, acc);
+  if (lane == 0) {  // the tallies are warp-uniform: lane 0 holds the warp's totals
+    if (w_gdeg) atomicAdd(a.work + kWorkBGroupDeg, (unsigned long long)w_gdeg);
+    atomicAdd(a.work + kWorkBDeg, (unsigned long long)w_deg);
+    atomicAdd(a.work + kWorkBT, (unsigned long long)w_t);
+    atomicAdd(a.work + kWorkBProbe, (unsigned long long)w_probe);
+    atomicAdd(a.work + kWorkBEdges, (unsigned long long)w_edges);
+  }
 }
 
 // ---------------- pass B for edges with a large T ----------------
-// One CTA per edge whose T exceeds a warp's shared buffer. T is written in
-// order to a per-CTA global buffer; when its id range fits, a shared-memory
-// bitmap over [min T, max T] answers "r in T" with one load in the 4-clique
-// step, otherwise a binary search in the buffer does.
+// One CTA per edge whose T has more than big_t members. T = Gamma(u) ∩ Gamma(v)
+// is found by binary search of Gamma(u)'s entries in Gamma(v) (the position
+// found also names the edge (a, v) for the cross term), written in order to a
+// per-CTA global buffer; when its id range fits, a shared-memory bitmap over
+// [min T, max T] answers "r in T" with one load in the 4-clique step
+// (binary search in the buffer otherwise). Only the bitmap words set for an
+// edge are cleared after it.
 __global__ void __launch_bounds__(kBigBlock, 1) k_pass_big(DevGraph g, CountArgs a) {
   extern __shared__ uint32_t bm[];  // kBigWords words
   __shared__ int32_t s_k, s_wcnt[kBigWarps], s_woff[kBigWarps + 1];
   __shared__ long long s_red[kBigWarps];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  uint32_t* tab = a.tables + (size_t)blockIdx.x * (size_t)g.table_n;
   int32_t* T = a.tbuf + (size_t)blockIdx.x * (size_t)a.tbuf_len;
   const int32_t n_def = min(*a.n_deferred, a.deferred_cap);
+  for (int32_t i = threadIdx.x; i < kBigWords; i += kBigBlock) bm[i] = 0u;  // kept zero between edges
   for (;;) {
     __syncthreads();
     if (threadIdx.x == 0) s_k = atomicAdd(a.cursor, 1);
@@ -345,7 +372,6 @@ __global__ void __launch_bounds__(kBigBlock, 1) k_pass_big(DevGraph g, CountArgs
     const int32_t v = a.deferred[2 * k], p = a.deferred[2 * k + 1];
     const int32_t u = g.ci[p], e = g.eid[p];
     const int32_t gid = g.vgid ? g.vgid[v] : 0;
-    const int32_t base = g.gbase[gid];
     const int64_t n_g = g.gn[gid], m_g = g.gm[gid];
     const int32_t vb = g.rp[v], ve = g.rp[v + 1];
     const int32_t ub = g.rp[u], ue = g.rp[u + 1];
@@ -354,17 +380,27 @@ __global__ void __launch_bounds__(kBigBlock, 1) k_pass_big(DevGraph g, CountArgs
       if (threadIdx.x == 0) atomicOr(a.status, (int32_t)kSpillOverflow);
       continue;
     }
-    for (int32_t q = vb + threadIdx.x; q < ve; q += kBigBlock) tab[g.ci[q] - base] = (uint32_t)(q - vb + 1);
-    __syncthreads();
     // T in order, and the cross term
     long long cross = 0;
     int32_t t = 0;
     for (int32_t q0 = ub; q0 < ue; q0 += kBigBlock) {
       const int32_t q = q0 + threadIdx.x;
-      const int32_t w = q < ue ? g.ci[q] : v;
-      const uint32_t ent = w != v ? tab[w - base] : 0u;
-      const bool inT = ent != 0u;
-      if (inT) cross += (long long)a.tri[g.eid[q]] + (long long)a.tri[g.eid[vb + (int32_t)ent - 1]] - 2;
+      bool inT = false;
+      int32_t w = 0;
+      if (q < ue) {
+        w = g.ci[q];
+        if (w != v) {
+          int32_t lo = vb, hi = ve;
+          while (lo < hi) {
+            const int32_t mid = (lo + hi) >> 1;
+            if (g.ci[mid] < w) lo = mid + 1; else hi = mid;
+          }
+          if (lo < ve && g.ci[lo] == w) {
+            inT = true;
+            cross += (long long)a.tri[g.eid[q]] + (long long)a.tri[g.eid[lo]] - 2;
+          }
+        }
+      }
       const unsigned mask = __ballot_sync(0xffffffffu, inT);
       if (lane == 0) s_wcnt[warp] = __popc(mask);
       __syncthreads();
@@ -379,7 +415,6 @@ __global__ void __launch_bounds__(kBigBlock, 1) k_pass_big(DevGraph g, CountArgs
       t += s_woff[kBigWarps];
       __syncthreads();
     }
-    // reduce cross over the CTA
     cross = warp_sum_ll(cross);
     if (lane == 0) s_red[warp] = cross;
     __syncthreads();
@@ -392,34 +427,37 @@ __global__ void __launch_bounds__(kBigBlock, 1) k_pass_big(DevGraph g, CountArgs
     cross = s_red[0];
     if (t != t_expect) {  // cannot happen on a valid graph
       if (threadIdx.x == 0) atomicOr(a.status, (int32_t)kSpillOverflow);
-      for (int32_t q = vb + threadIdx.x; q < ve; q += kBigBlock) tab[g.ci[q] - base] = 0u;
       continue;
     }
     const int32_t lo = T[0], hi = T[t - 1];
     const bool use_bm = (int64_t)hi - lo + 1 <= (int64_t)kBigWords * 32;
     if (use_bm) {
-      const int32_t words = (hi - lo) / 32 + 1;
-      for (int32_t i = threadIdx.x; i < words; i += kBigBlock) bm[i] = 0u;
-      __syncthreads();
       for (int32_t i = threadIdx.x; i < t; i += kBigBlock) {
         const int32_t d = T[i] - lo;
         atomicOr(&bm[d >> 5], 1u << (d & 31));
       }
     }
     __syncthreads();
-    long long x7;
+    long long x7, probes = 0;
     if (use_bm) {
-      x7 = warp_clique_count<4>(g, T, t, warp * 32, kBigBlock, lane, false, [&](int32_t r) {
+      x7 = warp_clique_count<4>(g, T, t, warp * 32, kBigBlock, lane, true, [&](int32_t r) {
         const int32_t d = r - lo;
         return (r >= lo && r <= hi) ? (int)((bm[d >> 5] >> (d & 31)) & 1u) : 0;
-      });
+      }, probes);
     } else {
       x7 = warp_clique_count<4>(g, T, t, warp * 32, kBigBlock, lane, true,
-                                [&](int32_t r) { return contains(T, t, r); });
+                                [&](int32_t r) { return contains(T, t, r); }, probes);
+    }
+    if (lane == 0 && probes) atomicAdd(a.work + kWorkBigProbe, (unsigned long long)probes);
+    if (threadIdx.x == 0) {
+      atomicAdd(a.work + kWorkBigDeg, (unsigned long long)((ve - vb) + (ue - ub)));
+      atomicAdd(a.work + kWorkBigT, (unsigned long long)t);
     }
     x7 = warp_sum_ll(x7);
     __syncthreads();
     if (lane == 0) s_red[warp] = x7;
+    if (use_bm)
+      for (int32_t i = threadIdx.x; i < t; i += kBigBlock) bm[(T[i] - lo) >> 5] = 0u;
     __syncthreads();
     if (threadIdx.x < 13) {
       long long xs = 0;
@@ -434,7 +472,6 @@ __global__ void __launch_bounds__(kBigBlock, 1) k_pass_big(DevGraph g, CountArgs
       const uint64_t cs = edge_column(csum_column(c), t, su, sv, D, xs, x10, m_g, du, dv);
       atomic_add_u128(a.csum + ((size_t)gid * 13 + c) * 2, (u128)cs);
     }
-    for (int32_t q = vb + threadIdx.x; q < ve; q += kBigBlock) tab[g.ci[q] - base] = 0u;
   }
 }
 
@@ -452,6 +489,7 @@ __global__ void __launch_bounds__(kBlock) k_pass_c(DevGraph g, CountArgs a) {
   uint32_t* tab = table_of<kSmemTable>(g, a, smem);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const bool zero_all = kSmemTable && g.table_n <= 4096;
+  long long w_wedge = 0;
   if (kSmemTable)
     for (int32_t i = threadIdx.x; i < g.table_n; i += kBlock) tab[i] = 0;
   for (;;) {
@@ -459,7 +497,10 @@ __global__ void __launch_bounds__(kBlock) k_pass_c(DevGraph g, CountArgs a) {
     if (threadIdx.x == 0) s_unit = atomicAdd(a.cursor, 1);
     __syncthreads();
     const int32_t k = s_unit;
-    if (k >= a.n_units) break;
+    if (k >= a.n_units) {
+      if (lane == 0 && w_wedge) atomicAdd(a.work + kWorkCWedge, (unsigned long long)w_wedge);
+      break;
+    }
     const int32_t h = a.units[k];
     const int32_t base = g.gbase[g.vgid ? g.vgid[h] : 0];
     const int32_t hb = g.rp[h], he = g.rp[h + 1];
@@ -486,6 +527,7 @@ __global__ void __launch_bounds__(kBlock) k_pass_c(DevGraph g, CountArgs a) {
           xe = lo;
         }
         unsigned long long s = 0;
+        if (pass == 0 && lane == 0) w_wedge += xe - xb;
         for (int32_t q = xb + lane; q < xe; q += 32) {
           const int32_t o = g.ci[q];
           if (!g.ranked && !rank_less(g.deg, o, h)) continue;
@@ -604,6 +646,15 @@ int count_grid_size() {
     g_grid = (sms > 0 ? sms : 1) * kCtasPerSm;
   }
   return g_grid;
+}
+
+int big_t_threshold() {
+  static int v = [] {
+    const char* e = getenv("GC_BIG_T");
+    int x = e ? atoi(e) : 1024;
+    return x < 16 ? 16 : (x > kTcap ? kTcap : x);
+  }();
+  return v;
 }
 
 // One CTA of kBigBlock threads per SM for the large-T edges.

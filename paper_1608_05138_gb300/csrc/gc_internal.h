@@ -50,9 +50,27 @@ struct CountArgs {
   int32_t* deferred;       // [deferred_cap][2] (v, slot of u in Gamma(v)) of large-T edges
   int32_t deferred_cap;
   int32_t* n_deferred;     // device counter of deferred edges
+  int32_t big_t;           // |T| above which an edge is deferred to k_pass_big
   uint64_t* per_edge;      // [m][13] device pointer or nullptr
   unsigned long long* csum;  // [G][13][2] 128-bit unrestricted counts (lo, hi)
   int32_t* status;         // device status word (0 = ok)
+  unsigned long long* work;  // [kNumWork] work counters of this count
+};
+
+// Work counters (units the kernels processed; bench.py turns them into
+// algorithmic bytes).
+enum Work {
+  kWorkBGroupDeg = 0,  // pass B: sum of d_v over chunks (Psi set + clear)
+  kWorkBDeg,           // pass B: sum of d_u over its edges (Gamma(u) scan)
+  kWorkBT,             // pass B: sum of |T|
+  kWorkBProbe,         // pass B: out-list entries tested against T
+  kWorkBEdges,         // pass B: edges finished
+  kWorkBigDeg,         // large-T pass: sum of d_v + d_u
+  kWorkBigT,           // large-T pass: sum of |T|
+  kWorkBigProbe,       // large-T pass: entries tested
+  kWorkCWedge,         // pass C: wedges h-x-o
+  kWorkAUnits,         // pass A: sum of d_v + sum of d_u
+  kNumWork
 };
 
 enum Status : int32_t { kOk = 0, kSpillOverflow = 1, kInexact = 2, kTimeout = 4 };
@@ -61,6 +79,9 @@ constexpr int kBlock = 512;            // threads per CTA of the counting kernel
 constexpr int kCtasPerSm = 2;          // resident CTAs per SM of the persistent grids
 constexpr int kWarps = kBlock / 32;
 constexpr int kTcap = 1024;            // per-warp T list in shared memory (entries)
+// Edges whose |T| exceeds big_t (default 1024, environment GC_BIG_T in
+// [16, kTcap]) are done by a whole CTA (k_pass_big).
+int big_t_threshold();
 constexpr int kSmemTableMax = 4096;    // Psi tables up to this many vertices live in shared memory
 constexpr int kBigBlock = 1024;        // threads per CTA for large-T edges
 constexpr int kBigWarps = kBigBlock / 32;
@@ -84,6 +105,7 @@ struct Scratch {
   int32_t tbuf_len = 0;
   int32_t* deferred = nullptr;       // [deferred_cap][2]
   int32_t deferred_cap = 0;
+  unsigned long long* work = nullptr;  // [kNumWork]
 };
 // Allocates what does not depend on the data (stream-ordered).
 gc_status scratch_init(Scratch* sc, int32_t m, int32_t n_units, int32_t table_n, cudaStream_t s);
@@ -136,7 +158,7 @@ gc_status run_max_tri(const int32_t* tri, int32_t m, int32_t* d_out, cudaStream_
 // off n_units + 1 ints; off[n_units] receives the number of chunks.
 gc_status run_make_chunks(const DevGraph& g, const int32_t* units, int32_t n_units,
                           const int32_t* tri, int32_t* chunks, int32_t* off,
-                          unsigned long long* total_dev, int32_t* n_big_dev, cudaStream_t s);
+                          unsigned long long* total_dev, int32_t* n_big_dev, int32_t big_t, cudaStream_t s);
 inline size_t chunk_capacity(int32_t n_units) { return (size_t)n_units + 8 * (size_t)count_grid_size() + 1; }
 // exclusive prefix sum of n int32 into out[0..n] (out[n] = total)
 gc_status exclusive_scan(int32_t n, const int32_t* in, int32_t* out, cudaStream_t s);

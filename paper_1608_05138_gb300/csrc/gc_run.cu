@@ -19,7 +19,7 @@ namespace gc {
 
 void scratch_free(Scratch* sc, cudaStream_t s) {
   for (void* p : {(void*)sc->tri, (void*)sc->P, (void*)sc->chunks, (void*)sc->off, (void*)sc->misc,
-                  (void*)sc->total, (void*)sc->tables, (void*)sc->tbuf, (void*)sc->deferred})
+                  (void*)sc->total, (void*)sc->tables, (void*)sc->tbuf, (void*)sc->deferred, (void*)sc->work})
     if (p) cudaFreeAsync(p, s);
   *sc = Scratch();
 }
@@ -37,6 +37,7 @@ gc_status scratch_init(Scratch* sc, int32_t m, int32_t n_units, int32_t table_n,
   GS_TRY(cudaMallocAsync(&sc->off, sizeof(int32_t) * ((size_t)n_units + 1), s));
   GS_TRY(cudaMallocAsync(&sc->misc, sizeof(int32_t) * 8, s));
   GS_TRY(cudaMallocAsync(&sc->total, sizeof(unsigned long long), s));
+  GS_TRY(cudaMallocAsync(&sc->work, sizeof(unsigned long long) * kNumWork, s));
   if (table_n > kSmemTableMax) {
     sc->tables_n = (size_t)count_grid_size() * (size_t)table_n;
     GS_TRY(cudaMallocAsync(&sc->tables, sizeof(uint32_t) * sc->tables_n, s));
@@ -77,10 +78,13 @@ gc_status run_count(const DevGraph& g, const int32_t* units, int32_t n_units, ui
   a.deferred = nullptr;
   a.deferred_cap = 0;
   a.n_deferred = ndef_dev;
+  a.big_t = big_t_threshold();
   a.per_edge = per_edge;
   a.csum = csum;
   a.status = status;
+  a.work = sc->work;
   GR_TRY(cudaMemsetAsync(sc->misc, 0, sizeof(int32_t) * 8, s), "memset misc");
+  GR_TRY(cudaMemsetAsync(sc->work, 0, sizeof(unsigned long long) * kNumWork, s), "memset work");
   GR_TRY(cudaMemsetAsync(csum, 0, sizeof(unsigned long long) * 26 * (size_t)g.G, s), "memset sums");
   GR_EVENT(kPhasePassA);
   int32_t nbig = 0;
@@ -91,19 +95,13 @@ gc_status run_count(const DevGraph& g, const int32_t* units, int32_t n_units, ui
     GR_TRY(cudaMemsetAsync(sc->P, 0, sizeof(unsigned long long) * (size_t)g.m, s), "zero P");
     GR_TRY(cudaMemsetAsync(cursor, 0, sizeof(int32_t), s), "reset cursor");
     if ((st = run_pass_c(g, a, s)) != GC_OK) return st;
-    if ((st = run_make_chunks(g, units, n_units, sc->tri, sc->chunks, sc->off, sc->total, nbig_dev, s)) != GC_OK)
+    if ((st = run_make_chunks(g, units, n_units, sc->tri, sc->chunks, sc->off, sc->total, nbig_dev, a.big_t, s)) != GC_OK)
       return st;
     int32_t hm[2] = {0, 0};  // max |T|, number of large-T edges (complete: the chunking synchronised)
     GR_TRY(cudaMemcpyAsync(hm, tmax_dev, sizeof(hm), cudaMemcpyDeviceToHost, s), "copy counts");
     GR_TRY(cudaStreamSynchronize(s), "sync counts");
     nbig = hm[1];
     if (nbig > 0) {
-      if (!sc->tables || sc->tables_n < (size_t)count_grid_size() * (size_t)g.table_n) {
-        if (sc->tables) cudaFreeAsync(sc->tables, s);
-        sc->tables_n = (size_t)count_grid_size() * (size_t)g.table_n;
-        GR_TRY(cudaMallocAsync(&sc->tables, sizeof(uint32_t) * sc->tables_n, s), "alloc tables");
-        GR_TRY(cudaMemsetAsync(sc->tables, 0, sizeof(uint32_t) * sc->tables_n, s), "zero tables");
-      }
       if (sc->tbuf_len < hm[0]) {
         if (sc->tbuf) cudaFreeAsync(sc->tbuf, s);
         sc->tbuf_len = hm[0];
@@ -130,10 +128,8 @@ gc_status run_count(const DevGraph& g, const int32_t* units, int32_t n_units, ui
   }
   GR_EVENT(kPhaseBig);
   if (nbig > 0) {
-    CountArgs ab = a;
-    ab.tables = sc->tables;
     GR_TRY(cudaMemsetAsync(cursor, 0, sizeof(int32_t), s), "reset cursor");
-    if ((st = run_pass_big(g, ab, nbig, s)) != GC_OK) return st;
+    if ((st = run_pass_big(g, a, nbig, s)) != GC_OK) return st;
   }
   GR_EVENT(kPhaseDerive);
   if ((st = run_derive(g, csum, x, status, s)) != GC_OK) return st;

@@ -29,7 +29,7 @@ __device__ __forceinline__ bool rank_less(const int32_t* __restrict__ deg, int32
 
 __global__ void k_group_work(DevGraph g, const int32_t* __restrict__ units, int32_t n_units,
                              const int32_t* __restrict__ tri, long long* __restrict__ W,
-                             unsigned long long* __restrict__ total, int32_t* __restrict__ n_big) {
+                             unsigned long long* __restrict__ total, int32_t* __restrict__ n_big, int32_t big_t) {
   const int lane = threadIdx.x & 31;
   const int warps = (gridDim.x * blockDim.x) >> 5;
   for (int32_t k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < n_units; k += warps) {
@@ -40,7 +40,7 @@ __global__ void k_group_work(DevGraph g, const int32_t* __restrict__ units, int3
       const int32_t u = g.ci[p];
       if (rank_less(g.deg, u, v)) {
         const int32_t t = tri[g.eid[p]];
-        if (t > kTcap) ++big; else w += edge_cost(g.deg[u], t);  // large-T edges go to their own pass
+        if (t > big_t) ++big; else w += edge_cost(g.deg[u], t);  // large-T edges go to their own pass
       }
     }
     for (int o = 16; o; o >>= 1) {
@@ -74,7 +74,7 @@ __global__ void k_chunk_count(const int32_t* __restrict__ units, int32_t n_units
 // Warp per group: cut its slots where the running cost crosses j * W / nc.
 __global__ void k_chunk_emit(DevGraph g, const int32_t* __restrict__ units, int32_t n_units,
                              const int32_t* __restrict__ tri, const long long* __restrict__ W,
-                             const int32_t* __restrict__ off, int32_t* __restrict__ chunks) {
+                             const int32_t* __restrict__ off, int32_t* __restrict__ chunks, int32_t big_t) {
   const int lane = threadIdx.x & 31;
   const int warps = (gridDim.x * blockDim.x) >> 5;
   for (int32_t k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < n_units; k += warps) {
@@ -98,7 +98,7 @@ __global__ void k_chunk_emit(DevGraph g, const int32_t* __restrict__ units, int3
         const int32_t u = g.ci[p];
         if (rank_less(g.deg, u, v)) {
           const int32_t t = tri[g.eid[p]];
-          c = t > kTcap ? 0 : edge_cost(g.deg[u], t);
+          c = t > big_t ? 0 : edge_cost(g.deg[u], t);
         }
       }
       if (p == e - 1) c += 16;  // matches the constant added to W
@@ -133,7 +133,7 @@ int blocks_for(long long threads) {
 
 gc_status run_make_chunks(const DevGraph& g, const int32_t* units, int32_t n_units,
                           const int32_t* tri, int32_t* chunks, int32_t* off,
-                          unsigned long long* total_dev, int32_t* n_big_dev, cudaStream_t s) {
+                          unsigned long long* total_dev, int32_t* n_big_dev, int32_t big_t, cudaStream_t s) {
   long long* W = nullptr;
   int32_t* nch = nullptr;
   cudaError_t e = cudaMallocAsync(&W, sizeof(long long) * (n_units > 0 ? n_units : 1), s);
@@ -148,7 +148,7 @@ gc_status run_make_chunks(const DevGraph& g, const int32_t* units, int32_t n_uni
   const int grid = count_grid_size();
   cudaMemsetAsync(total_dev, 0, sizeof(unsigned long long), s);
   k_group_work<<<blocks_for((long long)n_units * 32), 256, 0, s>>>(g, units, n_units, tri, W, total_dev,
-                                                                    n_big_dev);
+                                                                    n_big_dev, big_t);
   e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaMemcpyAsync(&total, total_dev, sizeof(total), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -164,7 +164,7 @@ gc_status run_make_chunks(const DevGraph& g, const int32_t* units, int32_t n_uni
     if (st == GC_OK) st = exclusive_scan(n_units, nch, off, s);  // off[n_units] = number of chunks
     if (st == GC_OK) {
       k_chunk_emit<<<blocks_for((long long)n_units * 32), 256, 0, s>>>(g, units, n_units, tri, W,
-                                                                       off, chunks);
+                                                                       off, chunks, big_t);
       e = cudaGetLastError();
       if (e != cudaSuccess) st = cuda_fail(e, "k_chunk_emit");
     }
