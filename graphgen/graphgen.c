@@ -387,41 +387,67 @@ static void gg_batch_params(uint64_t seed, int64_t g, int32_t n_lo, int32_t n_hi
   }
 }
 
-int gg_batch(int64_t G, int32_t n_lo, int32_t n_hi, double p_lo, double p_hi,
-             double g_lo, double g_hi, uint64_t seed,
-             int32_t** nvert_out, int64_t** voff_out, int64_t** eoff_out,
-             int32_t** rp_out, int32_t** ci_out, int64_t* total_rows_out, int64_t* total_nnz_out) {
-  if (G < 0 || n_lo < 2 || n_hi < n_lo || n_hi > 65535) return -3;
-  int32_t* nvert = (int32_t*)malloc((size_t)(G > 0 ? G : 1) * sizeof(int32_t));
-  int64_t* voff = (int64_t*)malloc((size_t)(G + 1) * sizeof(int64_t));
-  int64_t* eoff = (int64_t*)malloc((size_t)(G + 1) * sizeof(int64_t));
-  int32_t** rps = (int32_t**)calloc((size_t)(G > 0 ? G : 1), sizeof(int32_t*));
-  int32_t** cis = (int32_t**)calloc((size_t)(G > 0 ? G : 1), sizeof(int32_t*));
-  if (!nvert || !voff || !eoff || !rps || !cis) return -1;
-  int rc = 0;
-  voff[0] = 0; eoff[0] = 0;
-  for (int64_t g = 0; g < G && rc == 0; ++g) {
+typedef struct {
+  int64_t G, t, T; int32_t n_lo, n_hi; double p_lo, p_hi, g_lo, g_hi; uint64_t seed;
+  int32_t* nvert; int64_t* m; int32_t** rps; int32_t** cis; int rc;
+} gg_batch_job_t;
+
+static void* gg_batch_worker(void* arg) {
+  gg_batch_job_t* j = (gg_batch_job_t*)arg;
+  for (int64_t g = j->t; g < j->G && j->rc == 0; g += j->T) {
     gg_bparams_t bp;
-    gg_batch_params(seed, g, n_lo, n_hi, p_lo, p_hi, g_lo, g_hi, &bp);
+    gg_batch_params(j->seed, g, j->n_lo, j->n_hi, j->p_lo, j->p_hi, j->g_lo, j->g_hi, &bp);
     int64_t m = 0;
+    int rc;
     if (bp.kind == 0) {
       uint64_t pairs = (uint64_t)bp.n * (uint64_t)(bp.n - 1) / 2;
       uint64_t* keys = (uint64_t*)malloc((size_t)(pairs > 0 ? pairs : 1) * sizeof(uint64_t));
-      if (!keys) { rc = -1; break; }
+      if (!keys) { j->rc = -1; break; }
       int64_t k = gg_er_keys(bp.n, bp.p_or_gamma, gg_key(bp.seed2, 1), keys);
-      rc = gg_finish(bp.n, keys, k, &m, &rps[g], &cis[g]);
+      rc = gg_finish(bp.n, keys, k, &m, &j->rps[g], &j->cis[g]);
       free(keys);
     } else {
       int64_t mt = (int64_t)((double)bp.n * bp.dbar / 2.0 + 0.5);
       uint64_t* keys; int64_t k;
       rc = gg_chung_lu_keys(bp.n, mt, bp.p_or_gamma, (double)bp.n * bp.dbar, (double)(bp.n - 1),
                             gg_key(bp.seed2, 2), &keys, &k);
-      if (rc == 0) { rc = gg_finish(bp.n, keys, k, &m, &rps[g], &cis[g]); free(keys); }
+      if (rc == 0) { rc = gg_finish(bp.n, keys, k, &m, &j->rps[g], &j->cis[g]); free(keys); }
     }
-    nvert[g] = bp.n;
-    voff[g + 1] = voff[g] + bp.n + 1;
-    eoff[g + 1] = eoff[g] + 2 * m;
+    if (rc) { j->rc = rc; break; }
+    j->nvert[g] = bp.n;
+    j->m[g] = m;
   }
+  return NULL;
+}
+
+int gg_batch(int64_t G, int32_t n_lo, int32_t n_hi, double p_lo, double p_hi,
+             double g_lo, double g_hi, uint64_t seed,
+             int32_t** nvert_out, int64_t** voff_out, int64_t** eoff_out,
+             int32_t** rp_out, int32_t** ci_out, int64_t* total_rows_out, int64_t* total_nnz_out) {
+  if (G < 0 || n_lo < 2 || n_hi < n_lo || n_hi > 65535) return -3;
+  int32_t* nvert = (int32_t*)malloc((size_t)(G > 0 ? G : 1) * sizeof(int32_t));
+  int64_t* mm = (int64_t*)malloc((size_t)(G > 0 ? G : 1) * sizeof(int64_t));
+  int64_t* voff = (int64_t*)malloc((size_t)(G + 1) * sizeof(int64_t));
+  int64_t* eoff = (int64_t*)malloc((size_t)(G + 1) * sizeof(int64_t));
+  int32_t** rps = (int32_t**)calloc((size_t)(G > 0 ? G : 1), sizeof(int32_t*));
+  int32_t** cis = (int32_t**)calloc((size_t)(G > 0 ? G : 1), sizeof(int32_t*));
+  if (!nvert || !mm || !voff || !eoff || !rps || !cis) return -1;
+  int T = gg_threads();
+  if (G < 64) T = 1;
+  gg_batch_job_t jobs[32];
+  pthread_t th[32];
+  for (int t = 0; t < T; ++t) {
+    gg_batch_job_t jb = {G, t, T, n_lo, n_hi, p_lo, p_hi, g_lo, g_hi, seed, nvert, mm, rps, cis, 0};
+    jobs[t] = jb;
+  }
+  for (int t = 1; t < T; ++t) pthread_create(&th[t], NULL, gg_batch_worker, &jobs[t]);
+  gg_batch_worker(&jobs[0]);
+  for (int t = 1; t < T; ++t) pthread_join(th[t], NULL);
+  int rc = 0;
+  for (int t = 0; t < T; ++t) if (jobs[t].rc) rc = jobs[t].rc;
+  voff[0] = 0; eoff[0] = 0;
+  if (rc == 0)
+    for (int64_t g = 0; g < G; ++g) { voff[g + 1] = voff[g] + nvert[g] + 1; eoff[g + 1] = eoff[g] + 2 * mm[g]; }
   if (rc == 0) {
     int32_t* rp = (int32_t*)malloc((size_t)(voff[G] > 0 ? voff[G] : 1) * sizeof(int32_t));
     int32_t* ci = (int32_t*)malloc((size_t)(eoff[G] > 0 ? eoff[G] : 1) * sizeof(int32_t));
@@ -436,7 +462,7 @@ int gg_batch(int64_t G, int32_t n_lo, int32_t n_hi, double p_lo, double p_hi,
     }
   }
   for (int64_t g = 0; g < G; ++g) { free(rps[g]); free(cis[g]); }
-  free(rps); free(cis);
+  free(rps); free(cis); free(mm);
   if (rc != 0) { free(nvert); free(voff); free(eoff); return rc; }
   *nvert_out = nvert; *voff_out = voff; *eoff_out = eoff;
   return 0;
