@@ -1,7 +1,7 @@
 """Benchmark: per-edge 3/4-node graphlet counts, edges/s on R-MAT scale 22.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload rmat22|chung_lu|er2000] [--scale S]
+                    [--workload rmat22|chung_lu|er2000|er_dense|batched|serving] [--scale S]
 
 One step = one full count of the resident graph through the C ABI
 (gc_count_edge_graphlets): triangle pass, clique/cycle pass with the per-edge
@@ -48,6 +48,9 @@ def load_workload(name: str, scale: int):
     elif name == "er2000":
         rp, ci = graphgen.config_er2000()
         desc = "Erdos-Renyi G(2000, 0.01), seed 1"
+    elif name == "er_dense":
+        rp, ci = graphgen.config_er_dense()
+        desc = "Erdos-Renyi G(1000, 0.3), seed 1 (1K vertices, ~150K edges)"
     else:
         raise SystemExit(f"unknown workload {name}")
     return rp, ci, desc
@@ -183,13 +186,173 @@ def run_reference(args, rank, world):
     print(json.dumps(line))
 
 
+def _pct(xs, q):
+    xs = sorted(xs)
+    return xs[min(len(xs) - 1, int(round(q * (len(xs) - 1))))] if xs else None
+
+
+def run_batched(args):
+    """Batched form: many small graphs in one launch of the batch runtime
+    (gc_batch_*), against the plain per-graph loop (upload, count, free).
+    Wall-clock through the C ABI from host CSR to host results."""
+    import graphgen
+    import oracle
+    import paper_1608_05138_gb300 as gcb
+    from paper_1608_05138_gb300 import build as gcbuild
+    gcbuild.build()
+    B = graphgen.batch(args.graphs)
+    G = len(B)
+    edges = B.total_edges
+    # plain per-graph loop on an evenly spaced sample
+    idx = list(range(0, G, max(1, G // 2000)))
+    plain = {}
+    t0 = time.perf_counter()
+    for i in idx:
+        with gcb.Graph(*B.graph(i)) as g:
+            plain[i] = g.count()
+    plain_gps = len(idx) / (time.perf_counter() - t0)
+    times, res = [], None
+    for step in range(args.warmup + args.steps):
+        b = gcb.gc_batch_create(200 << 30, gcb.GC_BATCH_MANUAL)
+        t0 = time.perf_counter()
+        tickets = [gcb.gc_batch_submit(b, *B.graph(i)) for i in range(G)]
+        t1 = time.perf_counter()
+        gcb.gc_batch_flush(b)
+        t2 = time.perf_counter()
+        out = [gcb.gc_batch_poll(b, t, timeout_us=-1) for t in tickets]
+        dt = time.perf_counter() - t0
+        gcb.gc_batch_destroy(b)
+        if step >= args.warmup:
+            times.append(dt)
+            split = {"submit_s": t1 - t0, "flush_s": t2 - t1, "poll_s": t0 + dt - t2}
+        res = out
+    mism = sum(res[i] != plain[i] for i in idx)
+    orc = list(range(0, G, max(1, G // 20)))
+    omis = sum(res[i] != oracle.count(*B.graph(i), per_edge=False)["X"] for i in orc)
+    dt = statistics.mean(times)
+    line = {"metric": "batched form: graphs/s, 100k small graphs in one launch vs the plain per-graph loop",
+            "value": G / dt, "unit": "graphs/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000 * dt, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "int64", "data": "synthetic",
+            "config": {"workload": f"{G} graphs, n uniform in [20, 500], half ER p in [0.05, 0.5], half "
+                                   "Chung-Lu gamma in [2, 3]", "edges": edges},
+            "edges_per_s": edges / dt, "plain_loop_graphs_per_s": plain_gps, "time_split": split,
+            "speedup_vs_plain_loop": (G / dt) / plain_gps,
+            "parity": {"vs_plain_sample": f"{len(idx) - mism}/{len(idx)} equal",
+                       "vs_oracle_sample": f"{len(orc) - omis}/{len(orc)} equal"},
+            "e2e": {"value": G / dt, "unit": "graphs/s", "h2d_bytes_per_step": int(B.row_ptr.nbytes + B.col_idx.nbytes),
+                    "d2h_bytes_per_step": G * 17 * 16, "includes": "validation, copy-in, count, results to host"}}
+    print(json.dumps(line))
+
+
+def run_serving(args):
+    """Serving form: a Poisson stream of Chung-Lu graphs (m log-uniform in
+    [1e3, 2e6]) served by the continuous-batching runtime (120 GB budget),
+    against the plain per-request loop; latency = arrival -> result."""
+    import threading as th
+    import graphgen
+    import paper_1608_05138_gb300 as gcb
+    from paper_1608_05138_gb300 import build as gcbuild
+    gcbuild.build()
+    R = args.requests
+    params = graphgen.serving_params(R)
+    graphs = [graphgen.serving_graph(params, r) for r in range(R)]
+    sizes = [len(c) // 2 for _, c in graphs]
+    # warm up the device and the library
+    with gcb.Graph(*graphs[0]) as g:
+        g.count()
+
+    def plain_serve(arrivals):
+        lat, done = [], []
+        t0 = time.perf_counter()
+        res = []
+        for r in range(R):
+            now = time.perf_counter() - t0
+            if arrivals[r] > now:
+                time.sleep(arrivals[r] - now)
+            with gcb.Graph(*graphs[r]) as g:
+                res.append(g.count())
+            f = time.perf_counter() - t0
+            lat.append(f - arrivals[r])
+            done.append(f)
+        return lat, max(done), res
+
+    def batched_serve(arrivals):
+        b = gcb.gc_batch_create(120 << 30, 0)
+        tickets = [None] * R
+        fin = [None] * R
+        res = [None] * R
+        t0 = time.perf_counter()
+
+        def submitter():
+            for r in range(R):
+                now = time.perf_counter() - t0
+                if arrivals[r] > now:
+                    time.sleep(arrivals[r] - now)
+                while True:
+                    t = gcb.gc_batch_try_submit(b, *graphs[r])
+                    if t is not None:
+                        tickets[r] = t
+                        break
+                    time.sleep(0.0005)
+
+        sub = th.Thread(target=submitter)
+        sub.start()
+        left = set(range(R))
+        while left:
+            for r in list(left):
+                if tickets[r] is None:
+                    continue
+                x = gcb.gc_batch_poll(b, tickets[r], timeout_us=0)
+                if x is not None:
+                    fin[r] = time.perf_counter() - t0
+                    res[r] = x
+                    left.discard(r)
+            time.sleep(0.0002)
+        sub.join()
+        gcb.gc_batch_destroy(b)
+        lat = [fin[r] - arrivals[r] for r in range(R)]
+        return lat, max(fin), res
+
+    zero = [0.0] * R
+    _, t_plain_cap, res_plain = plain_serve(zero)
+    cap_plain = R / t_plain_cap
+    _, t_batch_cap, res_batch = batched_serve(zero)
+    cap_batch = R / t_batch_cap
+    rate = args.rate_factor * cap_plain
+    gaps = np.asarray(params["gap"], np.float64) / rate
+    arrivals = list(np.cumsum(gaps) - gaps[0])
+    lat_p, span_p, _ = plain_serve(arrivals)
+    lat_b, span_b, res_b2 = batched_serve(arrivals)
+    same = sum(a == b for a, b in zip(res_plain, res_batch)) + sum(a == b for a, b in zip(res_plain, res_b2))
+    line = {"metric": "serving form: graphs/s and p50/p99 latency (ms), Poisson stream, continuous batching",
+            "value": R / span_b, "unit": "graphs/s", "n_gpus": 1, "steps": 1, "warmup": 1,
+            "ms_per_step": 1000 * span_b, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "int64", "data": "synthetic",
+            "config": {"workload": f"{R} Chung-Lu requests, m log-uniform in [1e3, 2e6], gamma in [2.1, 2.5], "
+                                   "n = max(64, m/8), budget 120 GB", "edges": int(sum(sizes)),
+                       "arrival_rate_graphs_per_s": rate},
+            "served": {"graphs_per_s": R / span_b, "edges_per_s": sum(sizes) / span_b,
+                       "p50_ms": 1000 * _pct(lat_b, 0.5), "p99_ms": 1000 * _pct(lat_b, 0.99)},
+            "plain_loop": {"graphs_per_s": R / span_p, "edges_per_s": sum(sizes) / span_p,
+                           "p50_ms": 1000 * _pct(lat_p, 0.5), "p99_ms": 1000 * _pct(lat_p, 0.99)},
+            "capacity": {"plain_loop_graphs_per_s": cap_plain, "batched_graphs_per_s": cap_batch,
+                         "speedup": cap_batch / cap_plain},
+            "parity": f"{same}/{2 * R} results equal to the plain loop's"}
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="rmat22", choices=["rmat22", "chung_lu", "er2000"])
+    ap.add_argument("--workload", default="rmat22", choices=["rmat22", "chung_lu", "er2000", "er_dense", "batched",
+                                                              "serving"])
+    ap.add_argument("--graphs", type=int, default=100_000, help="batched: number of graphs")
+    ap.add_argument("--requests", type=int, default=300, help="serving: number of requests")
+    ap.add_argument("--rate-factor", type=float, default=0.9, help="serving: arrival rate / plain-loop capacity")
     ap.add_argument("--scale", type=int, default=22)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -200,6 +363,10 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.workload == "batched":
+        return run_batched(args)
+    if args.workload == "serving":
+        return run_serving(args)
 
     import torch
     import paper_1608_05138_gb300 as gcb

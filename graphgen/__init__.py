@@ -207,3 +207,9 @@ def config_chung_lu(seed: int = 1, n: int = 1_000_000, m: int = 10_000_000):
 def config_rmat(scale: int = 22, seed: int = 1):
     """R-MAT scale 22, edge factor 16, (0.57, 0.19, 0.19, 0.05)."""
     return rmat(scale, 16, 0.57, 0.19, 0.19, seed)
+
+
+def config_er_dense(seed: int = 1):
+    """Dense Erdos-Renyi G(n=1000, p=0.3), about 150k edges: the 1K-vertex /
+    150K-edge shape of the paper's single-GPU comparison (Sec. 5, Fig. 3)."""
+    return er(1000, 0.3, seed)

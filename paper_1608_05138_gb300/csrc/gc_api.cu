@@ -79,6 +79,22 @@ gc_status validate_csr(int32_t n, const int32_t* rp, const int32_t* ci) {
     for (int t = 0; t < nt; ++t)
       if (r1[t] != GC_OK) { set_error(m1[t]); return r1[t]; }
   }
+  if (nt == 1) {
+    // one O(nnz) pass: scanning rows x in order, the k-th row that names y
+    // must be the k-th entry of row y (rows ascend), which is exactly
+    // symmetry once every entry has found its place
+    std::vector<int32_t> fill((size_t)(n > 0 ? n : 1), 0);
+    for (int32_t x = 0; x < n; ++x)
+      for (int32_t p = rp[x]; p < rp[x + 1]; ++p) {
+        const int32_t y = ci[p];
+        const int32_t q = rp[y] + fill[y]++;
+        if (q >= rp[y + 1] || ci[q] != x) {
+          set_error("edge (" + std::to_string(x) + "," + std::to_string(y) + ") has no reverse");
+          return GC_ERR_ASYMMETRIC;
+        }
+      }
+    return GC_OK;
+  }
   std::vector<std::thread> th;
   for (int t = 1; t < nt; ++t) th.emplace_back(work, t);
   work(0);
@@ -355,6 +371,7 @@ gc_status gc_count_edge_graphlets(gc_graph g, uint64_t* per_edge_out, uint64_t* 
   dg.eid = g->prep.eid;
   dg.out_ptr = g->prep.out_ptr;
   dg.out_idx = g->prep.out_idx;
+  dg.rev = g->prep.rev;
   dg.G = 1;
   dg.vgid = nullptr;
   dg.gbase = g->d_gbase;

@@ -187,6 +187,7 @@ void run_launch(std::vector<PendingGraph>& graphs, cudaStream_t s, Launch* L) {
     dg.eid = prep.eid;
     dg.out_ptr = prep.out_ptr;
     dg.out_idx = prep.out_idx;
+    dg.rev = prep.rev;
     dg.G = G;
     dg.vgid = d_vgid;
     dg.gbase = d_desc;

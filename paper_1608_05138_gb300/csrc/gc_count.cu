@@ -273,6 +273,7 @@ __global__ void __launch_bounds__(kBlock, kCtasPerSm) k_pass_b(DevGraph g, Count
       const int32_t u = g.ci[p];
       if (!rank_less(g.deg, u, v)) continue;
       const int32_t e = g.eid[p];
+      if (e >= g.m) continue;  // sink of an asymmetric input slot: nothing to count
       const int32_t t_expect = a.tri[e];
       if (t_expect > a.big_t) {  // large T: a whole CTA takes this edge later
         if (lane == 0) {
@@ -302,7 +303,7 @@ __global__ void __launch_bounds__(kBlock, kCtasPerSm) k_pass_b(DevGraph g, Count
         t += __popc(mask);
       }
       cross = warp_sum_ll(cross);
-      const long long P = (long long)a.P[e];
+      const long long P = (long long)(a.P[p] + a.P[g.rev[p]]);
       if (t != t_expect) {  // cannot happen on a valid graph
         if (lane == 0) atomicOr(a.status, (int32_t)kSpillOverflow);
         continue;
@@ -462,7 +463,7 @@ __global__ void __launch_bounds__(kBigBlock, 1) k_pass_big(DevGraph g, CountArgs
     if (threadIdx.x < 13) {
       long long xs = 0;
       for (int i = 0; i < kBigWarps; ++i) xs += s_red[i];
-      const long long x10 = (long long)a.P[e] - cross + 2 * xs;
+      const long long x10 = (long long)(a.P[p] + a.P[g.rev[p]]) - cross + 2 * xs;
       const int64_t du = ue - ub, dv = ve - vb;
       const int64_t su = du - t - 1, sv = dv - t - 1;
       const int64_t D = n_g - 2 - t - su - sv;
@@ -536,7 +537,7 @@ __global__ void __launch_bounds__(kBlock) k_pass_c(DevGraph g, CountArgs a) {
           } else if (pass == 1) {
             const uint32_t c = tab[o - base] - 1u;
             if (c) {
-              atomicAdd(&a.P[g.eid[q]], (unsigned long long)c);
+              atomicAdd(&a.P[q], (unsigned long long)c);  // slot (x, o): consecutive over the lanes
               s += c;
             }
           } else {
@@ -545,7 +546,7 @@ __global__ void __launch_bounds__(kBlock) k_pass_c(DevGraph g, CountArgs a) {
         }
         if (pass == 1) {
           for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-          if (lane == 0 && s) atomicAdd(&a.P[g.eid[p]], s);
+          if (lane == 0 && s) atomicAdd(&a.P[p], s);  // slot (h, x)
         }
       }
       __syncthreads();

@@ -26,6 +26,7 @@ struct DevGraph {
   const int32_t* eid;      // [2m] slot -> edge id
   const int32_t* out_ptr;  // [n + 1] degree-oriented out-lists (Pi order)
   const int32_t* out_idx;  // [m]
+  const int32_t* rev;      // [2m] slot of (y, x) for the slot of (x, y)
   int32_t G;               // graphs in the union (>= 1)
   const int32_t* vgid;     // [n] graph of each vertex, or nullptr when G == 1
   const int32_t* gbase;    // [G] first global vertex id of each graph
@@ -44,7 +45,8 @@ struct CountArgs {
   int32_t* cursor;         // work-stealing cursor (device int, zeroed before launch)
   uint32_t* tables;        // global Psi tables (grid x table_n) or nullptr (shared memory)
   int32_t* tri;            // [m] per-edge |T| (written by pass A, read by pass B)
-  unsigned long long* P;   // [m] 4-cycles through each edge (pass C, zeroed before)
+  unsigned long long* P;   // [2m] per slot: 4-cycles through its edge counted at that slot
+                           // (pass C, zeroed before); an edge's count = sum of its two slots
   int32_t* tbuf;           // large-T edges: per-CTA T buffer (big grid x tbuf_len)
   int32_t tbuf_len;
   int32_t* deferred;       // [deferred_cap][2] (v, slot of u in Gamma(v)) of large-T edges
@@ -132,6 +134,7 @@ struct PrepBuffers {
   int32_t n_units = 0;
   int32_t dmax = 0;
   long long* S = nullptr;  // [n] sum of neighbour degrees (Psi build cost of a v-group)
+  int32_t* rev = nullptr;  // [2m] slot of the reverse direction of every slot
 };
 // Builds degrees, edge ids, the edge list, degree-oriented out-lists and the
 // binned unit list on `stream`. vgid may be nullptr (single graph).

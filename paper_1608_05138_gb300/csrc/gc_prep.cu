@@ -83,7 +83,7 @@ __global__ void k_edges(int32_t n, const int32_t* __restrict__ rp, const int32_t
                         const int32_t* __restrict__ deg, const int32_t* __restrict__ up,
                         const int32_t* __restrict__ upoff, const int32_t* __restrict__ out_ptr,
                         int32_t* __restrict__ eid, int32_t* __restrict__ uv,
-                        int32_t* __restrict__ out_idx, bool write_ids) {
+                        int32_t* __restrict__ out_idx, int32_t* __restrict__ rev, bool write_ids) {
   const int lane = threadIdx.x & 31;
   const int warps = (gridDim.x * blockDim.x) >> 5;
   for (int32_t x = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < n; x += warps) {
@@ -95,6 +95,11 @@ __global__ void k_edges(int32_t n, const int32_t* __restrict__ rp, const int32_t
       bool valid = p < e;
       int32_t y = valid ? ci[p] : 0;
       bool is_out = valid && rank_less(deg, x, y);
+      if (valid) {  // the slot of (y, x)
+        const int32_t yb = rp[y], ye = rp[y + 1];
+        const int32_t q = lower_bound_i32(ci, yb, ye, x);
+        rev[p] = (q < ye && ci[q] == x) ? q : p;  // p itself only for invalid input
+      }
       if (valid && write_ids) {
         int32_t id;
         if (y > x) {
@@ -289,6 +294,7 @@ void free_prep(PrepBuffers* p, cudaStream_t s) {
   if (p->out_idx) cudaFreeAsync(p->out_idx, s);
   if (p->units) cudaFreeAsync(p->units, s);
   if (p->S) cudaFreeAsync(p->S, s);
+  if (p->rev) cudaFreeAsync(p->rev, s);
   *p = PrepBuffers();
 }
 
@@ -313,6 +319,7 @@ gc_status prepare_graph(int32_t n, int32_t m, const int32_t* d_rp, const int32_t
   } while (0)
   GC_TRY(cudaMallocAsync(&P.deg, sizeof(int32_t) * (n > 0 ? n : 1), s), "alloc deg");
   if (!P.eid) GC_TRY(cudaMallocAsync(&P.eid, sizeof(int32_t) * (nnz > 0 ? nnz : 1), s), "alloc eid");
+  GC_TRY(cudaMallocAsync(&P.rev, sizeof(int32_t) * (nnz > 0 ? nnz : 1), s), "alloc rev");
   GC_TRY(cudaMallocAsync(&P.uv, sizeof(int32_t) * (nnz > 0 ? nnz : 1), s), "alloc uv");
   GC_TRY(cudaMallocAsync(&P.out_ptr, sizeof(int32_t) * ((int64_t)n + 1), s), "alloc out_ptr");
   GC_TRY(cudaMallocAsync(&P.out_idx, sizeof(int32_t) * (m > 0 ? m : 1), s), "alloc out_idx");
@@ -333,7 +340,7 @@ gc_status prepare_graph(int32_t n, int32_t m, const int32_t* d_rp, const int32_t
     GC_TRY(cudaGetLastError(), "k_out_cnt");
     if ((st = exclusive_scan(n, out_cnt, P.out_ptr, s)) != GC_OK) goto fail;
     k_edges<<<grid_for((int64_t)n * 32, 256), 256, 0, s>>>(n, d_rp, d_ci, P.deg, up, upoff,
-                                                            P.out_ptr, P.eid, P.uv, P.out_idx,
+                                                            P.out_ptr, P.eid, P.uv, P.out_idx, P.rev,
                                                             d_eid_given == nullptr);
     GC_TRY(cudaGetLastError(), "k_edges");
     if (d_eid_given) {

@@ -32,7 +32,7 @@ gc_status scratch_init(Scratch* sc, int32_t m, int32_t n_units, int32_t table_n,
     if (e != cudaSuccess) return cuda_fail(e, "scratch alloc"); \
   } while (0)
   GS_TRY(cudaMallocAsync(&sc->tri, sizeof(int32_t) * (size_t)(m > 0 ? m : 1), s));
-  GS_TRY(cudaMallocAsync(&sc->P, sizeof(unsigned long long) * (size_t)(m > 0 ? m : 1), s));
+  GS_TRY(cudaMallocAsync(&sc->P, sizeof(unsigned long long) * (size_t)(m > 0 ? 2 * (size_t)m : 1), s));
   GS_TRY(cudaMallocAsync(&sc->chunks, sizeof(int32_t) * 3 * chunk_capacity(n_units), s));
   GS_TRY(cudaMallocAsync(&sc->off, sizeof(int32_t) * ((size_t)n_units + 1), s));
   GS_TRY(cudaMallocAsync(&sc->misc, sizeof(int32_t) * 8, s));
@@ -92,7 +92,7 @@ gc_status run_count(const DevGraph& g, const int32_t* units, int32_t n_units, ui
     if ((st = run_pass_a(g, a, s)) != GC_OK) return st;
     if ((st = run_max_tri(sc->tri, g.m, tmax_dev, s)) != GC_OK) return st;
     GR_EVENT(kPhasePassC);
-    GR_TRY(cudaMemsetAsync(sc->P, 0, sizeof(unsigned long long) * (size_t)g.m, s), "zero P");
+    GR_TRY(cudaMemsetAsync(sc->P, 0, sizeof(unsigned long long) * 2 * (size_t)g.m, s), "zero P");
     GR_TRY(cudaMemsetAsync(cursor, 0, sizeof(int32_t), s), "reset cursor");
     if ((st = run_pass_c(g, a, s)) != GC_OK) return st;
     if ((st = run_make_chunks(g, units, n_units, sc->tri, sc->chunks, sc->off, sc->total, nbig_dev, a.big_t, s)) != GC_OK)

@@ -46,6 +46,13 @@ def test_er2000_config_bit_exact():
     assert X[0] == len(ci) // 2
 
 
+def test_dense_er_1k_150k_bit_exact():
+    # the 1K-vertex / 150K-edge dense shape of the paper's GPU comparison
+    rp, ci = graphgen.config_er_dense()
+    X, _ = assert_parity(rp, ci)
+    assert 140000 < X[0] < 160000
+
+
 @pytest.mark.parametrize("seed", range(1, 13))
 def test_random_graphs(seed):
     for n, p in ((7, 0.5), (40, 0.3), (150, 0.08), (300, 0.02), (64, 0.9)):
@@ -252,3 +259,22 @@ def test_served_result_same_alone_and_in_mix():
     assert mix == alone
     for g, r in zip(gs[:4], mix[:4]):
         assert r == _oracle_X(*g)
+
+
+
+def test_batch_rejects_asymmetric_graph_and_keeps_the_others():
+    good = [graphgen.er(60, 0.2, 70 + i) for i in range(3)]
+    bad_rp = np.array([0, 2, 3, 4], np.int32)
+    bad_ci = np.array([1, 2, 2, 0], np.int32)   # 0:{1,2} 1:{2} 2:{0}: (0,1) has no reverse
+    b = gcb.gc_batch_create(1 << 30, gcb.GC_BATCH_MANUAL)
+    try:
+        t0 = gcb.gc_batch_submit(b, *good[0])
+        with pytest.raises(gcb.GcError) as ei:
+            gcb.gc_batch_submit(b, bad_rp, bad_ci)
+        assert ei.value.status == -5
+        ts = [t0, gcb.gc_batch_submit(b, *good[1]), gcb.gc_batch_submit(b, *good[2])]
+        gcb.gc_batch_flush(b)
+        res = [gcb.gc_batch_poll(b, t, timeout_us=120_000_000) for t in ts]
+    finally:
+        gcb.gc_batch_destroy(b)
+    assert res == [_oracle_X(*g) for g in good]
