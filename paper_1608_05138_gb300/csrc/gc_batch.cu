@@ -16,6 +16,7 @@
 // which releases their share of the budget.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -59,6 +60,7 @@ struct Result {
 
 struct Launch {
   std::vector<uint64_t> tickets;
+  std::vector<int32_t> slot;          // ticket k's row in h_x
   int64_t bytes = 0;
   cudaStream_t stream = nullptr;
   cudaEvent_t done = nullptr;
@@ -102,14 +104,18 @@ namespace {
 // Counts `graphs` as one launch on `s`. Fills L (results land in L->h_x when
 // L->done completes). Runs in the dispatcher thread (or the flushing thread
 // in manual mode) without holding the batch lock.
-void run_launch(std::vector<PendingGraph>& graphs, cudaStream_t s, Launch* L) {
+// The graphs too large for the bitmatrix kernel, as one disjoint union
+// through the general passes. Results go to h_x_dst ([G][17][2], pinned) and
+// the launch status word to *h_status_dst.
+gc_status run_union(std::vector<PendingGraph*>& graphs, cudaStream_t s, Launch* L, unsigned long long* h_x_dst,
+                    int32_t* h_status_dst) {
   const int32_t G = (int32_t)graphs.size();
   int64_t n_total = 0, nnz_total = 0;
   int32_t table_n = 0;
-  for (auto& pg : graphs) {
-    n_total += pg.n;
-    nnz_total += 2 * pg.m;
-    if (pg.n > table_n) table_n = pg.n;
+  for (auto* pg : graphs) {
+    n_total += pg->n;
+    nnz_total += 2 * pg->m;
+    if (pg->n > table_n) table_n = pg->n;
   }
   const int32_t n = (int32_t)n_total;
   const int32_t m = (int32_t)(nnz_total / 2);
@@ -119,7 +125,7 @@ void run_launch(std::vector<PendingGraph>& graphs, cudaStream_t s, Launch* L) {
   {
     int64_t vo = 0, eo = 0;
     for (int32_t gi = 0; gi < G; ++gi) {
-      PendingGraph& pg = graphs[gi];
+      PendingGraph& pg = *graphs[gi];
       for (int32_t i = 0; i < pg.n; ++i) {
         h_rp[vo + i] = (int32_t)(eo + pg.rp[i]);
         h_vgid[vo + i] = gi;
@@ -199,9 +205,9 @@ void run_launch(std::vector<PendingGraph>& graphs, cudaStream_t s, Launch* L) {
       L->error = gc_last_error();
       goto out;
     }
-    GB_TRY(cudaMemcpyAsync(L->h_x, d_x, sizeof(unsigned long long) * (size_t)G * 34, cudaMemcpyDeviceToHost, s),
+    GB_TRY(cudaMemcpyAsync(h_x_dst, d_x, sizeof(unsigned long long) * (size_t)G * 34, cudaMemcpyDeviceToHost, s),
            "batch copy out");
-    GB_TRY(cudaMemcpyAsync(L->h_status, sc.misc + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, s), "batch copy out");
+    GB_TRY(cudaMemcpyAsync(h_status_dst, sc.misc + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, s), "batch copy out");
   }
 out:
 #undef GB_TRY
@@ -209,12 +215,111 @@ out:
   scratch_free(&sc, s);
   for (void* p : {(void*)d_rp, (void*)d_ci, (void*)d_vgid, (void*)d_desc, (void*)d_gm, (void*)d_csum, (void*)d_x})
     if (p) cudaFreeAsync(p, s);
+  return st;
+}
+
+// Graphs of at most kSmallN vertices: packed as they are (local ids) and
+// counted one CTA per graph on a shared-memory bitmatrix.
+gc_status run_small(std::vector<PendingGraph*>& graphs, cudaStream_t s, Launch* L, unsigned long long* h_x_dst) {
+  const int32_t G = (int32_t)graphs.size();
+  std::vector<int64_t> h_voff((size_t)G + 1), h_eoff((size_t)G + 1), h_gm((size_t)G);
+  std::vector<int32_t> h_gn((size_t)G), h_order((size_t)G);
+  h_voff[0] = h_eoff[0] = 0;
+  for (int32_t gi = 0; gi < G; ++gi) {
+    h_voff[gi + 1] = h_voff[gi] + graphs[gi]->n + 1;
+    h_eoff[gi + 1] = h_eoff[gi] + 2 * graphs[gi]->m;
+    h_gn[gi] = graphs[gi]->n;
+    h_gm[gi] = graphs[gi]->m;
+    h_order[gi] = gi;
+  }
+  std::sort(h_order.begin(), h_order.end(), [&](int32_t a, int32_t b) { return h_gm[a] > h_gm[b]; });
+  std::vector<int32_t> h_rp((size_t)h_voff[G] + 1), h_ci((size_t)(h_eoff[G] > 0 ? h_eoff[G] : 1));
+  for (int32_t gi = 0; gi < G; ++gi) {
+    std::memcpy(h_rp.data() + h_voff[gi], graphs[gi]->rp.data(), sizeof(int32_t) * (graphs[gi]->n + 1));
+    if (graphs[gi]->m > 0)
+      std::memcpy(h_ci.data() + h_eoff[gi], graphs[gi]->ci.data(), sizeof(int32_t) * 2 * graphs[gi]->m);
+  }
+  int32_t *d_rp = nullptr, *d_ci = nullptr, *d_gn = nullptr, *d_order = nullptr, *d_misc = nullptr;
+  int64_t *d_voff = nullptr, *d_eoff = nullptr, *d_gm = nullptr;
+  unsigned long long *d_csum = nullptr, *d_x = nullptr;
+  cudaError_t e = cudaSuccess;
+  gc_status st = GC_OK;
+#define GS_TRY(call, what)                   \
+  do {                                       \
+    e = (call);                              \
+    if (e != cudaSuccess) {                  \
+      st = cuda_fail(e, what);               \
+      L->error = gc_last_error();            \
+      goto out;                              \
+    }                                        \
+  } while (0)
+  GS_TRY(cudaMallocAsync(&d_rp, sizeof(int32_t) * h_rp.size(), s), "small alloc");
+  GS_TRY(cudaMallocAsync(&d_ci, sizeof(int32_t) * h_ci.size(), s), "small alloc");
+  GS_TRY(cudaMallocAsync(&d_voff, sizeof(int64_t) * h_voff.size(), s), "small alloc");
+  GS_TRY(cudaMallocAsync(&d_eoff, sizeof(int64_t) * h_eoff.size(), s), "small alloc");
+  GS_TRY(cudaMallocAsync(&d_gn, sizeof(int32_t) * G, s), "small alloc");
+  GS_TRY(cudaMallocAsync(&d_gm, sizeof(int64_t) * G, s), "small alloc");
+  GS_TRY(cudaMallocAsync(&d_order, sizeof(int32_t) * G, s), "small alloc");
+  GS_TRY(cudaMallocAsync(&d_misc, sizeof(int32_t) * 2, s), "small alloc");
+  GS_TRY(cudaMallocAsync(&d_csum, sizeof(unsigned long long) * (size_t)G * 26, s), "small alloc");
+  GS_TRY(cudaMallocAsync(&d_x, sizeof(unsigned long long) * (size_t)G * 34, s), "small alloc");
+  GS_TRY(cudaMemcpyAsync(d_rp, h_rp.data(), sizeof(int32_t) * h_rp.size(), cudaMemcpyHostToDevice, s), "small copy");
+  GS_TRY(cudaMemcpyAsync(d_ci, h_ci.data(), sizeof(int32_t) * h_ci.size(), cudaMemcpyHostToDevice, s), "small copy");
+  GS_TRY(cudaMemcpyAsync(d_voff, h_voff.data(), sizeof(int64_t) * h_voff.size(), cudaMemcpyHostToDevice, s),
+         "small copy");
+  GS_TRY(cudaMemcpyAsync(d_eoff, h_eoff.data(), sizeof(int64_t) * h_eoff.size(), cudaMemcpyHostToDevice, s),
+         "small copy");
+  GS_TRY(cudaMemcpyAsync(d_gn, h_gn.data(), sizeof(int32_t) * G, cudaMemcpyHostToDevice, s), "small copy");
+  GS_TRY(cudaMemcpyAsync(d_gm, h_gm.data(), sizeof(int64_t) * G, cudaMemcpyHostToDevice, s), "small copy");
+  GS_TRY(cudaMemcpyAsync(d_order, h_order.data(), sizeof(int32_t) * G, cudaMemcpyHostToDevice, s), "small copy");
+  GS_TRY(cudaMemsetAsync(d_misc, 0, sizeof(int32_t) * 2, s), "small memset");
+  GS_TRY(cudaMemsetAsync(d_csum, 0, sizeof(unsigned long long) * (size_t)G * 26, s), "small memset");
+  if ((st = run_small_graphs(d_rp, d_voff, d_ci, d_eoff, d_order, G, d_misc, d_csum, s)) != GC_OK) {
+    L->error = gc_last_error();
+    goto out;
+  }
+  {
+    DevGraph dg = DevGraph();
+    dg.G = G;
+    dg.gn = d_gn;
+    dg.gm = d_gm;
+    if ((st = run_derive(dg, d_csum, d_x, d_misc + 1, s)) != GC_OK) {
+      L->error = gc_last_error();
+      goto out;
+    }
+  }
+  GS_TRY(cudaMemcpyAsync(h_x_dst, d_x, sizeof(unsigned long long) * (size_t)G * 34, cudaMemcpyDeviceToHost, s),
+         "small copy out");
+out:
+#undef GS_TRY
+  for (void* p : {(void*)d_rp, (void*)d_ci, (void*)d_voff, (void*)d_eoff, (void*)d_gn, (void*)d_gm, (void*)d_order,
+                  (void*)d_misc, (void*)d_csum, (void*)d_x})
+    if (p) cudaFreeAsync(p, s);
+  return st;
+}
+
+// Counts `graphs` as one launch on `s`: small graphs on the bitmatrix kernel,
+// the others as one disjoint union. Results land in L->h_x when L->done
+// completes. Runs in the dispatcher thread (or the flushing thread in manual
+// mode) without holding the batch lock.
+void run_launch(std::vector<PendingGraph>& graphs, cudaStream_t s, Launch* L) {
+  std::vector<PendingGraph*> small, large;
+  for (auto& pg : graphs) (pg.n <= kSmallN ? small : large).push_back(&pg);
+  L->slot.resize(graphs.size());
+  {
+    int32_t is = 0, il = (int32_t)small.size();
+    for (size_t k = 0; k < graphs.size(); ++k) L->slot[k] = graphs[k].n <= kSmallN ? is++ : il++;
+  }
+  gc_status st = GC_OK;
+  L->h_status[0] = 0;
+  if (!small.empty()) st = run_small(small, s, L, L->h_x);
+  if (st == GC_OK && !large.empty()) st = run_union(large, s, L, L->h_x + 34 * small.size(), L->h_status);
   L->launch_status = st;
   if (st == GC_OK) {
-    e = cudaEventRecord(L->done, s);
+    cudaError_t e = cudaEventRecord(L->done, s);
     if (e != cudaSuccess) {
-      fail(e, "batch event");
-      L->launch_status = st;
+      L->launch_status = cuda_fail(e, "batch event");
+      L->error = gc_last_error();
     }
   }
 }
@@ -238,7 +343,7 @@ void retire_locked(gc_batch b) {
     for (size_t k = 0; k < L->tickets.size(); ++k) {
       Result r;
       if (L->launch_status == GC_OK) {
-        std::memcpy(r.x, L->h_x + 34 * k, sizeof(r.x));
+        std::memcpy(r.x, L->h_x + 34 * (size_t)L->slot[k], sizeof(r.x));
         int32_t dst = *L->h_status;
         r.status = dst == 0 ? GC_OK : ((dst & kTimeout) ? GC_ERR_TIMEOUT : GC_ERR_CUDA);
       } else {

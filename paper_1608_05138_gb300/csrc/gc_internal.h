@@ -81,6 +81,7 @@ constexpr int kBlock = 512;            // threads per CTA of the counting kernel
 constexpr int kCtasPerSm = 2;          // resident CTAs per SM of the persistent grids
 constexpr int kWarps = kBlock / 32;
 constexpr int kTcap = 1024;            // per-warp T list in shared memory (entries)
+constexpr int kSmallN = 512;           // graphs up to this many vertices use the bitmatrix kernel
 // Edges whose |T| exceeds big_t (default 1024, environment GC_BIG_T in
 // [16, kTcap]) are done by a whole CTA (k_pass_big).
 int big_t_threshold();
@@ -145,6 +146,14 @@ gc_status prepare_graph(int32_t n, int32_t m, const int32_t* d_rp, const int32_t
                         const int32_t* d_vgid, int32_t* d_eid_given, const int32_t* d_perm,
                         PrepBuffers* out, cudaStream_t stream);
 void free_prep(PrepBuffers* p, cudaStream_t s);
+
+// ---- small graphs on a shared-memory bitmatrix (gc_small.cu) ----
+// rp/voff: concatenated local row pointers and their offsets ([G'+1] for the
+// packed graphs); ci/eoff: concatenated local columns; order: the G graph
+// indices to count, largest first; csum [G'][13][2] zeroed.
+gc_status run_small_graphs(const int32_t* rp, const int64_t* voff, const int32_t* ci, const int64_t* eoff,
+                           const int32_t* order, int32_t G, int32_t* cursor, unsigned long long* csum,
+                           cudaStream_t s);
 
 // ---- counting (gc_count.cu) ----
 int count_grid_size();
