@@ -215,7 +215,7 @@ def run_batched(args):
     for step in range(args.warmup + args.steps):
         b = gcb.gc_batch_create(200 << 30, gcb.GC_BATCH_MANUAL)
         t0 = time.perf_counter()
-        tickets = [gcb.gc_batch_submit(b, *B.graph(i)) for i in range(G)]
+        tickets = [int(t) for t in gcb.gc_batch_submit_many(b, B.nvert, B.voff, B.eoff, B.row_ptr, B.col_idx)]
         t1 = time.perf_counter()
         gcb.gc_batch_flush(b)
         t2 = time.perf_counter()

@@ -175,6 +175,15 @@ gc_status gc_graph_free(gc_graph g);
 gc_status gc_batch_create(int64_t device_mem_budget_bytes, uint32_t flags, gc_batch* out);
 gc_status gc_batch_submit(gc_batch b, int32_t n, const int32_t* row_ptr, const int32_t* col_idx,
                           uint64_t* ticket_out);
+/* Submit G graphs at once from one concatenated buffer (the batched form's
+ * input): graph g has nvert[g] vertices, local row pointers
+ * row_ptr[voff[g] .. voff[g] + nvert[g]] (starting at 0) and local columns
+ * col_idx[eoff[g] .. eoff[g + 1]). All graphs are validated (in parallel)
+ * and admitted together, or none is: the first invalid graph's error is
+ * returned (message names its index), GC_ERR_BUSY if they do not fit in the
+ * budget now. tickets_out receives G tickets. Host pointers; copied. */
+gc_status gc_batch_submit_many(gc_batch b, int64_t G, const int32_t* nvert, const int64_t* voff, const int64_t* eoff,
+                               const int32_t* row_ptr, const int32_t* col_idx, uint64_t* tickets_out);
 gc_status gc_batch_flush(gc_batch b);
 gc_status gc_batch_poll(gc_batch b, uint64_t ticket, uint64_t* global_out, uint64_t* global_hi,
                         int32_t timeout_us);

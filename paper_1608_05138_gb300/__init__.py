@@ -36,7 +36,7 @@ EXPORTED = ["gc_last_error", "gc_graph_upload", "gc_graph_info", "gc_graph_edges
             "gc_count_edge_graphlets", "gc_graph_csums", "gc_phase_count", "gc_phase_name",
             "gc_graph_phase_ms", "gc_graph_free", "gc_batch_create", "gc_batch_submit",
             "gc_batch_flush", "gc_batch_poll", "gc_batch_destroy", "gc_edge_triangles_noalloc",
-            "gc_graph_work_counts"]
+            "gc_graph_work_counts", "gc_batch_submit_many"]
 WORK_NAMES = ["b_group_deg", "b_deg", "b_T", "b_probes", "b_edges", "big_deg", "big_T", "big_probes",
               "c_wedges", "a_units"]
 
@@ -77,10 +77,11 @@ def lib():
             L.gc_batch_destroy.argtypes = [vp]
             L.gc_edge_triangles_noalloc.argtypes = [i32, vp, vp, vp, vp]
             L.gc_graph_work_counts.argtypes = [vp, vp]
+            L.gc_batch_submit_many.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp]
             for name in ("gc_graph_upload", "gc_graph_info", "gc_graph_edges", "gc_count_edge_graphlets",
                          "gc_graph_csums", "gc_graph_phase_ms", "gc_graph_free", "gc_batch_create",
                          "gc_batch_submit", "gc_batch_flush", "gc_batch_poll", "gc_batch_destroy",
-                         "gc_edge_triangles_noalloc", "gc_graph_work_counts"):
+                         "gc_edge_triangles_noalloc", "gc_graph_work_counts", "gc_batch_submit_many"):
                 getattr(L, name).restype = C.c_int
             _lib = L
     return _lib
@@ -257,6 +258,20 @@ def gc_batch_try_submit(b, row_ptr, col_idx):
         return None
     _check(st, "gc_batch_submit")
     return t.value
+
+
+def gc_batch_submit_many(b, nvert, voff, eoff, row_ptr, col_idx):
+    """Submit many graphs from one concatenated CSR (int32 local ids, int64
+    offsets; see include/gc.h). Returns the tickets as a uint64 array."""
+    nv = np.ascontiguousarray(nvert, np.int32)
+    vo = np.ascontiguousarray(voff, np.int64)
+    eo = np.ascontiguousarray(eoff, np.int64)
+    rp = np.ascontiguousarray(row_ptr, np.int32)
+    ci = np.ascontiguousarray(col_idx, np.int32)
+    t = np.zeros(len(nv), np.uint64)
+    _check(lib().gc_batch_submit_many(b, len(nv), _ptr(nv), _ptr(vo), _ptr(eo), _ptr(rp),
+                                      _ptr(ci) if len(ci) else None, _ptr(t)), "gc_batch_submit_many")
+    return t
 
 
 def gc_batch_flush(b):

@@ -484,6 +484,75 @@ gc_status gc_batch_submit(gc_batch b, int32_t n, const int32_t* row_ptr, const i
   return GC_OK;
 }
 
+gc_status gc_batch_submit_many(gc_batch b, int64_t G, const int32_t* nvert, const int64_t* voff, const int64_t* eoff,
+                               const int32_t* row_ptr, const int32_t* col_idx, uint64_t* tickets_out) {
+  if (!b || G < 0 || (G > 0 && (!nvert || !voff || !eoff || !row_ptr || !tickets_out))) {
+    set_error("bad arguments");
+    return GC_ERR_ARG;
+  }
+  if (G == 0) return GC_OK;
+  std::vector<PendingGraph> pgs((size_t)G);
+  unsigned hw = std::thread::hardware_concurrency();
+  const int nt = (int)std::min<int64_t>(std::max(1u, std::min(hw, 32u)), G);
+  std::vector<gc_status> res(nt, GC_OK);
+  std::vector<std::string> msg(nt);
+  auto work = [&](int t) {
+    for (int64_t g = t; g < G; g += nt) {
+      const int32_t n = nvert[g];
+      const int32_t* rp = row_ptr + voff[g];
+      const int32_t* ci = col_idx ? col_idx + eoff[g] : nullptr;
+      if (n < 0 || (int64_t)rp[n] != eoff[g + 1] - eoff[g]) {
+        res[t] = GC_ERR_ARG;
+        msg[t] = "graph " + std::to_string(g) + ": offsets disagree with row_ptr";
+        return;
+      }
+      gc_status st = validate_csr(n, rp, ci);
+      if (st != GC_OK) {
+        res[t] = st;
+        msg[t] = "graph " + std::to_string(g) + ": " + gc_last_error();
+        return;
+      }
+      PendingGraph& pg = pgs[(size_t)g];
+      pg.n = n;
+      pg.m = rp[n] / 2;
+      pg.bytes = footprint(n, pg.m);
+      pg.rp.assign(rp, rp + n + 1);
+      if (pg.m > 0) pg.ci.assign(ci, ci + 2 * pg.m);
+    }
+  };
+  std::vector<std::thread> th;
+  for (int t = 1; t < nt; ++t) th.emplace_back(work, t);
+  work(0);
+  for (auto& x : th) x.join();
+  for (int t = 0; t < nt; ++t)
+    if (res[t] != GC_OK) {
+      set_error(msg[t]);
+      return res[t];
+    }
+  int64_t bytes = 0;
+  for (auto& pg : pgs) bytes += pg.bytes;
+  {
+    std::lock_guard<std::mutex> lk(b->mu);
+    if (bytes > b->budget) {
+      set_error("graphs need more device memory than the whole budget");
+      return GC_ERR_NOMEM;
+    }
+    if (b->in_use + bytes > b->budget) {
+      set_error("device-memory budget is full");
+      return GC_ERR_BUSY;
+    }
+    b->in_use += bytes;
+    for (int64_t g = 0; g < G; ++g) {
+      pgs[(size_t)g].ticket = b->next_ticket++;
+      tickets_out[g] = pgs[(size_t)g].ticket;
+      b->live.insert(pgs[(size_t)g].ticket);
+      b->pending.push_back(std::move(pgs[(size_t)g]));
+    }
+  }
+  b->cv.notify_all();
+  return GC_OK;
+}
+
 gc_status gc_batch_flush(gc_batch b) {
   if (!b) { set_error("batch is NULL"); return GC_ERR_ARG; }
   if (b->flags & GC_BATCH_MANUAL) {

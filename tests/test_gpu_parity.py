@@ -278,3 +278,16 @@ def test_batch_rejects_asymmetric_graph_and_keeps_the_others():
     finally:
         gcb.gc_batch_destroy(b)
     assert res == [_oracle_X(*g) for g in good]
+
+
+def test_batch_submit_many_matches_single_submits():
+    B = graphgen.batch(200, n_lo=20, n_hi=700, seed=33)   # small and large (n > 512) graphs
+    b = gcb.gc_batch_create(8 << 30, gcb.GC_BATCH_MANUAL)
+    try:
+        ts = gcb.gc_batch_submit_many(b, B.nvert, B.voff, B.eoff, B.row_ptr, B.col_idx)
+        gcb.gc_batch_flush(b)
+        res = [gcb.gc_batch_poll(b, int(t), timeout_us=120_000_000) for t in ts]
+    finally:
+        gcb.gc_batch_destroy(b)
+    for i in range(0, len(B), 7):
+        assert res[i] == _oracle_X(*B.graph(i)), i
