@@ -67,12 +67,23 @@ __device__ __forceinline__ int contains(const int32_t* a, int32_t len, int32_t k
 }
 
 
+// Lower bound of key in T[0..p2), p2 a power of two, T padded with INT_MAX
+// from t to p2: a fixed number of halving steps, no early exit.
+__device__ __forceinline__ int lower_bound_pow2(const int32_t* T, int32_t p2, int32_t key) {
+  int32_t lo = 0;
+  for (int32_t step = p2 >> 1; step > 0; step >>= 1)
+    if (T[lo + step - 1] < key) lo += step;
+  return lo;
+}
+
 // 4-clique count of one edge: sum over members a of T (ascending, t of them)
 // of |out(a) ∩ T|, for one warp. Members are taken 32 at a time; the entries
-// of their out-lists are flattened over the lanes (coalesced loads, no idle
-// lanes) and each lane keeps kMLP loads in flight before probing. in_T(r)
-// answers membership; a member whose out-list is longer than T (when
-// long_ok) has T's members searched in its out-list instead.
+// of their out-lists are laid end to end and dealt to the lanes 32 at a time
+// (coalesced loads, no idle lanes), kMLP windows per round so that several
+// loads are in flight; each entry's owner is found by a 5-step shuffle search
+// over the 32 lists' starts. in_T(r) answers membership; a member whose
+// out-list is longer than T (when long_ok) has T's members searched in its
+// out-list instead.
 template <int kMLP, class InT>
 __device__ __forceinline__ long long warp_clique_count(const DevGraph& g, const int32_t* T, int32_t t,
                                                        int32_t i_begin, int32_t i_stride, int lane,
@@ -311,8 +322,14 @@ __global__ void __launch_bounds__(kBlock, kCtasPerSm) k_pass_b(DevGraph g, Count
       __syncwarp();
       // 4-cliques: each adjacent pair of T is counted once, through the
       // out-list of its lower-rank member; membership by binary search in T.
-      long long x7 = warp_clique_count<4>(g, buf, t, 0, 32, lane, true,
-                                          [&](int32_t r) { return contains(buf, t, r); }, w_probe);
+      int32_t p2 = 1;
+      while (p2 < t) p2 <<= 1;
+      for (int32_t i = t + lane; i < p2; i += 32) buf[i] = 0x7fffffff;  // sentinels up to a power of two
+      __syncwarp();
+      long long x7 = warp_clique_count<4>(g, buf, t, 0, 32, lane, true, [&](int32_t r) {
+        const int32_t q = lower_bound_pow2(buf, p2, r);
+        return (int)(q < t && buf[q] == r);
+      }, w_probe);
       x7 = warp_sum_ll(x7);
       __syncwarp();
       const long long x10 = P - cross + 2 * x7;

@@ -171,7 +171,15 @@ gc_status run_max_tri(const int32_t* tri, int32_t m, int32_t* d_out, cudaStream_
 gc_status run_make_chunks(const DevGraph& g, const int32_t* units, int32_t n_units,
                           const int32_t* tri, int32_t* chunks, int32_t* off,
                           unsigned long long* total_dev, int32_t* n_big_dev, int32_t big_t, cudaStream_t s);
-inline size_t chunk_capacity(int32_t n_units) { return (size_t)n_units + 8 * (size_t)count_grid_size() + 1; }
+// Target chunks per CTA of the persistent grid (environment GC_CHUNK_FACTOR,
+// default 8, range 1..256).
+int chunk_factor();
+inline size_t chunk_capacity(int32_t n_units) {
+  return (size_t)n_units + (size_t)chunk_factor() * (size_t)count_grid_size() + 1;
+}
+// Unit ordering key (environment GC_ORDER): 0 = vol (default: d_v + sum of
+// neighbour degrees, heaviest bin first), 1 = degree d_v, 2 = none (vertex id).
+int order_key();
 // exclusive prefix sum of n int32 into out[0..n] (out[n] = total)
 gc_status exclusive_scan(int32_t n, const int32_t* in, int32_t* out, cudaStream_t s);
 

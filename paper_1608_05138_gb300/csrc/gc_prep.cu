@@ -143,14 +143,19 @@ __device__ __forceinline__ int bin_of(long long cost) {
   return cost <= 1 ? 0 : 63 - __clzll(cost);
 }
 
+// Bin key of a v-group under the chosen ordering (0 vol, 1 degree, 2 none).
+__device__ __forceinline__ int unit_bin(int key, long long S, int32_t d) {
+  return key == 0 ? bin_of(S + d) : (key == 1 ? bin_of(d) : 0);
+}
+
 __global__ void k_bin_hist(int32_t n, const int32_t* __restrict__ deg,
                            const int32_t* __restrict__ out_cnt, const long long* __restrict__ S,
-                           int32_t* __restrict__ hist) {
+                           int32_t* __restrict__ hist, int key) {
   __shared__ int32_t h[64];
   if (threadIdx.x < 64) h[threadIdx.x] = 0;
   __syncthreads();
   for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
-    if (deg[v] - out_cnt[v] > 0) atomicAdd(&h[bin_of(S[v] + deg[v])], 1);
+    if (deg[v] - out_cnt[v] > 0) atomicAdd(&h[unit_bin(key, S[v], deg[v])], 1);
   }
   __syncthreads();
   if (threadIdx.x < 64 && h[threadIdx.x]) atomicAdd(&hist[threadIdx.x], h[threadIdx.x]);
@@ -159,10 +164,10 @@ __global__ void k_bin_hist(int32_t n, const int32_t* __restrict__ deg,
 __global__ void k_bin_scatter(int32_t n, const int32_t* __restrict__ deg,
                               const int32_t* __restrict__ out_cnt,
                               const long long* __restrict__ S, int32_t* __restrict__ cursor,
-                              int32_t* __restrict__ units) {
+                              int32_t* __restrict__ units, int key) {
   for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
     if (deg[v] - out_cnt[v] > 0) {
-      int32_t pos = atomicAdd(&cursor[bin_of(S[v] + deg[v])], 1);
+      int32_t pos = atomicAdd(&cursor[unit_bin(key, S[v], deg[v])], 1);
       units[pos] = v;
     }
   }
@@ -347,7 +352,7 @@ gc_status prepare_graph(int32_t n, int32_t m, const int32_t* d_rp, const int32_t
       k_uv_perm<<<grid_for((int64_t)n * 32, 256), 256, 0, s>>>(n, d_rp, d_ci, P.eid, d_perm, P.uv);
       GC_TRY(cudaGetLastError(), "k_uv_perm");
     }
-    k_bin_hist<<<grid_for(n, 256), 256, 0, s>>>(n, P.deg, out_cnt, S, hist);
+    k_bin_hist<<<grid_for(n, 256), 256, 0, s>>>(n, P.deg, out_cnt, S, hist, order_key());
     GC_TRY(cudaGetLastError(), "k_bin_hist");
     {
       int32_t h[65];
@@ -362,7 +367,7 @@ gc_status prepare_graph(int32_t n, int32_t m, const int32_t* d_rp, const int32_t
       }
       P.n_units = acc;
       GC_TRY(cudaMemcpyAsync(hist, cur, sizeof(cur), cudaMemcpyHostToDevice, s), "copy cursors");
-      k_bin_scatter<<<grid_for(n, 256), 256, 0, s>>>(n, P.deg, out_cnt, S, hist, P.units);
+      k_bin_scatter<<<grid_for(n, 256), 256, 0, s>>>(n, P.deg, out_cnt, S, hist, P.units, order_key());
       GC_TRY(cudaGetLastError(), "k_bin_scatter");
     }
   } else {

@@ -11,6 +11,9 @@
 // of the groups (the queue Pi).
 #include <cuda_runtime.h>
 
+#include <cstdlib>
+#include <cstring>
+
 #include "gc_internal.h"
 
 namespace gc {
@@ -122,6 +125,30 @@ __global__ void k_chunk_emit(DevGraph g, const int32_t* __restrict__ units, int3
   }
 }
 
+}  // namespace
+
+int chunk_factor() {
+  static int v = [] {
+    const char* e = getenv("GC_CHUNK_FACTOR");
+    int x = e ? atoi(e) : 8;
+    return x < 1 ? 1 : (x > 256 ? 256 : x);
+  }();
+  return v;
+}
+
+int order_key() {
+  static int v = [] {
+    const char* e = getenv("GC_ORDER");
+    if (!e) return 0;
+    if (!strcmp(e, "deg")) return 1;
+    if (!strcmp(e, "none")) return 2;
+    return 0;
+  }();
+  return v;
+}
+
+namespace {
+
 int blocks_for(long long threads) {
   long long b = (threads + 255) / 256;
   if (b < 1) b = 1;
@@ -155,8 +182,9 @@ gc_status run_make_chunks(const DevGraph& g, const int32_t* units, int32_t n_uni
   if (e != cudaSuccess) {
     st = cuda_fail(e, "chunk work");
   } else {
-    // ceil so that sum_k ceil(W_k / U) <= n_units + 8 * grid
-    long long U = (long long)((total + (unsigned long long)(8 * grid) - 1) / (unsigned long long)(8 * grid));
+    // ceil so that sum_k ceil(W_k / U) <= n_units + chunk_factor * grid
+    const unsigned long long per = (unsigned long long)chunk_factor() * (unsigned long long)grid;
+    long long U = (long long)((total + per - 1) / per);
     if (U < 1) U = 1;
     k_chunk_count<<<blocks_for(n_units), 256, 0, s>>>(units, n_units, W, g.deg, U, nch);
     e = cudaGetLastError();
