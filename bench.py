@@ -58,21 +58,21 @@ def load_workload(name: str, scale: int):
 
 def algorithmic_bytes(work: dict) -> dict:
     """Algorithmic bytes per launch of each counting kernel, from the units the
-    kernels report (gc_graph_work_counts); per-unit figures are in the design doc §7:
-      pass A: 8 per entry of Gamma(v) and of the Gamma(u) scans (read + Psi)
+    kernels report (gc_graph_work_counts); the per-unit figures:
+      pass A: 8 per entry of Gamma(v) and of the Gamma(u) scans (read + Psi),
+              plus 16 per edge for re-indexing |T| by out-slot
       pass C: 48 per wedge h-x-o (entry read, count RMW, attribution read,
               edge id, P atomic, clear)
-      pass B: 16 per d_v of a chunk (Psi set and clear), 8 per d_u (Gamma(u)
-              read + Psi lookup), 28 per member of T (edge ids, triangle
-              counts, out-list bounds, T store), 4 per out-list entry tested,
-              120 per edge (13-column row, P, |T|, edge id)
-      large-T pass: 16 per d_u + d_v, 28 per member of T, 4 per entry tested."""
+      pass K: 48 per member of out(a) (id, |T|, out-list bounds, two 8-byte
+              read-modify-write flushes), 4 per out-list entry scanned, 36 per
+              edge of H_a (|T| gather, two 8-byte read-modify-write atomics)
+      finish: 168 per edge (64 read: slot maps, endpoints, degrees, |T|, P of
+              both slots, x7, cross; 104 written: the 13-column row)"""
     return {
-        "k_pass_a": 8 * work["a_units"],
+        "k_pass_a": 8 * work["a_units"] + 16 * work["finish_edges"],
         "k_pass_c": 48 * work["c_wedges"],
-        "k_pass_b": 16 * work["b_group_deg"] + 8 * work["b_deg"] + 28 * work["b_T"] + 4 * work["b_probes"]
-        + 120 * work["b_edges"],
-        "k_pass_big": 16 * work["big_deg"] + 28 * work["big_T"] + 4 * work["big_probes"],
+        "k_pass_k": 48 * work["k_members"] + 4 * work["k_scan"] + 36 * work["k_local_edges"],
+        "k_finish": 168 * work["finish_edges"],
     }
 
 
@@ -445,7 +445,7 @@ def main():
             peak, peak_src = 6800.0, "fallback"
     ph_ms = {k: statistics.mean(p[k] for p in phases) for k in phases[0]}
     kernel_ms = {"k_pass_a": ph_ms["pass_a_triangles"], "k_pass_c": ph_ms["pass_c_cycles"],
-                 "k_pass_b": ph_ms["pass_b_cliques_finish"], "k_pass_big": ph_ms["pass_b_large_T"]}
+                 "k_pass_k": ph_ms["pass_k_cliques"], "k_finish": ph_ms["finish_columns"]}
     ab = algorithmic_bytes(work)
     kernels = {k: {"ms": kernel_ms[k], "algorithmic_bytes": ab[k],
                    "gbs": ab[k] / (kernel_ms[k] / 1000.0) / 1e9 if kernel_ms[k] > 0 else None,
@@ -462,7 +462,7 @@ def main():
             "config": {"workload": desc, "n": len(rp) - 1, "m": m, "per_edge_rows": "device",
                        "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas{world}"},
             "phases_ms": ph_ms, "work": work,
-            "roofline": roof, "clocks": clk.summary(), "gpu_launches": 4 * args.steps,
+            "roofline": roof, "clocks": clk.summary(), "gpu_launches": int(work["launches"]) * args.steps,
             "e2e": e2e}
     if not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(rp, ci, m)

@@ -129,20 +129,26 @@ gc_status gc_graph_csums(gc_graph g, uint64_t* lo, uint64_t* hi);
 
 /* Device time of each phase of the last gc_count_edge_graphlets, measured
  * with CUDA events on the graph's stream. ms: host array of
- * gc_phase_count() doubles. */
+ * gc_phase_count() doubles. Phases, in order: "pass_a_triangles" (Alg. 1),
+ * "pass_c_cycles" (4-cycles through each edge, Alg. 4/6), "pass_k_cliques"
+ * (4-cliques and cross terms, Alg. 3/5), "finish_columns" (Sec. 4.5 columns
+ * and sums), "derive" (Sec. 4.6), "copy_out". */
 int gc_phase_count(void);
 const char* gc_phase_name(int i);
 gc_status gc_graph_phase_ms(gc_graph g, double* ms);
 
 /* Units of work the kernels processed in the last gc_count_edge_graphlets on
  * g (host pointer, GC_NUM_WORK uint64), in this order:
- *   0 pass B sum of d_v over its chunks   1 pass B sum of d_u over its edges
- *   2 pass B sum of |T|                    3 pass B out-list entries tested (4-cliques)
- *   4 pass B edges                         5 large-T pass sum of d_u + d_v
- *   6 large-T pass sum of |T|              7 large-T pass entries tested
- *   8 pass C wedges h-x-o                  9 pass A sum of d_v + d_u
+ *   0 pass A (triangles): sum of d_v over v-groups plus d_u over their edges
+ *   1 pass C (4-cycles): wedges h-x-o
+ *   2 pass K (4-cliques): sum over lowest vertices a of |out(a)|
+ *   3 pass K: out-list entries scanned to build the induced subgraphs H_a
+ *   4 pass K: edges of the H_a (= triangles, each once)
+ *   5 pass K: bitmatrix words ANDed (edges of H_a x row words)
+ *   6 finish: edges whose columns were written
+ *   7 kernels launched by the count
  * Used to turn kernel times into algorithmic bytes per second. */
-#define GC_NUM_WORK 10
+#define GC_NUM_WORK 8
 gc_status gc_graph_work_counts(gc_graph g, uint64_t* out);
 
 /* Release the graph and all its device memory. NULL is accepted. */

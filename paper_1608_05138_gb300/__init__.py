@@ -37,8 +37,7 @@ EXPORTED = ["gc_last_error", "gc_graph_upload", "gc_graph_info", "gc_graph_edges
             "gc_graph_phase_ms", "gc_graph_free", "gc_batch_create", "gc_batch_submit",
             "gc_batch_flush", "gc_batch_poll", "gc_batch_destroy", "gc_edge_triangles_noalloc",
             "gc_graph_work_counts", "gc_batch_submit_many"]
-WORK_NAMES = ["b_group_deg", "b_deg", "b_T", "b_probes", "b_edges", "big_deg", "big_T", "big_probes",
-              "c_wedges", "a_units"]
+WORK_NAMES = ["a_units", "c_wedges", "k_members", "k_scan", "k_local_edges", "k_words", "finish_edges", "launches"]
 
 
 class GcError(RuntimeError):

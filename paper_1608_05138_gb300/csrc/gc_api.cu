@@ -305,7 +305,7 @@ gc_status gc_graph_upload(int32_t n, const int32_t* row_ptr, const int32_t* col_
   GC_CHECK(cudaMalloc(&g->d_csum, sizeof(unsigned long long) * (13 * 2 + 17 * 2)), "alloc sums");
   g->d_x = g->d_csum + 13 * 2;
   {
-    gc_status st2 = scratch_init(&g->sc, g->m, g->prep.n_units, n, s);
+    gc_status st2 = scratch_init(&g->sc, g->m, n, g->prep.kmax, s);
     if (st2 != GC_OK) { graph_release(g); return st2; }
   }
   for (auto& ev : g->ev) GC_CHECK(cudaEventCreate(&ev), "event create");
@@ -371,6 +371,7 @@ gc_status gc_count_edge_graphlets(gc_graph g, uint64_t* per_edge_out, uint64_t* 
   dg.eid = g->prep.eid;
   dg.out_ptr = g->prep.out_ptr;
   dg.out_idx = g->prep.out_idx;
+  dg.ocsr = g->prep.ocsr;
   dg.rev = g->prep.rev;
   dg.G = 1;
   dg.vgid = nullptr;
@@ -379,7 +380,10 @@ gc_status gc_count_edge_graphlets(gc_graph g, uint64_t* per_edge_out, uint64_t* 
   dg.gm = g->d_gm;
   dg.table_n = g->n;
   dg.ranked = true;
-  if ((st = run_count(dg, g->prep.units, g->prep.n_units, pe_dev, g->d_csum, g->d_x, &g->sc, s, g->ev)) != GC_OK)
+  KUnits ku;
+  ku.units = g->prep.kunits;
+  for (int t = 0; t <= kNumTiers; ++t) ku.tier_off[t] = g->prep.ktier_off[t];
+  if ((st = run_count(dg, g->prep.units, g->prep.n_units, ku, pe_dev, g->d_csum, g->d_x, &g->sc, s, g->ev)) != GC_OK)
     return st;
   unsigned long long hx[17 * 2 + 13 * 2];
   int32_t hstatus = 0;
@@ -395,7 +399,7 @@ gc_status gc_count_edge_graphlets(gc_graph g, uint64_t* per_edge_out, uint64_t* 
   GC_CHECK(cudaStreamSynchronize(s), "sync count");
 #undef GC_CHECK
   if (hstatus & kSpillOverflow) {
-    set_error("internal: triangle list exceeded its buffer");
+    set_error("internal: a pass-K unit exceeded its tier");
     return GC_ERR_CUDA;
   }
   if (hstatus & kInexact) {
@@ -435,14 +439,15 @@ gc_status gc_graph_work_counts(gc_graph g, uint64_t* out) {
   if (!g->counted) { set_error("graph not counted yet"); return GC_ERR_ARG; }
   static_assert(kNumWork == GC_NUM_WORK, "work counter count");
   for (int i = 0; i < kNumWork; ++i) out[i] = g->work[i];
+  out[kWorkLaunches] = (uint64_t)g->sc.launches;
   return GC_OK;
 }
 
 int gc_phase_count(void) { return kNumPhases; }
 
 const char* gc_phase_name(int i) {
-  static const char* names[kNumPhases] = {"pass_a_triangles", "pass_c_cycles", "pass_b_cliques_finish",
-                                          "pass_b_large_T", "derive", "copy_out"};
+  static const char* names[kNumPhases] = {"pass_a_triangles", "pass_c_cycles", "pass_k_cliques",
+                                          "finish_columns", "derive", "copy_out"};
   return (i >= 0 && i < kNumPhases) ? names[i] : "";
 }
 

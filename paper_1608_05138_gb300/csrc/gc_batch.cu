@@ -179,7 +179,7 @@ gc_status run_union(std::vector<PendingGraph*>& graphs, cudaStream_t s, Launch* 
     L->error = gc_last_error();
     goto out;
   }
-  if ((st = scratch_init(&sc, m, prep.n_units, table_n, s)) != GC_OK) {
+  if ((st = scratch_init(&sc, m, table_n, prep.kmax, s)) != GC_OK) {
     L->error = gc_last_error();
     goto out;
   }
@@ -193,6 +193,7 @@ gc_status run_union(std::vector<PendingGraph*>& graphs, cudaStream_t s, Launch* 
     dg.eid = prep.eid;
     dg.out_ptr = prep.out_ptr;
     dg.out_idx = prep.out_idx;
+    dg.ocsr = prep.ocsr;
     dg.rev = prep.rev;
     dg.G = G;
     dg.vgid = d_vgid;
@@ -201,7 +202,10 @@ gc_status run_union(std::vector<PendingGraph*>& graphs, cudaStream_t s, Launch* 
     dg.gm = d_gm;
     dg.table_n = table_n;
     dg.ranked = false;
-    if ((st = run_count(dg, prep.units, prep.n_units, nullptr, d_csum, d_x, &sc, s, nullptr)) != GC_OK) {
+    KUnits ku;
+    ku.units = prep.kunits;
+    for (int t = 0; t <= kNumTiers; ++t) ku.tier_off[t] = prep.ktier_off[t];
+    if ((st = run_count(dg, prep.units, prep.n_units, ku, nullptr, d_csum, d_x, &sc, s, nullptr)) != GC_OK) {
       L->error = gc_last_error();
       goto out;
     }

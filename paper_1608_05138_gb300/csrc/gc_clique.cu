@@ -1,0 +1,294 @@
+// gc_clique.cu -- pass K: the 4-clique step (Alg. 3/5) and the cross term of
+// the 4-cycle step, organised by the lowest vertex of every clique.
+//
+// Each 4-clique {a, b, c, d} has exactly one lowest-rank vertex a (rank =
+// (degree, id), the P3 orientation), and then b, c, d all lie in out(a), the
+// higher-rank neighbours of a. So the 4-cliques whose lowest vertex is a are
+// exactly the triangles of H_a, the subgraph induced on out(a), and the
+// triangles whose lowest vertex is a are exactly the edges of H_a. Both are
+// counted per edge of the original graph:
+//
+//   x7(a, b_i)   += #triangles of H_a through vertex i = 1/2 sum_j c_ij
+//   x7(b_i, b_j) += c_ij = |N_H(i) ∩ N_H(j)|          for every edge (i, j) of H_a
+//
+// and for the triangle {a, b_i, b_j} of every edge (i, j) of H_a the term
+// |T_(w,x)| + |T_(w,y)| - 2 of its third vertex w goes to each of its three
+// edges (x, y) -- summed, that is cross(e) = sum_{w in T_e} (|T_(w,u)| +
+// |T_(w,v)| - 2), the term that turns the 4-cycles through e into Alg. 4/6's
+// induced count x10 (see gc_count.cu, finish).
+//
+// Per unit a (one CTA): out(a) (k ids, ascending) is loaded with the |T| of
+// its edges, a hash table maps an id to its position i in out(a) (Psi of
+// Alg. 1 restricted to out(a)), and H_a is built as a k x k bitmatrix (rows
+// padded to an odd word stride, so that lanes reading different rows hit
+// different banks). Phase 1 scans out(b) for every b in out(a) and sets the
+// bits of the edges found; phase 2 scans again, and for every edge (i, j) of
+// H_a (met once, from its lower-rank end) counts c_ij with popcounts over the
+// two rows -- Alg. 5's "count adjacent members of T" as bit operations, with
+// the Psi reset of Alg. 5 replaced by counting each clique from one vertex.
+// Edges of H_a found by a warp go through a 64-entry ring so that every lane
+// of the popcount loop has an edge.
+//
+// Tiers by k: the bitmatrix (k * ((k+31)/32 | 1) words) stays in shared
+// memory for k <= 1024; above that the same code runs on a per-CTA global
+// buffer. Work per unit is about sum_{b in out(a)} |out(b)| (triangle
+// listing) plus (#edges of H_a) * k / 32 words.
+#include <cuda_runtime.h>
+
+#include "gc_internal.h"
+
+namespace gc {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__host__ __device__ constexpr int row_stride(int k) { return ((k + 31) >> 5) | 1; }
+
+__device__ __forceinline__ uint32_t khash(int32_t key, int bits) {
+  return ((uint32_t)key * 0x9E3779B1u) >> (32 - bits);
+}
+
+// Byte offsets of the per-unit arrays for a capacity of cap members.
+struct KLayout {
+  size_t vx7, vcr, ids, ta, hash, rows, total;
+  int hcap;
+  __host__ __device__ static size_t up16(size_t x) { return (x + 15) & ~(size_t)15; }
+  __host__ __device__ explicit KLayout(int cap) {
+    int hb = 1;
+    while ((1 << hb) < 2 * cap) ++hb;
+    hcap = 1 << hb;
+    size_t o = 0;
+    vx7 = o; o = up16(o + 8 * (size_t)cap);
+    vcr = o; o = up16(o + 8 * (size_t)cap);
+    ids = o; o = up16(o + 4 * (size_t)cap);
+    ta = o; o = up16(o + 4 * (size_t)cap);
+    hash = o; o = up16(o + 4 * (size_t)hcap);
+    rows = o; o = up16(o + 4 * (size_t)cap * (size_t)row_stride(cap));
+    total = o;
+  }
+};
+
+template <int kCap, int kThreads>
+__global__ void __launch_bounds__(kThreads, 65536 / (kThreads * 64)) k_pass_k(DevGraph g, CountArgs a, int tier) {
+  constexpr int kW = kThreads / 32;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int32_t s_unit, s_cur1, s_cur2;
+  __shared__ int32_t s_qj[kW][64], s_qq[kW][64];
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int cap = kCap ? kCap : a.kbuf_cap;
+  const KLayout L(cap);
+  unsigned char* base = kCap ? smem : a.kbuf + (size_t)blockIdx.x * a.kbuf_stride;
+  unsigned long long* vx7 = reinterpret_cast<unsigned long long*>(base + L.vx7);
+  unsigned long long* vcr = reinterpret_cast<unsigned long long*>(base + L.vcr);
+  int32_t* ids = reinterpret_cast<int32_t*>(base + L.ids);
+  int32_t* ta = reinterpret_cast<int32_t*>(base + L.ta);
+  int32_t* hash = reinterpret_cast<int32_t*>(base + L.hash);
+  uint32_t* rows = reinterpret_cast<uint32_t*>(base + L.rows);
+  int32_t* qj = s_qj[warp];
+  int32_t* qq = s_qq[warp];
+
+  const int32_t u0 = a.ktier_off[tier], u1 = a.ktier_off[tier + 1];
+  int32_t* cursor = a.cursor + 2 + tier;
+  long long w_members = 0, w_scan = 0, w_edges = 0, w_words = 0;  // per warp, lane 0
+
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      s_unit = u0 + atomicAdd(cursor, 1);
+      s_cur1 = 0;
+      s_cur2 = 0;
+    }
+    __syncthreads();
+    const int32_t ui = s_unit;
+    if (ui >= u1) break;
+    const int32_t av = a.kunits[ui];
+    const int32_t ob = g.out_ptr[av];
+    const int32_t k = g.out_ptr[av + 1] - ob;
+    if (k > cap) {  // cannot happen: units are binned by k
+      if (threadIdx.x == 0) atomicOr(a.status, (int32_t)kSpillOverflow);
+      continue;
+    }
+    const int W = (k + 31) >> 5, S = W | 1;
+    int hbits = 1;
+    while ((1 << hbits) < 2 * k) ++hbits;
+    const uint32_t hmask = (1u << hbits) - 1u;
+
+    for (int32_t i = threadIdx.x; i < k; i += kThreads) {
+      ids[i] = g.out_idx[ob + i];
+      ta[i] = a.trio[ob + i];
+      vx7[i] = 0ull;
+      vcr[i] = 0ull;
+    }
+    for (int32_t i = threadIdx.x; i <= (int32_t)hmask; i += kThreads) hash[i] = 0;
+    for (int32_t i = threadIdx.x; i < k * S; i += kThreads) rows[i] = 0u;
+    if (threadIdx.x == 0) w_members += k;
+    __syncthreads();
+    for (int32_t i = threadIdx.x; i < k; i += kThreads) {  // Psi: id -> 1 + position in out(a)
+      uint32_t h = khash(ids[i], hbits);
+      while (atomicCAS(&hash[h], 0, i + 1) != 0) h = (h + 1) & hmask;  // table at most half full
+    }
+    __syncthreads();
+    const int32_t cmax = ids[k - 1];
+    auto lookup = [&](int32_t c) -> int32_t {
+      uint32_t h = khash(c, hbits);
+      for (;;) {
+        const int32_t s = hash[h];
+        if (s == 0) return -1;
+        if (ids[s - 1] == c) return s - 1;
+        h = (h + 1) & hmask;
+      }
+    };
+
+    // Phase 1: the edges of H_a, as symmetric bits.
+    for (;;) {
+      int32_t i = 0;
+      if (lane == 0) i = atomicAdd(&s_cur1, 1);
+      i = __shfl_sync(kFull, i, 0);
+      if (i >= k) break;
+      const int32_t b = ids[i];
+      const int32_t bb = g.out_ptr[b], be = g.out_ptr[b + 1];
+      for (int32_t q0 = bb; q0 < be; q0 += 32) {
+        const int32_t q = q0 + lane;
+        const int32_t c = q < be ? g.out_idx[q] : 0x7fffffff;
+        if (__shfl_sync(kFull, c, 0) > cmax) break;  // out(b) ascends: nothing further is in out(a)
+        if (lane == 0) w_scan += min(32, be - q0);
+        const int32_t j = c <= cmax ? lookup(c) : -1;
+        if (j >= 0) {
+          atomicOr(&rows[i * S + (j >> 5)], 1u << (j & 31));
+          atomicOr(&rows[j * S + (i >> 5)], 1u << (i & 31));
+        }
+      }
+    }
+    __syncthreads();
+
+    // Phase 2: per edge (i, j) of H_a, c_ij and the cross terms.
+    for (;;) {
+      int32_t i = 0;
+      if (lane == 0) i = atomicAdd(&s_cur2, 1);
+      i = __shfl_sync(kFull, i, 0);
+      if (i >= k) break;
+      const int32_t b = ids[i];
+      const int32_t bb = g.out_ptr[b], be = g.out_ptr[b + 1];
+      const int32_t ti = ta[i];
+      const uint32_t* ri = rows + i * S;
+      unsigned long long ax7 = 0, acr = 0;
+      uint32_t head = 0, tail = 0;
+      auto process = [&](int32_t j, int32_t q) {
+        const uint32_t* rj = rows + j * S;
+        int c4 = 0;
+        for (int w = 0; w < W; ++w) c4 += __popc(ri[w] & rj[w]);
+        const int32_t tj = ta[j];
+        const int32_t tij = a.trio[q];
+        if (c4) atomicAdd(&a.x7o[q], (unsigned long long)c4);
+        atomicAdd(&a.cro[q], (unsigned long long)(ti + tj - 2));
+        if (c4) atomicAdd(&vx7[j], (unsigned long long)c4);
+        atomicAdd(&vcr[j], (unsigned long long)(ti + tij - 2));
+        ax7 += (unsigned long long)c4;
+        acr += (unsigned long long)(tj + tij - 2);
+      };
+      for (int32_t q0 = bb; q0 < be; q0 += 32) {
+        const int32_t q = q0 + lane;
+        const int32_t c = q < be ? g.out_idx[q] : 0x7fffffff;
+        if (__shfl_sync(kFull, c, 0) > cmax) break;
+        const int32_t j = c <= cmax ? lookup(c) : -1;
+        const unsigned hit = __ballot_sync(kFull, j >= 0);
+        if (j >= 0) {
+          const uint32_t pos = (tail + __popc(hit & ((1u << lane) - 1u))) & 63u;
+          qj[pos] = j;
+          qq[pos] = q;
+        }
+        tail += __popc(hit);
+        __syncwarp();
+        if (tail - head >= 32) {
+          const uint32_t pos = (head + lane) & 63u;
+          process(qj[pos], qq[pos]);
+          head += 32;
+          if (lane == 0) {
+            w_edges += 32;
+            w_words += 32LL * W;
+          }
+          __syncwarp();
+        }
+      }
+      const uint32_t left = tail - head;
+      if (lane < (int)left) {
+        const uint32_t pos = (head + lane) & 63u;
+        process(qj[pos], qq[pos]);
+      }
+      if (lane == 0) {
+        w_edges += left;
+        w_words += (long long)left * W;
+      }
+      __syncwarp();
+      for (int o = 16; o; o >>= 1) {
+        ax7 += __shfl_xor_sync(kFull, ax7, o);
+        acr += __shfl_xor_sync(kFull, acr, o);
+      }
+      if (lane == 0) {
+        if (ax7) atomicAdd(&vx7[i], ax7);
+        if (acr) atomicAdd(&vcr[i], acr);
+      }
+    }
+    __syncthreads();
+
+    // Edges (a, b_i): triangles of H_a through i (each counted from both of
+    // its edges at i, hence the halving) and the cross terms gathered above.
+    for (int32_t i = threadIdx.x; i < k; i += kThreads) {
+      const unsigned long long x = vx7[i], c = vcr[i];
+      if (x) atomicAdd(&a.x7o[ob + i], x >> 1);
+      if (c) atomicAdd(&a.cro[ob + i], c);
+    }
+  }
+  if (lane == 0) {
+    if (w_members) atomicAdd(a.work + kWorkKMembers, (unsigned long long)w_members);
+    if (w_scan) atomicAdd(a.work + kWorkKScan, (unsigned long long)w_scan);
+    if (w_edges) atomicAdd(a.work + kWorkKLocalEdges, (unsigned long long)w_edges);
+    if (w_words) atomicAdd(a.work + kWorkKWords, (unsigned long long)w_words);
+  }
+}
+
+template <int kCap, int kThreads>
+gc_status launch_tier(const DevGraph& g, const CountArgs& a, int tier, cudaStream_t s, int* launches) {
+  const int32_t units = a.ktier_off[tier + 1] - a.ktier_off[tier];
+  if (units <= 0) return GC_OK;
+  const size_t smem = kCap ? KLayout(kCap).total : 0;
+  auto kern = k_pass_k<kCap, kThreads>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return cuda_fail(e, "k_pass_k attribute");
+  int grid = 0;
+  if (kCap) {
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
+    if (e != cudaSuccess) return cuda_fail(e, "k_pass_k occupancy");
+    grid = (per_sm > 0 ? per_sm : 1) * (count_grid_size() / kCtasPerSm);
+  } else {
+    grid = a.kbuf_ctas;
+  }
+  if (grid > units) grid = units;
+  if (grid < 1) return GC_OK;
+  kern<<<grid, kThreads, smem, s>>>(g, a, tier);
+  ++*launches;
+  e = cudaGetLastError();
+  return e == cudaSuccess ? GC_OK : cuda_fail(e, "k_pass_k");
+}
+
+}  // namespace
+
+size_t kbuf_bytes(int32_t cap) { return cap > 0 ? KLayout(cap).total : 0; }
+
+gc_status run_pass_k(const DevGraph& g, const CountArgs& a, cudaStream_t s, int* launches) {
+  gc_status st;
+  if (a.ktier_off[kTierGlobal + 1] > a.ktier_off[kTierGlobal]) {
+    if (!a.kbuf || a.kbuf_ctas < 1) {
+      set_error("internal: pass K global buffers missing");
+      return GC_ERR_CUDA;
+    }
+    if ((st = launch_tier<0, 1024>(g, a, kTierGlobal, s, launches)) != GC_OK) return st;
+  }
+  if ((st = launch_tier<1024, 1024>(g, a, kTier1024, s, launches)) != GC_OK) return st;
+  if ((st = launch_tier<512, 512>(g, a, kTier512, s, launches)) != GC_OK) return st;
+  return launch_tier<256, 512>(g, a, kTier256, s, launches);
+}
+
+}  // namespace gc

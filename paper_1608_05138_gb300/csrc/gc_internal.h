@@ -24,8 +24,9 @@ struct DevGraph {
   const int32_t* ci;       // [2m] column ids (global ids), rows ascending
   const int32_t* deg;      // [n]
   const int32_t* eid;      // [2m] slot -> edge id
-  const int32_t* out_ptr;  // [n + 1] degree-oriented out-lists (Pi order)
-  const int32_t* out_idx;  // [m]
+  const int32_t* out_ptr;  // [n + 1] degree-oriented out-lists (P3 orientation)
+  const int32_t* out_idx;  // [m] ascending ids within each list; position = out-slot
+  const int32_t* ocsr;     // [m] out-slot -> CSR slot of the same direction (row of the owner)
   const int32_t* rev;      // [2m] slot of (y, x) for the slot of (x, y)
   int32_t G;               // graphs in the union (>= 1)
   const int32_t* vgid;     // [n] graph of each vertex, or nullptr when G == 1
@@ -36,23 +37,30 @@ struct DevGraph {
   bool ranked;             // ids are the (degree, id) ranks and rows ascend
 };
 
+// Pass K (4-cliques and cross terms by lowest vertex) runs in tiers by the
+// out-degree k of the lowest vertex: the local bitmatrix of out(a) lives in
+// shared memory up to k = 1024 and in a per-CTA global buffer above.
+enum KTier { kTierGlobal = 0, kTier1024, kTier512, kTier256, kNumTiers };
+constexpr int kTierCap[kNumTiers] = {0, 1024, 512, 256};
+
 // Counting configuration chosen on the host.
 struct CountArgs {
-  const int32_t* units;    // pass A: v-groups (high endpoints), heaviest bin first
+  const int32_t* units;    // passes A and C: v-groups (high endpoints), heaviest bin first
   int32_t n_units;
-  const int32_t* chunks;   // pass B: [n_chunks][3] = (v, first slot, end slot) of Gamma(v)
-  const int32_t* n_chunks; // device count of chunks
-  int32_t* cursor;         // work-stealing cursor (device int, zeroed before launch)
+  const int32_t* kunits;   // pass K: lowest vertices a with |out(a)| >= 2, tiers in KTier order
+  int32_t ktier_off[kNumTiers + 1];  // tier t = kunits[ktier_off[t] .. ktier_off[t + 1])
+  int32_t* cursor;         // work-stealing cursors (device ints, zeroed before each launch)
   uint32_t* tables;        // global Psi tables (grid x table_n) or nullptr (shared memory)
-  int32_t* tri;            // [m] per-edge |T| (written by pass A, read by pass B)
+  int32_t* tri;            // [m] per-edge |T| by edge id (pass A)
+  int32_t* trio;           // [m] |T| by out-slot
   unsigned long long* P;   // [2m] per slot: 4-cycles through its edge counted at that slot
                            // (pass C, zeroed before); an edge's count = sum of its two slots
-  int32_t* tbuf;           // large-T edges: per-CTA T buffer (big grid x tbuf_len)
-  int32_t tbuf_len;
-  int32_t* deferred;       // [deferred_cap][2] (v, slot of u in Gamma(v)) of large-T edges
-  int32_t deferred_cap;
-  int32_t* n_deferred;     // device counter of deferred edges
-  int32_t big_t;           // |T| above which an edge is deferred to k_pass_big
+  unsigned long long* x7o;   // [m] per out-slot: 4-cliques through the edge (pass K)
+  unsigned long long* cro;   // [m] per out-slot: sum over T of (|T_(a,u)| + |T_(a,v)| - 2) (pass K)
+  unsigned char* kbuf;     // global-tier per-CTA buffers (kbuf_ctas x kbuf_stride bytes)
+  size_t kbuf_stride;
+  int32_t kbuf_ctas;
+  int32_t kbuf_cap;        // largest k the global tier holds
   uint64_t* per_edge;      // [m][13] device pointer or nullptr
   unsigned long long* csum;  // [G][13][2] 128-bit unrestricted counts (lo, hi)
   int32_t* status;         // device status word (0 = ok)
@@ -62,63 +70,60 @@ struct CountArgs {
 // Work counters (units the kernels processed; bench.py turns them into
 // algorithmic bytes).
 enum Work {
-  kWorkBGroupDeg = 0,  // pass B: sum of d_v over chunks (Psi set + clear)
-  kWorkBDeg,           // pass B: sum of d_u over its edges (Gamma(u) scan)
-  kWorkBT,             // pass B: sum of |T|
-  kWorkBProbe,         // pass B: out-list entries tested against T
-  kWorkBEdges,         // pass B: edges finished
-  kWorkBigDeg,         // large-T pass: sum of d_v + d_u
-  kWorkBigT,           // large-T pass: sum of |T|
-  kWorkBigProbe,       // large-T pass: entries tested
+  kWorkAUnits = 0,     // pass A: sum of d_v + sum of d_u
   kWorkCWedge,         // pass C: wedges h-x-o
-  kWorkAUnits,         // pass A: sum of d_v + sum of d_u
+  kWorkKMembers,       // pass K: sum over units of |out(a)|
+  kWorkKScan,          // pass K: out-list entries scanned to build the local graphs
+  kWorkKLocalEdges,    // pass K: local edges = triangles (each once)
+  kWorkKWords,         // pass K: bitmatrix words ANDed (local edges x row words)
+  kWorkFinishEdges,    // finish: edges written
+  kWorkLaunches,       // kernels launched by the count (counted on the host)
   kNumWork
 };
 
 enum Status : int32_t { kOk = 0, kSpillOverflow = 1, kInexact = 2, kTimeout = 4 };
 
-constexpr int kBlock = 512;            // threads per CTA of the counting kernels
+constexpr int kBlock = 512;            // threads per CTA of passes A and C
 constexpr int kCtasPerSm = 2;          // resident CTAs per SM of the persistent grids
 constexpr int kWarps = kBlock / 32;
-constexpr int kTcap = 1024;            // per-warp T list in shared memory (entries)
 constexpr int kSmallN = 512;           // graphs up to this many vertices use the bitmatrix kernel
-// Edges whose |T| exceeds big_t (default 1024, environment GC_BIG_T in
-// [16, kTcap]) are done by a whole CTA (k_pass_big).
-int big_t_threshold();
 constexpr int kSmemTableMax = 4096;    // Psi tables up to this many vertices live in shared memory
-constexpr int kBigBlock = 1024;        // threads per CTA for large-T edges
-constexpr int kBigWarps = kBigBlock / 32;
-constexpr int kBigWords = 49152;       // shared bitmap words (1.5 M ids) for T of a large edge
 
 // Phases timed with CUDA events.
-enum Phase { kPhasePassA = 0, kPhasePassC, kPhasePassB, kPhaseBig, kPhaseDerive, kPhaseCopy, kNumPhases };
+enum Phase { kPhasePassA = 0, kPhasePassC, kPhasePassK, kPhaseFinish, kPhaseDerive, kPhaseCopy, kNumPhases };
 
 // Device scratch of one count (lazily grown; owned by a graph handle or by
 // one batch launch).
 struct Scratch {
   int32_t* tri = nullptr;            // [m]
-  unsigned long long* P = nullptr;   // [m]
-  int32_t* chunks = nullptr;         // [chunk_capacity][3]
-  int32_t* off = nullptr;            // [n_units + 1]
-  int32_t* misc = nullptr;           // cursor, status, max |T|, #large-T, deferred counter
-  unsigned long long* total = nullptr;
+  int32_t* trio = nullptr;           // [m]
+  unsigned long long* P = nullptr;   // [2m]
+  unsigned long long* x7o = nullptr; // [m]
+  unsigned long long* cro = nullptr; // [m]
+  int32_t* misc = nullptr;           // cursors, status
   uint32_t* tables = nullptr;        // count_grid_size() x table_n
   size_t tables_n = 0;
-  int32_t* tbuf = nullptr;           // big_grid_size() x tbuf_len
-  int32_t tbuf_len = 0;
-  int32_t* deferred = nullptr;       // [deferred_cap][2]
-  int32_t deferred_cap = 0;
+  unsigned char* kbuf = nullptr;     // pass K global tier
+  size_t kbuf_stride = 0;
+  int32_t kbuf_ctas = 0;
+  int32_t kbuf_cap = 0;
   unsigned long long* work = nullptr;  // [kNumWork]
+  int32_t launches = 0;              // kernels launched by the last run_count
 };
-// Allocates what does not depend on the data (stream-ordered).
-gc_status scratch_init(Scratch* sc, int32_t m, int32_t n_units, int32_t table_n, cudaStream_t s);
+// Allocates the scratch of a graph with m edges, Psi tables of table_n
+// vertices and largest out-degree kmax (stream-ordered).
+gc_status scratch_init(Scratch* sc, int32_t m, int32_t table_n, int32_t kmax, cudaStream_t s);
 void scratch_free(Scratch* sc, cudaStream_t s);
-// The whole count: passes A, C, B (+ large-T edges), derive. csum [G][13][2]
-// and x [G][17][2] are device arrays; ev (optional) receives kNumPhases + 1
-// events. Returns after the derive is queued (no final sync).
-gc_status run_count(const DevGraph& g, const int32_t* units, int32_t n_units, uint64_t* per_edge,
-                    unsigned long long* csum, unsigned long long* x, Scratch* sc, cudaStream_t s,
-                    cudaEvent_t* ev);
+// The whole count: passes A, C, K, finish, derive. csum [G][13][2] and
+// x [G][17][2] are device arrays; ev (optional) receives kNumPhases + 1
+// events. Returns after the derive is queued (no host synchronisation).
+struct KUnits {
+  const int32_t* units;
+  int32_t tier_off[kNumTiers + 1];
+};
+gc_status run_count(const DevGraph& g, const int32_t* units, int32_t n_units, const KUnits& ku,
+                    uint64_t* per_edge, unsigned long long* csum, unsigned long long* x, Scratch* sc,
+                    cudaStream_t s, cudaEvent_t* ev);
 
 // ---- host helpers (gc_api.cu) ----
 void set_error(const std::string& msg);
@@ -136,6 +141,10 @@ struct PrepBuffers {
   int32_t dmax = 0;
   long long* S = nullptr;  // [n] sum of neighbour degrees (Psi build cost of a v-group)
   int32_t* rev = nullptr;  // [2m] slot of the reverse direction of every slot
+  int32_t* ocsr = nullptr;  // [m] out-slot -> CSR slot
+  int32_t* kunits = nullptr;  // pass K units (see CountArgs::kunits)
+  int32_t ktier_off[kNumTiers + 1] = {0, 0, 0, 0, 0};
+  int32_t kmax = 0;         // largest out-degree
 };
 // Builds degrees, edge ids, the edge list, degree-oriented out-lists and the
 // binned unit list on `stream`. vgid may be nullptr (single graph).
@@ -155,28 +164,17 @@ gc_status run_small_graphs(const int32_t* rp, const int64_t* voff, const int32_t
                            const int32_t* order, int32_t G, int32_t* cursor, unsigned long long* csum,
                            cudaStream_t s);
 
-// ---- counting (gc_count.cu) ----
+// ---- counting (gc_count.cu: passes A, C, derive; gc_clique.cu: pass K, finish) ----
 int count_grid_size();
 gc_status run_pass_a(const DevGraph& g, const CountArgs& a, cudaStream_t s);
-gc_status run_pass_b(const DevGraph& g, const CountArgs& a, cudaStream_t s);
 gc_status run_pass_c(const DevGraph& g, const CountArgs& a, cudaStream_t s);
-gc_status run_pass_big(const DevGraph& g, const CountArgs& a, int32_t n_deferred, cudaStream_t s);
-int big_grid_size();
 gc_status run_derive(const DevGraph& g, const unsigned long long* csum, unsigned long long* x,
                      int32_t* status, cudaStream_t s);
-gc_status run_max_tri(const int32_t* tri, int32_t m, int32_t* d_out, cudaStream_t s);
-// Splits v-groups into edge chunks of balanced estimated work (needs |T| per
-// edge from pass A). chunks must hold (n_units + 8 * grid + 1) triples and
-// off n_units + 1 ints; off[n_units] receives the number of chunks.
-gc_status run_make_chunks(const DevGraph& g, const int32_t* units, int32_t n_units,
-                          const int32_t* tri, int32_t* chunks, int32_t* off,
-                          unsigned long long* total_dev, int32_t* n_big_dev, int32_t big_t, cudaStream_t s);
-// Target chunks per CTA of the persistent grid (environment GC_CHUNK_FACTOR,
-// default 8, range 1..256).
-int chunk_factor();
-inline size_t chunk_capacity(int32_t n_units) {
-  return (size_t)n_units + (size_t)chunk_factor() * (size_t)count_grid_size() + 1;
-}
+gc_status run_trio(const DevGraph& g, const CountArgs& a, cudaStream_t s);
+gc_status run_pass_k(const DevGraph& g, const CountArgs& a, cudaStream_t s, int* launches);
+gc_status run_finish(const DevGraph& g, const CountArgs& a, cudaStream_t s);
+// Bytes of one global-tier buffer for out-degrees up to cap.
+size_t kbuf_bytes(int32_t cap);
 // Unit ordering key (environment GC_ORDER): 0 = vol (default: d_v + sum of
 // neighbour degrees, heaviest bin first), 1 = degree d_v, 2 = none (vertex id).
 int order_key();

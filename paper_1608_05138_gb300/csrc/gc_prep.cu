@@ -17,6 +17,8 @@
 //     (a vertex analogue of the vol ordering of Table 4).
 #include <cuda_runtime.h>
 
+#include <cstdlib>
+#include <cstring>
 #include <vector>
 
 #include "gc_internal.h"
@@ -54,7 +56,7 @@ __global__ void k_deg_up(int32_t n, const int32_t* __restrict__ rp, const int32_
 // maximum degree.
 __global__ void k_out_cnt(int32_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                           const int32_t* __restrict__ deg, int32_t* __restrict__ out_cnt,
-                          long long* __restrict__ S, int32_t* __restrict__ dmax) {
+                          long long* __restrict__ S, int32_t* __restrict__ dmax, int32_t* __restrict__ kmax) {
   const int lane = threadIdx.x & 31;
   const int warps = (gridDim.x * blockDim.x) >> 5;
   for (int32_t x = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < n; x += warps) {
@@ -74,6 +76,7 @@ __global__ void k_out_cnt(int32_t n, const int32_t* __restrict__ rp, const int32
       out_cnt[x] = c;
       S[x] = s;
       if (e - b > 0) atomicMax(dmax, e - b);
+      if (c > 0) atomicMax(kmax, c);
     }
   }
 }
@@ -83,7 +86,8 @@ __global__ void k_edges(int32_t n, const int32_t* __restrict__ rp, const int32_t
                         const int32_t* __restrict__ deg, const int32_t* __restrict__ up,
                         const int32_t* __restrict__ upoff, const int32_t* __restrict__ out_ptr,
                         int32_t* __restrict__ eid, int32_t* __restrict__ uv,
-                        int32_t* __restrict__ out_idx, int32_t* __restrict__ rev, bool write_ids) {
+                        int32_t* __restrict__ out_idx, int32_t* __restrict__ ocsr, int32_t* __restrict__ rev,
+                        bool write_ids) {
   const int lane = threadIdx.x & 31;
   const int warps = (gridDim.x * blockDim.x) >> 5;
   for (int32_t x = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < n; x += warps) {
@@ -114,7 +118,11 @@ __global__ void k_edges(int32_t n, const int32_t* __restrict__ rp, const int32_t
         eid[p] = id;
       }
       unsigned mask = __ballot_sync(0xffffffffu, is_out);
-      if (is_out) out_idx[o + __popc(mask & ((1u << lane) - 1u))] = y;
+      if (is_out) {
+        const int32_t os = o + __popc(mask & ((1u << lane) - 1u));
+        out_idx[os] = y;
+        ocsr[os] = p;
+      }
       o += __popc(mask);
     }
   }
@@ -171,6 +179,28 @@ __global__ void k_bin_scatter(int32_t n, const int32_t* __restrict__ deg,
       units[pos] = v;
     }
   }
+}
+
+// Pass K units: every vertex a with |out(a)| = k >= 2 (a triangle needs two
+// higher-rank neighbours), binned by ceil(log2 k) and listed largest bin
+// first, so that the tiers of pass K (k > 1024, <= 1024, <= 512, <= 256) are
+// contiguous ranges of the list.
+__device__ __forceinline__ int kbin_of(int32_t k) { return 32 - __clz(k - 1); }
+
+__global__ void k_kbin_hist(int32_t n, const int32_t* __restrict__ out_cnt, int32_t* __restrict__ hist) {
+  __shared__ int32_t h[32];
+  if (threadIdx.x < 32) h[threadIdx.x] = 0;
+  __syncthreads();
+  for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+    if (out_cnt[v] >= 2) atomicAdd(&h[kbin_of(out_cnt[v])], 1);
+  __syncthreads();
+  if (threadIdx.x < 32 && h[threadIdx.x]) atomicAdd(&hist[threadIdx.x], h[threadIdx.x]);
+}
+
+__global__ void k_kbin_scatter(int32_t n, const int32_t* __restrict__ out_cnt, int32_t* __restrict__ cursor,
+                               int32_t* __restrict__ units) {
+  for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+    if (out_cnt[v] >= 2) units[atomicAdd(&cursor[kbin_of(out_cnt[v])], 1)] = v;
 }
 
 // ---- exclusive scan of int32 (totals fit int32) ----
@@ -274,6 +304,17 @@ int grid_for(int64_t work, int block) {
 
 }  // namespace
 
+int order_key() {
+  static int v = [] {
+    const char* e = getenv("GC_ORDER");
+    if (!e) return 0;
+    if (!strcmp(e, "deg")) return 1;
+    if (!strcmp(e, "none")) return 2;
+    return 0;
+  }();
+  return v;
+}
+
 gc_status exclusive_scan(int32_t n, const int32_t* in, int32_t* out, cudaStream_t s) {
   if (n == 0) {
     cudaError_t e = cudaMemsetAsync(out, 0, sizeof(int32_t), s);
@@ -300,6 +341,8 @@ void free_prep(PrepBuffers* p, cudaStream_t s) {
   if (p->units) cudaFreeAsync(p->units, s);
   if (p->S) cudaFreeAsync(p->S, s);
   if (p->rev) cudaFreeAsync(p->rev, s);
+  if (p->ocsr) cudaFreeAsync(p->ocsr, s);
+  if (p->kunits) cudaFreeAsync(p->kunits, s);
   *p = PrepBuffers();
 }
 
@@ -329,23 +372,26 @@ gc_status prepare_graph(int32_t n, int32_t m, const int32_t* d_rp, const int32_t
   GC_TRY(cudaMallocAsync(&P.out_ptr, sizeof(int32_t) * ((int64_t)n + 1), s), "alloc out_ptr");
   GC_TRY(cudaMallocAsync(&P.out_idx, sizeof(int32_t) * (m > 0 ? m : 1), s), "alloc out_idx");
   GC_TRY(cudaMallocAsync(&P.units, sizeof(int32_t) * (n > 0 ? n : 1), s), "alloc units");
+  GC_TRY(cudaMallocAsync(&P.ocsr, sizeof(int32_t) * (m > 0 ? m : 1), s), "alloc ocsr");
+  GC_TRY(cudaMallocAsync(&P.kunits, sizeof(int32_t) * (n > 0 ? n : 1), s), "alloc kunits");
   GC_TRY(cudaMallocAsync(&up, sizeof(int32_t) * (n > 0 ? n : 1), s), "alloc up");
   GC_TRY(cudaMallocAsync(&upoff, sizeof(int32_t) * ((int64_t)n + 1), s), "alloc upoff");
   GC_TRY(cudaMallocAsync(&out_cnt, sizeof(int32_t) * (n > 0 ? n : 1), s), "alloc out_cnt");
   GC_TRY(cudaMallocAsync(&P.S, sizeof(long long) * (n > 0 ? n : 1), s), "alloc S");
   S = P.S;
-  GC_TRY(cudaMallocAsync(&dmax, sizeof(int32_t) * 65, s), "alloc dmax");
+  // [0] max degree, [1..64] v-group bins, [65] max out-degree, [66..97] pass-K bins
+  GC_TRY(cudaMallocAsync(&dmax, sizeof(int32_t) * 98, s), "alloc dmax");
   hist = dmax + 1;
-  GC_TRY(cudaMemsetAsync(dmax, 0, sizeof(int32_t) * 65, s), "memset");
+  GC_TRY(cudaMemsetAsync(dmax, 0, sizeof(int32_t) * 98, s), "memset");
   if (n > 0) {
     k_deg_up<<<grid_for(n, 256), 256, 0, s>>>(n, d_rp, d_ci, P.deg, up);
     GC_TRY(cudaGetLastError(), "k_deg_up");
     if ((st = exclusive_scan(n, up, upoff, s)) != GC_OK) goto fail;
-    k_out_cnt<<<grid_for((int64_t)n * 32, 256), 256, 0, s>>>(n, d_rp, d_ci, P.deg, out_cnt, S, dmax);
+    k_out_cnt<<<grid_for((int64_t)n * 32, 256), 256, 0, s>>>(n, d_rp, d_ci, P.deg, out_cnt, S, dmax, dmax + 65);
     GC_TRY(cudaGetLastError(), "k_out_cnt");
     if ((st = exclusive_scan(n, out_cnt, P.out_ptr, s)) != GC_OK) goto fail;
     k_edges<<<grid_for((int64_t)n * 32, 256), 256, 0, s>>>(n, d_rp, d_ci, P.deg, up, upoff,
-                                                            P.out_ptr, P.eid, P.uv, P.out_idx, P.rev,
+                                                            P.out_ptr, P.eid, P.uv, P.out_idx, P.ocsr, P.rev,
                                                             d_eid_given == nullptr);
     GC_TRY(cudaGetLastError(), "k_edges");
     if (d_eid_given) {
@@ -354,11 +400,30 @@ gc_status prepare_graph(int32_t n, int32_t m, const int32_t* d_rp, const int32_t
     }
     k_bin_hist<<<grid_for(n, 256), 256, 0, s>>>(n, P.deg, out_cnt, S, hist, order_key());
     GC_TRY(cudaGetLastError(), "k_bin_hist");
+    k_kbin_hist<<<grid_for(n, 256), 256, 0, s>>>(n, out_cnt, dmax + 66);
+    GC_TRY(cudaGetLastError(), "k_kbin_hist");
     {
-      int32_t h[65];
+      int32_t h[98];
       GC_TRY(cudaMemcpyAsync(h, dmax, sizeof(h), cudaMemcpyDeviceToHost, s), "copy hist");
       GC_TRY(cudaStreamSynchronize(s), "sync hist");
       P.dmax = h[0];
+      P.kmax = h[65];
+      {  // pass-K units, largest bin first; tier boundaries at k = 1024, 512, 256
+        int32_t kc[32];
+        int32_t acc = 0;
+        for (int b = 31; b >= 0; --b) {
+          if (b == 10) P.ktier_off[kTier1024] = acc;
+          if (b == 9) P.ktier_off[kTier512] = acc;
+          if (b == 8) P.ktier_off[kTier256] = acc;
+          kc[b] = acc;
+          acc += h[66 + b];
+        }
+        P.ktier_off[kTierGlobal] = 0;
+        P.ktier_off[kNumTiers] = acc;
+        GC_TRY(cudaMemcpyAsync(dmax + 66, kc, sizeof(kc), cudaMemcpyHostToDevice, s), "copy k cursors");
+        k_kbin_scatter<<<grid_for(n, 256), 256, 0, s>>>(n, out_cnt, dmax + 66, P.kunits);
+        GC_TRY(cudaGetLastError(), "k_kbin_scatter");
+      }
       int32_t cur[64];
       int32_t acc = 0;
       for (int b = 63; b >= 0; --b) {  // heaviest bin first

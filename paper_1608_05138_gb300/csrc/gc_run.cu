@@ -2,54 +2,69 @@
 // batched paths.
 //
 //   pass A  triangle step: |T| per edge                          (Alg. 1)
+//   trio    |T| re-indexed by out-slot
 //   pass C  4-cycles through every edge, degree-ordered wedges   (Alg. 4/6)
-//   chunks  split v-groups into balanced units (|T| now known)   (Sec. 4.5)
-//   pass B  4-cliques, per-edge columns, unrestricted sums       (Alg. 5, Sec. 4.5)
-//   big     the edges whose T exceeds a warp buffer, one CTA each
+//   pass K  4-cliques and cross terms by lowest vertex           (Alg. 3/5)
+//   finish  x10, per-edge columns, unrestricted sums             (Sec. 4.5)
 //   derive  X_1..X_17                                            (Sec. 4.6)
 //
-// Two host synchronisations sit inside: after pass A (largest |T|, to size
-// the large-T buffers) folded into the chunking step, which reads back the
-// total estimated work.
+// Everything is queued on one stream with no host synchronisation: the unit
+// lists and their tier boundaries are fixed when the graph is prepared.
 #include <cuda_runtime.h>
 
 #include "gc_internal.h"
 
 namespace gc {
 
+namespace {
+// Total bytes the pass-K global tier may hold at once.
+constexpr size_t kKbufBudget = size_t(2) << 30;
+}  // namespace
+
 void scratch_free(Scratch* sc, cudaStream_t s) {
-  for (void* p : {(void*)sc->tri, (void*)sc->P, (void*)sc->chunks, (void*)sc->off, (void*)sc->misc,
-                  (void*)sc->total, (void*)sc->tables, (void*)sc->tbuf, (void*)sc->deferred, (void*)sc->work})
+  for (void* p : {(void*)sc->tri, (void*)sc->trio, (void*)sc->P, (void*)sc->x7o, (void*)sc->cro, (void*)sc->misc,
+                  (void*)sc->tables, (void*)sc->kbuf, (void*)sc->work})
     if (p) cudaFreeAsync(p, s);
   *sc = Scratch();
 }
 
-gc_status scratch_init(Scratch* sc, int32_t m, int32_t n_units, int32_t table_n, cudaStream_t s) {
+gc_status scratch_init(Scratch* sc, int32_t m, int32_t table_n, int32_t kmax, cudaStream_t s) {
   cudaError_t e = cudaSuccess;
 #define GS_TRY(call)                                \
   do {                                              \
     e = (call);                                     \
     if (e != cudaSuccess) return cuda_fail(e, "scratch alloc"); \
   } while (0)
-  GS_TRY(cudaMallocAsync(&sc->tri, sizeof(int32_t) * (size_t)(m > 0 ? m : 1), s));
-  GS_TRY(cudaMallocAsync(&sc->P, sizeof(unsigned long long) * (size_t)(m > 0 ? 2 * (size_t)m : 1), s));
-  GS_TRY(cudaMallocAsync(&sc->chunks, sizeof(int32_t) * 3 * chunk_capacity(n_units), s));
-  GS_TRY(cudaMallocAsync(&sc->off, sizeof(int32_t) * ((size_t)n_units + 1), s));
+  const size_t m1 = (size_t)(m > 0 ? m : 1);
+  GS_TRY(cudaMallocAsync(&sc->tri, sizeof(int32_t) * m1, s));
+  GS_TRY(cudaMallocAsync(&sc->trio, sizeof(int32_t) * m1, s));
+  GS_TRY(cudaMallocAsync(&sc->P, sizeof(unsigned long long) * 2 * m1, s));
+  GS_TRY(cudaMallocAsync(&sc->x7o, sizeof(unsigned long long) * m1, s));
+  GS_TRY(cudaMallocAsync(&sc->cro, sizeof(unsigned long long) * m1, s));
   GS_TRY(cudaMallocAsync(&sc->misc, sizeof(int32_t) * 8, s));
-  GS_TRY(cudaMallocAsync(&sc->total, sizeof(unsigned long long), s));
   GS_TRY(cudaMallocAsync(&sc->work, sizeof(unsigned long long) * kNumWork, s));
   if (table_n > kSmemTableMax) {
     sc->tables_n = (size_t)count_grid_size() * (size_t)table_n;
     GS_TRY(cudaMallocAsync(&sc->tables, sizeof(uint32_t) * sc->tables_n, s));
     GS_TRY(cudaMemsetAsync(sc->tables, 0, sizeof(uint32_t) * sc->tables_n, s));
   }
+  if (kmax > kTierCap[kTier1024]) {
+    sc->kbuf_cap = kmax;
+    sc->kbuf_stride = kbuf_bytes(kmax);
+    size_t ctas = kKbufBudget / sc->kbuf_stride;
+    const size_t sms = (size_t)(count_grid_size() / kCtasPerSm);
+    if (ctas > sms) ctas = sms;
+    if (ctas < 1) ctas = 1;
+    sc->kbuf_ctas = (int32_t)ctas;
+    GS_TRY(cudaMallocAsync(&sc->kbuf, sc->kbuf_stride * ctas, s));
+  }
 #undef GS_TRY
   return GC_OK;
 }
 
-gc_status run_count(const DevGraph& g, const int32_t* units, int32_t n_units, uint64_t* per_edge,
-                    unsigned long long* csum, unsigned long long* x, Scratch* sc, cudaStream_t s,
-                    cudaEvent_t* ev) {
+gc_status run_count(const DevGraph& g, const int32_t* units, int32_t n_units, const KUnits& ku,
+                    uint64_t* per_edge, unsigned long long* csum, unsigned long long* x, Scratch* sc,
+                    cudaStream_t s, cudaEvent_t* ev) {
   cudaError_t e = cudaSuccess;
   gc_status st = GC_OK;
 #define GR_TRY(call, what)                  \
@@ -59,80 +74,56 @@ gc_status run_count(const DevGraph& g, const int32_t* units, int32_t n_units, ui
   } while (0)
 #define GR_EVENT(i) \
   if (ev) GR_TRY(cudaEventRecord(ev[i], s), "event")
-  int32_t* cursor = sc->misc;
-  int32_t* status = sc->misc + 1;
-  int32_t* tmax_dev = sc->misc + 2;
-  int32_t* nbig_dev = sc->misc + 3;
-  int32_t* ndef_dev = sc->misc + 4;
   CountArgs a;
   a.units = units;
   a.n_units = n_units;
-  a.chunks = sc->chunks;
-  a.n_chunks = sc->off + n_units;
-  a.cursor = cursor;
+  a.kunits = ku.units;
+  for (int t = 0; t <= kNumTiers; ++t) a.ktier_off[t] = ku.tier_off[t];
+  a.cursor = sc->misc;  // [0] passes A and C, [2 + tier] pass K
+  a.status = sc->misc + 1;
   a.tables = g.table_n > kSmemTableMax ? sc->tables : nullptr;
   a.tri = sc->tri;
+  a.trio = sc->trio;
   a.P = sc->P;
-  a.tbuf = nullptr;
-  a.tbuf_len = 0;
-  a.deferred = nullptr;
-  a.deferred_cap = 0;
-  a.n_deferred = ndef_dev;
-  a.big_t = big_t_threshold();
+  a.x7o = sc->x7o;
+  a.cro = sc->cro;
+  a.kbuf = sc->kbuf;
+  a.kbuf_stride = sc->kbuf_stride;
+  a.kbuf_ctas = sc->kbuf_ctas;
+  a.kbuf_cap = sc->kbuf_cap;
   a.per_edge = per_edge;
   a.csum = csum;
-  a.status = status;
   a.work = sc->work;
+  const size_t m1 = (size_t)(g.m > 0 ? g.m : 1);
   GR_TRY(cudaMemsetAsync(sc->misc, 0, sizeof(int32_t) * 8, s), "memset misc");
   GR_TRY(cudaMemsetAsync(sc->work, 0, sizeof(unsigned long long) * kNumWork, s), "memset work");
   GR_TRY(cudaMemsetAsync(csum, 0, sizeof(unsigned long long) * 26 * (size_t)g.G, s), "memset sums");
+  GR_TRY(cudaMemsetAsync(sc->P, 0, sizeof(unsigned long long) * 2 * m1, s), "zero P");
+  GR_TRY(cudaMemsetAsync(sc->x7o, 0, sizeof(unsigned long long) * m1, s), "zero x7");
+  GR_TRY(cudaMemsetAsync(sc->cro, 0, sizeof(unsigned long long) * m1, s), "zero cross");
+  int launches = 0;
   GR_EVENT(kPhasePassA);
-  int32_t nbig = 0;
   if (n_units > 0) {
     if ((st = run_pass_a(g, a, s)) != GC_OK) return st;
-    if ((st = run_max_tri(sc->tri, g.m, tmax_dev, s)) != GC_OK) return st;
-    GR_EVENT(kPhasePassC);
-    GR_TRY(cudaMemsetAsync(sc->P, 0, sizeof(unsigned long long) * 2 * (size_t)g.m, s), "zero P");
-    GR_TRY(cudaMemsetAsync(cursor, 0, sizeof(int32_t), s), "reset cursor");
-    if ((st = run_pass_c(g, a, s)) != GC_OK) return st;
-    if ((st = run_make_chunks(g, units, n_units, sc->tri, sc->chunks, sc->off, sc->total, nbig_dev, a.big_t, s)) != GC_OK)
-      return st;
-    int32_t hm[2] = {0, 0};  // max |T|, number of large-T edges (complete: the chunking synchronised)
-    GR_TRY(cudaMemcpyAsync(hm, tmax_dev, sizeof(hm), cudaMemcpyDeviceToHost, s), "copy counts");
-    GR_TRY(cudaStreamSynchronize(s), "sync counts");
-    nbig = hm[1];
-    if (nbig > 0) {
-      if (sc->tbuf_len < hm[0]) {
-        if (sc->tbuf) cudaFreeAsync(sc->tbuf, s);
-        sc->tbuf_len = hm[0];
-        GR_TRY(cudaMallocAsync(&sc->tbuf, sizeof(int32_t) * (size_t)big_grid_size() * sc->tbuf_len, s),
-               "alloc T buffers");
-      }
-      if (sc->deferred_cap < nbig) {
-        if (sc->deferred) cudaFreeAsync(sc->deferred, s);
-        sc->deferred_cap = nbig;
-        GR_TRY(cudaMallocAsync(&sc->deferred, sizeof(int32_t) * 2 * (size_t)nbig, s), "alloc deferred");
-      }
-      a.deferred = sc->deferred;
-      a.deferred_cap = sc->deferred_cap;
-      a.tbuf = sc->tbuf;
-      a.tbuf_len = sc->tbuf_len;
-    }
-    GR_TRY(cudaMemsetAsync(cursor, 0, sizeof(int32_t), s), "reset cursor");
-  } else {
-    GR_EVENT(kPhasePassC);
+    if ((st = run_trio(g, a, s)) != GC_OK) return st;
+    launches += 2;
   }
-  GR_EVENT(kPhasePassB);
+  GR_EVENT(kPhasePassC);
   if (n_units > 0) {
-    if ((st = run_pass_b(g, a, s)) != GC_OK) return st;
+    GR_TRY(cudaMemsetAsync(a.cursor, 0, sizeof(int32_t), s), "reset cursor");
+    if ((st = run_pass_c(g, a, s)) != GC_OK) return st;
+    launches += 1;
   }
-  GR_EVENT(kPhaseBig);
-  if (nbig > 0) {
-    GR_TRY(cudaMemsetAsync(cursor, 0, sizeof(int32_t), s), "reset cursor");
-    if ((st = run_pass_big(g, a, nbig, s)) != GC_OK) return st;
-  }
+  GR_EVENT(kPhasePassK);
+  int k_launches = 0;
+  if ((st = run_pass_k(g, a, s, &k_launches)) != GC_OK) return st;
+  launches += k_launches;
+  GR_EVENT(kPhaseFinish);
+  if ((st = run_finish(g, a, s)) != GC_OK) return st;
+  launches += g.m > 0 ? 1 : 0;
   GR_EVENT(kPhaseDerive);
-  if ((st = run_derive(g, csum, x, status, s)) != GC_OK) return st;
+  if ((st = run_derive(g, csum, x, a.status, s)) != GC_OK) return st;
+  sc->launches = launches + 1;
   GR_EVENT(kPhaseCopy);
 #undef GR_EVENT
 #undef GR_TRY

@@ -91,7 +91,7 @@ def test_wide_counts_need_high_words():
         assert ei.value.status == -9
 
 
-def test_triangle_list_beyond_shared_buffer():
+def test_large_common_neighbourhood():
     # book graph: two adjacent hubs sharing 1500 neighbours (|T| = 1500), with
     # a matching and a few triangles among the shared neighbours.
     k = 1500
@@ -166,6 +166,31 @@ def _sampled_check(rp, ci, k=1500, seed=0):
         from math import comb
         assert sum(X[6:17]) == comb(n, 4) and sum(X[2:6]) == comb(n, 3)
         assert X[3] == int(sum(comb(int(d), 2) for d in deg)) - 3 * X[2]
+
+
+def test_dense_graph_reaches_every_clique_tier():
+    # out-degrees up to ~1100: the 4-clique pass runs its shared-memory tiers
+    # (k <= 256, 512, 1024) and its global-memory tier (k > 1024)
+    rp, ci = graphgen.er(1200, 0.92, 41)
+    deg = np.diff(rp)
+    assert deg.max() > 1024
+    _sampled_check(rp, ci, k=150, seed=3)
+
+
+def test_complete_graph_every_clique_tier():
+    # K_n: |T| = n - 2, x7 = C(n-2, 2), no S_u, S_v or D_e (Table 1 / Sec. 4.5)
+    from math import comb
+    n = 1100
+    rp, ci = graphs.complete(n)
+    m = n * (n - 1) // 2
+    with gcb.Graph(rp, ci) as g:
+        pe = np.zeros((g.m, 13), np.uint64)
+        X = g.count(pe)
+    row = np.array([n - 2, 0, 0, comb(n - 2, 2), 0, comb(n - 2, 2), 0, 0, 0, 0, m - 2 * (n - 1) + 1, 0, 0],
+                   np.uint64)
+    assert (pe == row).all()
+    assert X == [m, 0, comb(n, 3), 0, 0, 0, comb(n, 4)] + [0] * 10
+    np.testing.assert_array_equal(pe[[0, m // 2, m - 1]], oracle.count_sample(rp, ci, np.array([0, m // 2, m - 1])))
 
 
 def test_chung_lu_1m_config_sampled():
