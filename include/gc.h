@@ -147,8 +147,10 @@ gc_status gc_graph_phase_ms(gc_graph g, double* ms);
  *   5 pass K: bitmatrix words ANDed (edges of H_a x row words)
  *   6 finish: edges whose columns were written
  *   7 kernels launched by the count
+ *   8 pass C: wedges of the hub units (counted in shared-memory blocks)
+ *   9 pass C: lower neighbours swept, summed over the blocks of the hub units
  * Used to turn kernel times into algorithmic bytes per second. */
-#define GC_NUM_WORK 8
+#define GC_NUM_WORK 10
 gc_status gc_graph_work_counts(gc_graph g, uint64_t* out);
 
 /* Release the graph and all its device memory. NULL is accepted. */

@@ -305,7 +305,7 @@ gc_status gc_graph_upload(int32_t n, const int32_t* row_ptr, const int32_t* col_
   GC_CHECK(cudaMalloc(&g->d_csum, sizeof(unsigned long long) * (13 * 2 + 17 * 2)), "alloc sums");
   g->d_x = g->d_csum + 13 * 2;
   {
-    gc_status st2 = scratch_init(&g->sc, g->m, n, g->prep.kmax, s);
+    gc_status st2 = scratch_init(&g->sc, g->m, n, g->prep.kmax, g->prep.cnx_max, s);
     if (st2 != GC_OK) { graph_release(g); return st2; }
   }
   for (auto& ev : g->ev) GC_CHECK(cudaEventCreate(&ev), "event create");
@@ -382,6 +382,8 @@ gc_status gc_count_edge_graphlets(gc_graph g, uint64_t* per_edge_out, uint64_t* 
   dg.ranked = true;
   KUnits ku;
   ku.units = g->prep.kunits;
+  ku.cunits = g->prep.cunits;
+  ku.n_cheavy = g->prep.n_cheavy;
   for (int t = 0; t <= kNumTiers; ++t) ku.tier_off[t] = g->prep.ktier_off[t];
   if ((st = run_count(dg, g->prep.units, g->prep.n_units, ku, pe_dev, g->d_csum, g->d_x, &g->sc, s, g->ev)) != GC_OK)
     return st;

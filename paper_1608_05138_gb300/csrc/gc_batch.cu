@@ -179,7 +179,7 @@ gc_status run_union(std::vector<PendingGraph*>& graphs, cudaStream_t s, Launch* 
     L->error = gc_last_error();
     goto out;
   }
-  if ((st = scratch_init(&sc, m, table_n, prep.kmax, s)) != GC_OK) {
+  if ((st = scratch_init(&sc, m, table_n, prep.kmax, prep.cnx_max, s)) != GC_OK) {
     L->error = gc_last_error();
     goto out;
   }
@@ -204,6 +204,8 @@ gc_status run_union(std::vector<PendingGraph*>& graphs, cudaStream_t s, Launch* 
     dg.ranked = false;
     KUnits ku;
     ku.units = prep.kunits;
+    ku.cunits = prep.cunits;
+    ku.n_cheavy = prep.n_cheavy;
     for (int t = 0; t <= kNumTiers; ++t) ku.tier_off[t] = prep.ktier_off[t];
     if ((st = run_count(dg, prep.units, prep.n_units, ku, nullptr, d_csum, d_x, &sc, s, nullptr)) != GC_OK) {
       L->error = gc_last_error();

@@ -281,6 +281,157 @@ __global__ void __launch_bounds__(kBlock) k_pass_c(DevGraph g, CountArgs a) {
   }
 }
 
+// ---------------- pass C for hub units: the count table in shared memory ----------------
+// The same wedges and attribution as k_pass_c, for the units h whose wedges
+// (a few thousand hubs carry almost all of them on power-law graphs) would
+// otherwise hit a vertex-indexed table in DRAM at random. Ids are ranks, so
+// the lower-rank neighbours X of h are a prefix of Gamma(h) and, for x in X,
+// the o < h are a prefix of Gamma(x), ascending. The o-range [0, h) is swept
+// in blocks of kHeavyTab ids: cnt_h(o) for the block is built in shared
+// memory from each x's run of o in the block (a per-x cursor walks Gamma(x)
+// once over all blocks), then the wedges of the block are attributed with
+// the block's counts. Runs are dealt to the lanes of a warp end to end (32
+// x's at a time, owner found by a shuffle search), so that the P atomics of
+// consecutive lanes hit consecutive slots.
+constexpr int kHeavyBlock = 1024;
+constexpr int kHeavyWarps = kHeavyBlock / 32;
+
+__global__ void __launch_bounds__(kHeavyBlock, 1) k_pass_c_heavy(DevGraph g, CountArgs a) {
+  extern __shared__ uint32_t tab[];  // kHeavyTab counters
+  __shared__ int32_t s_unit, s_nx;
+  __shared__ unsigned long long s_sx[kHeavyWarps][32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int32_t* beg = a.cbuf + (size_t)blockIdx.x * 3 * (size_t)a.cbuf_nx;
+  int32_t* cur = beg + a.cbuf_nx;
+  int32_t* endp = cur + a.cbuf_nx;
+  long long w_wedge = 0, w_blocks = 0;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_unit = atomicAdd(a.cursor + 6, 1);
+    __syncthreads();
+    const int32_t k = s_unit;
+    if (k >= a.n_cheavy) break;
+    const int32_t h = a.cunits[k];
+    const int32_t hb = g.rp[h], he = g.rp[h + 1];
+    if (threadIdx.x == 0) {
+      int32_t lo = hb, hi = he;  // first slot of Gamma(h) with id >= h
+      while (lo < hi) {
+        const int32_t mid = (lo + hi) >> 1;
+        if (g.ci[mid] < h) lo = mid + 1; else hi = mid;
+      }
+      s_nx = lo - hb;
+    }
+    __syncthreads();
+    const int32_t nx = s_nx;
+    if (nx > a.cbuf_nx) {  // cannot happen: the buffers are sized for the largest hub
+      if (threadIdx.x == 0) atomicOr(a.status, (int32_t)kSpillOverflow);
+      continue;
+    }
+    for (int32_t i = threadIdx.x; i < nx; i += kHeavyBlock) {
+      const int32_t x = g.ci[hb + i];
+      const int32_t xb = g.rp[x];
+      int32_t lo = xb, hi = g.rp[x + 1];
+      while (lo < hi) {
+        const int32_t mid = (lo + hi) >> 1;
+        if (g.ci[mid] < h) lo = mid + 1; else hi = mid;
+      }
+      cur[i] = xb;
+      endp[i] = lo;
+      w_wedge += lo - xb;
+    }
+    for (int32_t r0 = 0; r0 < h; r0 += kHeavyTab) {
+      const int32_t r1 = min(r0 + kHeavyTab, h);
+      for (int32_t i = threadIdx.x; i < r1 - r0; i += kHeavyBlock) tab[i] = 0u;
+      if (threadIdx.x == 0) w_blocks += nx;
+      __syncthreads();
+      // counts of the block: each thread walks the run of one x (X ascends
+      // by degree, so neighbouring threads have runs of similar length)
+      for (int32_t i = threadIdx.x; i < nx; i += kHeavyBlock) {
+        int32_t p = cur[i];
+        const int32_t e = endp[i];
+        beg[i] = p;
+        while (p < e) {
+          int32_t o[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) o[j] = p + j < e ? g.ci[p + j] : 0x7fffffff;
+          int j = 0;
+#pragma unroll
+          for (; j < 4; ++j) {
+            if (o[j] >= r1) break;
+            atomicAdd(&tab[o[j] - r0], 1u);
+          }
+          p += j;
+          if (j < 4) break;
+        }
+        cur[i] = p;
+      }
+      __syncthreads();
+      // attribution of the block's wedges
+      for (int32_t i0 = warp * 32; i0 < nx; i0 += kHeavyBlock) {
+        const int32_t i = i0 + lane;
+        int32_t st = 0, L = 0;
+        if (i < nx) {
+          st = beg[i];
+          L = cur[i] - st;
+        }
+        int32_t incl = L;
+        for (int o = 1; o < 32; o <<= 1) {
+          const int32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += y;
+        }
+        const int32_t excl = incl - L;
+        const int32_t total = __shfl_sync(0xffffffffu, incl, 31);
+        s_sx[warp][lane] = 0ull;
+        __syncwarp();
+        for (int32_t k0 = 0; k0 < total; k0 += 128) {
+          int32_t q[4], ol[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int32_t kk = k0 + 32 * j + lane;
+            int32_t lo = 0, hi = 31;  // owner: last lane whose run starts at or before kk
+#pragma unroll
+            for (int it = 0; it < 5; ++it) {
+              const int32_t mid = (lo + hi + 1) >> 1;
+              if (__shfl_sync(0xffffffffu, excl, mid) <= kk) lo = mid; else hi = mid - 1;
+            }
+            const int32_t sj = __shfl_sync(0xffffffffu, st, lo);
+            const int32_t ej = __shfl_sync(0xffffffffu, excl, lo);
+            ol[j] = lo;
+            q[j] = kk < total ? sj + (kk - ej) : -1;
+          }
+          int32_t o[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) o[j] = q[j] >= 0 ? g.ci[q[j]] : 0;
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            if (q[j] < 0) continue;
+            const uint32_t c = tab[o[j] - r0] - 1u;
+            if (c) {
+              atomicAdd(&a.P[q[j]], (unsigned long long)c);  // slot (x, o)
+              atomicAdd(&s_sx[warp][ol[j]], (unsigned long long)c);
+            }
+          }
+        }
+        __syncwarp();
+        if (i < nx) {
+          const unsigned long long sx = s_sx[warp][lane];
+          if (sx) atomicAdd(&a.P[hb + i], sx);  // slot (h, x)
+        }
+        __syncwarp();
+      }
+      __syncthreads();
+    }
+  }
+  for (int o = 16; o; o >>= 1) {
+    w_wedge += __shfl_xor_sync(0xffffffffu, w_wedge, o);
+  }
+  if (lane == 0 && w_wedge) {
+    atomicAdd(a.work + kWorkCWedge, (unsigned long long)w_wedge);
+    atomicAdd(a.work + kWorkCHeavyWedge, (unsigned long long)w_wedge);
+  }
+  if (threadIdx.x == 0 && w_blocks) atomicAdd(a.work + kWorkCBlocks, (unsigned long long)w_blocks);
+}
+
 // ---------------- derive X_1..X_17 per graph ----------------
 __device__ __forceinline__ bool div_exact(u128 num, u128 den, u128* q) {
   if (num % den != 0) return false;
@@ -372,6 +523,18 @@ gc_status run_pass_c(const DevGraph& g, const CountArgs& a, cudaStream_t s) {
   const bool sm = a.tables == nullptr;
   if (sm) return launch(k_pass_c<true>, smem_bytes(true, g.table_n), g, a, s, "k_pass_c");
   return launch(k_pass_c<false>, smem_bytes(false, g.table_n), g, a, s, "k_pass_c");
+}
+
+gc_status run_pass_c_heavy(const DevGraph& g, const CountArgs& a, cudaStream_t s) {
+  if (a.n_cheavy <= 0) return GC_OK;
+  const size_t smem = sizeof(uint32_t) * kHeavyTab;
+  cudaError_t e = cudaFuncSetAttribute(k_pass_c_heavy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return cuda_fail(e, "k_pass_c_heavy");
+  int grid = count_grid_size() / kCtasPerSm;
+  if (grid > a.n_cheavy) grid = a.n_cheavy;
+  k_pass_c_heavy<<<grid, kHeavyBlock, smem, s>>>(g, a);
+  e = cudaGetLastError();
+  return e == cudaSuccess ? GC_OK : cuda_fail(e, "k_pass_c_heavy");
 }
 
 gc_status run_trio(const DevGraph& g, const CountArgs& a, cudaStream_t s) {

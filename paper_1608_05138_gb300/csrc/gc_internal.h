@@ -47,6 +47,10 @@ constexpr int kTierCap[kNumTiers] = {0, 1024, 512, 256};
 struct CountArgs {
   const int32_t* units;    // passes A and C: v-groups (high endpoints), heaviest bin first
   int32_t n_units;
+  const int32_t* cunits;   // pass C: hub units first (blocked kernel), then the others
+  int32_t n_cheavy;        // hub units of pass C (cunits[0 .. n_cheavy))
+  int32_t* cbuf;           // pass C hub kernel: per-CTA cursors (cbuf_ctas x 3 x cbuf_nx ints)
+  int32_t cbuf_nx;
   const int32_t* kunits;   // pass K: lowest vertices a with |out(a)| >= 2, tiers in KTier order
   int32_t ktier_off[kNumTiers + 1];  // tier t = kunits[ktier_off[t] .. ktier_off[t + 1])
   int32_t* cursor;         // work-stealing cursors (device ints, zeroed before each launch)
@@ -78,6 +82,8 @@ enum Work {
   kWorkKWords,         // pass K: bitmatrix words ANDed (local edges x row words)
   kWorkFinishEdges,    // finish: edges written
   kWorkLaunches,       // kernels launched by the count (counted on the host)
+  kWorkCHeavyWedge,    // pass C: wedges of the hub units (blocked kernel)
+  kWorkCBlocks,        // pass C: lower neighbours swept, summed over the blocks of the hub units
   kNumWork
 };
 
@@ -101,6 +107,8 @@ struct Scratch {
   unsigned long long* x7o = nullptr; // [m]
   unsigned long long* cro = nullptr; // [m]
   int32_t* misc = nullptr;           // cursors, status
+  int32_t* cbuf = nullptr;           // pass C hub cursors
+  int32_t cbuf_nx = 0;
   uint32_t* tables = nullptr;        // count_grid_size() x table_n
   size_t tables_n = 0;
   unsigned char* kbuf = nullptr;     // pass K global tier
@@ -112,7 +120,7 @@ struct Scratch {
 };
 // Allocates the scratch of a graph with m edges, Psi tables of table_n
 // vertices and largest out-degree kmax (stream-ordered).
-gc_status scratch_init(Scratch* sc, int32_t m, int32_t table_n, int32_t kmax, cudaStream_t s);
+gc_status scratch_init(Scratch* sc, int32_t m, int32_t table_n, int32_t kmax, int32_t cnx_max, cudaStream_t s);
 void scratch_free(Scratch* sc, cudaStream_t s);
 // The whole count: passes A, C, K, finish, derive. csum [G][13][2] and
 // x [G][17][2] are device arrays; ev (optional) receives kNumPhases + 1
@@ -120,6 +128,8 @@ void scratch_free(Scratch* sc, cudaStream_t s);
 struct KUnits {
   const int32_t* units;
   int32_t tier_off[kNumTiers + 1];
+  const int32_t* cunits;   // pass C units, hub units first
+  int32_t n_cheavy;
 };
 gc_status run_count(const DevGraph& g, const int32_t* units, int32_t n_units, const KUnits& ku,
                     uint64_t* per_edge, unsigned long long* csum, unsigned long long* x, Scratch* sc,
@@ -145,6 +155,9 @@ struct PrepBuffers {
   int32_t* kunits = nullptr;  // pass K units (see CountArgs::kunits)
   int32_t ktier_off[kNumTiers + 1] = {0, 0, 0, 0, 0};
   int32_t kmax = 0;         // largest out-degree
+  int32_t* cunits = nullptr;  // pass C units: hub units (heaviest first), then the rest in unit order
+  int32_t n_cheavy = 0;
+  int32_t cnx_max = 0;      // most lower neighbours of a hub unit
 };
 // Builds degrees, edge ids, the edge list, degree-oriented out-lists and the
 // binned unit list on `stream`. vgid may be nullptr (single graph).
@@ -154,6 +167,11 @@ struct PrepBuffers {
 gc_status prepare_graph(int32_t n, int32_t m, const int32_t* d_rp, const int32_t* d_ci,
                         const int32_t* d_vgid, int32_t* d_eid_given, const int32_t* d_perm,
                         PrepBuffers* out, cudaStream_t stream);
+// Splits the pass-C units of a ranked graph (ids = ranks, rows ascending)
+// into hub units for the blocked kernel and the rest (fills cunits,
+// n_cheavy, cnx_max; without hubs cunits is a copy of units).
+gc_status classify_c_units(int32_t n, const int32_t* d_rp, const int32_t* d_ci, bool ranked, PrepBuffers* p,
+                           cudaStream_t stream);
 void free_prep(PrepBuffers* p, cudaStream_t s);
 
 // ---- small graphs on a shared-memory bitmatrix (gc_small.cu) ----
@@ -168,6 +186,8 @@ gc_status run_small_graphs(const int32_t* rp, const int64_t* voff, const int32_t
 int count_grid_size();
 gc_status run_pass_a(const DevGraph& g, const CountArgs& a, cudaStream_t s);
 gc_status run_pass_c(const DevGraph& g, const CountArgs& a, cudaStream_t s);
+gc_status run_pass_c_heavy(const DevGraph& g, const CountArgs& a, cudaStream_t s);
+constexpr int kHeavyTab = 49152;  // o-range block of the hub kernel of pass C (entries in shared memory)
 gc_status run_derive(const DevGraph& g, const unsigned long long* csum, unsigned long long* x,
                      int32_t* status, cudaStream_t s);
 gc_status run_trio(const DevGraph& g, const CountArgs& a, cudaStream_t s);

@@ -19,6 +19,7 @@
 
 #include <cstdlib>
 #include <cstring>
+#include <algorithm>
 #include <vector>
 
 #include "gc_internal.h"
@@ -203,6 +204,29 @@ __global__ void k_kbin_scatter(int32_t n, const int32_t* __restrict__ out_cnt, i
     if (out_cnt[v] >= 2) units[atomicAdd(&cursor[kbin_of(out_cnt[v])], 1)] = v;
 }
 
+// Wedges of every pass-C unit h of a ranked graph: W_h = sum over the
+// lower-rank neighbours x of h of |{o in Gamma(x) : o < h}| (warp per unit).
+__global__ void k_cwork(int32_t n_units, const int32_t* __restrict__ units, const int32_t* __restrict__ rp,
+                        const int32_t* __restrict__ ci, long long* __restrict__ W, int32_t* __restrict__ NX) {
+  const int lane = threadIdx.x & 31;
+  const int warps = (gridDim.x * blockDim.x) >> 5;
+  for (int32_t k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < n_units; k += warps) {
+    const int32_t h = units[k];
+    const int32_t hb = rp[h];
+    const int32_t nx = lower_bound_i32(ci, hb, rp[h + 1], h) - hb;
+    long long w = 0;
+    for (int32_t i = lane; i < nx; i += 32) {
+      const int32_t x = ci[hb + i];
+      w += lower_bound_i32(ci, rp[x], rp[x + 1], h) - rp[x];
+    }
+    for (int o = 16; o; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+    if (lane == 0) {
+      W[k] = w;
+      NX[k] = nx;
+    }
+  }
+}
+
 // ---- exclusive scan of int32 (totals fit int32) ----
 __global__ void k_scan_tile_sums(int32_t n, const int32_t* __restrict__ in, int32_t* __restrict__ sums) {
   __shared__ int32_t ws[8];
@@ -332,6 +356,57 @@ gc_status exclusive_scan(int32_t n, const int32_t* in, int32_t* out, cudaStream_
   return e == cudaSuccess ? GC_OK : cuda_fail(e, "scan launch");
 }
 
+gc_status classify_c_units(int32_t n, const int32_t* d_rp, const int32_t* d_ci, bool ranked, PrepBuffers* p,
+                           cudaStream_t s) {
+  const int32_t nu = p->n_units;
+  cudaError_t e = cudaMallocAsync(&p->cunits, sizeof(int32_t) * (nu > 0 ? nu : 1), s);
+  if (e != cudaSuccess) return cuda_fail(e, "alloc cunits");
+  p->n_cheavy = 0;
+  p->cnx_max = 0;
+  if (!ranked || n <= kSmemTableMax || nu == 0) {
+    e = nu > 0 ? cudaMemcpyAsync(p->cunits, p->units, sizeof(int32_t) * nu, cudaMemcpyDeviceToDevice, s) : cudaSuccess;
+    return e == cudaSuccess ? GC_OK : cuda_fail(e, "copy cunits");
+  }
+  long long* dW = nullptr;
+  int32_t* dNX = nullptr;
+  std::vector<long long> W(nu);
+  std::vector<int32_t> NX(nu), U(nu), out;
+  out.reserve(nu);
+  e = cudaMallocAsync(&dW, sizeof(long long) * nu, s);
+  if (e == cudaSuccess) e = cudaMallocAsync(&dNX, sizeof(int32_t) * nu, s);
+  if (e == cudaSuccess) {
+    k_cwork<<<grid_for((int64_t)nu * 32, 256), 256, 0, s>>>(nu, p->units, d_rp, d_ci, dW, dNX);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(W.data(), dW, sizeof(long long) * nu, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(NX.data(), dNX, sizeof(int32_t) * nu, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(U.data(), p->units, sizeof(int32_t) * nu, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (dW) cudaFreeAsync(dW, s);
+  if (dNX) cudaFreeAsync(dNX, s);
+  if (e != cudaSuccess) return cuda_fail(e, "classify pass-C units");
+  // A hub unit pays a sweep of its lower neighbours per shared-memory block of
+  // the o-range; it is worth it when the wedges clearly outnumber that.
+  std::vector<int32_t> heavy;
+  for (int32_t k = 0; k < nu; ++k) {
+    const long long blocks = ((long long)U[k] + kHeavyTab - 1) / kHeavyTab;
+    if (W[k] >= 65536 && W[k] >= blocks * (2048 + 4LL * NX[k])) heavy.push_back(k);
+  }
+  std::sort(heavy.begin(), heavy.end(), [&](int32_t a, int32_t b) { return W[a] > W[b]; });
+  std::vector<char> is_heavy(nu, 0);
+  for (int32_t k : heavy) {
+    out.push_back(U[k]);
+    is_heavy[k] = 1;
+    if (NX[k] > p->cnx_max) p->cnx_max = NX[k];
+  }
+  for (int32_t k = 0; k < nu; ++k)
+    if (!is_heavy[k]) out.push_back(U[k]);
+  p->n_cheavy = (int32_t)heavy.size();
+  e = cudaMemcpyAsync(p->cunits, out.data(), sizeof(int32_t) * nu, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return e == cudaSuccess ? GC_OK : cuda_fail(e, "copy cunits");
+}
+
 void free_prep(PrepBuffers* p, cudaStream_t s) {
   if (p->deg) cudaFreeAsync(p->deg, s);
   if (p->eid) cudaFreeAsync(p->eid, s);
@@ -343,6 +418,7 @@ void free_prep(PrepBuffers* p, cudaStream_t s) {
   if (p->rev) cudaFreeAsync(p->rev, s);
   if (p->ocsr) cudaFreeAsync(p->ocsr, s);
   if (p->kunits) cudaFreeAsync(p->kunits, s);
+  if (p->cunits) cudaFreeAsync(p->cunits, s);
   *p = PrepBuffers();
 }
 
@@ -438,7 +514,8 @@ gc_status prepare_graph(int32_t n, int32_t m, const int32_t* d_rp, const int32_t
   } else {
     GC_TRY(cudaMemsetAsync(P.out_ptr, 0, sizeof(int32_t), s), "memset out_ptr");
   }
-    cudaFreeAsync(up, s);
+  if ((st = classify_c_units(n, d_rp, d_ci, d_perm != nullptr, &P, s)) != GC_OK) goto fail;
+  cudaFreeAsync(up, s);
   cudaFreeAsync(upoff, s);
   cudaFreeAsync(out_cnt, s);
   cudaFreeAsync(dmax, s);

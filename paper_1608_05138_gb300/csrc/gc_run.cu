@@ -23,12 +23,12 @@ constexpr size_t kKbufBudget = size_t(2) << 30;
 
 void scratch_free(Scratch* sc, cudaStream_t s) {
   for (void* p : {(void*)sc->tri, (void*)sc->trio, (void*)sc->P, (void*)sc->x7o, (void*)sc->cro, (void*)sc->misc,
-                  (void*)sc->tables, (void*)sc->kbuf, (void*)sc->work})
+                  (void*)sc->cbuf, (void*)sc->tables, (void*)sc->kbuf, (void*)sc->work})
     if (p) cudaFreeAsync(p, s);
   *sc = Scratch();
 }
 
-gc_status scratch_init(Scratch* sc, int32_t m, int32_t table_n, int32_t kmax, cudaStream_t s) {
+gc_status scratch_init(Scratch* sc, int32_t m, int32_t table_n, int32_t kmax, int32_t cnx_max, cudaStream_t s) {
   cudaError_t e = cudaSuccess;
 #define GS_TRY(call)                                \
   do {                                              \
@@ -47,6 +47,10 @@ gc_status scratch_init(Scratch* sc, int32_t m, int32_t table_n, int32_t kmax, cu
     sc->tables_n = (size_t)count_grid_size() * (size_t)table_n;
     GS_TRY(cudaMallocAsync(&sc->tables, sizeof(uint32_t) * sc->tables_n, s));
     GS_TRY(cudaMemsetAsync(sc->tables, 0, sizeof(uint32_t) * sc->tables_n, s));
+  }
+  if (cnx_max > 0) {
+    sc->cbuf_nx = cnx_max;
+    GS_TRY(cudaMallocAsync(&sc->cbuf, sizeof(int32_t) * 3 * (size_t)cnx_max * (size_t)(count_grid_size() / kCtasPerSm), s));
   }
   if (kmax > kTierCap[kTier1024]) {
     sc->kbuf_cap = kmax;
@@ -78,8 +82,12 @@ gc_status run_count(const DevGraph& g, const int32_t* units, int32_t n_units, co
   a.units = units;
   a.n_units = n_units;
   a.kunits = ku.units;
+  a.cunits = ku.cunits;
+  a.n_cheavy = ku.n_cheavy;
+  a.cbuf = sc->cbuf;
+  a.cbuf_nx = sc->cbuf_nx;
   for (int t = 0; t <= kNumTiers; ++t) a.ktier_off[t] = ku.tier_off[t];
-  a.cursor = sc->misc;  // [0] passes A and C, [2 + tier] pass K
+  a.cursor = sc->misc;  // [0] passes A and C, [2 + tier] pass K, [6] pass C hubs
   a.status = sc->misc + 1;
   a.tables = g.table_n > kSmemTableMax ? sc->tables : nullptr;
   a.tri = sc->tri;
@@ -110,9 +118,18 @@ gc_status run_count(const DevGraph& g, const int32_t* units, int32_t n_units, co
   }
   GR_EVENT(kPhasePassC);
   if (n_units > 0) {
-    GR_TRY(cudaMemsetAsync(a.cursor, 0, sizeof(int32_t), s), "reset cursor");
-    if ((st = run_pass_c(g, a, s)) != GC_OK) return st;
-    launches += 1;
+    if (a.n_cheavy > 0) {
+      if ((st = run_pass_c_heavy(g, a, s)) != GC_OK) return st;
+      launches += 1;
+    }
+    if (n_units > a.n_cheavy) {
+      CountArgs al = a;  // the remaining units on the vertex-indexed tables
+      al.units = a.cunits + a.n_cheavy;
+      al.n_units = n_units - a.n_cheavy;
+      GR_TRY(cudaMemsetAsync(a.cursor, 0, sizeof(int32_t), s), "reset cursor");
+      if ((st = run_pass_c(g, al, s)) != GC_OK) return st;
+      launches += 1;
+    }
   }
   GR_EVENT(kPhasePassK);
   int k_launches = 0;

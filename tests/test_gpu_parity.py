@@ -107,6 +107,12 @@ def test_global_psi_tables():
     assert_parity(*graphgen.chung_lu(60000, 300000, 2.1, 600000.0, 3000.0, 21))
 
 
+def test_hub_units_of_the_cycle_pass():
+    # n > 2 x 49152 and ~100 hub vertices whose wedges are counted in
+    # shared-memory blocks of the vertex range (several blocks each)
+    assert_parity(*graphgen.chung_lu(120000, 600000, 2.1, 1.2e6, 4000.0, 7))
+
+
 def test_relabelling_is_metamorphic():
     rp, ci = graphgen.chung_lu(2000, 12000, 2.1, 24000.0, 500.0, 22)
     n = len(rp) - 1
