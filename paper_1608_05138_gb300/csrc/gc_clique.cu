@@ -31,7 +31,7 @@
 //
 // Tiers by k: the bitmatrix (k * ((k+31)/32 | 1) words) stays in shared
 // memory for k <= 1024; above that the same code runs on a per-CTA global
-// buffer. Work per unit is about sum_{b in out(a)} |out(b)| (triangle
+// buffer; units with k <= 32 run one per warp (k_pass_k_warp). Work per unit is about sum_{b in out(a)} |out(b)| (triangle
 // listing) plus (#edges of H_a) * k / 32 words.
 #include <cuda_runtime.h>
 
@@ -248,6 +248,110 @@ __global__ void __launch_bounds__(kThreads, 65536 / (kThreads * 64)) k_pass_k(De
   }
 }
 
+// Units with k <= 32: one warp per unit, lane i holding member b_i, its
+// row of H_a as a 32-bit mask and the out-slots of the edges found from it
+// (shared memory). Membership of an id in out(a) is a 5-step binary search
+// over the lanes' ids (ascending). Same attribution as k_pass_k.
+constexpr int kWBlock = 256;
+constexpr int kWWarps = kWBlock / 32;
+
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long x) {
+  for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+  return x;
+}
+
+__global__ void __launch_bounds__(kWBlock) k_pass_k_warp(DevGraph g, CountArgs a, int tier) {
+  __shared__ int32_t s_q[kWWarps][32 * 32];  // out-slot of edge (i, j) found from member i
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int32_t* qs = s_q[warp];
+  const int32_t u0 = a.ktier_off[tier], u1 = a.ktier_off[tier + 1];
+  int32_t* cursor = a.cursor + 2 + tier;
+  long long w_members = 0, w_scan = 0, w_edges = 0;  // lane 0
+  for (;;) {
+    int32_t ui = 0;
+    if (lane == 0) ui = u0 + atomicAdd(cursor, 1);
+    ui = __shfl_sync(kFull, ui, 0);
+    if (ui >= u1) break;
+    const int32_t av = a.kunits[ui];
+    const int32_t ob = g.out_ptr[av];
+    const int32_t k = g.out_ptr[av + 1] - ob;
+    if (k > 32) {  // cannot happen: units are binned by k
+      if (lane == 0) atomicOr(a.status, (int32_t)kSpillOverflow);
+      continue;
+    }
+    const int32_t id = lane < k ? g.out_idx[ob + lane] : 0x7fffffff;
+    const int32_t ti = lane < k ? a.trio[ob + lane] : 0;
+    const int32_t cmax = __shfl_sync(kFull, id, k - 1);
+    unsigned row = 0u, found = 0u;
+    // Phase 1: the edges of H_a.
+    for (int i = 0; i < k; ++i) {
+      const int32_t b = __shfl_sync(kFull, id, i);
+      const int32_t bb = g.out_ptr[b], be = g.out_ptr[b + 1];
+      unsigned hits = 0u;
+      for (int32_t q0 = bb; q0 < be; q0 += 32) {
+        const int32_t q = q0 + lane;
+        const int32_t c = q < be ? g.out_idx[q] : 0x7fffffff;
+        if (__shfl_sync(kFull, c, 0) > cmax) break;
+        if (lane == 0) w_scan += min(32, be - q0);
+        int lo = 0;
+#pragma unroll
+        for (int step = 16; step; step >>= 1)
+          if (__shfl_sync(kFull, id, lo + step) <= c) lo += step;
+        const bool hit = __shfl_sync(kFull, id, lo) == c && lo < k;  // lanes >= k hold padding ids
+        if (hit) qs[i * 32 + lo] = q;
+        hits |= __reduce_or_sync(kFull, hit ? 1u << lo : 0u);
+      }
+      if (lane == i) {
+        found = hits;
+        row |= hits;
+      }
+      if ((hits >> lane) & 1u) row |= 1u << i;
+      if (lane == 0) w_edges += __popc(hits);
+    }
+    __syncwarp();
+    // Phase 2: c_ij and the cross terms of every edge (i, j) of H_a.
+    unsigned long long vx = 0, vc = 0;  // for the edge (a, b_lane)
+    for (int i = 0; i < k; ++i) {
+      const unsigned ri = __shfl_sync(kFull, row, i);
+      const unsigned fi = __shfl_sync(kFull, found, i);
+      const int32_t tI = __shfl_sync(kFull, ti, i);
+      if (fi == 0u) continue;  // warp-uniform
+      unsigned long long cx = 0, cc = 0;
+      if ((fi >> lane) & 1u) {
+        const int32_t q = qs[i * 32 + lane];
+        const int c4 = __popc(ri & row);
+        const int32_t tij = a.trio[q];
+        if (c4) atomicAdd(&a.x7o[q], (unsigned long long)c4);
+        atomicAdd(&a.cro[q], (unsigned long long)(tI + ti - 2));
+        vx += (unsigned long long)c4;
+        vc += (unsigned long long)(tI + tij - 2);
+        cx = (unsigned long long)c4;
+        cc = (unsigned long long)(ti + tij - 2);
+      }
+      cx = warp_sum_u64(cx);
+      cc = warp_sum_u64(cc);
+      if (lane == i) {
+        vx += cx;
+        vc += cc;
+      }
+    }
+    if (lane < k) {
+      if (vx) atomicAdd(&a.x7o[ob + lane], vx >> 1);
+      if (vc) atomicAdd(&a.cro[ob + lane], vc);
+    }
+    if (lane == 0) w_members += k;
+    __syncwarp();
+  }
+  if (lane == 0) {
+    if (w_members) atomicAdd(a.work + kWorkKMembers, (unsigned long long)w_members);
+    if (w_scan) atomicAdd(a.work + kWorkKScan, (unsigned long long)w_scan);
+    if (w_edges) {
+      atomicAdd(a.work + kWorkKLocalEdges, (unsigned long long)w_edges);
+      atomicAdd(a.work + kWorkKWords, (unsigned long long)w_edges);
+    }
+  }
+}
+
 template <int kCap, int kThreads>
 gc_status launch_tier(const DevGraph& g, const CountArgs& a, int tier, cudaStream_t s, int* launches) {
   const int32_t units = a.ktier_off[tier + 1] - a.ktier_off[tier];
@@ -288,7 +392,21 @@ gc_status run_pass_k(const DevGraph& g, const CountArgs& a, cudaStream_t s, int*
   }
   if ((st = launch_tier<1024, 1024>(g, a, kTier1024, s, launches)) != GC_OK) return st;
   if ((st = launch_tier<512, 512>(g, a, kTier512, s, launches)) != GC_OK) return st;
-  return launch_tier<256, 512>(g, a, kTier256, s, launches);
+  if ((st = launch_tier<256, 512>(g, a, kTier256, s, launches)) != GC_OK) return st;
+  const int32_t units = a.ktier_off[kTier32 + 1] - a.ktier_off[kTier32];
+  if (units > 0) {
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pass_k_warp, kWBlock, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "k_pass_k_warp occupancy");
+    int grid = (per_sm > 0 ? per_sm : 1) * (count_grid_size() / kCtasPerSm);
+    const int need = (units + kWWarps - 1) / kWWarps;
+    if (grid > need) grid = need;
+    k_pass_k_warp<<<grid, kWBlock, 0, s>>>(g, a, kTier32);
+    ++*launches;
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "k_pass_k_warp");
+  }
+  return GC_OK;
 }
 
 }  // namespace gc

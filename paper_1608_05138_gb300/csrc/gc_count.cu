@@ -289,25 +289,89 @@ __global__ void __launch_bounds__(kBlock) k_pass_c(DevGraph g, CountArgs a) {
 // the o < h are a prefix of Gamma(x), ascending. The o-range [0, h) is swept
 // in blocks of kHeavyTab ids: cnt_h(o) for the block is built in shared
 // memory from each x's run of o in the block (a per-x cursor walks Gamma(x)
-// once over all blocks), then the wedges of the block are attributed with
-// the block's counts. Runs are dealt to the lanes of a warp end to end (32
-// x's at a time, owner found by a shuffle search), so that the P atomics of
+// once over all blocks; the end of the run is found by galloping search),
+// then the wedges of the block are attributed with the block's counts.
+// In both phases a warp takes 32 x's at a time (heaviest chunk first, from a
+// shared counter) and deals their runs to its lanes end to end, so that run
+// lengths, however skewed, do not leave lanes idle, and the P atomics of
 // consecutive lanes hit consecutive slots.
 constexpr int kHeavyBlock = 1024;
 constexpr int kHeavyWarps = kHeavyBlock / 32;
 
+// Counters of the block: 32-bit, or two 16-bit counters per word when the
+// unit has fewer than 65536 lower neighbours (no count can exceed that, so no
+// carry crosses into the other half) -- twice the o-range per block.
+__device__ __forceinline__ void add_count(uint32_t* tab, int32_t slot, bool half) {
+  if (half) atomicAdd(&tab[slot >> 1], 1u << ((slot & 1) << 4));
+  else atomicAdd(&tab[slot], 1u);
+}
+__device__ __forceinline__ uint32_t read_count(const uint32_t* tab, int32_t slot, bool half) {
+  return half ? (tab[slot >> 1] >> ((slot & 1) << 4)) & 0xffffu : tab[slot];
+}
+
+// first index in [p, e) with a[index] >= key; a ascending
+__device__ __forceinline__ int32_t gallop_lower_bound(const int32_t* __restrict__ a, int32_t p, int32_t e,
+                                                      int32_t key) {
+  if (p >= e || a[p] >= key) return p;
+  int32_t lo = p, step = 1;  // a[lo] < key throughout
+  while (lo + step < e && a[lo + step] < key) {
+    lo += step;
+    step <<= 1;
+  }
+  int32_t hi = min(lo + step, e);
+  ++lo;
+  while (lo < hi) {
+    const int32_t mid = (lo + hi) >> 1;
+    if (a[mid] < key) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+// Runs of 32 lanes laid end to end: lane ranks of the non-empty runs, for
+// the owner lookup of deal_owner (call with the whole warp).
+struct Deal {
+  int32_t excl, total;
+  unsigned nz;
+};
+__device__ __forceinline__ Deal deal_setup(int32_t L, int32_t* comp, int lane) {
+  Deal d;
+  int32_t incl = L;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  d.excl = incl - L;
+  d.total = __shfl_sync(0xffffffffu, incl, 31);
+  d.nz = __ballot_sync(0xffffffffu, L > 0);
+  if (L > 0) comp[__popc(d.nz & ((1u << lane) - 1u))] = lane;
+  __syncwarp();
+  return d;
+}
+// Owner lane of position k0 + lane (k0 a multiple of 32, call with the whole
+// warp): the runs starting in the window mark a 32-bit mask, and the owner is
+// the last non-empty run starting at or before the position.
+__device__ __forceinline__ int deal_owner(const Deal& d, int32_t L, int32_t k0, const int32_t* comp, int lane) {
+  const bool in_win = L > 0 && d.excl >= k0 && d.excl < k0 + 32;
+  const unsigned M = __reduce_or_sync(0xffffffffu, in_win ? 1u << (d.excl - k0) : 0u);
+  const int before = __popc(__ballot_sync(0xffffffffu, L > 0 && d.excl < k0));
+  const int r = before + __popc(M & (0xffffffffu >> (31 - lane))) - 1;
+  return comp[r < 0 ? 0 : r];
+}
+
 __global__ void __launch_bounds__(kHeavyBlock, 1) k_pass_c_heavy(DevGraph g, CountArgs a) {
   extern __shared__ uint32_t tab[];  // kHeavyTab counters
-  __shared__ int32_t s_unit, s_nx;
+  __shared__ int32_t s_unit, s_nx, s_chunk[2];
   __shared__ unsigned long long s_sx[kHeavyWarps][32];
+  __shared__ int32_t s_comp[kHeavyWarps][32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int32_t* beg = a.cbuf + (size_t)blockIdx.x * 3 * (size_t)a.cbuf_nx;
   int32_t* cur = beg + a.cbuf_nx;
   int32_t* endp = cur + a.cbuf_nx;
+  int32_t* comp = s_comp[warp];
   long long w_wedge = 0, w_blocks = 0;
   for (;;) {
     __syncthreads();
-    if (threadIdx.x == 0) s_unit = atomicAdd(a.cursor + 6, 1);
+    if (threadIdx.x == 0) s_unit = atomicAdd(a.cursor + 8, 1);
     __syncthreads();
     const int32_t k = s_unit;
     if (k >= a.n_cheavy) break;
@@ -327,6 +391,9 @@ __global__ void __launch_bounds__(kHeavyBlock, 1) k_pass_c_heavy(DevGraph g, Cou
       if (threadIdx.x == 0) atomicOr(a.status, (int32_t)kSpillOverflow);
       continue;
     }
+    const int32_t nchunks = (nx + 31) >> 5;
+    const bool half = nx < 65536;
+    const int32_t span = half ? 2 * kHeavyTab : kHeavyTab;
     for (int32_t i = threadIdx.x; i < nx; i += kHeavyBlock) {
       const int32_t x = g.ci[hb + i];
       const int32_t xb = g.rp[x];
@@ -339,80 +406,107 @@ __global__ void __launch_bounds__(kHeavyBlock, 1) k_pass_c_heavy(DevGraph g, Cou
       endp[i] = lo;
       w_wedge += lo - xb;
     }
-    for (int32_t r0 = 0; r0 < h; r0 += kHeavyTab) {
-      const int32_t r1 = min(r0 + kHeavyTab, h);
-      for (int32_t i = threadIdx.x; i < r1 - r0; i += kHeavyBlock) tab[i] = 0u;
-      if (threadIdx.x == 0) w_blocks += nx;
+    for (int64_t lo64 = 0; lo64 < h; lo64 += span) {
+      const int32_t lo_id = (int32_t)lo64;
+      const int32_t r1 = (int32_t)min(lo64 + span, (int64_t)h);
+      const int32_t words = half ? (r1 - lo_id + 1) >> 1 : r1 - lo_id;
+      for (int32_t i = threadIdx.x; i < words; i += kHeavyBlock) tab[i] = 0u;
+      if (threadIdx.x == 0) {
+        w_blocks += nx;
+        s_chunk[0] = 0;
+        s_chunk[1] = 0;
+      }
       __syncthreads();
-      // counts of the block: each thread walks the run of one x (X ascends
-      // by degree, so neighbouring threads have runs of similar length)
-      for (int32_t i = threadIdx.x; i < nx; i += kHeavyBlock) {
-        int32_t p = cur[i];
-        const int32_t e = endp[i];
-        beg[i] = p;
-        while (p < e) {
+      // counts of the block
+      for (;;) {
+        int32_t c = 0;
+        if (lane == 0) c = atomicAdd(&s_chunk[0], 1);
+        c = __shfl_sync(0xffffffffu, c, 0);
+        if (c >= nchunks) break;
+        const int32_t i = (nchunks - 1 - c) * 32 + lane;  // X ascends by degree: heaviest chunk first
+        int32_t st = 0, L = 0;
+        if (i < nx) {
+          st = cur[i];
+          const int32_t en = gallop_lower_bound(g.ci, st, endp[i], r1);
+          L = en - st;
+          beg[i] = st;
+          cur[i] = en;
+        }
+        const Deal d = deal_setup(L, comp, lane);
+        for (int32_t k0 = 0; k0 < d.total; k0 += 128) {
+          int32_t q[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int ol = deal_owner(d, L, k0 + 32 * j, comp, lane);
+            const int32_t kk = k0 + 32 * j + lane;
+            const int32_t sj = __shfl_sync(0xffffffffu, st, ol);
+            const int32_t ej = __shfl_sync(0xffffffffu, d.excl, ol);
+            q[j] = kk < d.total ? sj + (kk - ej) : -1;
+          }
           int32_t o[4];
 #pragma unroll
-          for (int j = 0; j < 4; ++j) o[j] = p + j < e ? g.ci[p + j] : 0x7fffffff;
-          int j = 0;
+          for (int j = 0; j < 4; ++j) o[j] = q[j] >= 0 ? g.ci[q[j]] : lo_id;
 #pragma unroll
-          for (; j < 4; ++j) {
-            if (o[j] >= r1) break;
-            atomicAdd(&tab[o[j] - r0], 1u);
-          }
-          p += j;
-          if (j < 4) break;
+          for (int j = 0; j < 4; ++j)
+            if (q[j] >= 0) add_count(tab, o[j] - lo_id, half);
         }
-        cur[i] = p;
+        __syncwarp();
       }
       __syncthreads();
       // attribution of the block's wedges
-      for (int32_t i0 = warp * 32; i0 < nx; i0 += kHeavyBlock) {
-        const int32_t i = i0 + lane;
+      for (;;) {
+        int32_t c = 0;
+        if (lane == 0) c = atomicAdd(&s_chunk[1], 1);
+        c = __shfl_sync(0xffffffffu, c, 0);
+        if (c >= nchunks) break;
+        const int32_t i = (nchunks - 1 - c) * 32 + lane;
         int32_t st = 0, L = 0;
         if (i < nx) {
           st = beg[i];
           L = cur[i] - st;
         }
-        int32_t incl = L;
-        for (int o = 1; o < 32; o <<= 1) {
-          const int32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-          if (lane >= o) incl += y;
-        }
-        const int32_t excl = incl - L;
-        const int32_t total = __shfl_sync(0xffffffffu, incl, 31);
-        s_sx[warp][lane] = 0ull;
+        const Deal d = deal_setup(L, comp, lane);
+        s_sx[warp][lane] = 0ull;  // per x of the chunk: sum of its wedges' counts
         __syncwarp();
-        for (int32_t k0 = 0; k0 < total; k0 += 128) {
-          int32_t q[4], ol[4];
+        for (int32_t k0 = 0; k0 < d.total; k0 += 128) {
+          int32_t q[4], ol[4], ej[4], lj[4];
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
+            ol[j] = deal_owner(d, L, k0 + 32 * j, comp, lane);
             const int32_t kk = k0 + 32 * j + lane;
-            int32_t lo = 0, hi = 31;  // owner: last lane whose run starts at or before kk
-#pragma unroll
-            for (int it = 0; it < 5; ++it) {
-              const int32_t mid = (lo + hi + 1) >> 1;
-              if (__shfl_sync(0xffffffffu, excl, mid) <= kk) lo = mid; else hi = mid - 1;
-            }
-            const int32_t sj = __shfl_sync(0xffffffffu, st, lo);
-            const int32_t ej = __shfl_sync(0xffffffffu, excl, lo);
-            ol[j] = lo;
-            q[j] = kk < total ? sj + (kk - ej) : -1;
+            const int32_t sj = __shfl_sync(0xffffffffu, st, ol[j]);
+            ej[j] = __shfl_sync(0xffffffffu, d.excl, ol[j]);
+            lj[j] = __shfl_sync(0xffffffffu, L, ol[j]);
+            q[j] = kk < d.total ? sj + (kk - ej[j]) : -1;
           }
           int32_t o[4];
 #pragma unroll
-          for (int j = 0; j < 4; ++j) o[j] = q[j] >= 0 ? g.ci[q[j]] : 0;
+          for (int j = 0; j < 4; ++j) o[j] = q[j] >= 0 ? g.ci[q[j]] : lo_id;
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
-            if (q[j] < 0) continue;
-            const uint32_t c = tab[o[j] - r0] - 1u;
-            if (c) {
-              atomicAdd(&a.P[q[j]], (unsigned long long)c);  // slot (x, o)
-              atomicAdd(&s_sx[warp][ol[j]], (unsigned long long)c);
+            uint32_t cnt = 0u;
+            if (q[j] >= 0) {
+              cnt = read_count(tab, o[j] - lo_id, half) - 1u;
+              if (cnt) atomicAdd(&a.P[q[j]], (unsigned long long)cnt);  // slot (x, o)
             }
+            // per-owner sums of this window: a prefix sum over the lanes, read
+            // at the last lane of each owner's segment
+            uint32_t S = cnt;
+            for (int off = 1; off < 32; off <<= 1) {
+              const uint32_t y = __shfl_up_sync(0xffffffffu, S, off);
+              if (lane >= off) S += y;
+            }
+            const int32_t kb = k0 + 32 * j;
+            const int head = max(ej[j] - kb, 0);
+            const uint32_t before = __shfl_sync(0xffffffffu, S, head > 0 ? head - 1 : 0);
+            const int32_t kk = kb + lane;
+            const bool tail = q[j] >= 0 && (lane == 31 || kk + 1 == ej[j] + lj[j]);
+            const uint32_t seg = S - (head > 0 ? before : 0u);
+            // tails of one window belong to distinct owners
+            if (tail && seg) s_sx[warp][ol[j]] += seg;
+            __syncwarp();
           }
         }
-        __syncwarp();
         if (i < nx) {
           const unsigned long long sx = s_sx[warp][lane];
           if (sx) atomicAdd(&a.P[hb + i], sx);  // slot (h, x)
@@ -422,9 +516,7 @@ __global__ void __launch_bounds__(kHeavyBlock, 1) k_pass_c_heavy(DevGraph g, Cou
       __syncthreads();
     }
   }
-  for (int o = 16; o; o >>= 1) {
-    w_wedge += __shfl_xor_sync(0xffffffffu, w_wedge, o);
-  }
+  for (int o = 16; o; o >>= 1) w_wedge += __shfl_xor_sync(0xffffffffu, w_wedge, o);
   if (lane == 0 && w_wedge) {
     atomicAdd(a.work + kWorkCWedge, (unsigned long long)w_wedge);
     atomicAdd(a.work + kWorkCHeavyWedge, (unsigned long long)w_wedge);

@@ -40,8 +40,9 @@ struct DevGraph {
 // Pass K (4-cliques and cross terms by lowest vertex) runs in tiers by the
 // out-degree k of the lowest vertex: the local bitmatrix of out(a) lives in
 // shared memory up to k = 1024 and in a per-CTA global buffer above.
-enum KTier { kTierGlobal = 0, kTier1024, kTier512, kTier256, kNumTiers };
-constexpr int kTierCap[kNumTiers] = {0, 1024, 512, 256};
+// Units with k <= 32 are done by one warp each, with the rows in registers.
+enum KTier { kTierGlobal = 0, kTier1024, kTier512, kTier256, kTier32, kNumTiers };
+constexpr int kTierCap[kNumTiers] = {0, 1024, 512, 256, 32};
 
 // Counting configuration chosen on the host.
 struct CountArgs {
@@ -106,7 +107,7 @@ struct Scratch {
   unsigned long long* P = nullptr;   // [2m]
   unsigned long long* x7o = nullptr; // [m]
   unsigned long long* cro = nullptr; // [m]
-  int32_t* misc = nullptr;           // cursors, status
+  int32_t* misc = nullptr;           // [16] cursors, status
   int32_t* cbuf = nullptr;           // pass C hub cursors
   int32_t cbuf_nx = 0;
   uint32_t* tables = nullptr;        // count_grid_size() x table_n
@@ -153,7 +154,7 @@ struct PrepBuffers {
   int32_t* rev = nullptr;  // [2m] slot of the reverse direction of every slot
   int32_t* ocsr = nullptr;  // [m] out-slot -> CSR slot
   int32_t* kunits = nullptr;  // pass K units (see CountArgs::kunits)
-  int32_t ktier_off[kNumTiers + 1] = {0, 0, 0, 0, 0};
+  int32_t ktier_off[kNumTiers + 1] = {0, 0, 0, 0, 0, 0};
   int32_t kmax = 0;         // largest out-degree
   int32_t* cunits = nullptr;  // pass C units: hub units (heaviest first), then the rest in unit order
   int32_t n_cheavy = 0;

@@ -184,8 +184,8 @@ __global__ void k_bin_scatter(int32_t n, const int32_t* __restrict__ deg,
 
 // Pass K units: every vertex a with |out(a)| = k >= 2 (a triangle needs two
 // higher-rank neighbours), binned by ceil(log2 k) and listed largest bin
-// first, so that the tiers of pass K (k > 1024, <= 1024, <= 512, <= 256) are
-// contiguous ranges of the list.
+// first, so that the tiers of pass K (k > 1024, <= 1024, <= 512, <= 256,
+// <= 32) are contiguous ranges of the list.
 __device__ __forceinline__ int kbin_of(int32_t k) { return 32 - __clz(k - 1); }
 
 __global__ void k_kbin_hist(int32_t n, const int32_t* __restrict__ out_cnt, int32_t* __restrict__ hist) {
@@ -389,8 +389,9 @@ gc_status classify_c_units(int32_t n, const int32_t* d_rp, const int32_t* d_ci, 
   // the o-range; it is worth it when the wedges clearly outnumber that.
   std::vector<int32_t> heavy;
   for (int32_t k = 0; k < nu; ++k) {
-    const long long blocks = ((long long)U[k] + kHeavyTab - 1) / kHeavyTab;
-    if (W[k] >= 65536 && W[k] >= blocks * (2048 + 4LL * NX[k])) heavy.push_back(k);
+    const long long span = NX[k] < 65536 ? 2LL * kHeavyTab : kHeavyTab;  // 16-bit counters below 65536
+    const long long blocks = ((long long)U[k] + span - 1) / span;
+    if (W[k] >= 65536 && W[k] >= blocks * (2048 + 4LL * NX[k]) && NX[k] < (1 << 26)) heavy.push_back(k);
   }
   std::sort(heavy.begin(), heavy.end(), [&](int32_t a, int32_t b) { return W[a] > W[b]; });
   std::vector<char> is_heavy(nu, 0);
@@ -484,13 +485,14 @@ gc_status prepare_graph(int32_t n, int32_t m, const int32_t* d_rp, const int32_t
       GC_TRY(cudaStreamSynchronize(s), "sync hist");
       P.dmax = h[0];
       P.kmax = h[65];
-      {  // pass-K units, largest bin first; tier boundaries at k = 1024, 512, 256
+      {  // pass-K units, largest bin first; tier boundaries at k = 1024, 512, 256, 32
         int32_t kc[32];
         int32_t acc = 0;
         for (int b = 31; b >= 0; --b) {
           if (b == 10) P.ktier_off[kTier1024] = acc;
           if (b == 9) P.ktier_off[kTier512] = acc;
           if (b == 8) P.ktier_off[kTier256] = acc;
+          if (b == 5) P.ktier_off[kTier32] = acc;
           kc[b] = acc;
           acc += h[66 + b];
         }

@@ -41,7 +41,7 @@ gc_status scratch_init(Scratch* sc, int32_t m, int32_t table_n, int32_t kmax, in
   GS_TRY(cudaMallocAsync(&sc->P, sizeof(unsigned long long) * 2 * m1, s));
   GS_TRY(cudaMallocAsync(&sc->x7o, sizeof(unsigned long long) * m1, s));
   GS_TRY(cudaMallocAsync(&sc->cro, sizeof(unsigned long long) * m1, s));
-  GS_TRY(cudaMallocAsync(&sc->misc, sizeof(int32_t) * 8, s));
+  GS_TRY(cudaMallocAsync(&sc->misc, sizeof(int32_t) * 16, s));
   GS_TRY(cudaMallocAsync(&sc->work, sizeof(unsigned long long) * kNumWork, s));
   if (table_n > kSmemTableMax) {
     sc->tables_n = (size_t)count_grid_size() * (size_t)table_n;
@@ -87,7 +87,7 @@ gc_status run_count(const DevGraph& g, const int32_t* units, int32_t n_units, co
   a.cbuf = sc->cbuf;
   a.cbuf_nx = sc->cbuf_nx;
   for (int t = 0; t <= kNumTiers; ++t) a.ktier_off[t] = ku.tier_off[t];
-  a.cursor = sc->misc;  // [0] passes A and C, [2 + tier] pass K, [6] pass C hubs
+  a.cursor = sc->misc;  // [0] passes A and C, [2 + tier] pass K, [8] pass C hubs
   a.status = sc->misc + 1;
   a.tables = g.table_n > kSmemTableMax ? sc->tables : nullptr;
   a.tri = sc->tri;
@@ -103,7 +103,7 @@ gc_status run_count(const DevGraph& g, const int32_t* units, int32_t n_units, co
   a.csum = csum;
   a.work = sc->work;
   const size_t m1 = (size_t)(g.m > 0 ? g.m : 1);
-  GR_TRY(cudaMemsetAsync(sc->misc, 0, sizeof(int32_t) * 8, s), "memset misc");
+  GR_TRY(cudaMemsetAsync(sc->misc, 0, sizeof(int32_t) * 16, s), "memset misc");
   GR_TRY(cudaMemsetAsync(sc->work, 0, sizeof(unsigned long long) * kNumWork, s), "memset work");
   GR_TRY(cudaMemsetAsync(csum, 0, sizeof(unsigned long long) * 26 * (size_t)g.G, s), "memset sums");
   GR_TRY(cudaMemsetAsync(sc->P, 0, sizeof(unsigned long long) * 2 * m1, s), "zero P");
