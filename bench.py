@@ -59,8 +59,9 @@ def load_workload(name: str, scale: int):
 def algorithmic_bytes(work: dict) -> dict:
     """Algorithmic bytes per launch of each counting kernel, from the units the
     kernels report (gc_graph_work_counts); the per-unit figures:
-      pass A: 8 per entry of Gamma(v) and of the Gamma(u) scans (read + Psi),
-              plus 16 per edge for re-indexing |T| by out-slot
+      pass T: 20 per member of out(a) (id, out-list bounds, 4-byte
+              read-modify-write flush), 4 per out-list entry scanned, 8 per
+              triangle (4-byte read-modify-write of |T| of the found edge)
       pass C: 48 per wedge h-x-o (entry read, count RMW, attribution read,
               edge id, P atomic, clear)
       pass K: 48 per member of out(a) (id, |T|, out-list bounds, two 8-byte
@@ -69,7 +70,7 @@ def algorithmic_bytes(work: dict) -> dict:
       finish: 168 per edge (64 read: slot maps, endpoints, degrees, |T|, P of
               both slots, x7, cross; 104 written: the 13-column row)"""
     return {
-        "k_pass_a": 8 * work["a_units"] + 16 * work["finish_edges"],
+        "k_pass_t": 20 * work["t_members"] + 4 * work["t_scan"] + 8 * work["t_triangles"],
         "k_pass_c": 48 * work["c_wedges"],
         "k_pass_k": 48 * work["k_members"] + 4 * work["k_scan"] + 36 * work["k_local_edges"],
         "k_finish": 168 * work["finish_edges"],
@@ -444,7 +445,7 @@ def main():
         except Exception:
             peak, peak_src = 6800.0, "fallback"
     ph_ms = {k: statistics.mean(p[k] for p in phases) for k in phases[0]}
-    kernel_ms = {"k_pass_a": ph_ms["pass_a_triangles"], "k_pass_c": ph_ms["pass_c_cycles"],
+    kernel_ms = {"k_pass_t": ph_ms["pass_t_triangles"], "k_pass_c": ph_ms["pass_c_cycles"],
                  "k_pass_k": ph_ms["pass_k_cliques"], "k_finish": ph_ms["finish_columns"]}
     ab = algorithmic_bytes(work)
     kernels = {k: {"ms": kernel_ms[k], "algorithmic_bytes": ab[k],

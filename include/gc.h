@@ -129,7 +129,7 @@ gc_status gc_graph_csums(gc_graph g, uint64_t* lo, uint64_t* hi);
 
 /* Device time of each phase of the last gc_count_edge_graphlets, measured
  * with CUDA events on the graph's stream. ms: host array of
- * gc_phase_count() doubles. Phases, in order: "pass_a_triangles" (Alg. 1),
+ * gc_phase_count() doubles. Phases, in order: "pass_t_triangles" (Alg. 1),
  * "pass_c_cycles" (4-cycles through each edge, Alg. 4/6), "pass_k_cliques"
  * (4-cliques and cross terms, Alg. 3/5), "finish_columns" (Sec. 4.5 columns
  * and sums), "derive" (Sec. 4.6), "copy_out". */
@@ -139,7 +139,7 @@ gc_status gc_graph_phase_ms(gc_graph g, double* ms);
 
 /* Units of work the kernels processed in the last gc_count_edge_graphlets on
  * g (host pointer, GC_NUM_WORK uint64), in this order:
- *   0 pass A (triangles): sum of d_v over v-groups plus d_u over their edges
+ *   0 pass T (triangles): sum over lowest vertices a of |out(a)|
  *   1 pass C (4-cycles): wedges h-x-o
  *   2 pass K (4-cliques): sum over lowest vertices a of |out(a)|
  *   3 pass K: out-list entries scanned to build the induced subgraphs H_a
@@ -149,8 +149,10 @@ gc_status gc_graph_phase_ms(gc_graph g, double* ms);
  *   7 kernels launched by the count
  *   8 pass C: wedges of the hub units (counted in shared-memory blocks)
  *   9 pass C: lower neighbours swept, summed over the blocks of the hub units
+ *  10 pass T: out-list entries scanned
+ *  11 pass T: triangles (each once)
  * Used to turn kernel times into algorithmic bytes per second. */
-#define GC_NUM_WORK 10
+#define GC_NUM_WORK 12
 gc_status gc_graph_work_counts(gc_graph g, uint64_t* out);
 
 /* Release the graph and all its device memory. NULL is accepted. */

@@ -37,8 +37,8 @@ EXPORTED = ["gc_last_error", "gc_graph_upload", "gc_graph_info", "gc_graph_edges
             "gc_graph_phase_ms", "gc_graph_free", "gc_batch_create", "gc_batch_submit",
             "gc_batch_flush", "gc_batch_poll", "gc_batch_destroy", "gc_edge_triangles_noalloc",
             "gc_graph_work_counts", "gc_batch_submit_many"]
-WORK_NAMES = ["a_units", "c_wedges", "k_members", "k_scan", "k_local_edges", "k_words", "finish_edges", "launches",
-              "c_heavy_wedges", "c_heavy_sweeps"]
+WORK_NAMES = ["t_members", "c_wedges", "k_members", "k_scan", "k_local_edges", "k_words", "finish_edges", "launches",
+              "c_heavy_wedges", "c_heavy_sweeps", "t_scan", "t_triangles"]
 
 
 class GcError(RuntimeError):

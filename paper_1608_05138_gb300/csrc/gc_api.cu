@@ -448,7 +448,7 @@ gc_status gc_graph_work_counts(gc_graph g, uint64_t* out) {
 int gc_phase_count(void) { return kNumPhases; }
 
 const char* gc_phase_name(int i) {
-  static const char* names[kNumPhases] = {"pass_a_triangles", "pass_c_cycles", "pass_k_cliques",
+  static const char* names[kNumPhases] = {"pass_t_triangles", "pass_c_cycles", "pass_k_cliques",
                                           "finish_columns", "derive", "copy_out"};
   return (i >= 0 && i < kNumPhases) ? names[i] : "";
 }

@@ -53,7 +53,7 @@ struct KLayout {
   size_t vx7, vcr, ids, ta, hash, rows, total;
   int hcap;
   __host__ __device__ static size_t up16(size_t x) { return (x + 15) & ~(size_t)15; }
-  __host__ __device__ explicit KLayout(int cap) {
+  __host__ __device__ explicit KLayout(int cap, bool with_rows = true) {
     int hb = 1;
     while ((1 << hb) < 2 * cap) ++hb;
     hcap = 1 << hb;
@@ -63,12 +63,15 @@ struct KLayout {
     ids = o; o = up16(o + 4 * (size_t)cap);
     ta = o; o = up16(o + 4 * (size_t)cap);
     hash = o; o = up16(o + 4 * (size_t)hcap);
-    rows = o; o = up16(o + 4 * (size_t)cap * (size_t)row_stride(cap));
+    rows = o; o = with_rows ? up16(o + 4 * (size_t)cap * (size_t)row_stride(cap)) : o;
     total = o;
   }
 };
 
-template <int kCap, int kThreads>
+// kTri: the triangle step alone (|T| per edge, Alg. 1): every triangle is an
+// edge of exactly one H_a, so phase 1 adds 1 to that edge and to the two
+// edges (a, b_i), (a, b_j), and nothing else runs.
+template <int kCap, int kThreads, bool kTri>
 __global__ void __launch_bounds__(kThreads, 65536 / (kThreads * 64)) k_pass_k(DevGraph g, CountArgs a, int tier) {
   constexpr int kW = kThreads / 32;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -77,7 +80,7 @@ __global__ void __launch_bounds__(kThreads, 65536 / (kThreads * 64)) k_pass_k(De
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int cap = kCap ? kCap : a.kbuf_cap;
-  const KLayout L(cap);
+  const KLayout L(cap, !kTri);
   unsigned char* base = kCap ? smem : a.kbuf + (size_t)blockIdx.x * a.kbuf_stride;
   unsigned long long* vx7 = reinterpret_cast<unsigned long long*>(base + L.vx7);
   unsigned long long* vcr = reinterpret_cast<unsigned long long*>(base + L.vcr);
@@ -89,7 +92,7 @@ __global__ void __launch_bounds__(kThreads, 65536 / (kThreads * 64)) k_pass_k(De
   int32_t* qq = s_qq[warp];
 
   const int32_t u0 = a.ktier_off[tier], u1 = a.ktier_off[tier + 1];
-  int32_t* cursor = a.cursor + 2 + tier;
+  int32_t* cursor = a.cursor + (kTri ? 10 : 2) + tier;
   long long w_members = 0, w_scan = 0, w_edges = 0, w_words = 0;  // per warp, lane 0
 
   for (;;) {
@@ -116,12 +119,15 @@ __global__ void __launch_bounds__(kThreads, 65536 / (kThreads * 64)) k_pass_k(De
 
     for (int32_t i = threadIdx.x; i < k; i += kThreads) {
       ids[i] = g.out_idx[ob + i];
-      ta[i] = a.trio[ob + i];
       vx7[i] = 0ull;
-      vcr[i] = 0ull;
+      if (!kTri) {
+        ta[i] = a.trio[ob + i];
+        vcr[i] = 0ull;
+      }
     }
     for (int32_t i = threadIdx.x; i <= (int32_t)hmask; i += kThreads) hash[i] = 0;
-    for (int32_t i = threadIdx.x; i < k * S; i += kThreads) rows[i] = 0u;
+    if (!kTri)
+      for (int32_t i = threadIdx.x; i < k * S; i += kThreads) rows[i] = 0u;
     if (threadIdx.x == 0) w_members += k;
     __syncthreads();
     for (int32_t i = threadIdx.x; i < k; i += kThreads) {  // Psi: id -> 1 + position in out(a)
@@ -154,13 +160,28 @@ __global__ void __launch_bounds__(kThreads, 65536 / (kThreads * 64)) k_pass_k(De
         if (__shfl_sync(kFull, c, 0) > cmax) break;  // out(b) ascends: nothing further is in out(a)
         if (lane == 0) w_scan += min(32, be - q0);
         const int32_t j = c <= cmax ? lookup(c) : -1;
-        if (j >= 0) {
+        if (kTri) {
+          const unsigned hit = __ballot_sync(kFull, j >= 0);
+          if (j >= 0) {
+            atomicAdd(&a.trio[q], 1);  // edge (b_i, c)
+            atomicAdd(&vx7[j], 1ull);  // edge (a, c)
+          }
+          if (lane == 0 && hit) {
+            atomicAdd(&vx7[i], (unsigned long long)__popc(hit));  // edge (a, b_i)
+            w_edges += __popc(hit);
+          }
+        } else if (j >= 0) {
           atomicOr(&rows[i * S + (j >> 5)], 1u << (j & 31));
           atomicOr(&rows[j * S + (i >> 5)], 1u << (i & 31));
         }
       }
     }
     __syncthreads();
+    if (kTri) {
+      for (int32_t i = threadIdx.x; i < k; i += kThreads)
+        if (vx7[i]) atomicAdd(&a.trio[ob + i], (int32_t)vx7[i]);
+      continue;
+    }
 
     // Phase 2: per edge (i, j) of H_a, c_ij and the cross terms.
     for (;;) {
@@ -241,9 +262,9 @@ __global__ void __launch_bounds__(kThreads, 65536 / (kThreads * 64)) k_pass_k(De
     }
   }
   if (lane == 0) {
-    if (w_members) atomicAdd(a.work + kWorkKMembers, (unsigned long long)w_members);
-    if (w_scan) atomicAdd(a.work + kWorkKScan, (unsigned long long)w_scan);
-    if (w_edges) atomicAdd(a.work + kWorkKLocalEdges, (unsigned long long)w_edges);
+    if (w_members) atomicAdd(a.work + (kTri ? kWorkTMembers : kWorkKMembers), (unsigned long long)w_members);
+    if (w_scan) atomicAdd(a.work + (kTri ? kWorkTScan : kWorkKScan), (unsigned long long)w_scan);
+    if (w_edges) atomicAdd(a.work + (kTri ? kWorkTTriangles : kWorkKLocalEdges), (unsigned long long)w_edges);
     if (w_words) atomicAdd(a.work + kWorkKWords, (unsigned long long)w_words);
   }
 }
@@ -260,12 +281,13 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long x)
   return x;
 }
 
+template <bool kTri>
 __global__ void __launch_bounds__(kWBlock) k_pass_k_warp(DevGraph g, CountArgs a, int tier) {
   __shared__ int32_t s_q[kWWarps][32 * 32];  // out-slot of edge (i, j) found from member i
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int32_t* qs = s_q[warp];
   const int32_t u0 = a.ktier_off[tier], u1 = a.ktier_off[tier + 1];
-  int32_t* cursor = a.cursor + 2 + tier;
+  int32_t* cursor = a.cursor + (kTri ? 10 : 2) + tier;
   long long w_members = 0, w_scan = 0, w_edges = 0;  // lane 0
   for (;;) {
     int32_t ui = 0;
@@ -280,7 +302,7 @@ __global__ void __launch_bounds__(kWBlock) k_pass_k_warp(DevGraph g, CountArgs a
       continue;
     }
     const int32_t id = lane < k ? g.out_idx[ob + lane] : 0x7fffffff;
-    const int32_t ti = lane < k ? a.trio[ob + lane] : 0;
+    const int32_t ti = (!kTri && lane < k) ? a.trio[ob + lane] : 0;
     const int32_t cmax = __shfl_sync(kFull, id, k - 1);
     unsigned row = 0u, found = 0u;
     // Phase 1: the edges of H_a.
@@ -298,7 +320,11 @@ __global__ void __launch_bounds__(kWBlock) k_pass_k_warp(DevGraph g, CountArgs a
         for (int step = 16; step; step >>= 1)
           if (__shfl_sync(kFull, id, lo + step) <= c) lo += step;
         const bool hit = __shfl_sync(kFull, id, lo) == c && lo < k;  // lanes >= k hold padding ids
-        if (hit) qs[i * 32 + lo] = q;
+        if (kTri) {
+          if (hit) atomicAdd(&a.trio[q], 1);  // edge (b_i, c)
+        } else if (hit) {
+          qs[i * 32 + lo] = q;
+        }
         hits |= __reduce_or_sync(kFull, hit ? 1u << lo : 0u);
       }
       if (lane == i) {
@@ -307,6 +333,11 @@ __global__ void __launch_bounds__(kWBlock) k_pass_k_warp(DevGraph g, CountArgs a
       }
       if ((hits >> lane) & 1u) row |= 1u << i;
       if (lane == 0) w_edges += __popc(hits);
+    }
+    if (kTri) {  // edge (a, b_lane): one triangle per edge of H_a at lane
+      if (lane < k && row) atomicAdd(&a.trio[ob + lane], __popc(row));
+      if (lane == 0) w_members += k;
+      continue;
     }
     __syncwarp();
     // Phase 2: c_ij and the cross terms of every edge (i, j) of H_a.
@@ -343,21 +374,21 @@ __global__ void __launch_bounds__(kWBlock) k_pass_k_warp(DevGraph g, CountArgs a
     __syncwarp();
   }
   if (lane == 0) {
-    if (w_members) atomicAdd(a.work + kWorkKMembers, (unsigned long long)w_members);
-    if (w_scan) atomicAdd(a.work + kWorkKScan, (unsigned long long)w_scan);
+    if (w_members) atomicAdd(a.work + (kTri ? kWorkTMembers : kWorkKMembers), (unsigned long long)w_members);
+    if (w_scan) atomicAdd(a.work + (kTri ? kWorkTScan : kWorkKScan), (unsigned long long)w_scan);
     if (w_edges) {
-      atomicAdd(a.work + kWorkKLocalEdges, (unsigned long long)w_edges);
-      atomicAdd(a.work + kWorkKWords, (unsigned long long)w_edges);
+      atomicAdd(a.work + (kTri ? kWorkTTriangles : kWorkKLocalEdges), (unsigned long long)w_edges);
+      if (!kTri) atomicAdd(a.work + kWorkKWords, (unsigned long long)w_edges);
     }
   }
 }
 
-template <int kCap, int kThreads>
+template <int kCap, int kThreads, bool kTri>
 gc_status launch_tier(const DevGraph& g, const CountArgs& a, int tier, cudaStream_t s, int* launches) {
   const int32_t units = a.ktier_off[tier + 1] - a.ktier_off[tier];
   if (units <= 0) return GC_OK;
-  const size_t smem = kCap ? KLayout(kCap).total : 0;
-  auto kern = k_pass_k<kCap, kThreads>;
+  const size_t smem = kCap ? KLayout(kCap, !kTri).total : 0;
+  auto kern = k_pass_k<kCap, kThreads, kTri>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return cuda_fail(e, "k_pass_k attribute");
   int grid = 0;
@@ -377,36 +408,45 @@ gc_status launch_tier(const DevGraph& g, const CountArgs& a, int tier, cudaStrea
   return e == cudaSuccess ? GC_OK : cuda_fail(e, "k_pass_k");
 }
 
-}  // namespace
-
-size_t kbuf_bytes(int32_t cap) { return cap > 0 ? KLayout(cap).total : 0; }
-
-gc_status run_pass_k(const DevGraph& g, const CountArgs& a, cudaStream_t s, int* launches) {
+template <bool kTri>
+gc_status run_tiers(const DevGraph& g, const CountArgs& a, cudaStream_t s, int* launches) {
   gc_status st;
   if (a.ktier_off[kTierGlobal + 1] > a.ktier_off[kTierGlobal]) {
     if (!a.kbuf || a.kbuf_ctas < 1) {
       set_error("internal: pass K global buffers missing");
       return GC_ERR_CUDA;
     }
-    if ((st = launch_tier<0, 1024>(g, a, kTierGlobal, s, launches)) != GC_OK) return st;
+    if ((st = launch_tier<0, 1024, kTri>(g, a, kTierGlobal, s, launches)) != GC_OK) return st;
   }
-  if ((st = launch_tier<1024, 1024>(g, a, kTier1024, s, launches)) != GC_OK) return st;
-  if ((st = launch_tier<512, 512>(g, a, kTier512, s, launches)) != GC_OK) return st;
-  if ((st = launch_tier<256, 512>(g, a, kTier256, s, launches)) != GC_OK) return st;
+  if ((st = launch_tier<1024, 1024, kTri>(g, a, kTier1024, s, launches)) != GC_OK) return st;
+  if ((st = launch_tier<512, 512, kTri>(g, a, kTier512, s, launches)) != GC_OK) return st;
+  if ((st = launch_tier<256, 512, kTri>(g, a, kTier256, s, launches)) != GC_OK) return st;
   const int32_t units = a.ktier_off[kTier32 + 1] - a.ktier_off[kTier32];
   if (units > 0) {
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pass_k_warp, kWBlock, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pass_k_warp<kTri>, kWBlock, 0);
     if (e != cudaSuccess) return cuda_fail(e, "k_pass_k_warp occupancy");
     int grid = (per_sm > 0 ? per_sm : 1) * (count_grid_size() / kCtasPerSm);
     const int need = (units + kWWarps - 1) / kWWarps;
     if (grid > need) grid = need;
-    k_pass_k_warp<<<grid, kWBlock, 0, s>>>(g, a, kTier32);
+    k_pass_k_warp<kTri><<<grid, kWBlock, 0, s>>>(g, a, kTier32);
     ++*launches;
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "k_pass_k_warp");
   }
   return GC_OK;
+}
+
+}  // namespace
+
+size_t kbuf_bytes(int32_t cap) { return cap > 0 ? KLayout(cap).total : 0; }
+
+gc_status run_pass_k(const DevGraph& g, const CountArgs& a, cudaStream_t s, int* launches) {
+  return run_tiers<false>(g, a, s, launches);
+}
+
+gc_status run_pass_t(const DevGraph& g, const CountArgs& a, cudaStream_t s, int* launches) {
+  return run_tiers<true>(g, a, s, launches);
 }
 
 }  // namespace gc

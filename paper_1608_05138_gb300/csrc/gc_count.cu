@@ -1,14 +1,13 @@
 // gc_count.cu -- the triangle and 4-cycle passes, the per-edge finish and the
 // derivation of the global counts.
 //
-// Work unit of passes A and C: one "v-group" = a vertex v and every edge
-// e = (u, v) for which v is the high endpoint (P3, Sec. 4.3: d_v >= d_u, ties
-// to the larger id). One CTA owns one unit at a time and a Psi table indexed
-// by vertex; CTAs take units from an atomic cursor over the difficulty-ordered
+// Work unit of pass C: one "v-group" = a vertex v and every edge e = (u, v)
+// for which v is the high endpoint (P3, Sec. 4.3: d_v >= d_u, ties to the
+// larger id). One CTA owns one unit at a time and a count table indexed by
+// vertex; CTAs take units from an atomic cursor over the difficulty-ordered
 // unit list (work stealing over Pi, Sec. 4.4).
 //
-// Pass A -- triangle step (Alg. 1): Psi(r) = lambda1 for r in Gamma(v); for
-//   every low neighbour u, |T| = #{w in Gamma(u) : Psi(w) = lambda1}.
+// Pass T (gc_clique.cu) -- triangle step (Alg. 1): |T| per edge.
 //
 // Pass C -- 4-cycle step (Alg. 4/6) reorganised: P(e), the number of
 //   4-cycles (as subgraphs) through e = #{(w, r) : w in Gamma(u)\{v},
@@ -40,15 +39,6 @@ namespace {
 __device__ __forceinline__ bool rank_less(const int32_t* __restrict__ deg, int32_t a, int32_t b) {
   int32_t da = deg[a], db = deg[b];
   return da < db || (da == db && a < b);
-}
-
-__device__ __forceinline__ int warp_sum_i(int x) {
-  for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-  return x;
-}
-__device__ __forceinline__ long long warp_sum_ll(long long x) {
-  for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-  return x;
 }
 
 __device__ __forceinline__ void atomic_add_u128(unsigned long long* p, u128 v) {
@@ -90,59 +80,6 @@ __device__ __forceinline__ int csum_column(int k) {
 template <bool kSmemTable>
 __device__ __forceinline__ uint32_t* table_of(const DevGraph& g, const CountArgs& a, uint32_t* smem) {
   return kSmemTable ? smem : a.tables + (size_t)blockIdx.x * (size_t)g.table_n;
-}
-
-// ---------------- pass A: |T| per edge ----------------
-template <bool kSmemTable>
-__global__ void __launch_bounds__(kBlock) k_pass_a(DevGraph g, CountArgs a) {
-  extern __shared__ uint32_t smem[];
-  __shared__ int32_t s_unit, s_next;
-  uint32_t* tab = table_of<kSmemTable>(g, a, smem);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  long long w_units = 0;
-  if (kSmemTable)
-    for (int32_t i = threadIdx.x; i < g.table_n; i += kBlock) tab[i] = 0;
-  for (;;) {
-    __syncthreads();
-    if (threadIdx.x == 0) s_unit = atomicAdd(a.cursor, 1);
-    __syncthreads();
-    const int32_t k = s_unit;
-    if (k >= a.n_units) {
-      if (lane == 0 && w_units) atomicAdd(a.work + kWorkAUnits, (unsigned long long)w_units);
-      break;
-    }
-    const int32_t v = a.units[k];
-    const int32_t base = g.gbase[g.vgid ? g.vgid[v] : 0];
-    const int32_t vb = g.rp[v], ve = g.rp[v + 1];
-    for (int32_t p = vb + threadIdx.x; p < ve; p += kBlock) tab[g.ci[p] - base] = 1u;
-    if (threadIdx.x == 0) w_units += ve - vb;
-    if (threadIdx.x == 0) s_next = vb;
-    __syncthreads();
-    for (;;) {  // edges of the group handed to warps one at a time
-      int32_t p = 0;
-      if (lane == 0) p = atomicAdd(&s_next, 1);
-      p = __shfl_sync(0xffffffffu, p, 0);
-      if (p >= ve) break;
-      const int32_t u = g.ci[p];
-      if (!rank_less(g.deg, u, v)) continue;
-      const int32_t ub = g.rp[u], ue = g.rp[u + 1];
-      int c = 0;
-      for (int32_t q = ub + lane; q < ue; q += 32) c += tab[g.ci[q] - base] != 0u;
-      c = warp_sum_i(c);
-      if (lane == 0) {
-        a.tri[g.eid[p]] = c;
-        w_units += ue - ub;
-      }
-    }
-    __syncthreads();
-    for (int32_t p = vb + threadIdx.x; p < ve; p += kBlock) tab[g.ci[p] - base] = 0u;
-  }
-}
-
-// ---------------- per-edge |T| by out-slot ----------------
-__global__ void k_trio(DevGraph g, const int32_t* __restrict__ tri, int32_t* __restrict__ trio) {
-  for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < g.m; o += (int64_t)gridDim.x * blockDim.x)
-    trio[o] = tri[g.eid[g.ocsr[o]]];
 }
 
 // ---------------- finish: x10, per-edge columns, sums ----------------
@@ -212,7 +149,7 @@ __global__ void __launch_bounds__(kBlock) k_pass_c(DevGraph g, CountArgs a) {
   extern __shared__ uint32_t smem[];
   __shared__ int32_t s_unit, s_next[3];
   uint32_t* tab = table_of<kSmemTable>(g, a, smem);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31;
   const bool zero_all = kSmemTable && g.table_n <= 4096;
   long long w_wedge = 0;
   if (kSmemTable)
@@ -605,12 +542,6 @@ int count_grid_size() {
   return g_grid;
 }
 
-gc_status run_pass_a(const DevGraph& g, const CountArgs& a, cudaStream_t s) {
-  const bool sm = a.tables == nullptr;
-  if (sm) return launch(k_pass_a<true>, smem_bytes(true, g.table_n), g, a, s, "k_pass_a");
-  return launch(k_pass_a<false>, smem_bytes(false, g.table_n), g, a, s, "k_pass_a");
-}
-
 gc_status run_pass_c(const DevGraph& g, const CountArgs& a, cudaStream_t s) {
   const bool sm = a.tables == nullptr;
   if (sm) return launch(k_pass_c<true>, smem_bytes(true, g.table_n), g, a, s, "k_pass_c");
@@ -627,14 +558,6 @@ gc_status run_pass_c_heavy(const DevGraph& g, const CountArgs& a, cudaStream_t s
   k_pass_c_heavy<<<grid, kHeavyBlock, smem, s>>>(g, a);
   e = cudaGetLastError();
   return e == cudaSuccess ? GC_OK : cuda_fail(e, "k_pass_c_heavy");
-}
-
-gc_status run_trio(const DevGraph& g, const CountArgs& a, cudaStream_t s) {
-  if (g.m == 0) return GC_OK;
-  int blocks = (int)min((int64_t)count_grid_size() * 4, ((int64_t)g.m + 255) / 256);
-  k_trio<<<blocks, 256, 0, s>>>(g, a.tri, a.trio);
-  cudaError_t e = cudaGetLastError();
-  return e == cudaSuccess ? GC_OK : cuda_fail(e, "k_trio");
 }
 
 gc_status run_finish(const DevGraph& g, const CountArgs& a, cudaStream_t s) {

@@ -46,7 +46,7 @@ constexpr int kTierCap[kNumTiers] = {0, 1024, 512, 256, 32};
 
 // Counting configuration chosen on the host.
 struct CountArgs {
-  const int32_t* units;    // passes A and C: v-groups (high endpoints), heaviest bin first
+  const int32_t* units;    // pass C: v-groups (high endpoints), heaviest bin first
   int32_t n_units;
   const int32_t* cunits;   // pass C: hub units first (blocked kernel), then the others
   int32_t n_cheavy;        // hub units of pass C (cunits[0 .. n_cheavy))
@@ -56,8 +56,7 @@ struct CountArgs {
   int32_t ktier_off[kNumTiers + 1];  // tier t = kunits[ktier_off[t] .. ktier_off[t + 1])
   int32_t* cursor;         // work-stealing cursors (device ints, zeroed before each launch)
   uint32_t* tables;        // global Psi tables (grid x table_n) or nullptr (shared memory)
-  int32_t* tri;            // [m] per-edge |T| by edge id (pass A)
-  int32_t* trio;           // [m] |T| by out-slot
+  int32_t* trio;           // [m] |T| by out-slot (pass T)
   unsigned long long* P;   // [2m] per slot: 4-cycles through its edge counted at that slot
                            // (pass C, zeroed before); an edge's count = sum of its two slots
   unsigned long long* x7o;   // [m] per out-slot: 4-cliques through the edge (pass K)
@@ -75,7 +74,7 @@ struct CountArgs {
 // Work counters (units the kernels processed; bench.py turns them into
 // algorithmic bytes).
 enum Work {
-  kWorkAUnits = 0,     // pass A: sum of d_v + sum of d_u
+  kWorkTMembers = 0,   // pass T: sum over units of |out(a)|
   kWorkCWedge,         // pass C: wedges h-x-o
   kWorkKMembers,       // pass K: sum over units of |out(a)|
   kWorkKScan,          // pass K: out-list entries scanned to build the local graphs
@@ -85,6 +84,8 @@ enum Work {
   kWorkLaunches,       // kernels launched by the count (counted on the host)
   kWorkCHeavyWedge,    // pass C: wedges of the hub units (blocked kernel)
   kWorkCBlocks,        // pass C: lower neighbours swept, summed over the blocks of the hub units
+  kWorkTScan,          // pass T: out-list entries scanned
+  kWorkTTriangles,     // pass T: triangles (each once)
   kNumWork
 };
 
@@ -97,12 +98,11 @@ constexpr int kSmallN = 512;           // graphs up to this many vertices use th
 constexpr int kSmemTableMax = 4096;    // Psi tables up to this many vertices live in shared memory
 
 // Phases timed with CUDA events.
-enum Phase { kPhasePassA = 0, kPhasePassC, kPhasePassK, kPhaseFinish, kPhaseDerive, kPhaseCopy, kNumPhases };
+enum Phase { kPhasePassT = 0, kPhasePassC, kPhasePassK, kPhaseFinish, kPhaseDerive, kPhaseCopy, kNumPhases };
 
 // Device scratch of one count (lazily grown; owned by a graph handle or by
 // one batch launch).
 struct Scratch {
-  int32_t* tri = nullptr;            // [m]
   int32_t* trio = nullptr;           // [m]
   unsigned long long* P = nullptr;   // [2m]
   unsigned long long* x7o = nullptr; // [m]
@@ -123,7 +123,7 @@ struct Scratch {
 // vertices and largest out-degree kmax (stream-ordered).
 gc_status scratch_init(Scratch* sc, int32_t m, int32_t table_n, int32_t kmax, int32_t cnx_max, cudaStream_t s);
 void scratch_free(Scratch* sc, cudaStream_t s);
-// The whole count: passes A, C, K, finish, derive. csum [G][13][2] and
+// The whole count: passes T, C, K, finish, derive. csum [G][13][2] and
 // x [G][17][2] are device arrays; ev (optional) receives kNumPhases + 1
 // events. Returns after the derive is queued (no host synchronisation).
 struct KUnits {
@@ -183,15 +183,14 @@ gc_status run_small_graphs(const int32_t* rp, const int64_t* voff, const int32_t
                            const int32_t* order, int32_t G, int32_t* cursor, unsigned long long* csum,
                            cudaStream_t s);
 
-// ---- counting (gc_count.cu: passes A, C, derive; gc_clique.cu: pass K, finish) ----
+// ---- counting (gc_count.cu: pass C, finish, derive; gc_clique.cu: passes T and K) ----
 int count_grid_size();
-gc_status run_pass_a(const DevGraph& g, const CountArgs& a, cudaStream_t s);
 gc_status run_pass_c(const DevGraph& g, const CountArgs& a, cudaStream_t s);
 gc_status run_pass_c_heavy(const DevGraph& g, const CountArgs& a, cudaStream_t s);
 constexpr int kHeavyTab = 49152;  // o-range block of the hub kernel of pass C (entries in shared memory)
 gc_status run_derive(const DevGraph& g, const unsigned long long* csum, unsigned long long* x,
                      int32_t* status, cudaStream_t s);
-gc_status run_trio(const DevGraph& g, const CountArgs& a, cudaStream_t s);
+gc_status run_pass_t(const DevGraph& g, const CountArgs& a, cudaStream_t s, int* launches);
 gc_status run_pass_k(const DevGraph& g, const CountArgs& a, cudaStream_t s, int* launches);
 gc_status run_finish(const DevGraph& g, const CountArgs& a, cudaStream_t s);
 // Bytes of one global-tier buffer for out-degrees up to cap.

@@ -1,8 +1,7 @@
 // gc_run.cu -- the sequence of one count, shared by the whole-graph and the
 // batched paths.
 //
-//   pass A  triangle step: |T| per edge                          (Alg. 1)
-//   trio    |T| re-indexed by out-slot
+//   pass T  triangle step: |T| per edge, by lowest vertex         (Alg. 1)
 //   pass C  4-cycles through every edge, degree-ordered wedges   (Alg. 4/6)
 //   pass K  4-cliques and cross terms by lowest vertex           (Alg. 3/5)
 //   finish  x10, per-edge columns, unrestricted sums             (Sec. 4.5)
@@ -22,7 +21,7 @@ constexpr size_t kKbufBudget = size_t(2) << 30;
 }  // namespace
 
 void scratch_free(Scratch* sc, cudaStream_t s) {
-  for (void* p : {(void*)sc->tri, (void*)sc->trio, (void*)sc->P, (void*)sc->x7o, (void*)sc->cro, (void*)sc->misc,
+  for (void* p : {(void*)sc->trio, (void*)sc->P, (void*)sc->x7o, (void*)sc->cro, (void*)sc->misc,
                   (void*)sc->cbuf, (void*)sc->tables, (void*)sc->kbuf, (void*)sc->work})
     if (p) cudaFreeAsync(p, s);
   *sc = Scratch();
@@ -36,7 +35,6 @@ gc_status scratch_init(Scratch* sc, int32_t m, int32_t table_n, int32_t kmax, in
     if (e != cudaSuccess) return cuda_fail(e, "scratch alloc"); \
   } while (0)
   const size_t m1 = (size_t)(m > 0 ? m : 1);
-  GS_TRY(cudaMallocAsync(&sc->tri, sizeof(int32_t) * m1, s));
   GS_TRY(cudaMallocAsync(&sc->trio, sizeof(int32_t) * m1, s));
   GS_TRY(cudaMallocAsync(&sc->P, sizeof(unsigned long long) * 2 * m1, s));
   GS_TRY(cudaMallocAsync(&sc->x7o, sizeof(unsigned long long) * m1, s));
@@ -87,10 +85,9 @@ gc_status run_count(const DevGraph& g, const int32_t* units, int32_t n_units, co
   a.cbuf = sc->cbuf;
   a.cbuf_nx = sc->cbuf_nx;
   for (int t = 0; t <= kNumTiers; ++t) a.ktier_off[t] = ku.tier_off[t];
-  a.cursor = sc->misc;  // [0] passes A and C, [2 + tier] pass K, [8] pass C hubs
+  a.cursor = sc->misc;  // [0] pass C, [2 + tier] pass K, [8] pass C hubs, [10 + tier] pass T
   a.status = sc->misc + 1;
   a.tables = g.table_n > kSmemTableMax ? sc->tables : nullptr;
-  a.tri = sc->tri;
   a.trio = sc->trio;
   a.P = sc->P;
   a.x7o = sc->x7o;
@@ -109,13 +106,12 @@ gc_status run_count(const DevGraph& g, const int32_t* units, int32_t n_units, co
   GR_TRY(cudaMemsetAsync(sc->P, 0, sizeof(unsigned long long) * 2 * m1, s), "zero P");
   GR_TRY(cudaMemsetAsync(sc->x7o, 0, sizeof(unsigned long long) * m1, s), "zero x7");
   GR_TRY(cudaMemsetAsync(sc->cro, 0, sizeof(unsigned long long) * m1, s), "zero cross");
+  GR_TRY(cudaMemsetAsync(sc->trio, 0, sizeof(int32_t) * m1, s), "zero T");
   int launches = 0;
-  GR_EVENT(kPhasePassA);
-  if (n_units > 0) {
-    if ((st = run_pass_a(g, a, s)) != GC_OK) return st;
-    if ((st = run_trio(g, a, s)) != GC_OK) return st;
-    launches += 2;
-  }
+  GR_EVENT(kPhasePassT);
+  int t_launches = 0;
+  if ((st = run_pass_t(g, a, s, &t_launches)) != GC_OK) return st;
+  launches += t_launches;
   GR_EVENT(kPhasePassC);
   if (n_units > 0) {
     if (a.n_cheavy > 0) {
