@@ -385,13 +385,18 @@ gc_status classify_c_units(int32_t n, const int32_t* d_rp, const int32_t* d_ci, 
   if (dW) cudaFreeAsync(dW, s);
   if (dNX) cudaFreeAsync(dNX, s);
   if (e != cudaSuccess) return cuda_fail(e, "classify pass-C units");
-  // A hub unit pays a sweep of its lower neighbours per shared-memory block of
-  // the o-range; it is worth it when the wedges clearly outnumber that.
+  // A hub unit pays, per shared-memory block of the o-range, a few
+  // microseconds of barriers and cursor searches (more when it has more than
+  // a CTA's worth of lower neighbours), against roughly 10 ns per wedge on an
+  // SM for a wedge that goes through the vertex-indexed table in DRAM; the
+  // hub kernel is taken when the wedges exceed blocks x max(1024, nx), about
+  // three times the break-even point.
   std::vector<int32_t> heavy;
   for (int32_t k = 0; k < nu; ++k) {
     const long long span = NX[k] < 65536 ? 2LL * kHeavyTab : kHeavyTab;  // 16-bit counters below 65536
     const long long blocks = ((long long)U[k] + span - 1) / span;
-    if (W[k] >= 65536 && W[k] >= blocks * (2048 + 4LL * NX[k]) && NX[k] < (1 << 26)) heavy.push_back(k);
+    const long long per_block = NX[k] > 1024 ? NX[k] : 1024;
+    if (W[k] >= 16384 && W[k] >= blocks * per_block && NX[k] < (1 << 26)) heavy.push_back(k);
   }
   std::sort(heavy.begin(), heavy.end(), [&](int32_t a, int32_t b) { return W[a] > W[b]; });
   std::vector<char> is_heavy(nu, 0);
