@@ -47,10 +47,29 @@ __host__ __device__ constexpr int row_stride(int k) { return ((k + 31) >> 5) | 1
 __device__ __forceinline__ uint32_t khash(int32_t key, int bits) {
   return ((uint32_t)key * 0x9E3779B1u) >> (32 - bits);
 }
+// Second hash, for the bit filter in front of the table.
+__device__ __forceinline__ uint32_t fhash(int32_t key, int bits) {
+  return ((uint32_t)key * 0x85EBCA6Bu) >> (32 - bits);
+}
+
+// 64-bit per-member sums kept as two 32-bit words (lo[i], hi[i]), so that
+// shared-memory updates are plain 32-bit atomics.
+__device__ __forceinline__ void add_split(uint32_t* lo, uint32_t* hi, int32_t i, unsigned long long v) {
+  const uint32_t l = (uint32_t)v;
+  uint32_t h = (uint32_t)(v >> 32);
+  if (l) {
+    const uint32_t old = atomicAdd(&lo[i], l);
+    if (old + l < old) ++h;
+  }
+  if (h) atomicAdd(&hi[i], h);
+}
+__device__ __forceinline__ unsigned long long read_split(const uint32_t* lo, const uint32_t* hi, int32_t i) {
+  return ((unsigned long long)hi[i] << 32) | lo[i];
+}
 
 // Byte offsets of the per-unit arrays for a capacity of cap members.
 struct KLayout {
-  size_t vx7, vcr, ids, ta, hash, rows, total;
+  size_t vx7, vcr, ids, ta, hash, filt, rows, total;
   int hcap;
   __host__ __device__ static size_t up16(size_t x) { return (x + 15) & ~(size_t)15; }
   __host__ __device__ explicit KLayout(int cap, bool with_rows = true) {
@@ -63,6 +82,7 @@ struct KLayout {
     ids = o; o = up16(o + 4 * (size_t)cap);
     ta = o; o = up16(o + 4 * (size_t)cap);
     hash = o; o = up16(o + 4 * (size_t)hcap);
+    filt = o; o = up16(o + (size_t)hcap);  // 8 filter bits per hash slot
     rows = o; o = with_rows ? up16(o + 4 * (size_t)cap * (size_t)row_stride(cap)) : o;
     total = o;
   }
@@ -75,21 +95,26 @@ template <int kCap, int kThreads, bool kTri>
 __global__ void __launch_bounds__(kThreads, 65536 / (kThreads * 64)) k_pass_k(DevGraph g, CountArgs a, int tier) {
   constexpr int kW = kThreads / 32;
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ int32_t s_unit, s_cur1, s_cur2;
+  __shared__ int32_t s_unit, s_cur1, s_cur2, s_nhit;
   __shared__ int32_t s_qj[kW][64], s_qq[kW][64];
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int cap = kCap ? kCap : a.kbuf_cap;
   const KLayout L(cap, !kTri);
   unsigned char* base = kCap ? smem : a.kbuf + (size_t)blockIdx.x * a.kbuf_stride;
-  unsigned long long* vx7 = reinterpret_cast<unsigned long long*>(base + L.vx7);
-  unsigned long long* vcr = reinterpret_cast<unsigned long long*>(base + L.vcr);
+  uint32_t* vx7 = reinterpret_cast<uint32_t*>(base + L.vx7);  // [cap] lo, [cap] hi
+  uint32_t* vx7h = vx7 + cap;
+  uint32_t* vcr = reinterpret_cast<uint32_t*>(base + L.vcr);
+  uint32_t* vcrh = vcr + cap;
   int32_t* ids = reinterpret_cast<int32_t*>(base + L.ids);
   int32_t* ta = reinterpret_cast<int32_t*>(base + L.ta);
   int32_t* hash = reinterpret_cast<int32_t*>(base + L.hash);
+  uint32_t* filt = reinterpret_cast<uint32_t*>(base + L.filt);
   uint32_t* rows = reinterpret_cast<uint32_t*>(base + L.rows);
   int32_t* qj = s_qj[warp];
   int32_t* qq = s_qq[warp];
+  // phase-1 hits of pass K (i, j, out-slot), so that phase 2 needs no rescan
+  int32_t* hits = kTri ? nullptr : a.hitbuf + (size_t)blockIdx.x * 3 * (size_t)a.hitcap;
 
   const int32_t u0 = a.ktier_off[tier], u1 = a.ktier_off[tier + 1];
   int32_t* cursor = a.cursor + (kTri ? 10 : 2) + tier;
@@ -101,6 +126,7 @@ __global__ void __launch_bounds__(kThreads, 65536 / (kThreads * 64)) k_pass_k(De
       s_unit = u0 + atomicAdd(cursor, 1);
       s_cur1 = 0;
       s_cur2 = 0;
+      s_nhit = 0;
     }
     __syncthreads();
     const int32_t ui = s_unit;
@@ -116,16 +142,20 @@ __global__ void __launch_bounds__(kThreads, 65536 / (kThreads * 64)) k_pass_k(De
     int hbits = 1;
     while ((1 << hbits) < 2 * k) ++hbits;
     const uint32_t hmask = (1u << hbits) - 1u;
+    const int fbits = hbits + 3;
 
     for (int32_t i = threadIdx.x; i < k; i += kThreads) {
       ids[i] = g.out_idx[ob + i];
-      vx7[i] = 0ull;
+      vx7[i] = 0u;
+      vx7h[i] = 0u;
       if (!kTri) {
         ta[i] = a.trio[ob + i];
-        vcr[i] = 0ull;
+        vcr[i] = 0u;
+        vcrh[i] = 0u;
       }
     }
     for (int32_t i = threadIdx.x; i <= (int32_t)hmask; i += kThreads) hash[i] = 0;
+    for (int32_t i = threadIdx.x; i < (1 << fbits) / 32; i += kThreads) filt[i] = 0u;
     if (!kTri)
       for (int32_t i = threadIdx.x; i < k * S; i += kThreads) rows[i] = 0u;
     if (threadIdx.x == 0) w_members += k;
@@ -133,10 +163,14 @@ __global__ void __launch_bounds__(kThreads, 65536 / (kThreads * 64)) k_pass_k(De
     for (int32_t i = threadIdx.x; i < k; i += kThreads) {  // Psi: id -> 1 + position in out(a)
       uint32_t h = khash(ids[i], hbits);
       while (atomicCAS(&hash[h], 0, i + 1) != 0) h = (h + 1) & hmask;  // table at most half full
+      const uint32_t f = fhash(ids[i], fbits);
+      atomicOr(&filt[f >> 5], 1u << (f & 31));
     }
     __syncthreads();
     const int32_t cmax = ids[k - 1];
     auto lookup = [&](int32_t c) -> int32_t {
+      const uint32_t f = fhash(c, fbits);
+      if (!((filt[f >> 5] >> (f & 31)) & 1u)) return -1;  // at most one bit in 16 set
       uint32_t h = khash(c, hbits);
       for (;;) {
         const int32_t s = hash[h];
@@ -160,19 +194,30 @@ __global__ void __launch_bounds__(kThreads, 65536 / (kThreads * 64)) k_pass_k(De
         if (__shfl_sync(kFull, c, 0) > cmax) break;  // out(b) ascends: nothing further is in out(a)
         if (lane == 0) w_scan += min(32, be - q0);
         const int32_t j = c <= cmax ? lookup(c) : -1;
+        const unsigned hit = __ballot_sync(kFull, j >= 0);
         if (kTri) {
-          const unsigned hit = __ballot_sync(kFull, j >= 0);
           if (j >= 0) {
             atomicAdd(&a.trio[q], 1);  // edge (b_i, c)
-            atomicAdd(&vx7[j], 1ull);  // edge (a, c)
+            atomicAdd(&vx7[j], 1u);    // edge (a, c)
           }
           if (lane == 0 && hit) {
-            atomicAdd(&vx7[i], (unsigned long long)__popc(hit));  // edge (a, b_i)
+            atomicAdd(&vx7[i], (uint32_t)__popc(hit));  // edge (a, b_i)
             w_edges += __popc(hit);
           }
-        } else if (j >= 0) {
-          atomicOr(&rows[i * S + (j >> 5)], 1u << (j & 31));
-          atomicOr(&rows[j * S + (i >> 5)], 1u << (i & 31));
+        } else if (hit) {
+          int32_t base_h = 0;
+          if (lane == 0) base_h = atomicAdd(&s_nhit, __popc(hit));
+          base_h = __shfl_sync(kFull, base_h, 0);
+          if (j >= 0) {
+            atomicOr(&rows[i * S + (j >> 5)], 1u << (j & 31));
+            atomicOr(&rows[j * S + (i >> 5)], 1u << (i & 31));
+            const int32_t slot = base_h + __popc(hit & ((1u << lane) - 1u));
+            if (slot < a.hitcap) {
+              hits[3 * (size_t)slot] = i;
+              hits[3 * (size_t)slot + 1] = j;
+              hits[3 * (size_t)slot + 2] = q;
+            }
+          }
         }
       }
     }
@@ -182,6 +227,41 @@ __global__ void __launch_bounds__(kThreads, 65536 / (kThreads * 64)) k_pass_k(De
         if (vx7[i]) atomicAdd(&a.trio[ob + i], (int32_t)vx7[i]);
       continue;
     }
+    const int32_t nhit = s_nhit;
+
+    if (nhit <= a.hitcap) {
+      // Phase 2 over the recorded edges of H_a: lane per edge.
+      for (int32_t e0 = warp * 32; e0 < nhit; e0 += kThreads) {
+        const int32_t e = e0 + lane;
+        if (e < nhit) {
+          const int32_t i = hits[3 * (size_t)e], j = hits[3 * (size_t)e + 1], q = hits[3 * (size_t)e + 2];
+          const uint32_t* ri = rows + i * S;
+          const uint32_t* rj = rows + j * S;
+          int c4 = 0;
+          for (int w = 0; w < W; ++w) c4 += __popc(ri[w] & rj[w]);
+          const int32_t ti = ta[i], tj = ta[j];
+          const int32_t tij = a.trio[q];
+          if (c4) {
+            atomicAdd(&a.x7o[q], (unsigned long long)c4);
+            if (kCap) {  // at most k^2 per member: no carry for k <= 1024
+              atomicAdd(&vx7[i], (uint32_t)c4);
+              atomicAdd(&vx7[j], (uint32_t)c4);
+            } else {
+              add_split(vx7, vx7h, i, (unsigned long long)c4);
+              add_split(vx7, vx7h, j, (unsigned long long)c4);
+            }
+          }
+          atomicAdd(&a.cro[q], (unsigned long long)(ti + tj - 2));
+          add_split(vcr, vcrh, i, (unsigned long long)(tj + tij - 2));
+          add_split(vcr, vcrh, j, (unsigned long long)(ti + tij - 2));
+        }
+        if (lane == 0) {
+          const int32_t cnt = min(32, nhit - e0);
+          w_edges += cnt;
+          w_words += (long long)cnt * W;
+        }
+      }
+    } else {
 
     // Phase 2: per edge (i, j) of H_a, c_ij and the cross terms.
     for (;;) {
@@ -203,8 +283,8 @@ __global__ void __launch_bounds__(kThreads, 65536 / (kThreads * 64)) k_pass_k(De
         const int32_t tij = a.trio[q];
         if (c4) atomicAdd(&a.x7o[q], (unsigned long long)c4);
         atomicAdd(&a.cro[q], (unsigned long long)(ti + tj - 2));
-        if (c4) atomicAdd(&vx7[j], (unsigned long long)c4);
-        atomicAdd(&vcr[j], (unsigned long long)(ti + tij - 2));
+        if (c4) add_split(vx7, vx7h, j, (unsigned long long)c4);
+        add_split(vcr, vcrh, j, (unsigned long long)(ti + tij - 2));
         ax7 += (unsigned long long)c4;
         acr += (unsigned long long)(tj + tij - 2);
       };
@@ -247,16 +327,17 @@ __global__ void __launch_bounds__(kThreads, 65536 / (kThreads * 64)) k_pass_k(De
         acr += __shfl_xor_sync(kFull, acr, o);
       }
       if (lane == 0) {
-        if (ax7) atomicAdd(&vx7[i], ax7);
-        if (acr) atomicAdd(&vcr[i], acr);
+        if (ax7) add_split(vx7, vx7h, i, ax7);
+        if (acr) add_split(vcr, vcrh, i, acr);
       }
     }
+    }  // phase 2
     __syncthreads();
 
     // Edges (a, b_i): triangles of H_a through i (each counted from both of
     // its edges at i, hence the halving) and the cross terms gathered above.
     for (int32_t i = threadIdx.x; i < k; i += kThreads) {
-      const unsigned long long x = vx7[i], c = vcr[i];
+      const unsigned long long x = read_split(vx7, vx7h, i), c = read_split(vcr, vcrh, i);
       if (x) atomicAdd(&a.x7o[ob + i], x >> 1);
       if (c) atomicAdd(&a.cro[ob + i], c);
     }
@@ -400,6 +481,7 @@ gc_status launch_tier(const DevGraph& g, const CountArgs& a, int tier, cudaStrea
   } else {
     grid = a.kbuf_ctas;
   }
+  if (!kTri && grid > a.hitbuf_ctas) grid = a.hitbuf_ctas;  // one hit buffer per CTA
   if (grid > units) grid = units;
   if (grid < 1) return GC_OK;
   kern<<<grid, kThreads, smem, s>>>(g, a, tier);

@@ -65,6 +65,9 @@ struct CountArgs {
   size_t kbuf_stride;
   int32_t kbuf_ctas;
   int32_t kbuf_cap;        // largest k the global tier holds
+  int32_t* hitbuf;         // pass K: per-CTA lists of the edges of H_a (hitbuf_ctas x hitcap x 3 ints)
+  int32_t hitcap;
+  int32_t hitbuf_ctas;
   uint64_t* per_edge;      // [m][13] device pointer or nullptr
   unsigned long long* csum;  // [G][13][2] 128-bit unrestricted counts (lo, hi)
   int32_t* status;         // device status word (0 = ok)
@@ -116,6 +119,9 @@ struct Scratch {
   size_t kbuf_stride = 0;
   int32_t kbuf_ctas = 0;
   int32_t kbuf_cap = 0;
+  int32_t* hitbuf = nullptr;         // pass K edge lists
+  int32_t hitcap = 0;
+  int32_t hitbuf_ctas = 0;
   unsigned long long* work = nullptr;  // [kNumWork]
   int32_t launches = 0;              // kernels launched by the last run_count
 };

@@ -18,11 +18,14 @@ namespace gc {
 namespace {
 // Total bytes the pass-K global tier may hold at once.
 constexpr size_t kKbufBudget = size_t(2) << 30;
+// Largest per-CTA list of H_a edges in pass K (units with more edges rescan
+// their out-lists instead).
+constexpr long long kHitCapMax = 1 << 19;
 }  // namespace
 
 void scratch_free(Scratch* sc, cudaStream_t s) {
   for (void* p : {(void*)sc->trio, (void*)sc->P, (void*)sc->x7o, (void*)sc->cro, (void*)sc->misc,
-                  (void*)sc->cbuf, (void*)sc->tables, (void*)sc->kbuf, (void*)sc->work})
+                  (void*)sc->cbuf, (void*)sc->tables, (void*)sc->kbuf, (void*)sc->hitbuf, (void*)sc->work})
     if (p) cudaFreeAsync(p, s);
   *sc = Scratch();
 }
@@ -49,6 +52,12 @@ gc_status scratch_init(Scratch* sc, int32_t m, int32_t table_n, int32_t kmax, in
   if (cnx_max > 0) {
     sc->cbuf_nx = cnx_max;
     GS_TRY(cudaMallocAsync(&sc->cbuf, sizeof(int32_t) * 3 * (size_t)cnx_max * (size_t)(count_grid_size() / kCtasPerSm), s));
+  }
+  {  // pass K: each CTA records the edges of its current H_a (at most C(kmax, 2))
+    const long long full = (long long)kmax * (kmax - 1) / 2;
+    sc->hitcap = (int32_t)(full < kHitCapMax ? (full > 0 ? full : 1) : kHitCapMax);
+    sc->hitbuf_ctas = count_grid_size();
+    GS_TRY(cudaMallocAsync(&sc->hitbuf, sizeof(int32_t) * 3 * (size_t)sc->hitcap * (size_t)sc->hitbuf_ctas, s));
   }
   if (kmax > kTierCap[kTier1024]) {
     sc->kbuf_cap = kmax;
@@ -96,6 +105,9 @@ gc_status run_count(const DevGraph& g, const int32_t* units, int32_t n_units, co
   a.kbuf_stride = sc->kbuf_stride;
   a.kbuf_ctas = sc->kbuf_ctas;
   a.kbuf_cap = sc->kbuf_cap;
+  a.hitbuf = sc->hitbuf;
+  a.hitcap = sc->hitcap;
+  a.hitbuf_ctas = sc->hitbuf_ctas;
   a.per_edge = per_edge;
   a.csum = csum;
   a.work = sc->work;
