@@ -11,6 +11,8 @@
 // lists and their tier boundaries are fixed when the graph is prepared.
 #include <cuda_runtime.h>
 
+#include <cstdlib>
+
 #include "gc_internal.h"
 
 namespace gc {
@@ -19,8 +21,16 @@ namespace {
 // Total bytes the pass-K global tier may hold at once.
 constexpr size_t kKbufBudget = size_t(2) << 30;
 // Largest per-CTA list of H_a edges in pass K (units with more edges rescan
-// their out-lists instead).
-constexpr long long kHitCapMax = 1 << 19;
+// their out-lists instead): 2^19 entries, or the environment's GC_K_LIST_CAP
+// (1 .. 2^19), read once per process.
+long long k_list_cap() {
+  static long long v = [] {
+    const char* e = getenv("GC_K_LIST_CAP");
+    long long x = e ? atoll(e) : (1LL << 19);
+    return x < 1 ? 1LL : (x > (1LL << 19) ? (1LL << 19) : x);
+  }();
+  return v;
+}
 }  // namespace
 
 void scratch_free(Scratch* sc, cudaStream_t s) {
@@ -55,7 +65,8 @@ gc_status scratch_init(Scratch* sc, int32_t m, int32_t table_n, int32_t kmax, in
   }
   {  // pass K: each CTA records the edges of its current H_a (at most C(kmax, 2))
     const long long full = (long long)kmax * (kmax - 1) / 2;
-    sc->hitcap = (int32_t)(full < kHitCapMax ? (full > 0 ? full : 1) : kHitCapMax);
+    const long long cap = k_list_cap();
+    sc->hitcap = (int32_t)(full < cap ? (full > 0 ? full : 1) : cap);
     sc->hitbuf_ctas = count_grid_size();
     GS_TRY(cudaMallocAsync(&sc->hitbuf, sizeof(int32_t) * 3 * (size_t)sc->hitcap * (size_t)sc->hitbuf_ctas, s));
   }

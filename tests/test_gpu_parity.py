@@ -113,6 +113,24 @@ def test_hub_units_of_the_cycle_pass():
     assert_parity(*graphgen.chung_lu(120000, 600000, 2.1, 1.2e6, 4000.0, 7))
 
 
+def test_clique_pass_rescan_when_edge_list_is_full():
+    # pass K keeps the edges of each H_a in a per-CTA list; a unit whose list
+    # overflows scans its out-lists again. Force that with a 64-entry list.
+    import subprocess
+    import sys
+    code = ("import numpy as np, graphgen, oracle, paper_1608_05138_gb300 as gcb\n"
+            "rp, ci = graphgen.rmat(12, 16, 0.57, 0.19, 0.19, 29)\n"
+            "g = gcb.Graph(rp, ci); pe = np.zeros((g.m, 13), np.uint64); X = g.count(pe); g.close()\n"
+            "o = oracle.count(rp, ci)\n"
+            "assert X == o['X'] and (pe == o['per_edge']).all()\n"
+            "print('ok')\n")
+    import os
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, GC_K_LIST_CAP="64", PYTHONPATH=root)
+    r = subprocess.run([sys.executable, "-c", code], env=env, cwd=root, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0 and "ok" in r.stdout, r.stdout + r.stderr
+
+
 def test_relabelling_is_metamorphic():
     rp, ci = graphgen.chung_lu(2000, 12000, 2.1, 24000.0, 500.0, 22)
     n = len(rp) - 1
