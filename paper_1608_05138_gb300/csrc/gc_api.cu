@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstring>
 #include <functional>
+#include <memory>
 #include <string>
 #include <thread>
 #include <vector>
@@ -28,107 +29,155 @@ gc_status cuda_fail(cudaError_t e, const char* what) {
   return GC_ERR_CUDA;
 }
 
-// Host checks of a CSR (multi-threaded over rows). Symmetry is checked too:
-// for every (x, y) the row of y must contain x.
-gc_status validate_csr(int32_t n, const int32_t* rp, const int32_t* ci) {
-  if (n < 0) { set_error("n < 0"); return GC_ERR_ARG; }
-  if (rp[0] != 0) { set_error("row_ptr[0] != 0"); return GC_ERR_RANGE; }
-  for (int32_t x = 0; x < n; ++x)
-    if (rp[x + 1] < rp[x]) {
-      set_error("row_ptr decreases at row " + std::to_string(x));
-      return GC_ERR_UNSORTED;
-    }
-  if (rp[n] % 2 != 0) { set_error("row_ptr[n] is odd: the graph cannot be symmetric"); return GC_ERR_ASYMMETRIC; }
-  unsigned hw = std::thread::hardware_concurrency();
-  int nt = (int)std::min<unsigned>(hw ? hw : 1, 16);
-  if ((int64_t)rp[n] < 1000000) nt = 1;
-  std::vector<gc_status> res(nt, GC_OK);
-  std::vector<std::string> msg(nt);
-  auto work = [&](int t) {  // symmetry; rows are known sorted here
-    int32_t x0 = (int32_t)((int64_t)n * t / nt), x1 = (int32_t)((int64_t)n * (t + 1) / nt);
-    for (int32_t x = x0; x < x1; ++x)
-      for (int32_t p = rp[x]; p < rp[x + 1]; ++p) {
-        int32_t y = ci[p];
-        if (!std::binary_search(ci + rp[y], ci + rp[y + 1], x)) {
-          res[t] = GC_ERR_ASYMMETRIC;
-          msg[t] = "edge (" + std::to_string(x) + "," + std::to_string(y) + ") has no reverse";
-          return;
-        }
-      }
-  };
-  // Range, loop, duplicate and order checks finish for every row before the
-  // symmetry check, whose binary search needs sorted rows.
-  {
-    std::vector<gc_status> r1(nt, GC_OK);
-    std::vector<std::string> m1(nt);
-    auto sorted_only = [&](int t) {
-      int32_t x0 = (int32_t)((int64_t)n * t / nt), x1 = (int32_t)((int64_t)n * (t + 1) / nt);
-      for (int32_t x = x0; x < x1; ++x)
-        for (int32_t p = rp[x]; p < rp[x + 1]; ++p) {
-          int32_t y = ci[p];
-          if (y < 0 || y >= n) { r1[t] = GC_ERR_RANGE; m1[t] = "column " + std::to_string(y) + " out of range in row " + std::to_string(x); return; }
-          if (y == x) { r1[t] = GC_ERR_SELF_LOOP; m1[t] = "self-loop at vertex " + std::to_string(x); return; }
-          if (p > rp[x] && ci[p - 1] == y) { r1[t] = GC_ERR_DUPLICATE; m1[t] = "duplicate neighbour " + std::to_string(y) + " in row " + std::to_string(x); return; }
-          if (p > rp[x] && ci[p - 1] > y) { r1[t] = GC_ERR_UNSORTED; m1[t] = "row " + std::to_string(x) + " not ascending"; return; }
-        }
-    };
-    std::vector<std::thread> th;
-    for (int t = 1; t < nt; ++t) th.emplace_back(sorted_only, t);
-    sorted_only(0);
-    for (auto& x : th) x.join();
-    for (int t = 0; t < nt; ++t)
-      if (r1[t] != GC_OK) { set_error(m1[t]); return r1[t]; }
+namespace {
+
+int host_threads() {
+  const unsigned hw = std::thread::hardware_concurrency();
+  return (int)std::min<unsigned>(hw ? hw : 1, 32);
+}
+
+// Row ranges [b[t], b[t+1]) holding about equal numbers of entries.
+std::vector<int32_t> nnz_chunks(int32_t n, const int32_t* rp, int nt) {
+  std::vector<int32_t> b((size_t)nt + 1, n);
+  b[0] = 0;
+  const int64_t nnz = rp[n];
+  for (int t = 1; t < nt; ++t) {
+    const int32_t target = (int32_t)(nnz * t / nt);
+    int32_t x = (int32_t)(std::upper_bound(rp, rp + n + 1, target) - rp) - 1;  // last row starting at or before
+    if (x < b[t - 1]) x = b[t - 1];
+    if (x > n) x = n;
+    b[t] = x;
   }
-  if (nt == 1) {
-    // one O(nnz) pass: scanning rows x in order, the k-th row that names y
-    // must be the k-th entry of row y (rows ascend), which is exactly
-    // symmetry once every entry has found its place
-    std::vector<int32_t> fill((size_t)(n > 0 ? n : 1), 0);
-    for (int32_t x = 0; x < n; ++x)
-      for (int32_t p = rp[x]; p < rp[x + 1]; ++p) {
-        const int32_t y = ci[p];
-        const int32_t q = rp[y] + fill[y]++;
-        if (q >= rp[y + 1] || ci[q] != x) {
-          set_error("edge (" + std::to_string(x) + "," + std::to_string(y) + ") has no reverse");
-          return GC_ERR_ASYMMETRIC;
-        }
+  return b;
+}
+
+template <class F>
+void run_threads(int nt, F f) {
+  std::vector<std::thread> th;
+  for (int t = 1; t < nt; ++t) th.emplace_back(f, t);
+  f(0);
+  for (auto& x : th) x.join();
+}
+
+// First error of a multi-threaded check, by thread (thread order = row order).
+struct Checks {
+  std::vector<gc_status> st;
+  std::vector<std::string> msg;
+  explicit Checks(int nt) : st((size_t)nt, GC_OK), msg((size_t)nt) {}
+  gc_status first() {
+    for (size_t t = 0; t < st.size(); ++t)
+      if (st[t] != GC_OK) {
+        set_error(msg[t]);
+        return st[t];
       }
     return GC_OK;
   }
-  std::vector<std::thread> th;
-  for (int t = 1; t < nt; ++t) th.emplace_back(work, t);
-  work(0);
-  for (auto& x : th) x.join();
-  for (int t = 0; t < nt; ++t)
-    if (res[t] != GC_OK) { set_error(msg[t]); return res[t]; }
-  return GC_OK;
+};
+
+}  // namespace
+
+// Reverse slots of a CSR and, with check, the checks of Problem 1's input (a
+// simple undirected graph): row_ptr from 0 and non-decreasing, columns in
+// range, rows strictly ascending (no duplicates), no self-loops, symmetric.
+// rev (optional, [row_ptr[n]]): slot of (y, x) for the slot of (x, y).
+//
+// Symmetry: rows x are walked in order in chunks of about equal entries; the
+// k-th row (in order) that names y must name it from the k-th entry of row y,
+// so a per-chunk counter per y (started, on first use, at the number of
+// entries of row y below the chunk's first row) gives the slot where x must
+// stand in row y, and the entry there is compared with x. Every entry is
+// checked against a slot of row y, so a missing reverse always fails, and a
+// symmetric graph always passes. Without check, an entry whose reverse is not
+// found gets rev = its own slot.
+gc_status csr_reverse(int32_t n, const int32_t* rp, const int32_t* ci, int32_t* rev, bool check) {
+  if (n < 0) { set_error("n < 0"); return GC_ERR_ARG; }
+  if (check) {
+    if (rp[0] != 0) { set_error("row_ptr[0] != 0"); return GC_ERR_RANGE; }
+    for (int32_t x = 0; x < n; ++x)
+      if (rp[x + 1] < rp[x]) {
+        set_error("row_ptr decreases at row " + std::to_string(x));
+        return GC_ERR_UNSORTED;
+      }
+    if (rp[n] % 2 != 0) { set_error("row_ptr[n] is odd: the graph cannot be symmetric"); return GC_ERR_ASYMMETRIC; }
+  }
+  const int64_t nnz = rp[n];
+  int nt = host_threads();
+  if (nnz < (1 << 20)) nt = 1;
+  if (check) {  // range, loop, duplicate and order: every row before any symmetry probe
+    const std::vector<int32_t> b = nnz_chunks(n, rp, nt);
+    Checks c(nt);
+    run_threads(nt, [&](int t) {
+      for (int32_t x = b[t]; x < b[t + 1]; ++x)
+        for (int32_t p = rp[x]; p < rp[x + 1]; ++p) {
+          const int32_t y = ci[p];
+          if (y < 0 || y >= n) { c.st[t] = GC_ERR_RANGE; c.msg[t] = "column " + std::to_string(y) + " out of range in row " + std::to_string(x); return; }
+          if (y == x) { c.st[t] = GC_ERR_SELF_LOOP; c.msg[t] = "self-loop at vertex " + std::to_string(x); return; }
+          if (p > rp[x] && ci[p - 1] == y) { c.st[t] = GC_ERR_DUPLICATE; c.msg[t] = "duplicate neighbour " + std::to_string(y) + " in row " + std::to_string(x); return; }
+          if (p > rp[x] && ci[p - 1] > y) { c.st[t] = GC_ERR_UNSORTED; c.msg[t] = "row " + std::to_string(x) + " not ascending"; return; }
+        }
+    });
+    const gc_status st = c.first();
+    if (st != GC_OK) return st;
+  }
+  // per-chunk counters: n ints per thread, at most 1 GiB in all
+  const int64_t per = 4 * (int64_t)(n > 0 ? n : 1);
+  int nts = (int)std::max<int64_t>(1, std::min<int64_t>(nt, (int64_t(1) << 30) / per));
+  const std::vector<int32_t> b = nnz_chunks(n, rp, nts);
+  Checks c(nts);
+  run_threads(nts, [&](int t) {
+    std::vector<int32_t> fill((size_t)(n > 0 ? n : 1), -1);
+    const int32_t x0 = b[t];
+    for (int32_t x = x0; x < b[t + 1]; ++x)
+      for (int32_t p = rp[x]; p < rp[x + 1]; ++p) {
+        const int32_t y = ci[p];
+        const int32_t yb = rp[y], ye = rp[y + 1];
+        int32_t f = fill[y];
+        if (f < 0) f = (int32_t)(std::lower_bound(ci + yb, ci + ye, x0) - (ci + yb));
+        fill[y] = f + 1;
+        const int32_t q = yb + f;
+        if (q < ye && ci[q] == x) {
+          if (rev) rev[p] = q;
+        } else if (check) {
+          c.st[t] = GC_ERR_ASYMMETRIC;
+          c.msg[t] = "edge (" + std::to_string(x) + "," + std::to_string(y) + ") has no reverse";
+          return;
+        } else if (rev) {
+          const int32_t* r = std::lower_bound(ci + yb, ci + ye, x);
+          rev[p] = (r < ci + ye && *r == x) ? (int32_t)(r - ci) : p;
+        }
+      }
+  });
+  return c.first();
 }
+
+gc_status validate_csr(int32_t n, const int32_t* rp, const int32_t* ci) { return csr_reverse(n, rp, ci, nullptr, true); }
 
 // Preprocessing P1 (Sec. 4.3): relabel vertices by ascending degree (ties by
 // id), so that internal ids are the (degree, id) ranks used by P3 and by the
 // degree-ordered passes. Rows are re-sorted in the new ids. Edge ids stay
 // those of the caller's graph: eid[slot] of every internal slot is the
-// caller's edge id, and perm maps internal -> caller vertex ids.
-struct Relabeled {
-  std::vector<int32_t> rp, ci, eid, perm;
+// caller's edge id, and perm maps internal -> caller vertex ids. rev: the
+// reverse slots of the caller's CSR (csr_reverse).
+// Host arrays left uninitialised on allocation (every element is written
+// before use): a value-initialising std::vector would zero a gigabyte on one
+// thread for the larger graphs.
+struct HostArray {
+  std::unique_ptr<int32_t[]> p;
+  int32_t* data() { return p.get(); }
+  int32_t& operator[](size_t i) { return p[i]; }
+  void resize(size_t n) { p.reset(new int32_t[n > 0 ? n : 1]); }
 };
 
-static void parallel_for(int64_t n, int nt, const std::function<void(int64_t, int64_t)>& f) {
-  if (nt <= 1 || n < 4096) {
-    f(0, n);
-    return;
-  }
-  std::vector<std::thread> th;
-  for (int t = 1; t < nt; ++t) th.emplace_back(f, n * t / nt, n * (t + 1) / nt);
-  f(0, n / nt);
-  for (auto& x : th) x.join();
-}
+struct Relabeled {
+  HostArray rp, ci, eid, perm;
+};
 
-Relabeled relabel_by_degree(int32_t n, const int32_t* rp, const int32_t* ci) {
+Relabeled relabel_by_degree(int32_t n, const int32_t* rp, const int32_t* ci, const int32_t* rev) {
   Relabeled R;
   const int64_t nnz = rp[n];
-  unsigned hw = std::thread::hardware_concurrency();
-  const int nt = (int)std::min<unsigned>(hw ? hw : 1, 16);
+  const int32_t m = (int32_t)(nnz / 2);
+  int nt = host_threads();
+  if (nnz < (1 << 20)) nt = 1;
   int32_t dmax = 0;
   for (int32_t x = 0; x < n; ++x) dmax = std::max(dmax, rp[x + 1] - rp[x]);
   // stable counting sort by degree
@@ -138,42 +187,45 @@ Relabeled relabel_by_degree(int32_t n, const int32_t* rp, const int32_t* ci) {
   R.perm.resize((size_t)n);
   std::vector<int32_t> newid((size_t)n);
   for (int32_t x = 0; x < n; ++x) {
-    int32_t i = cnt[rp[x + 1] - rp[x]]++;
+    const int32_t i = cnt[rp[x + 1] - rp[x]]++;
     R.perm[i] = x;
     newid[x] = i;
   }
-  // caller's edge id of every caller slot
-  std::vector<int32_t> up((size_t)n + 1, 0);
-  parallel_for(n, nt, [&](int64_t a, int64_t b) {
-    for (int64_t x = a; x < b; ++x)
-      up[x + 1] = (int32_t)(rp[x + 1] - (std::upper_bound(ci + rp[x], ci + rp[x + 1], (int32_t)x) - ci));
-  });
-  for (int32_t x = 0; x < n; ++x) up[x + 1] += up[x];  // up[x] = first edge id of row x
-  std::vector<int32_t> eid_in((size_t)(nnz > 0 ? nnz : 1));
-  parallel_for(n, nt, [&](int64_t a, int64_t b) {
-    for (int64_t x = a; x < b; ++x) {
-      const int32_t* row = ci + rp[x];
-      const int32_t first_up = (int32_t)(std::upper_bound(row, ci + rp[x + 1], (int32_t)x) - ci);
-      for (int32_t p = rp[x]; p < rp[x + 1]; ++p) {
-        int32_t y = ci[p];
-        if (y > x) {
-          eid_in[p] = up[x] + (p - first_up);
-        } else {
-          const int32_t* q = std::lower_bound(ci + rp[y], ci + rp[y + 1], (int32_t)x);
-          const int32_t fu = (int32_t)(std::upper_bound(ci + rp[y], ci + rp[y + 1], y) - ci);
-          eid_in[p] = up[y] + (int32_t)(q - ci) - fu;
-        }
-      }
+  // caller's edge ids: row x's entries y > x are edges up[x], up[x] + 1, ...
+  std::vector<int32_t> first_up((size_t)n + 1), up((size_t)n + 1, 0);
+  const std::vector<int32_t> b = nnz_chunks(n, rp, nt);
+  run_threads(nt, [&](int t) {
+    for (int32_t x = b[t]; x < b[t + 1]; ++x) {
+      first_up[x] = (int32_t)(std::upper_bound(ci + rp[x], ci + rp[x + 1], x) - ci);
+      up[x + 1] = rp[x + 1] - first_up[x];
     }
+  });
+  for (int32_t x = 0; x < n; ++x) up[x + 1] += up[x];
+  HostArray eid_in;
+  eid_in.resize((size_t)nnz);
+  run_threads(nt, [&](int t) {
+    for (int32_t x = b[t]; x < b[t + 1]; ++x)
+      for (int32_t p = rp[x]; p < rp[x + 1]; ++p) {
+        const int32_t y = ci[p];
+        int32_t id;
+        if (y > x) {
+          id = up[x] + (p - first_up[x]);
+        } else {
+          const int32_t q = rev[p];  // (y, x) in row y, x > y
+          id = up[y] + (q - first_up[y]);
+        }
+        eid_in[p] = (id >= 0 && id < m) ? id : 0;  // out of range only for an input that skipped validation
+      }
   });
   R.rp.resize((size_t)n + 1);
   R.rp[0] = 0;
   for (int32_t i = 0; i < n; ++i) R.rp[i + 1] = R.rp[i] + (rp[R.perm[i] + 1] - rp[R.perm[i]]);
-  R.ci.resize((size_t)(nnz > 0 ? nnz : 1));
-  R.eid.resize((size_t)(nnz > 0 ? nnz : 1));
-  parallel_for(n, nt, [&](int64_t a, int64_t b) {
+  R.ci.resize((size_t)nnz);
+  R.eid.resize((size_t)nnz);
+  const std::vector<int32_t> bn = nnz_chunks(n, R.rp.data(), nt);
+  run_threads(nt, [&](int t) {
     std::vector<uint64_t> tmp;
-    for (int64_t i = a; i < b; ++i) {
+    for (int32_t i = bn[t]; i < bn[t + 1]; ++i) {
       const int32_t x = R.perm[i];
       tmp.clear();
       for (int32_t p = rp[x]; p < rp[x + 1]; ++p)
@@ -246,11 +298,18 @@ gc_status gc_graph_upload(int32_t n, const int32_t* row_ptr, const int32_t* col_
     return GC_ERR_ARG;
   }
   if (flags & ~GC_NO_VALIDATE) { set_error("unknown flags"); return GC_ERR_ARG; }
-  if (!(flags & GC_NO_VALIDATE)) {
-    gc_status st = validate_csr(n, row_ptr, col_idx);
-    if (st != GC_OK) return st;
-  }
   const int64_t nnz = row_ptr[n];
+  HostArray rev;
+  try {
+    rev.resize((size_t)(nnz > 0 ? nnz : 1));
+  } catch (...) {
+    set_error("host allocation failed");
+    return GC_ERR_NOMEM;
+  }
+  {
+    const gc_status st0 = csr_reverse(n, row_ptr, col_idx, rev.data(), !(flags & GC_NO_VALIDATE));
+    if (st0 != GC_OK) return st0;
+  }
   if (nnz < 0 || nnz % 2) { set_error("row_ptr[n] must be even and >= 0"); return GC_ERR_ARG; }
   gc_graph g = new (std::nothrow) gc_graph_s();
   if (!g) { set_error("host allocation failed"); return GC_ERR_NOMEM; }
@@ -269,7 +328,15 @@ gc_status gc_graph_upload(int32_t n, const int32_t* row_ptr, const int32_t* col_
       return st;                        \
     }                                   \
   } while (0)
-  Relabeled R = relabel_by_degree(n, row_ptr, col_idx);
+  Relabeled R;
+  try {
+    R = relabel_by_degree(n, row_ptr, col_idx, rev.data());
+  } catch (...) {
+    set_error("host allocation failed");
+    graph_release(g);
+    return GC_ERR_NOMEM;
+  }
+  rev.p.reset();
   int32_t* d_eid = nullptr;
   int32_t* d_perm = nullptr;
   GC_CHECK(cudaMalloc(&g->d_rp, sizeof(int32_t) * ((size_t)n + 1)), "alloc row_ptr");
