@@ -1,9 +1,9 @@
 // gc_api.cu -- C ABI of the plain whole-graph path (see include/gc.h).
 //
-// Host-side CSR validation (Problem 1's input: simple undirected graph), the
-// graph handle with its device-resident data, and the orchestration of one
-// count: pass A (triangle step), pass B (clique/cycle steps, per-edge
-// columns, unrestricted counts), derive (global counts), copies back.
+// Host-side CSR validation (Problem 1's input: simple undirected graph) and
+// the P1 relabelling, the graph handle with its device-resident data, and one
+// count (the sequence of gc_run.cu: passes T, C, K, finish, derive) with the
+// copies back.
 #include <cuda_runtime.h>
 
 #include <algorithm>

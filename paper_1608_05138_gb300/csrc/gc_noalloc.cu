@@ -5,7 +5,8 @@
 // inside another allocator's callback, under a hard budget that forbids
 // growth), cannot use gc_graph_upload: it allocates the CSR copy, the
 // preparation arrays and the per-CTA tables. This entry point is a variant
-// of the triangle step (pass A) that works directly on the caller's device
+// of the triangle step (Alg. 1: a Psi bitmap of Gamma(x), probed with the
+// neighbours of each neighbour) that works directly on the caller's device
 // CSR and writes the caller's device output. Its only scratch -- one bitmap
 // per CTA marking Gamma(x) -- lives in a file-scope __device__ array that
 // every GPU loading the library holds until the process exits:
