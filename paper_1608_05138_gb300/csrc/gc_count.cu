@@ -369,12 +369,34 @@ __global__ void __launch_bounds__(kHeavyBlock, 1) k_pass_c_heavy(DevGraph g, Cou
           beg[i] = st;
           cur[i] = en;
         }
-        const Deal d = deal_setup(L, comp, lane);
+        // runs of 32 or more entries (most of the wedges): the whole warp,
+        // one run at a time, consecutive entries over the lanes
+        unsigned lm = __ballot_sync(0xffffffffu, L >= 32);
+        while (lm) {
+          const int src = __ffs(lm) - 1;
+          lm &= lm - 1;
+          const int32_t s0 = __shfl_sync(0xffffffffu, st, src);
+          const int32_t n0 = __shfl_sync(0xffffffffu, L, src);
+          for (int32_t k0 = 0; k0 < n0; k0 += 128) {
+            int32_t o[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              const int32_t kk = k0 + 32 * j + lane;
+              o[j] = kk < n0 ? g.ci[s0 + kk] : -1;
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+              if (o[j] >= 0) add_count(tab, o[j] - lo_id, half);
+          }
+        }
+        // shorter runs dealt to the lanes end to end
+        const int32_t Ls = L < 32 ? L : 0;
+        const Deal d = deal_setup(Ls, comp, lane);
         for (int32_t k0 = 0; k0 < d.total; k0 += 128) {
           int32_t q[4];
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
-            const int ol = deal_owner(d, L, k0 + 32 * j, comp, lane);
+            const int ol = deal_owner(d, Ls, k0 + 32 * j, comp, lane);
             const int32_t kk = k0 + 32 * j + lane;
             const int32_t sj = __shfl_sync(0xffffffffu, st, ol);
             const int32_t ej = __shfl_sync(0xffffffffu, d.excl, ol);
@@ -402,18 +424,49 @@ __global__ void __launch_bounds__(kHeavyBlock, 1) k_pass_c_heavy(DevGraph g, Cou
           st = beg[i];
           L = cur[i] - st;
         }
-        const Deal d = deal_setup(L, comp, lane);
         s_sx[warp][lane] = 0ull;  // per x of the chunk: sum of its wedges' counts
         __syncwarp();
+        // runs of 32 or more entries: the whole warp, one run at a time
+        unsigned lm = __ballot_sync(0xffffffffu, L >= 32);
+        while (lm) {
+          const int src = __ffs(lm) - 1;
+          lm &= lm - 1;
+          const int32_t s0 = __shfl_sync(0xffffffffu, st, src);
+          const int32_t n0 = __shfl_sync(0xffffffffu, L, src);
+          unsigned long long acc = 0ull;
+          for (int32_t k0 = 0; k0 < n0; k0 += 128) {
+            int32_t o[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              const int32_t kk = k0 + 32 * j + lane;
+              o[j] = kk < n0 ? g.ci[s0 + kk] : -1;
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              if (o[j] < 0) continue;
+              const uint32_t cnt = read_count(tab, o[j] - lo_id, half) - 1u;
+              if (cnt) {
+                atomicAdd(&a.P[s0 + k0 + 32 * j + lane], (unsigned long long)cnt);  // slot (x, o)
+                acc += cnt;
+              }
+            }
+          }
+          for (int off = 16; off; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+          if (lane == src) s_sx[warp][lane] += acc;
+        }
+        __syncwarp();
+        // shorter runs dealt to the lanes end to end
+        const int32_t Ls = L < 32 ? L : 0;
+        const Deal d = deal_setup(Ls, comp, lane);
         for (int32_t k0 = 0; k0 < d.total; k0 += 128) {
           int32_t q[4], ol[4], ej[4], lj[4];
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
-            ol[j] = deal_owner(d, L, k0 + 32 * j, comp, lane);
+            ol[j] = deal_owner(d, Ls, k0 + 32 * j, comp, lane);
             const int32_t kk = k0 + 32 * j + lane;
             const int32_t sj = __shfl_sync(0xffffffffu, st, ol[j]);
             ej[j] = __shfl_sync(0xffffffffu, d.excl, ol[j]);
-            lj[j] = __shfl_sync(0xffffffffu, L, ol[j]);
+            lj[j] = __shfl_sync(0xffffffffu, Ls, ol[j]);
             q[j] = kk < d.total ? sj + (kk - ej[j]) : -1;
           }
           int32_t o[4];
