@@ -188,11 +188,22 @@ __global__ void __launch_bounds__(kThreads, 65536 / (kThreads * 64)) k_pass_k(De
       if (i >= k) break;
       const int32_t b = ids[i];
       const int32_t bb = g.out_ptr[b], be = g.out_ptr[b + 1];
-      for (int32_t q0 = bb; q0 < be; q0 += 32) {
-        const int32_t q = q0 + lane;
-        const int32_t c = q < be ? g.out_idx[q] : 0x7fffffff;
-        if (__shfl_sync(kFull, c, 0) > cmax) break;  // out(b) ascends: nothing further is in out(a)
-        if (lane == 0) w_scan += min(32, be - q0);
+      // four windows of 32 entries per round, so that four loads are in
+      // flight per lane; out(b) ascends, so the scan stops at the first round
+      // that reaches past max out(a)
+      for (int32_t q0 = bb; q0 < be; q0 += 128) {
+        int32_t cw[4];
+#pragma unroll
+        for (int w4 = 0; w4 < 4; ++w4) {
+          const int32_t q = q0 + 32 * w4 + lane;
+          cw[w4] = q < be ? g.out_idx[q] : 0x7fffffff;
+        }
+        if (lane == 0) w_scan += min(128, be - q0);
+        const bool past = __shfl_sync(kFull, cw[3], 31) > cmax;
+#pragma unroll
+        for (int w4 = 0; w4 < 4; ++w4) {
+        const int32_t q = q0 + 32 * w4 + lane;
+        const int32_t c = cw[w4];
         const int32_t j = c <= cmax ? lookup(c) : -1;
         const unsigned hit = __ballot_sync(kFull, j >= 0);
         if (kTri) {
@@ -219,6 +230,8 @@ __global__ void __launch_bounds__(kThreads, 65536 / (kThreads * 64)) k_pass_k(De
             }
           }
         }
+        }
+        if (past) break;
       }
     }
     __syncthreads();
