@@ -202,34 +202,34 @@ __global__ void __launch_bounds__(kThreads, 65536 / (kThreads * 64)) k_pass_k(De
         const bool past = __shfl_sync(kFull, cw[3], 31) > cmax;
 #pragma unroll
         for (int w4 = 0; w4 < 4; ++w4) {
-        const int32_t q = q0 + 32 * w4 + lane;
-        const int32_t c = cw[w4];
-        const int32_t j = c <= cmax ? lookup(c) : -1;
-        const unsigned hit = __ballot_sync(kFull, j >= 0);
-        if (kTri) {
-          if (j >= 0) {
-            atomicAdd(&a.trio[q], 1);  // edge (b_i, c)
-            atomicAdd(&vx7[j], 1u);    // edge (a, c)
-          }
-          if (lane == 0 && hit) {
-            atomicAdd(&vx7[i], (uint32_t)__popc(hit));  // edge (a, b_i)
-            w_edges += __popc(hit);
-          }
-        } else if (hit) {
-          int32_t base_h = 0;
-          if (lane == 0) base_h = atomicAdd(&s_nhit, __popc(hit));
-          base_h = __shfl_sync(kFull, base_h, 0);
-          if (j >= 0) {
-            atomicOr(&rows[i * S + (j >> 5)], 1u << (j & 31));
-            atomicOr(&rows[j * S + (i >> 5)], 1u << (i & 31));
-            const int32_t slot = base_h + __popc(hit & ((1u << lane) - 1u));
-            if (slot < a.hitcap) {
-              hits[3 * (size_t)slot] = i;
-              hits[3 * (size_t)slot + 1] = j;
-              hits[3 * (size_t)slot + 2] = q;
+          const int32_t q = q0 + 32 * w4 + lane;
+          const int32_t c = cw[w4];
+          const int32_t j = c <= cmax ? lookup(c) : -1;
+          const unsigned hit = __ballot_sync(kFull, j >= 0);
+          if (kTri) {
+            if (j >= 0) {
+              atomicAdd(&a.trio[q], 1);  // edge (b_i, c)
+              atomicAdd(&vx7[j], 1u);    // edge (a, c)
+            }
+            if (lane == 0 && hit) {
+              atomicAdd(&vx7[i], (uint32_t)__popc(hit));  // edge (a, b_i)
+              w_edges += __popc(hit);
+            }
+          } else if (hit) {
+            int32_t base_h = 0;
+            if (lane == 0) base_h = atomicAdd(&s_nhit, __popc(hit));
+            base_h = __shfl_sync(kFull, base_h, 0);
+            if (j >= 0) {
+              atomicOr(&rows[i * S + (j >> 5)], 1u << (j & 31));
+              atomicOr(&rows[j * S + (i >> 5)], 1u << (i & 31));
+              const int32_t slot = base_h + __popc(hit & ((1u << lane) - 1u));
+              if (slot < a.hitcap) {
+                hits[3 * (size_t)slot] = i;
+                hits[3 * (size_t)slot + 1] = j;
+                hits[3 * (size_t)slot + 2] = q;
+              }
             }
           }
-        }
         }
         if (past) break;
       }
@@ -404,22 +404,33 @@ __global__ void __launch_bounds__(kWBlock) k_pass_k_warp(DevGraph g, CountArgs a
       const int32_t b = __shfl_sync(kFull, id, i);
       const int32_t bb = g.out_ptr[b], be = g.out_ptr[b + 1];
       unsigned hits = 0u;
-      for (int32_t q0 = bb; q0 < be; q0 += 32) {
-        const int32_t q = q0 + lane;
-        const int32_t c = q < be ? g.out_idx[q] : 0x7fffffff;
-        if (__shfl_sync(kFull, c, 0) > cmax) break;
-        if (lane == 0) w_scan += min(32, be - q0);
-        int lo = 0;
+      for (int32_t q0 = bb; q0 < be; q0 += 128) {  // four windows of 32 in flight
+        int32_t cw[4];
 #pragma unroll
-        for (int step = 16; step; step >>= 1)
-          if (__shfl_sync(kFull, id, lo + step) <= c) lo += step;
-        const bool hit = __shfl_sync(kFull, id, lo) == c && lo < k;  // lanes >= k hold padding ids
-        if (kTri) {
-          if (hit) atomicAdd(&a.trio[q], 1);  // edge (b_i, c)
-        } else if (hit) {
-          qs[i * 32 + lo] = q;
+        for (int w4 = 0; w4 < 4; ++w4) {
+          const int32_t q = q0 + 32 * w4 + lane;
+          cw[w4] = q < be ? g.out_idx[q] : 0x7fffffff;
         }
-        hits |= __reduce_or_sync(kFull, hit ? 1u << lo : 0u);
+        if (lane == 0) w_scan += min(128, be - q0);
+        const bool past = __shfl_sync(kFull, cw[3], 31) > cmax;
+#pragma unroll
+        for (int w4 = 0; w4 < 4; ++w4) {
+          const int32_t q = q0 + 32 * w4 + lane;
+          const int32_t c = cw[w4];
+          int lo = 0;
+#pragma unroll
+          for (int step = 16; step; step >>= 1)
+            if (__shfl_sync(kFull, id, lo + step) <= c) lo += step;
+          const int32_t id_lo = __shfl_sync(kFull, id, lo);  // every lane takes part in the shuffle
+          const bool hit = c <= cmax && id_lo == c && lo < k;  // lanes >= k hold padding ids
+          if (kTri) {
+            if (hit) atomicAdd(&a.trio[q], 1);  // edge (b_i, c)
+          } else if (hit) {
+            qs[i * 32 + lo] = q;
+          }
+          hits |= __reduce_or_sync(kFull, hit ? 1u << lo : 0u);
+        }
+        if (past) break;
       }
       if (lane == i) {
         found = hits;
