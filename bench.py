@@ -78,6 +78,27 @@ def algorithmic_bytes(work: dict) -> dict:
     }
 
 
+def measured_traffic(phase: str, workload: str, scale: int):
+    """DRAM bytes per count of a phase from the committed ncu launch list
+    (profiles/roofline_traffic_rmat22.txt), or None when the workload differs
+    or the kernel sources changed since the counters were taken."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "roofline_traffic_rmat22.txt")
+    if workload != "rmat22" or scale != 22 or not os.path.exists(path):
+        return None
+    table, ok = {}, True
+    for line in open(path):
+        f = line.split()
+        if not f or f[0].startswith("#"):
+            continue
+        if f[0] == "source":
+            src = os.path.join(ROOT, "paper_1608_05138_gb300", "csrc", f[1])
+            ok &= os.path.exists(src) and hashlib.sha256(open(src, "rb").read()).hexdigest() == f[2]
+        else:
+            table[f[0]] = int(f[1])
+    return table.get(phase) if ok else None
+
+
 def paper_method_bytes(rp, ci):
     """Logical bytes of the paper's literal per-edge scans (Alg. 1/5/6):
     B_e = 4 (d_u + d_v + sum_{w in Gamma(u)\\{v}} d_w) + 120 per edge."""
@@ -455,8 +476,9 @@ def main():
         except Exception:
             peak, peak_src = 6800.0, "fallback"
     ph_ms = {k: statistics.mean(p[k] for p in phases) for k in phases[0]}
-    kernel_ms = {"k_pass_t": ph_ms["pass_t_triangles"], "k_pass_c": ph_ms["pass_c_cycles"],
-                 "k_pass_k": ph_ms["pass_k_cliques"], "k_finish": ph_ms["finish_columns"]}
+    phase_of = {"k_pass_t": "pass_t_triangles", "k_pass_c": "pass_c_cycles", "k_pass_k": "pass_k_cliques",
+                "k_finish": "finish_columns"}
+    kernel_ms = {k: ph_ms[ph] for k, ph in phase_of.items()}
     ab = algorithmic_bytes(work)
     kernels = {k: {"ms": kernel_ms[k], "algorithmic_bytes": ab[k],
                    "gbs": ab[k] / (kernel_ms[k] / 1000.0) / 1e9 if kernel_ms[k] > 0 else None,
@@ -464,8 +486,11 @@ def main():
     dom = max(kernel_ms, key=kernel_ms.get)
     achieved = kernels[dom]["gbs"]
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "peak_source": peak_src, "kernel": dom, "kernel_ms": kernel_ms[dom],
-            "algorithmic_bytes": ab[dom], "traffic": None, "kernels": kernels,
+            "peak_source": peak_src, "kernel": dom, "phase": phase_of[dom], "kernel_ms": kernel_ms[dom],
+            "algorithmic_bytes": ab[dom],
+            "traffic": measured_traffic(phase_of[dom], args.workload, args.scale),
+            "traffic_source": "profiles/launches_rmat22_count.md (ncu dram__bytes_read+write per count)",
+            "kernels": kernels,
             "logical_paper_method_gbs": paper_method_bytes(rp, ci) / (step_ms / 1000.0) / 1e9}
     line = {"metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
