@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(kThreads, 65536 / (kThreads * 64)) k_pass_k(De
   int32_t* qj = s_qj[warp];
   int32_t* qq = s_qq[warp];
   // phase-1 hits of pass K (i, j, out-slot), so that phase 2 needs no rescan
-  int32_t* hits = kTri ? nullptr : a.hitbuf + (size_t)blockIdx.x * 3 * (size_t)a.hitcap;
+  int32_t* hits = kTri ? nullptr : a.hitbuf + (size_t)blockIdx.x * 2 * (size_t)a.hitcap;
 
   const int32_t u0 = a.ktier_off[tier], u1 = a.ktier_off[tier + 1];
   int32_t* cursor = a.cursor + (kTri ? 10 : 2) + tier;
@@ -224,9 +224,8 @@ __global__ void __launch_bounds__(kThreads, 65536 / (kThreads * 64)) k_pass_k(De
               atomicOr(&rows[j * S + (i >> 5)], 1u << (i & 31));
               const int32_t slot = base_h + __popc(hit & ((1u << lane) - 1u));
               if (slot < a.hitcap) {
-                hits[3 * (size_t)slot] = i;
-                hits[3 * (size_t)slot + 1] = j;
-                hits[3 * (size_t)slot + 2] = q;
+                hits[2 * (size_t)slot] = (int32_t)(((uint32_t)i << 16) | (uint32_t)j);  // read only when k <= 65535
+                hits[2 * (size_t)slot + 1] = q;
               }
             }
           }
@@ -242,12 +241,13 @@ __global__ void __launch_bounds__(kThreads, 65536 / (kThreads * 64)) k_pass_k(De
     }
     const int32_t nhit = s_nhit;
 
-    if (nhit <= a.hitcap) {
+    if (nhit <= a.hitcap && k <= 65535) {  // (i, j) packed in 16 bits each
       // Phase 2 over the recorded edges of H_a: lane per edge.
       for (int32_t e0 = warp * 32; e0 < nhit; e0 += kThreads) {
         const int32_t e = e0 + lane;
         if (e < nhit) {
-          const int32_t i = hits[3 * (size_t)e], j = hits[3 * (size_t)e + 1], q = hits[3 * (size_t)e + 2];
+          const int32_t ij = hits[2 * (size_t)e], q = hits[2 * (size_t)e + 1];
+          const int32_t i = (int32_t)((uint32_t)ij >> 16), j = ij & 0xffff;
           const uint32_t* ri = rows + i * S;
           const uint32_t* rj = rows + j * S;
           int c4 = 0;
@@ -255,7 +255,7 @@ __global__ void __launch_bounds__(kThreads, 65536 / (kThreads * 64)) k_pass_k(De
           const int32_t ti = ta[i], tj = ta[j];
           const int32_t tij = a.trio[q];
           if (c4) {
-            atomicAdd(&a.x7o[q], (unsigned long long)c4);
+            atomicAdd(&a.xc[2 * (size_t)q], (unsigned long long)c4);
             if (kCap) {  // at most k^2 per member: no carry for k <= 1024
               atomicAdd(&vx7[i], (uint32_t)c4);
               atomicAdd(&vx7[j], (uint32_t)c4);
@@ -264,7 +264,7 @@ __global__ void __launch_bounds__(kThreads, 65536 / (kThreads * 64)) k_pass_k(De
               add_split(vx7, vx7h, j, (unsigned long long)c4);
             }
           }
-          atomicAdd(&a.cro[q], (unsigned long long)(ti + tj - 2));
+          atomicAdd(&a.xc[2 * (size_t)q + 1], (unsigned long long)(ti + tj - 2));
           add_split(vcr, vcrh, i, (unsigned long long)(tj + tij - 2));
           add_split(vcr, vcrh, j, (unsigned long long)(ti + tij - 2));
         }
@@ -294,8 +294,8 @@ __global__ void __launch_bounds__(kThreads, 65536 / (kThreads * 64)) k_pass_k(De
         for (int w = 0; w < W; ++w) c4 += __popc(ri[w] & rj[w]);
         const int32_t tj = ta[j];
         const int32_t tij = a.trio[q];
-        if (c4) atomicAdd(&a.x7o[q], (unsigned long long)c4);
-        atomicAdd(&a.cro[q], (unsigned long long)(ti + tj - 2));
+        if (c4) atomicAdd(&a.xc[2 * (size_t)q], (unsigned long long)c4);
+        atomicAdd(&a.xc[2 * (size_t)q + 1], (unsigned long long)(ti + tj - 2));
         if (c4) add_split(vx7, vx7h, j, (unsigned long long)c4);
         add_split(vcr, vcrh, j, (unsigned long long)(ti + tij - 2));
         ax7 += (unsigned long long)c4;
@@ -351,8 +351,8 @@ __global__ void __launch_bounds__(kThreads, 65536 / (kThreads * 64)) k_pass_k(De
     // its edges at i, hence the halving) and the cross terms gathered above.
     for (int32_t i = threadIdx.x; i < k; i += kThreads) {
       const unsigned long long x = read_split(vx7, vx7h, i), c = read_split(vcr, vcrh, i);
-      if (x) atomicAdd(&a.x7o[ob + i], x >> 1);
-      if (c) atomicAdd(&a.cro[ob + i], c);
+      if (x) atomicAdd(&a.xc[2 * (size_t)(ob + i)], x >> 1);
+      if (c) atomicAdd(&a.xc[2 * (size_t)(ob + i) + 1], c);
     }
   }
   if (lane == 0) {
@@ -457,8 +457,8 @@ __global__ void __launch_bounds__(kWBlock) k_pass_k_warp(DevGraph g, CountArgs a
         const int32_t q = qs[i * 32 + lane];
         const int c4 = __popc(ri & row);
         const int32_t tij = a.trio[q];
-        if (c4) atomicAdd(&a.x7o[q], (unsigned long long)c4);
-        atomicAdd(&a.cro[q], (unsigned long long)(tI + ti - 2));
+        if (c4) atomicAdd(&a.xc[2 * (size_t)q], (unsigned long long)c4);
+        atomicAdd(&a.xc[2 * (size_t)q + 1], (unsigned long long)(tI + ti - 2));
         vx += (unsigned long long)c4;
         vc += (unsigned long long)(tI + tij - 2);
         cx = (unsigned long long)c4;
@@ -472,8 +472,8 @@ __global__ void __launch_bounds__(kWBlock) k_pass_k_warp(DevGraph g, CountArgs a
       }
     }
     if (lane < k) {
-      if (vx) atomicAdd(&a.x7o[ob + lane], vx >> 1);
-      if (vc) atomicAdd(&a.cro[ob + lane], vc);
+      if (vx) atomicAdd(&a.xc[2 * (size_t)(ob + lane)], vx >> 1);
+      if (vc) atomicAdd(&a.xc[2 * (size_t)(ob + lane) + 1], vc);
     }
     if (lane == 0) w_members += k;
     __syncwarp();

@@ -107,8 +107,8 @@ __global__ void __launch_bounds__(kFinBlock) k_finish(DevGraph g, CountArgs a) {
       gid = g.vgid ? g.vgid[u] : 0;
       const int64_t du = g.deg[u], dv = g.deg[v];
       const int64_t t = a.trio[o];
-      const int64_t x7 = (int64_t)a.x7o[o];
-      const int64_t x10 = (int64_t)(a.P[p] + a.P[r]) - (int64_t)a.cro[o] + 2 * x7;
+      const int64_t x7 = (int64_t)a.xc[2 * o];
+      const int64_t x10 = (int64_t)(a.P[p] + a.P[r]) - (int64_t)a.xc[2 * o + 1] + 2 * x7;
       const int64_t su = du - t - 1, sv = dv - t - 1;
       const int64_t n_g = g.gn[gid], m_g = g.gm[gid];
       const int64_t D = n_g - 2 - t - su - sv;

@@ -59,13 +59,14 @@ struct CountArgs {
   int32_t* trio;           // [m] |T| by out-slot (pass T)
   unsigned long long* P;   // [2m] per slot: 4-cycles through its edge counted at that slot
                            // (pass C, zeroed before); an edge's count = sum of its two slots
-  unsigned long long* x7o;   // [m] per out-slot: 4-cliques through the edge (pass K)
-  unsigned long long* cro;   // [m] per out-slot: sum over T of (|T_(a,u)| + |T_(a,v)| - 2) (pass K)
+  unsigned long long* xc;    // [m][2] per out-slot: 4-cliques through the edge, and the sum over T of
+                             // (|T_(a,u)| + |T_(a,v)| - 2) (pass K); side by side, so that the two
+                             // atomics of an edge land in one 32-byte sector
   unsigned char* kbuf;     // global-tier per-CTA buffers (kbuf_ctas x kbuf_stride bytes)
   size_t kbuf_stride;
   int32_t kbuf_ctas;
   int32_t kbuf_cap;        // largest k the global tier holds
-  int32_t* hitbuf;         // pass K: per-CTA lists of the edges of H_a (hitbuf_ctas x hitcap x 3 ints)
+  int32_t* hitbuf;         // pass K: per-CTA lists of the edges of H_a (hitbuf_ctas x hitcap x 2 ints)
   int32_t hitcap;
   int32_t hitbuf_ctas;
   uint64_t* per_edge;      // [m][13] device pointer or nullptr
@@ -108,8 +109,7 @@ enum Phase { kPhasePassT = 0, kPhasePassC, kPhasePassK, kPhaseFinish, kPhaseDeri
 struct Scratch {
   int32_t* trio = nullptr;           // [m]
   unsigned long long* P = nullptr;   // [2m]
-  unsigned long long* x7o = nullptr; // [m]
-  unsigned long long* cro = nullptr; // [m]
+  unsigned long long* xc = nullptr;  // [m][2]
   int32_t* misc = nullptr;           // [16] cursors, status
   int32_t* cbuf = nullptr;           // pass C hub cursors
   int32_t cbuf_nx = 0;

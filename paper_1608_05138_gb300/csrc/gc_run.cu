@@ -34,7 +34,7 @@ long long k_list_cap() {
 }  // namespace
 
 void scratch_free(Scratch* sc, cudaStream_t s) {
-  for (void* p : {(void*)sc->trio, (void*)sc->P, (void*)sc->x7o, (void*)sc->cro, (void*)sc->misc,
+  for (void* p : {(void*)sc->trio, (void*)sc->P, (void*)sc->xc, (void*)sc->misc,
                   (void*)sc->cbuf, (void*)sc->tables, (void*)sc->kbuf, (void*)sc->hitbuf, (void*)sc->work})
     if (p) cudaFreeAsync(p, s);
   *sc = Scratch();
@@ -50,8 +50,7 @@ gc_status scratch_init(Scratch* sc, int32_t m, int32_t table_n, int32_t kmax, in
   const size_t m1 = (size_t)(m > 0 ? m : 1);
   GS_TRY(cudaMallocAsync(&sc->trio, sizeof(int32_t) * m1, s));
   GS_TRY(cudaMallocAsync(&sc->P, sizeof(unsigned long long) * 2 * m1, s));
-  GS_TRY(cudaMallocAsync(&sc->x7o, sizeof(unsigned long long) * m1, s));
-  GS_TRY(cudaMallocAsync(&sc->cro, sizeof(unsigned long long) * m1, s));
+  GS_TRY(cudaMallocAsync(&sc->xc, sizeof(unsigned long long) * 2 * m1, s));
   GS_TRY(cudaMallocAsync(&sc->misc, sizeof(int32_t) * 16, s));
   GS_TRY(cudaMallocAsync(&sc->work, sizeof(unsigned long long) * kNumWork, s));
   if (table_n > kSmemTableMax) {
@@ -68,7 +67,7 @@ gc_status scratch_init(Scratch* sc, int32_t m, int32_t table_n, int32_t kmax, in
     const long long cap = k_list_cap();
     sc->hitcap = (int32_t)(full < cap ? (full > 0 ? full : 1) : cap);
     sc->hitbuf_ctas = count_grid_size();
-    GS_TRY(cudaMallocAsync(&sc->hitbuf, sizeof(int32_t) * 3 * (size_t)sc->hitcap * (size_t)sc->hitbuf_ctas, s));
+    GS_TRY(cudaMallocAsync(&sc->hitbuf, sizeof(int32_t) * 2 * (size_t)sc->hitcap * (size_t)sc->hitbuf_ctas, s));
   }
   if (kmax > kTierCap[kTier1024]) {
     sc->kbuf_cap = kmax;
@@ -110,8 +109,7 @@ gc_status run_count(const DevGraph& g, const int32_t* units, int32_t n_units, co
   a.tables = g.table_n > kSmemTableMax ? sc->tables : nullptr;
   a.trio = sc->trio;
   a.P = sc->P;
-  a.x7o = sc->x7o;
-  a.cro = sc->cro;
+  a.xc = sc->xc;
   a.kbuf = sc->kbuf;
   a.kbuf_stride = sc->kbuf_stride;
   a.kbuf_ctas = sc->kbuf_ctas;
@@ -127,8 +125,7 @@ gc_status run_count(const DevGraph& g, const int32_t* units, int32_t n_units, co
   GR_TRY(cudaMemsetAsync(sc->work, 0, sizeof(unsigned long long) * kNumWork, s), "memset work");
   GR_TRY(cudaMemsetAsync(csum, 0, sizeof(unsigned long long) * 26 * (size_t)g.G, s), "memset sums");
   GR_TRY(cudaMemsetAsync(sc->P, 0, sizeof(unsigned long long) * 2 * m1, s), "zero P");
-  GR_TRY(cudaMemsetAsync(sc->x7o, 0, sizeof(unsigned long long) * m1, s), "zero x7");
-  GR_TRY(cudaMemsetAsync(sc->cro, 0, sizeof(unsigned long long) * m1, s), "zero cross");
+  GR_TRY(cudaMemsetAsync(sc->xc, 0, sizeof(unsigned long long) * 2 * m1, s), "zero x7 and cross");
   GR_TRY(cudaMemsetAsync(sc->trio, 0, sizeof(int32_t) * m1, s), "zero T");
   int launches = 0;
   GR_EVENT(kPhasePassT);
