@@ -11,7 +11,7 @@ CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 SO = os.path.join(HERE, "libgc.so")
 SOURCES = ["gc_api.cu", "gc_prep.cu", "gc_count.cu", "gc_run.cu", "gc_batch.cu", "gc_small.cu",
-           "gc_noalloc.cu", "gc_clique.cu"]
+           "gc_noalloc.cu", "gc_clique.cu", "gc_relabel.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "-I", os.path.join(HERE, "..", "include")]
 

@@ -76,55 +76,54 @@ struct Checks {
 
 }  // namespace
 
-// Reverse slots of a CSR and, with check, the checks of Problem 1's input (a
-// simple undirected graph): row_ptr from 0 and non-decreasing, columns in
-// range, rows strictly ascending (no duplicates), no self-loops, symmetric.
-// rev (optional, [row_ptr[n]]): slot of (y, x) for the slot of (x, y).
-//
-// Symmetry: rows x are walked in order in chunks of about equal entries; the
-// k-th row (in order) that names y must name it from the k-th entry of row y,
-// so a per-chunk counter per y (started, on first use, at the number of
-// entries of row y below the chunk's first row) gives the slot where x must
-// stand in row y, and the entry there is compared with x. Every entry is
-// checked against a slot of row y, so a missing reverse always fails, and a
-// symmetric graph always passes. Without check, an entry whose reverse is not
-// found gets rev = its own slot.
-gc_status csr_reverse(int32_t n, const int32_t* rp, const int32_t* ci, int32_t* rev, bool check) {
+// Checks of Problem 1's input (a simple undirected graph), in two parts.
+// Linear checks: row_ptr from 0 and non-decreasing, columns in range, rows
+// strictly ascending (no duplicates), no self-loops -- one pass over the
+// entries in threads over row ranges of equal entries.
+gc_status csr_linear_checks(int32_t n, const int32_t* rp, const int32_t* ci) {
   if (n < 0) { set_error("n < 0"); return GC_ERR_ARG; }
-  if (check) {
-    if (rp[0] != 0) { set_error("row_ptr[0] != 0"); return GC_ERR_RANGE; }
-    for (int32_t x = 0; x < n; ++x)
-      if (rp[x + 1] < rp[x]) {
-        set_error("row_ptr decreases at row " + std::to_string(x));
-        return GC_ERR_UNSORTED;
-      }
-    if (rp[n] % 2 != 0) { set_error("row_ptr[n] is odd: the graph cannot be symmetric"); return GC_ERR_ASYMMETRIC; }
-  }
+  if (rp[0] != 0) { set_error("row_ptr[0] != 0"); return GC_ERR_RANGE; }
+  for (int32_t x = 0; x < n; ++x)
+    if (rp[x + 1] < rp[x]) {
+      set_error("row_ptr decreases at row " + std::to_string(x));
+      return GC_ERR_UNSORTED;
+    }
+  if (rp[n] % 2 != 0) { set_error("row_ptr[n] is odd: the graph cannot be symmetric"); return GC_ERR_ASYMMETRIC; }
   const int64_t nnz = rp[n];
-  int nt = host_threads();
-  if (nnz < (1 << 20)) nt = 1;
-  if (check) {  // range, loop, duplicate and order: every row before any symmetry probe
-    const std::vector<int32_t> b = nnz_chunks(n, rp, nt);
-    Checks c(nt);
-    run_threads(nt, [&](int t) {
-      for (int32_t x = b[t]; x < b[t + 1]; ++x)
-        for (int32_t p = rp[x]; p < rp[x + 1]; ++p) {
-          const int32_t y = ci[p];
-          if (y < 0 || y >= n) { c.st[t] = GC_ERR_RANGE; c.msg[t] = "column " + std::to_string(y) + " out of range in row " + std::to_string(x); return; }
-          if (y == x) { c.st[t] = GC_ERR_SELF_LOOP; c.msg[t] = "self-loop at vertex " + std::to_string(x); return; }
-          if (p > rp[x] && ci[p - 1] == y) { c.st[t] = GC_ERR_DUPLICATE; c.msg[t] = "duplicate neighbour " + std::to_string(y) + " in row " + std::to_string(x); return; }
-          if (p > rp[x] && ci[p - 1] > y) { c.st[t] = GC_ERR_UNSORTED; c.msg[t] = "row " + std::to_string(x) + " not ascending"; return; }
-        }
-    });
-    const gc_status st = c.first();
-    if (st != GC_OK) return st;
-  }
+  const int nt = nnz < (1 << 20) ? 1 : host_threads();
+  const std::vector<int32_t> b = nnz_chunks(n, rp, nt);
+  Checks c(nt);
+  run_threads(nt, [&](int t) {
+    for (int32_t x = b[t]; x < b[t + 1]; ++x)
+      for (int32_t p = rp[x]; p < rp[x + 1]; ++p) {
+        const int32_t y = ci[p];
+        if (y < 0 || y >= n) { c.st[t] = GC_ERR_RANGE; c.msg[t] = "column " + std::to_string(y) + " out of range in row " + std::to_string(x); return; }
+        if (y == x) { c.st[t] = GC_ERR_SELF_LOOP; c.msg[t] = "self-loop at vertex " + std::to_string(x); return; }
+        if (p > rp[x] && ci[p - 1] == y) { c.st[t] = GC_ERR_DUPLICATE; c.msg[t] = "duplicate neighbour " + std::to_string(y) + " in row " + std::to_string(x); return; }
+        if (p > rp[x] && ci[p - 1] > y) { c.st[t] = GC_ERR_UNSORTED; c.msg[t] = "row " + std::to_string(x) + " not ascending"; return; }
+      }
+  });
+  return c.first();
+}
+
+// Symmetry (needs the linear checks passed): rows x are walked in order in
+// chunks of about equal entries; the k-th row (in order) that names y must
+// name it from the k-th entry of row y, so a per-chunk counter per y (started,
+// on first use, at the number of entries of row y below the chunk's first
+// row) gives the slot where x must stand in row y, and the entry there is
+// compared with x. Every entry is checked against a slot of row y, so a
+// missing reverse always fails, and a symmetric graph always passes. The
+// message of a failure is returned in *msg (the calling thread sets it).
+gc_status csr_symmetry(int32_t n, const int32_t* rp, const int32_t* ci, std::string* msg) {
+  const int64_t nnz = rp[n];
+  int nt = nnz < (1 << 20) ? 1 : host_threads();
   // per-chunk counters: n ints per thread, at most 1 GiB in all
   const int64_t per = 4 * (int64_t)(n > 0 ? n : 1);
-  int nts = (int)std::max<int64_t>(1, std::min<int64_t>(nt, (int64_t(1) << 30) / per));
-  const std::vector<int32_t> b = nnz_chunks(n, rp, nts);
-  Checks c(nts);
-  run_threads(nts, [&](int t) {
+  nt = (int)std::max<int64_t>(1, std::min<int64_t>(nt, (int64_t(1) << 30) / per));
+  const std::vector<int32_t> b = nnz_chunks(n, rp, nt);
+  std::vector<gc_status> st((size_t)nt, GC_OK);
+  std::vector<std::string> ms((size_t)nt);
+  run_threads(nt, [&](int t) {
     std::vector<int32_t> fill((size_t)(n > 0 ? n : 1), -1);
     const int32_t x0 = b[t];
     for (int32_t x = x0; x < b[t + 1]; ++x)
@@ -135,110 +134,80 @@ gc_status csr_reverse(int32_t n, const int32_t* rp, const int32_t* ci, int32_t* 
         if (f < 0) f = (int32_t)(std::lower_bound(ci + yb, ci + ye, x0) - (ci + yb));
         fill[y] = f + 1;
         const int32_t q = yb + f;
-        if (q < ye && ci[q] == x) {
-          if (rev) rev[p] = q;
-        } else if (check) {
-          c.st[t] = GC_ERR_ASYMMETRIC;
-          c.msg[t] = "edge (" + std::to_string(x) + "," + std::to_string(y) + ") has no reverse";
+        if (q >= ye || ci[q] != x) {
+          st[t] = GC_ERR_ASYMMETRIC;
+          ms[t] = "edge (" + std::to_string(x) + "," + std::to_string(y) + ") has no reverse";
           return;
-        } else if (rev) {
-          const int32_t* r = std::lower_bound(ci + yb, ci + ye, x);
-          rev[p] = (r < ci + ye && *r == x) ? (int32_t)(r - ci) : p;
         }
       }
   });
-  return c.first();
+  for (int t = 0; t < nt; ++t)
+    if (st[t] != GC_OK) {
+      *msg = ms[t];
+      return st[t];
+    }
+  return GC_OK;
 }
 
-gc_status validate_csr(int32_t n, const int32_t* rp, const int32_t* ci) { return csr_reverse(n, rp, ci, nullptr, true); }
+gc_status validate_csr(int32_t n, const int32_t* rp, const int32_t* ci) {
+  gc_status st = csr_linear_checks(n, rp, ci);
+  if (st != GC_OK) return st;
+  std::string msg;
+  st = csr_symmetry(n, rp, ci, &msg);
+  if (st != GC_OK) set_error(msg);
+  return st;
+}
 
-// Preprocessing P1 (Sec. 4.3): relabel vertices by ascending degree (ties by
-// id), so that internal ids are the (degree, id) ranks used by P3 and by the
-// degree-ordered passes. Rows are re-sorted in the new ids. Edge ids stay
-// those of the caller's graph: eid[slot] of every internal slot is the
-// caller's edge id, and perm maps internal -> caller vertex ids. rev: the
-// reverse slots of the caller's CSR (csr_reverse).
 // Host arrays left uninitialised on allocation (every element is written
-// before use): a value-initialising std::vector would zero a gigabyte on one
-// thread for the larger graphs.
-struct HostArray {
-  std::unique_ptr<int32_t[]> p;
-  int32_t* data() { return p.get(); }
-  int32_t& operator[](size_t i) { return p[i]; }
-  void resize(size_t n) { p.reset(new int32_t[n > 0 ? n : 1]); }
+// before use).
+template <class T>
+struct HostBuf {
+  std::unique_ptr<T[]> p;
+  T* data() { return p.get(); }
+  T& operator[](size_t i) { return p[i]; }
+  void resize(size_t n) { p.reset(new T[n > 0 ? n : 1]); }
 };
 
-struct Relabeled {
-  HostArray rp, ci, eid, perm;
+// The host half of preprocessing P1 (Sec. 4.3): vertices ranked by ascending
+// (degree, id) -- a stable counting sort of the degrees -- and what the
+// device relabel needs: internal row pointers, and the internal rows of more
+// than 32 entries listed by the sort that takes them.
+struct RelabelPlan {
+  HostBuf<int32_t> perm, newid, rp;
+  std::vector<int32_t> mid, longr;  // rows of 33..4096 entries, and longer ones
+  std::vector<int64_t> long_off;    // offset of each long row's padded copy
+  int64_t tmp_len = 0;
 };
 
-Relabeled relabel_by_degree(int32_t n, const int32_t* rp, const int32_t* ci, const int32_t* rev) {
-  Relabeled R;
-  const int64_t nnz = rp[n];
-  const int32_t m = (int32_t)(nnz / 2);
-  int nt = host_threads();
-  if (nnz < (1 << 20)) nt = 1;
+RelabelPlan plan_relabel(int32_t n, const int32_t* rp) {
+  RelabelPlan R;
   int32_t dmax = 0;
   for (int32_t x = 0; x < n; ++x) dmax = std::max(dmax, rp[x + 1] - rp[x]);
-  // stable counting sort by degree
   std::vector<int32_t> cnt((size_t)dmax + 2, 0);
   for (int32_t x = 0; x < n; ++x) cnt[rp[x + 1] - rp[x] + 1]++;
   for (int32_t d = 0; d <= dmax; ++d) cnt[d + 1] += cnt[d];
   R.perm.resize((size_t)n);
-  std::vector<int32_t> newid((size_t)n);
+  R.newid.resize((size_t)n);
   for (int32_t x = 0; x < n; ++x) {
     const int32_t i = cnt[rp[x + 1] - rp[x]]++;
     R.perm[i] = x;
-    newid[x] = i;
+    R.newid[x] = i;
   }
-  // caller's edge ids: row x's entries y > x are edges up[x], up[x] + 1, ...
-  std::vector<int32_t> first_up((size_t)n + 1), up((size_t)n + 1, 0);
-  const std::vector<int32_t> b = nnz_chunks(n, rp, nt);
-  run_threads(nt, [&](int t) {
-    for (int32_t x = b[t]; x < b[t + 1]; ++x) {
-      first_up[x] = (int32_t)(std::upper_bound(ci + rp[x], ci + rp[x + 1], x) - ci);
-      up[x + 1] = rp[x + 1] - first_up[x];
-    }
-  });
-  for (int32_t x = 0; x < n; ++x) up[x + 1] += up[x];
-  HostArray eid_in;
-  eid_in.resize((size_t)nnz);
-  run_threads(nt, [&](int t) {
-    for (int32_t x = b[t]; x < b[t + 1]; ++x)
-      for (int32_t p = rp[x]; p < rp[x + 1]; ++p) {
-        const int32_t y = ci[p];
-        int32_t id;
-        if (y > x) {
-          id = up[x] + (p - first_up[x]);
-        } else {
-          const int32_t q = rev[p];  // (y, x) in row y, x > y
-          id = up[y] + (q - first_up[y]);
-        }
-        eid_in[p] = (id >= 0 && id < m) ? id : 0;  // out of range only for an input that skipped validation
-      }
-  });
   R.rp.resize((size_t)n + 1);
   R.rp[0] = 0;
-  for (int32_t i = 0; i < n; ++i) R.rp[i + 1] = R.rp[i] + (rp[R.perm[i] + 1] - rp[R.perm[i]]);
-  R.ci.resize((size_t)nnz);
-  R.eid.resize((size_t)nnz);
-  const std::vector<int32_t> bn = nnz_chunks(n, R.rp.data(), nt);
-  run_threads(nt, [&](int t) {
-    std::vector<uint64_t> tmp;
-    for (int32_t i = bn[t]; i < bn[t + 1]; ++i) {
-      const int32_t x = R.perm[i];
-      tmp.clear();
-      for (int32_t p = rp[x]; p < rp[x + 1]; ++p)
-        tmp.push_back(((uint64_t)(uint32_t)newid[ci[p]] << 32) | (uint32_t)eid_in[p]);
-      std::sort(tmp.begin(), tmp.end());
-      int32_t o = R.rp[i];
-      for (uint64_t k : tmp) {
-        R.ci[o] = (int32_t)(k >> 32);
-        R.eid[o] = (int32_t)(k & 0xffffffffu);
-        ++o;
-      }
+  for (int32_t i = 0; i < n; ++i) {
+    const int32_t d = rp[R.perm[i] + 1] - rp[R.perm[i]];
+    R.rp[i + 1] = R.rp[i] + d;
+    if (d > 4096) {
+      int64_t P = 4096;
+      while (P < d) P <<= 1;
+      R.longr.push_back(i);
+      R.long_off.push_back(R.tmp_len);
+      R.tmp_len += P;
+    } else if (d > 32) {
+      R.mid.push_back(i);
     }
-  });
+  }
   return R;
 }
 
@@ -298,19 +267,25 @@ gc_status gc_graph_upload(int32_t n, const int32_t* row_ptr, const int32_t* col_
     return GC_ERR_ARG;
   }
   if (flags & ~GC_NO_VALIDATE) { set_error("unknown flags"); return GC_ERR_ARG; }
-  const int64_t nnz = row_ptr[n];
-  HostArray rev;
-  try {
-    rev.resize((size_t)(nnz > 0 ? nnz : 1));
-  } catch (...) {
-    set_error("host allocation failed");
-    return GC_ERR_NOMEM;
-  }
-  {
-    const gc_status st0 = csr_reverse(n, row_ptr, col_idx, rev.data(), !(flags & GC_NO_VALIDATE));
+  const bool validate = !(flags & GC_NO_VALIDATE);
+  if (validate) {
+    const gc_status st0 = csr_linear_checks(n, row_ptr, col_idx);
     if (st0 != GC_OK) return st0;
   }
+  const int64_t nnz = row_ptr[n];
   if (nnz < 0 || nnz % 2) { set_error("row_ptr[n] must be even and >= 0"); return GC_ERR_ARG; }
+  // The symmetry check runs on its own host threads while the device
+  // relabels and prepares the graph: the device steps are safe on an
+  // asymmetric input (columns in range, rows sorted), and nothing is counted
+  // before the check has passed.
+  gc_status sym_st = GC_OK;
+  std::string sym_msg;
+  std::thread sym;
+  if (validate) sym = std::thread([&] { sym_st = csr_symmetry(n, row_ptr, col_idx, &sym_msg); });
+  struct Joiner {
+    std::thread* t;
+    ~Joiner() { if (t->joinable()) t->join(); }
+  } joiner{&sym};
   gc_graph g = new (std::nothrow) gc_graph_s();
   if (!g) { set_error("host allocation failed"); return GC_ERR_NOMEM; }
   g->n = n;
@@ -319,45 +294,91 @@ gc_status gc_graph_upload(int32_t n, const int32_t* row_ptr, const int32_t* col_
   cudaStream_t s = g->stream;
   cudaError_t e;
   gc_status st = GC_OK;
+  RelabelPlan R;
+  int32_t *d_eid = nullptr, *d_perm = nullptr, *d_newid = nullptr, *d_rp0 = nullptr, *d_ci0 = nullptr;
+  int32_t *d_lists = nullptr, *d_tmp = nullptr;
+  int64_t* d_loff = nullptr;
+  auto drop_temps = [&] {
+    for (void* p : {(void*)d_newid, (void*)d_rp0, (void*)d_ci0, (void*)d_lists, (void*)d_tmp, (void*)d_loff})
+      if (p) cudaFreeAsync(p, s);
+    d_newid = d_rp0 = d_ci0 = d_lists = d_tmp = nullptr;
+    d_loff = nullptr;
+  };
+  // On a failure the symmetry check is awaited first: an invalid input is
+  // reported as such even when a device step failed too (a machine without a
+  // GPU still gets the validation codes).
+  auto fail = [&](gc_status code) -> gc_status {
+    drop_temps();
+    if (d_eid) cudaFreeAsync(d_eid, s);
+    if (d_perm) cudaFreeAsync(d_perm, s);
+    graph_release(g);
+    if (sym.joinable()) sym.join();
+    if (sym_st != GC_OK) {
+      set_error(sym_msg);
+      return sym_st;
+    }
+    return code;
+  };
 #define GC_CHECK(call, what)            \
   do {                                  \
     e = (call);                         \
-    if (e != cudaSuccess) {             \
-      st = cuda_fail(e, what);          \
-      graph_release(g);                 \
-      return st;                        \
-    }                                   \
+    if (e != cudaSuccess) return fail(cuda_fail(e, what)); \
   } while (0)
-  Relabeled R;
   try {
-    R = relabel_by_degree(n, row_ptr, col_idx, rev.data());
+    R = plan_relabel(n, row_ptr);
   } catch (...) {
     set_error("host allocation failed");
-    graph_release(g);
-    return GC_ERR_NOMEM;
+    return fail(GC_ERR_NOMEM);
   }
-  rev.p.reset();
-  int32_t* d_eid = nullptr;
-  int32_t* d_perm = nullptr;
+  const size_t nnz1 = (size_t)(nnz > 0 ? nnz : 1), n1 = (size_t)(n > 0 ? n : 1);
+  const size_t n_lists = R.mid.size() + R.longr.size();
   GC_CHECK(cudaMalloc(&g->d_rp, sizeof(int32_t) * ((size_t)n + 1)), "alloc row_ptr");
-  GC_CHECK(cudaMalloc(&g->d_ci, sizeof(int32_t) * (size_t)(nnz > 0 ? nnz : 1)), "alloc col_idx");
-  GC_CHECK(cudaMallocAsync(&d_eid, sizeof(int32_t) * (size_t)(nnz > 0 ? nnz : 1), s), "alloc eid");
-  GC_CHECK(cudaMallocAsync(&d_perm, sizeof(int32_t) * (size_t)(n > 0 ? n : 1), s), "alloc perm");
-  GC_CHECK(cudaMemcpyAsync(g->d_rp, R.rp.data(), sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyHostToDevice, s),
+  GC_CHECK(cudaMalloc(&g->d_ci, sizeof(int32_t) * nnz1), "alloc col_idx");
+  GC_CHECK(cudaMallocAsync(&d_eid, sizeof(int32_t) * nnz1, s), "alloc eid");
+  GC_CHECK(cudaMallocAsync(&d_perm, sizeof(int32_t) * n1, s), "alloc perm");
+  GC_CHECK(cudaMallocAsync(&d_newid, sizeof(int32_t) * n1, s), "alloc newid");
+  GC_CHECK(cudaMallocAsync(&d_rp0, sizeof(int32_t) * ((size_t)n + 1), s), "alloc caller row_ptr");
+  GC_CHECK(cudaMallocAsync(&d_ci0, sizeof(int32_t) * nnz1, s), "alloc caller col_idx");
+  GC_CHECK(cudaMallocAsync(&d_lists, sizeof(int32_t) * (n_lists > 0 ? n_lists : 1), s), "alloc row lists");
+  GC_CHECK(cudaMallocAsync(&d_loff, sizeof(int64_t) * (R.long_off.size() > 0 ? R.long_off.size() : 1), s),
+           "alloc row lists");
+  GC_CHECK(cudaMallocAsync(&d_tmp, sizeof(int32_t) * (size_t)(R.tmp_len > 0 ? R.tmp_len : 1), s), "alloc sort buffer");
+  GC_CHECK(cudaMemcpyAsync(d_rp0, row_ptr, sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyHostToDevice, s),
            "copy row_ptr");
-  if (nnz > 0) {
-    GC_CHECK(cudaMemcpyAsync(g->d_ci, R.ci.data(), sizeof(int32_t) * (size_t)nnz, cudaMemcpyHostToDevice, s),
-             "copy col_idx");
-    GC_CHECK(cudaMemcpyAsync(d_eid, R.eid.data(), sizeof(int32_t) * (size_t)nnz, cudaMemcpyHostToDevice, s),
-             "copy edge ids");
+  if (nnz > 0)
+    GC_CHECK(cudaMemcpyAsync(d_ci0, col_idx, sizeof(int32_t) * (size_t)nnz, cudaMemcpyHostToDevice, s), "copy col_idx");
+  GC_CHECK(cudaMemcpyAsync(g->d_rp, R.rp.data(), sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyHostToDevice, s),
+           "copy internal row_ptr");
+  if (n > 0) {
+    GC_CHECK(cudaMemcpyAsync(d_perm, R.perm.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice, s), "copy perm");
+    GC_CHECK(cudaMemcpyAsync(d_newid, R.newid.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice, s),
+             "copy ranks");
   }
-  if (n > 0)
-    GC_CHECK(cudaMemcpyAsync(d_perm, R.perm.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice, s),
-             "copy perm");
+  if (!R.mid.empty())
+    GC_CHECK(cudaMemcpyAsync(d_lists, R.mid.data(), sizeof(int32_t) * R.mid.size(), cudaMemcpyHostToDevice, s),
+             "copy row lists");
+  if (!R.longr.empty()) {
+    GC_CHECK(cudaMemcpyAsync(d_lists + R.mid.size(), R.longr.data(), sizeof(int32_t) * R.longr.size(),
+                             cudaMemcpyHostToDevice, s), "copy row lists");
+    GC_CHECK(cudaMemcpyAsync(d_loff, R.long_off.data(), sizeof(int64_t) * R.long_off.size(), cudaMemcpyHostToDevice, s),
+             "copy row lists");
+  }
+  st = relabel_on_device(n, g->m, d_rp0, d_ci0, d_perm, d_newid, g->d_rp, g->d_ci, d_eid, d_lists,
+                         (int32_t)R.mid.size(), d_lists + R.mid.size(), d_loff, (int32_t)R.longr.size(), d_tmp, s);
+  drop_temps();
+  if (st != GC_OK) return fail(st);
   st = prepare_graph(n, g->m, g->d_rp, g->d_ci, nullptr, d_eid, d_perm, &g->prep, s);
+  d_eid = nullptr;  // owned by the preparation buffers from here on
+  if (st != GC_OK) return fail(st);
   cudaFreeAsync(d_perm, s);
-  if (st != GC_OK) { graph_release(g); return st; }
-  cudaStreamSynchronize(s);  // host copies of R are released on return
+  d_perm = nullptr;
+  cudaStreamSynchronize(s);  // the host arrays of the plan are released on return
+  if (sym.joinable()) sym.join();
+  if (sym_st != GC_OK) {
+    set_error(sym_msg);
+    graph_release(g);
+    return sym_st;
+  }
   // single-graph descriptor block: gbase | gn | gm (gm 8-byte aligned)
   GC_CHECK(cudaMalloc(&g->d_gbase, 32), "alloc descriptors");
   {
@@ -373,7 +394,7 @@ gc_status gc_graph_upload(int32_t n, const int32_t* row_ptr, const int32_t* col_
   g->d_x = g->d_csum + 13 * 2;
   {
     gc_status st2 = scratch_init(&g->sc, g->m, n, g->prep.kmax, g->prep.cnx_max, s);
-    if (st2 != GC_OK) { graph_release(g); return st2; }
+    if (st2 != GC_OK) return fail(st2);
   }
   for (auto& ev : g->ev) GC_CHECK(cudaEventCreate(&ev), "event create");
   GC_CHECK(cudaStreamSynchronize(s), "sync upload");

@@ -146,6 +146,16 @@ gc_status run_count(const DevGraph& g, const int32_t* units, int32_t n_units, co
 void set_error(const std::string& msg);
 gc_status cuda_fail(cudaError_t e, const char* what);
 
+// ---- relabelling P1 on the device (gc_relabel.cu) ----
+// Internal row i = caller row perm[i] in internal ids (newid), sorted; eid:
+// caller's edge id of every internal slot. rp: internal row pointers (device);
+// mid_rows / long_rows: internal rows of 33..4096 and of more entries; the
+// long rows are sorted in padded copies at tmp + long_off[k].
+gc_status relabel_on_device(int32_t n, int32_t m, const int32_t* d_rp0, const int32_t* d_ci0,
+                            const int32_t* d_perm, const int32_t* d_newid, const int32_t* d_rp, int32_t* d_ci,
+                            int32_t* d_eid, const int32_t* d_mid_rows, int32_t n_mid, const int32_t* d_long_rows,
+                            const int64_t* d_long_off, int32_t n_long, int32_t* d_tmp, cudaStream_t s);
+
 // ---- preprocessing (gc_prep.cu) ----
 struct PrepBuffers {
   int32_t* deg = nullptr;
