@@ -274,18 +274,11 @@ gc_status gc_graph_upload(int32_t n, const int32_t* row_ptr, const int32_t* col_
   }
   const int64_t nnz = row_ptr[n];
   if (nnz < 0 || nnz % 2) { set_error("row_ptr[n] must be even and >= 0"); return GC_ERR_ARG; }
-  // The symmetry check runs on its own host threads while the device
-  // relabels and prepares the graph: the device steps are safe on an
-  // asymmetric input (columns in range, rows sorted), and nothing is counted
-  // before the check has passed.
-  gc_status sym_st = GC_OK;
-  std::string sym_msg;
-  std::thread sym;
-  if (validate) sym = std::thread([&] { sym_st = csr_symmetry(n, row_ptr, col_idx, &sym_msg); });
-  struct Joiner {
-    std::thread* t;
-    ~Joiner() { if (t->joinable()) t->join(); }
-  } joiner{&sym};
+  // Symmetry is checked on the device, where the preparation finds the
+  // reverse of every slot: the device steps are safe on an asymmetric input
+  // (columns in range, rows sorted), and nothing is counted before the check
+  // has passed. If a device step fails, the host checks symmetry instead, so
+  // that an invalid input is reported as such (also where there is no GPU).
   gc_graph g = new (std::nothrow) gc_graph_s();
   if (!g) { set_error("host allocation failed"); return GC_ERR_NOMEM; }
   g->n = n;
@@ -308,15 +301,20 @@ gc_status gc_graph_upload(int32_t n, const int32_t* row_ptr, const int32_t* col_
   // reported as such even when a device step failed too (a machine without a
   // GPU still gets the validation codes).
   auto fail = [&](gc_status code) -> gc_status {
+    const std::string err = gc_last_error();
     drop_temps();
     if (d_eid) cudaFreeAsync(d_eid, s);
     if (d_perm) cudaFreeAsync(d_perm, s);
     graph_release(g);
-    if (sym.joinable()) sym.join();
-    if (sym_st != GC_OK) {
-      set_error(sym_msg);
-      return sym_st;
+    if (validate) {
+      std::string msg;
+      const gc_status sym_st = csr_symmetry(n, row_ptr, col_idx, &msg);
+      if (sym_st != GC_OK) {
+        set_error(msg);
+        return sym_st;
+      }
     }
+    set_error(err);
     return code;
   };
 #define GC_CHECK(call, what)            \
@@ -372,13 +370,19 @@ gc_status gc_graph_upload(int32_t n, const int32_t* row_ptr, const int32_t* col_
   if (st != GC_OK) return fail(st);
   cudaFreeAsync(d_perm, s);
   d_perm = nullptr;
-  cudaStreamSynchronize(s);  // the host arrays of the plan are released on return
-  if (sym.joinable()) sym.join();
-  if (sym_st != GC_OK) {
-    set_error(sym_msg);
-    graph_release(g);
-    return sym_st;
+  if (validate) {
+    int32_t bad = -1;
+    if ((st = first_unreversed_slot(nnz, g->prep.rev, &bad, s)) != GC_OK) return fail(st);
+    if (bad >= 0) {  // name the edge in the caller's labels
+      int32_t y = 0;
+      GC_CHECK(cudaMemcpy(&y, g->d_ci + bad, sizeof(int32_t), cudaMemcpyDeviceToHost), "copy slot");
+      const int32_t x = (int32_t)(std::upper_bound(R.rp.data(), R.rp.data() + n + 1, bad) - R.rp.data()) - 1;
+      set_error("edge (" + std::to_string(R.perm[x]) + "," + std::to_string(R.perm[y]) + ") has no reverse");
+      graph_release(g);
+      return GC_ERR_ASYMMETRIC;
+    }
   }
+  cudaStreamSynchronize(s);  // the host arrays of the plan are released on return
   // single-graph descriptor block: gbase | gn | gm (gm 8-byte aligned)
   GC_CHECK(cudaMalloc(&g->d_gbase, 32), "alloc descriptors");
   {

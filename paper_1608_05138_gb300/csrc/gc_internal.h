@@ -190,6 +190,9 @@ gc_status prepare_graph(int32_t n, int32_t m, const int32_t* d_rp, const int32_t
 gc_status classify_c_units(int32_t n, const int32_t* d_rp, const int32_t* d_ci, bool ranked, PrepBuffers* p,
                            cudaStream_t stream);
 void free_prep(PrepBuffers* p, cudaStream_t s);
+// Smallest slot p with rev[p] == p (no reverse: the input is not symmetric),
+// or -1 (synchronises the stream).
+gc_status first_unreversed_slot(int64_t nnz, const int32_t* d_rev, int32_t* out, cudaStream_t s);
 
 // ---- small graphs on a shared-memory bitmatrix (gc_small.cu) ----
 // rp/voff: concatenated local row pointers and their offsets ([G'+1] for the

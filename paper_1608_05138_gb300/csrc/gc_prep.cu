@@ -227,6 +227,16 @@ __global__ void k_cwork(int32_t n_units, const int32_t* __restrict__ units, cons
   }
 }
 
+// Smallest slot whose reverse was not found (rev[p] == p): the input is not
+// symmetric exactly when there is one.
+__global__ void k_first_unreversed(int64_t nnz, const int32_t* __restrict__ rev, int32_t* __restrict__ first) {
+  int32_t best = 0x7fffffff;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nnz; p += (int64_t)gridDim.x * blockDim.x)
+    if (rev[p] == (int32_t)p) best = min(best, (int32_t)p);
+  for (int o = 16; o; o >>= 1) best = min(best, __shfl_xor_sync(0xffffffffu, best, o));
+  if ((threadIdx.x & 31) == 0 && best != 0x7fffffff) atomicMin(first, best);
+}
+
 // ---- exclusive scan of int32 (totals fit int32) ----
 __global__ void k_scan_tile_sums(int32_t n, const int32_t* __restrict__ in, int32_t* __restrict__ sums) {
   __shared__ int32_t ws[8];
@@ -411,6 +421,26 @@ gc_status classify_c_units(int32_t n, const int32_t* d_rp, const int32_t* d_ci, 
   e = cudaMemcpyAsync(p->cunits, out.data(), sizeof(int32_t) * nu, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   return e == cudaSuccess ? GC_OK : cuda_fail(e, "copy cunits");
+}
+
+gc_status first_unreversed_slot(int64_t nnz, const int32_t* d_rev, int32_t* out, cudaStream_t s) {
+  *out = -1;
+  if (nnz <= 0) return GC_OK;
+  int32_t* d = nullptr;
+  cudaError_t e = cudaMallocAsync(&d, sizeof(int32_t), s);
+  const int32_t init = 0x7fffffff;
+  int32_t h = init;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d, &init, sizeof(int32_t), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) {
+    k_first_unreversed<<<grid_for(nnz, 256) > 4096 ? 4096 : grid_for(nnz, 256), 256, 0, s>>>(nnz, d_rev, d);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (d) cudaFreeAsync(d, s);
+  if (e != cudaSuccess) return cuda_fail(e, "symmetry check");
+  *out = h == init ? -1 : h;
+  return GC_OK;
 }
 
 void free_prep(PrepBuffers* p, cudaStream_t s) {

@@ -80,6 +80,36 @@ def test_degenerate_graphs():
     assert_parity(*graphs.csr(40, [(0, 1), (1, 2), (0, 2), (30, 31)]))
 
 
+def test_asymmetric_input_rejected():
+    # symmetry is checked on the device from the reverse slots of the
+    # preparation; nothing is counted for an asymmetric input
+    def status(rp, ci):
+        with pytest.raises(gcb.GcError) as ei:
+            gcb.Graph(np.asarray(rp, np.int32), np.asarray(ci, np.int32))
+        return ei.value.status, str(ei.value)
+    st, msg = status([0, 2, 4, 5, 6], [1, 2, 0, 2, 3, 0])  # (0,2), (1,2), (2,3), (3,0) have no reverse
+    assert st == -5 and "no reverse" in msg
+    rp, ci = graphgen.chung_lu(5000, 40000, 2.1, 80000.0, 900.0, 9)
+    E = graphs.edges_of(rp, ci)
+    arcs = [(a, b) for a, b in E] + [(b, a) for a, b in E]
+    a, b = E[len(E) // 2]
+    arcs.remove((b, a))            # one direction dropped ...
+    nbr_a = set(int(x) for x in ci[rp[a]:rp[a + 1]])
+    c = next(x for x in range(len(rp) - 1) if x not in (a, b) and x not in nbr_a)
+    arcs.append((min(a, c), max(a, c)))  # ... and one arc added, so the entry count stays even
+    n = len(rp) - 1
+    order = sorted(arcs)
+    rp2 = np.zeros(n + 1, np.int64)
+    for x, _ in order:
+        rp2[x + 1] += 1
+    rp2 = np.cumsum(rp2).astype(np.int32)
+    ci2 = np.array([y for _, y in order], np.int32)
+    st, msg = status(rp2, ci2)
+    assert st == -5
+    # the graph handle of a valid graph still works after rejected uploads
+    assert_parity(rp, ci)
+
+
 def test_wide_counts_need_high_words():
     n = 200000  # C(n, 4) > 2^64
     rp, ci = graphs.csr(n, [(0, 1), (1, 2)])
