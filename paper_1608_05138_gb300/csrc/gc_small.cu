@@ -9,8 +9,9 @@
 //   S_u = row(u) & ~row(v) without v            S_v = row(v) & ~row(u) without u
 //   x7  = (1/2) sum_{a in T}   popc(row(a) & T)     (pairs of T counted twice)
 //   x10 =       sum_{w in S_u} popc(row(w) & S_v)   (Alg. 6 with the S_v test)
-// One lane holds one 32-bit word of each mask (16 words for 512 vertices), so
-// an edge costs about (|T| + |S_u|) broadcast-and-popcount steps for the warp.
+// One lane holds one 32-bit word of each mask (16 words for 512 vertices);
+// the members of T and S_u are listed and dealt to the lanes as (member, word)
+// pairs, so an edge costs about (|T| + |S_u|) * W / 32 steps for the warp.
 // One CTA per graph (work stealing over the graphs, largest first); per-edge
 // terms go into the 13 unrestricted sums of the graph in 128 bits.
 #include <cuda_runtime.h>
@@ -52,23 +53,34 @@ __device__ __forceinline__ uint64_t small_column(int k, int64_t t, int64_t su, i
   }
 }
 
-// sum over the members b of `mask` (one word per lane, words >= W are 0) of
-// popc(row(b) & other), for the whole warp
+// sum over the members b of `mask` (word w in lane w, words >= W are 0) of
+// popc(row(b) & other), for the whole warp. The members are listed in `list`
+// (the warp's shared buffer), then each lane takes one (member, word) pair:
+// Wp = the power of two >= W lanes per member, 32 / Wp members per step, so
+// that every lane has a word to AND whatever the graph's size.
 __device__ __forceinline__ long long masked_row_popc(const uint32_t* __restrict__ bm, uint32_t mask,
-                                                     uint32_t other, int lane, int W) {
-  long long acc = 0;
-  unsigned lanes = __ballot_sync(0xffffffffu, mask != 0u);
-  while (lanes) {
-    const int l = __ffs(lanes) - 1;
-    lanes &= lanes - 1;
-    uint32_t word = __shfl_sync(0xffffffffu, mask, l);
-    while (word) {
-      const int b = __ffs(word) - 1;
-      word &= word - 1;
-      const int32_t vert = l * 32 + b;
-      if (lane < W) acc += __popc(bm[vert * kSmallWords + lane] & other);
-    }
+                                                     uint32_t other, int lane, int Wp, int16_t* list) {
+  const int c = __popc(mask);
+  int incl = c;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
   }
+  const int total = __shfl_sync(0xffffffffu, incl, 31);
+  int pos = incl - c;
+  uint32_t word = mask;
+  while (word) {
+    const int b = __ffs(word) - 1;
+    word &= word - 1;
+    list[pos++] = (int16_t)(lane * 32 + b);
+  }
+  __syncwarp();
+  const int w = lane & (Wp - 1);
+  const uint32_t ow = __shfl_sync(0xffffffffu, other, w);  // word w of the other mask
+  const int per = 32 / Wp;
+  long long acc = 0;
+  for (int i = lane / Wp; i < total; i += per) acc += __popc(bm[list[i] * kSmallWords + w] & ow);
+  __syncwarp();
   return acc;
 }
 
@@ -80,6 +92,7 @@ __global__ void __launch_bounds__(kSmallBlock) k_small_graphs(const int32_t* __r
                                                               int32_t* __restrict__ cursor,
                                                               unsigned long long* __restrict__ csum) {
   __shared__ uint32_t bm[kSmallN * kSmallWords];
+  __shared__ int16_t s_list[kSmallWarps][kSmallN];  // members of a mask, per warp
   __shared__ int32_t s_g;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (;;) {
@@ -93,6 +106,8 @@ __global__ void __launch_bounds__(kSmallBlock) k_small_graphs(const int32_t* __r
     const int32_t n = (int32_t)(voff[g + 1] - voff[g]) - 1;
     const int64_t m = (eoff[g + 1] - eoff[g]) / 2;
     const int W = (n + 31) / 32;
+    int Wp = 1;
+    while (Wp < W) Wp <<= 1;
     for (int32_t i = threadIdx.x; i < n * kSmallWords; i += kSmallBlock) bm[i] = 0u;
     __syncthreads();
     for (int32_t x = warp; x < n; x += kSmallWarps)
@@ -119,8 +134,8 @@ __global__ void __launch_bounds__(kSmallBlock) k_small_graphs(const int32_t* __r
           su += __shfl_xor_sync(0xffffffffu, su, o);
           sv += __shfl_xor_sync(0xffffffffu, sv, o);
         }
-        long long x7 = masked_row_popc(bm, T, T, lane, W);
-        long long x10 = masked_row_popc(bm, Su, Sv, lane, W);
+        long long x7 = masked_row_popc(bm, T, T, lane, Wp, s_list[warp]);
+        long long x10 = masked_row_popc(bm, Su, Sv, lane, Wp, s_list[warp]);
         for (int o = 16; o; o >>= 1) {
           x7 += __shfl_xor_sync(0xffffffffu, x7, o);
           x10 += __shfl_xor_sync(0xffffffffu, x10, o);
