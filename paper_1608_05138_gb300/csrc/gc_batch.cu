@@ -26,6 +26,8 @@
 #include <thread>
 #include <unordered_map>
 #include <unordered_set>
+#include <memory>
+#include <thread>
 #include <vector>
 
 #include "gc_internal.h"
@@ -239,11 +241,32 @@ gc_status run_small(std::vector<PendingGraph*>& graphs, cudaStream_t s, Launch* 
     h_order[gi] = gi;
   }
   std::sort(h_order.begin(), h_order.end(), [&](int32_t a, int32_t b) { return h_gm[a] > h_gm[b]; });
-  std::vector<int32_t> h_rp((size_t)h_voff[G] + 1), h_ci((size_t)(h_eoff[G] > 0 ? h_eoff[G] : 1));
-  for (int32_t gi = 0; gi < G; ++gi) {
-    std::memcpy(h_rp.data() + h_voff[gi], graphs[gi]->rp.data(), sizeof(int32_t) * (graphs[gi]->n + 1));
-    if (graphs[gi]->m > 0)
-      std::memcpy(h_ci.data() + h_eoff[gi], graphs[gi]->ci.data(), sizeof(int32_t) * 2 * graphs[gi]->m);
+  // packed on all host cores into buffers that are not zeroed first (every
+  // entry is copied over)
+  struct Packed {
+    std::unique_ptr<int32_t[]> p;
+    size_t n;
+    int32_t* data() { return p.get(); }
+    size_t size() const { return n; }
+  } h_rp{std::unique_ptr<int32_t[]>(new int32_t[(size_t)h_voff[G] + 1]), (size_t)h_voff[G] + 1},
+    h_ci{std::unique_ptr<int32_t[]>(new int32_t[(size_t)(h_eoff[G] > 0 ? h_eoff[G] : 1)]),
+         (size_t)(h_eoff[G] > 0 ? h_eoff[G] : 1)};
+  {
+    const unsigned hw = std::thread::hardware_concurrency();
+    const int nt = h_eoff[G] < (1 << 22) ? 1 : (int)std::min<unsigned>(hw ? hw : 1, 32);
+    auto pack = [&](int t) {  // the graphs whose entries start in this thread's share
+      const int64_t e0 = h_eoff[G] * t / nt, e1 = h_eoff[G] * (t + 1) / nt;
+      int32_t gi = (int32_t)(std::lower_bound(h_eoff.begin(), h_eoff.begin() + G, e0) - h_eoff.begin());
+      for (; gi < G && (h_eoff[gi] < e1 || t == nt - 1); ++gi) {
+        std::memcpy(h_rp.data() + h_voff[gi], graphs[gi]->rp.data(), sizeof(int32_t) * (graphs[gi]->n + 1));
+        if (graphs[gi]->m > 0)
+          std::memcpy(h_ci.data() + h_eoff[gi], graphs[gi]->ci.data(), sizeof(int32_t) * 2 * graphs[gi]->m);
+      }
+    };
+    std::vector<std::thread> th;
+    for (int t = 1; t < nt; ++t) th.emplace_back(pack, t);
+    pack(0);
+    for (auto& x : th) x.join();
   }
   int32_t *d_rp = nullptr, *d_ci = nullptr, *d_gn = nullptr, *d_order = nullptr, *d_misc = nullptr;
   int64_t *d_voff = nullptr, *d_eoff = nullptr, *d_gm = nullptr;
