@@ -491,6 +491,7 @@ gc_status gc_count_edge_graphlets(gc_graph g, uint64_t* per_edge_out, uint64_t* 
              "copy per-edge");
   GC_CHECK(cudaEventRecord(g->ev[kNumPhases], s), "event");
   GC_CHECK(cudaStreamSynchronize(s), "sync count");
+  g->sc.tlist_want = (long long)g->work[kWorkTTriangles];  // the next count keeps pass T's edge lists
 #undef GC_CHECK
   if (hstatus & kSpillOverflow) {
     set_error("internal: a pass-K unit exceeded its tier");

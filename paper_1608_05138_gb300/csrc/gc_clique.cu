@@ -95,7 +95,8 @@ template <int kCap, int kThreads, bool kTri>
 __global__ void __launch_bounds__(kThreads, 65536 / (kThreads * 64)) k_pass_k(DevGraph g, CountArgs a, int tier) {
   constexpr int kW = kThreads / 32;
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ int32_t s_unit, s_cur1, s_cur2, s_nhit;
+  __shared__ int32_t s_unit, s_cur1, s_cur2, s_nhit, s_lcnt;
+  __shared__ long long s_loff;
   __shared__ int32_t s_qj[kW][64], s_qq[kW][64];
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -113,8 +114,9 @@ __global__ void __launch_bounds__(kThreads, 65536 / (kThreads * 64)) k_pass_k(De
   uint32_t* rows = reinterpret_cast<uint32_t*>(base + L.rows);
   int32_t* qj = s_qj[warp];
   int32_t* qq = s_qq[warp];
-  // phase-1 hits of pass K (i, j, out-slot), so that phase 2 needs no rescan
-  int32_t* hits = kTri ? nullptr : a.hitbuf + (size_t)blockIdx.x * 2 * (size_t)a.hitcap;
+  // phase-1 hits (i, j, out-slot): pass K's phase 2 needs no rescan, and
+  // pass T hands them on to pass K
+  int32_t* hits = (kTri && !a.tlist) ? nullptr : a.hitbuf + (size_t)blockIdx.x * 2 * (size_t)a.hitcap;
 
   const int32_t u0 = a.ktier_off[tier], u1 = a.ktier_off[tier + 1];
   int32_t* cursor = a.cursor + (kTri ? 10 : 2) + tier;
@@ -154,12 +156,59 @@ __global__ void __launch_bounds__(kThreads, 65536 / (kThreads * 64)) k_pass_k(De
         vcrh[i] = 0u;
       }
     }
-    for (int32_t i = threadIdx.x; i <= (int32_t)hmask; i += kThreads) hash[i] = 0;
-    for (int32_t i = threadIdx.x; i < (1 << fbits) / 32; i += kThreads) filt[i] = 0u;
+    // pass K with the edges of H_a kept by pass T: no hash, no scan
+    const int32_t lcnt = (!kTri && a.tlist) ? a.tl_cnt[ui] : -1;
+    if (lcnt < 0) {
+      for (int32_t i = threadIdx.x; i <= (int32_t)hmask; i += kThreads) hash[i] = 0;
+      for (int32_t i = threadIdx.x; i < (1 << fbits) / 32; i += kThreads) filt[i] = 0u;
+    }
     if (!kTri)
       for (int32_t i = threadIdx.x; i < k * S; i += kThreads) rows[i] = 0u;
     if (threadIdx.x == 0) w_members += k;
     __syncthreads();
+    if (lcnt >= 0) {
+      const int2* lst = a.tlist + a.tl_off[ui];
+      for (int32_t e = threadIdx.x; e < lcnt; e += kThreads) {
+        const int32_t ij = lst[e].x;
+        const int32_t i = (int32_t)((uint32_t)ij >> 16), j = ij & 0xffff;
+        atomicOr(&rows[i * S + (j >> 5)], 1u << (j & 31));
+        atomicOr(&rows[j * S + (i >> 5)], 1u << (i & 31));
+      }
+      __syncthreads();
+      for (int32_t e0 = warp * 32; e0 < lcnt; e0 += kThreads) {
+        const int32_t e = e0 + lane;
+        if (e < lcnt) {
+          const int2 en = lst[e];
+          const int32_t i = (int32_t)((uint32_t)en.x >> 16), j = en.x & 0xffff, q = en.y;
+          const uint32_t* ri = rows + i * S;
+          const uint32_t* rj = rows + j * S;
+          int c4 = 0;
+          for (int w = 0; w < W; ++w) c4 += __popc(ri[w] & rj[w]);
+          const int32_t ti = ta[i], tj = ta[j];
+          const int32_t tij = a.trio[q];
+          if (c4) {
+            atomicAdd(&a.xc[2 * (size_t)q], (unsigned long long)c4);
+            add_split(vx7, vx7h, i, (unsigned long long)c4);
+            add_split(vx7, vx7h, j, (unsigned long long)c4);
+          }
+          atomicAdd(&a.xc[2 * (size_t)q + 1], (unsigned long long)(ti + tj - 2));
+          add_split(vcr, vcrh, i, (unsigned long long)(tj + tij - 2));
+          add_split(vcr, vcrh, j, (unsigned long long)(ti + tij - 2));
+        }
+        if (lane == 0) {
+          const int32_t cnt = min(32, lcnt - e0);
+          w_edges += cnt;
+          w_words += (long long)cnt * W;
+        }
+      }
+      __syncthreads();
+      for (int32_t i = threadIdx.x; i < k; i += kThreads) {
+        const unsigned long long x = read_split(vx7, vx7h, i), c = read_split(vcr, vcrh, i);
+        if (x) atomicAdd(&a.xc[2 * (size_t)(ob + i)], x >> 1);
+        if (c) atomicAdd(&a.xc[2 * (size_t)(ob + i) + 1], c);
+      }
+      continue;
+    }
     for (int32_t i = threadIdx.x; i < k; i += kThreads) {  // Psi: id -> 1 + position in out(a)
       uint32_t h = khash(ids[i], hbits);
       while (atomicCAS(&hash[h], 0, i + 1) != 0) h = (h + 1) & hmask;  // table at most half full
@@ -215,6 +264,16 @@ __global__ void __launch_bounds__(kThreads, 65536 / (kThreads * 64)) k_pass_k(De
               atomicAdd(&vx7[i], (uint32_t)__popc(hit));  // edge (a, b_i)
               w_edges += __popc(hit);
             }
+            if (hits && hit) {  // recorded for pass K
+              int32_t base_h = 0;
+              if (lane == 0) base_h = atomicAdd(&s_nhit, __popc(hit));
+              base_h = __shfl_sync(kFull, base_h, 0);
+              const int32_t slot = base_h + __popc(hit & ((1u << lane) - 1u));
+              if (j >= 0 && slot < a.hitcap) {
+                hits[2 * (size_t)slot] = (int32_t)(((uint32_t)i << 16) | (uint32_t)j);
+                hits[2 * (size_t)slot + 1] = q;
+              }
+            }
           } else if (hit) {
             int32_t base_h = 0;
             if (lane == 0) base_h = atomicAdd(&s_nhit, __popc(hit));
@@ -237,6 +296,24 @@ __global__ void __launch_bounds__(kThreads, 65536 / (kThreads * 64)) k_pass_k(De
     if (kTri) {
       for (int32_t i = threadIdx.x; i < k; i += kThreads)
         if (vx7[i]) atomicAdd(&a.trio[ob + i], (int32_t)vx7[i]);
+      if (a.tlist) {  // hand the edges of H_a on to pass K, if they fit
+        const int32_t nh = s_nhit;
+        if (threadIdx.x == 0) {
+          long long off = -1;
+          if (nh <= a.hitcap && k <= 65535) {
+            const unsigned long long o = atomicAdd(a.tlist_fill, (unsigned long long)nh);
+            if ((long long)o + nh <= a.tlist_cap) off = (long long)o;
+          }
+          s_loff = off;
+          a.tl_off[ui] = off < 0 ? 0 : off;
+          a.tl_cnt[ui] = off < 0 ? -1 : nh;
+        }
+        __syncthreads();
+        const long long off = s_loff;
+        if (off >= 0)
+          for (int32_t e = threadIdx.x; e < nh; e += kThreads)
+            a.tlist[off + e] = make_int2(hits[2 * (size_t)e], hits[2 * (size_t)e + 1]);
+      }
       continue;
     }
     const int32_t nhit = s_nhit;
@@ -378,6 +455,7 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long x)
 template <bool kTri>
 __global__ void __launch_bounds__(kWBlock) k_pass_k_warp(DevGraph g, CountArgs a, int tier) {
   __shared__ int32_t s_q[kWWarps][32 * 32];  // out-slot of edge (i, j) found from member i
+  __shared__ uint32_t s_rowf[kWWarps][64];    // rows and found masks rebuilt from pass T's list
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int32_t* qs = s_q[warp];
   const int32_t u0 = a.ktier_off[tier], u1 = a.ktier_off[tier + 1];
@@ -399,6 +477,26 @@ __global__ void __launch_bounds__(kWBlock) k_pass_k_warp(DevGraph g, CountArgs a
     const int32_t ti = (!kTri && lane < k) ? a.trio[ob + lane] : 0;
     const int32_t cmax = __shfl_sync(kFull, id, k - 1);
     unsigned row = 0u, found = 0u;
+    const int32_t lcnt = (!kTri && a.tlist) ? a.tl_cnt[ui] : -1;
+    if (lcnt >= 0) {  // pass K with the edges of H_a kept by pass T
+      uint32_t* rw = s_rowf[warp];
+      rw[lane] = 0u;
+      rw[32 + lane] = 0u;
+      __syncwarp();
+      const int2* lst = a.tlist + a.tl_off[ui];
+      for (int32_t e = lane; e < lcnt; e += 32) {
+        const int2 en = lst[e];
+        const int32_t i = (int32_t)((uint32_t)en.x >> 16), j = en.x & 0xffff;
+        atomicOr(&rw[i], 1u << j);
+        atomicOr(&rw[j], 1u << i);
+        atomicOr(&rw[32 + i], 1u << j);
+        qs[i * 32 + j] = en.y;
+      }
+      __syncwarp();
+      row = rw[lane];
+      found = rw[32 + lane];
+      if (lane == 0) w_edges += lcnt;
+    } else {
     // Phase 1: the edges of H_a.
     for (int i = 0; i < k; ++i) {
       const int32_t b = __shfl_sync(kFull, id, i);
@@ -423,9 +521,8 @@ __global__ void __launch_bounds__(kWBlock) k_pass_k_warp(DevGraph g, CountArgs a
             if (__shfl_sync(kFull, id, lo + step) <= c) lo += step;
           const int32_t id_lo = __shfl_sync(kFull, id, lo);  // every lane takes part in the shuffle
           const bool hit = c <= cmax && id_lo == c && lo < k;  // lanes >= k hold padding ids
-          if (kTri) {
-            if (hit) atomicAdd(&a.trio[q], 1);  // edge (b_i, c)
-          } else if (hit) {
+          if (hit) {
+            if (kTri) atomicAdd(&a.trio[q], 1);  // edge (b_i, c)
             qs[i * 32 + lo] = q;
           }
           hits |= __reduce_or_sync(kFull, hit ? 1u << lo : 0u);
@@ -439,9 +536,37 @@ __global__ void __launch_bounds__(kWBlock) k_pass_k_warp(DevGraph g, CountArgs a
       if ((hits >> lane) & 1u) row |= 1u << i;
       if (lane == 0) w_edges += __popc(hits);
     }
+    }  // scan
     if (kTri) {  // edge (a, b_lane): one triangle per edge of H_a at lane
       if (lane < k && row) atomicAdd(&a.trio[ob + lane], __popc(row));
       if (lane == 0) w_members += k;
+      if (a.tlist) {  // hand the edges of H_a on to pass K
+        const int c = __popc(found);
+        int incl = c;
+        for (int o = 1; o < 32; o <<= 1) {
+          const int y = __shfl_up_sync(kFull, incl, o);
+          if (lane >= o) incl += y;
+        }
+        const int total = __shfl_sync(kFull, incl, 31);
+        long long off = -1;
+        if (lane == 0) {
+          const unsigned long long o = atomicAdd(a.tlist_fill, (unsigned long long)total);
+          if ((long long)o + total <= a.tlist_cap) off = (long long)o;
+          a.tl_off[ui] = off < 0 ? 0 : off;
+          a.tl_cnt[ui] = off < 0 ? -1 : total;
+        }
+        off = __shfl_sync(kFull, off, 0);
+        if (off >= 0) {
+          long long pos = off + (incl - c);
+          unsigned f = found;
+          while (f) {
+            const int j = __ffs(f) - 1;
+            f &= f - 1;
+            a.tlist[pos++] = make_int2((int32_t)(((uint32_t)lane << 16) | (uint32_t)j), qs[lane * 32 + j]);
+          }
+        }
+        __syncwarp();
+      }
       continue;
     }
     __syncwarp();
@@ -505,7 +630,7 @@ gc_status launch_tier(const DevGraph& g, const CountArgs& a, int tier, cudaStrea
   } else {
     grid = a.kbuf_ctas;
   }
-  if (!kTri && grid > a.hitbuf_ctas) grid = a.hitbuf_ctas;  // one hit buffer per CTA
+  if (grid > a.hitbuf_ctas) grid = a.hitbuf_ctas;  // one hit buffer per CTA
   if (grid > units) grid = units;
   if (grid < 1) return GC_OK;
   kern<<<grid, kThreads, smem, s>>>(g, a, tier);

@@ -66,9 +66,17 @@ struct CountArgs {
   size_t kbuf_stride;
   int32_t kbuf_ctas;
   int32_t kbuf_cap;        // largest k the global tier holds
-  int32_t* hitbuf;         // pass K: per-CTA lists of the edges of H_a (hitbuf_ctas x hitcap x 2 ints)
+  int32_t* hitbuf;         // passes T/K: per-CTA lists of the edges of H_a (hitbuf_ctas x hitcap x 2 ints)
   int32_t hitcap;
   int32_t hitbuf_ctas;
+  // Edges of every H_a, recorded by pass T for pass K (nullptr: not kept):
+  // entry = ((i << 16) | j, out-slot of (b_i, b_j)); unit ui (index into
+  // kunits) has tl_cnt[ui] entries from tl_off[ui], or tl_cnt[ui] = -1.
+  int2* tlist;
+  long long tlist_cap;
+  unsigned long long* tlist_fill;
+  long long* tl_off;
+  int32_t* tl_cnt;
   uint64_t* per_edge;      // [m][13] device pointer or nullptr
   unsigned long long* csum;  // [G][13][2] 128-bit unrestricted counts (lo, hi)
   int32_t* status;         // device status word (0 = ok)
@@ -119,9 +127,16 @@ struct Scratch {
   size_t kbuf_stride = 0;
   int32_t kbuf_ctas = 0;
   int32_t kbuf_cap = 0;
-  int32_t* hitbuf = nullptr;         // pass K edge lists
+  int32_t* hitbuf = nullptr;         // per-CTA H_a edge lists
   int32_t hitcap = 0;
   int32_t hitbuf_ctas = 0;
+  int2* tlist = nullptr;             // edges of all H_a, from pass T to pass K
+  long long tlist_cap = 0;           // entries
+  long long tlist_want = 0;          // triangles of the last count: the size to keep
+  long long* tl_off = nullptr;       // [units of pass K]
+  int32_t* tl_cnt = nullptr;
+  int32_t tl_units = 0;
+  unsigned long long* tl_fill = nullptr;
   unsigned long long* work = nullptr;  // [kNumWork]
   int32_t launches = 0;              // kernels launched by the last run_count
 };

@@ -20,6 +20,8 @@ namespace gc {
 namespace {
 // Total bytes the pass-K global tier may hold at once.
 constexpr size_t kKbufBudget = size_t(2) << 30;
+// Largest list of the edges of all H_a that pass T keeps for pass K.
+constexpr long long kTListBudget = 24LL << 30;
 // Largest per-CTA list of H_a edges in pass K (units with more edges rescan
 // their out-lists instead): 2^19 entries, or the environment's GC_K_LIST_CAP
 // (1 .. 2^19), read once per process.
@@ -35,7 +37,8 @@ long long k_list_cap() {
 
 void scratch_free(Scratch* sc, cudaStream_t s) {
   for (void* p : {(void*)sc->trio, (void*)sc->P, (void*)sc->xc, (void*)sc->misc,
-                  (void*)sc->cbuf, (void*)sc->tables, (void*)sc->kbuf, (void*)sc->hitbuf, (void*)sc->work})
+                  (void*)sc->cbuf, (void*)sc->tables, (void*)sc->kbuf, (void*)sc->hitbuf, (void*)sc->work,
+                  (void*)sc->tlist, (void*)sc->tl_off, (void*)sc->tl_cnt, (void*)sc->tl_fill})
     if (p) cudaFreeAsync(p, s);
   *sc = Scratch();
 }
@@ -66,7 +69,7 @@ gc_status scratch_init(Scratch* sc, int32_t m, int32_t table_n, int32_t kmax, in
     const long long full = (long long)kmax * (kmax - 1) / 2;
     const long long cap = k_list_cap();
     sc->hitcap = (int32_t)(full < cap ? (full > 0 ? full : 1) : cap);
-    sc->hitbuf_ctas = count_grid_size();
+    sc->hitbuf_ctas = 4 * (count_grid_size() / kCtasPerSm);  // up to four CTAs per SM in any tier
     GS_TRY(cudaMallocAsync(&sc->hitbuf, sizeof(int32_t) * 2 * (size_t)sc->hitcap * (size_t)sc->hitbuf_ctas, s));
   }
   if (kmax > kTierCap[kTier1024]) {
@@ -82,6 +85,8 @@ gc_status scratch_init(Scratch* sc, int32_t m, int32_t table_n, int32_t kmax, in
 #undef GS_TRY
   return GC_OK;
 }
+
+static int32_t ku_total(const KUnits& ku) { return ku.tier_off[kNumTiers]; }
 
 gc_status run_count(const DevGraph& g, const int32_t* units, int32_t n_units, const KUnits& ku,
                     uint64_t* per_edge, unsigned long long* csum, unsigned long long* x, Scratch* sc,
@@ -117,6 +122,36 @@ gc_status run_count(const DevGraph& g, const int32_t* units, int32_t n_units, co
   a.hitbuf = sc->hitbuf;
   a.hitcap = sc->hitcap;
   a.hitbuf_ctas = sc->hitbuf_ctas;
+  // Pass T keeps the edges of the H_a for pass K when the triangles of the
+  // previous count (of this scratch) fit the budget; the first count scans twice.
+  {
+    const int32_t nku = ku_total(ku);
+    const long long want = sc->tlist_want;
+    if (want > 0 && want * (long long)sizeof(int2) <= kTListBudget && nku > 0) {
+      if (want > sc->tlist_cap) {
+        if (sc->tlist) cudaFreeAsync(sc->tlist, s);
+        sc->tlist = nullptr;
+        sc->tlist_cap = 0;
+        const long long cap = want + want / 16 + 1024;
+        if (cudaMallocAsync(&sc->tlist, sizeof(int2) * (size_t)cap, s) == cudaSuccess) sc->tlist_cap = cap;
+        else cudaGetLastError();  // no list: pass K scans
+      }
+      if (nku > sc->tl_units) {
+        for (void* p : {(void*)sc->tl_off, (void*)sc->tl_cnt})
+          if (p) cudaFreeAsync(p, s);
+        GR_TRY(cudaMallocAsync(&sc->tl_off, sizeof(long long) * (size_t)nku, s), "alloc list index");
+        GR_TRY(cudaMallocAsync(&sc->tl_cnt, sizeof(int32_t) * (size_t)nku, s), "alloc list index");
+        sc->tl_units = nku;
+      }
+      if (!sc->tl_fill) GR_TRY(cudaMallocAsync(&sc->tl_fill, sizeof(unsigned long long), s), "alloc list fill");
+    }
+  }
+  a.tlist = sc->tlist_cap > 0 ? sc->tlist : nullptr;
+  a.tlist_cap = sc->tlist_cap;
+  a.tlist_fill = sc->tl_fill;
+  a.tl_off = sc->tl_off;
+  a.tl_cnt = sc->tl_cnt;
+  if (a.tlist) GR_TRY(cudaMemsetAsync(sc->tl_fill, 0, sizeof(unsigned long long), s), "zero list fill");
   a.per_edge = per_edge;
   a.csum = csum;
   a.work = sc->work;

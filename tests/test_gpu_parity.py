@@ -177,6 +177,30 @@ def test_relabelling_is_metamorphic():
         np.testing.assert_array_equal(pe1[i], pe2[j])
 
 
+def test_repeated_count_reuses_the_triangle_lists():
+    # from the second count on a handle, pass T keeps the edges of every H_a
+    # and pass K rebuilds its bitmatrices from them instead of scanning; both
+    # counts must equal the oracle, in every tier (k <= 32 warp tier, 256, 512,
+    # 1024 and the global tier above 1024)
+    for rp, ci in (graphgen.chung_lu(3000, 15000, 2.1, 30000.0, 800.0, 5), graphgen.rmat(12, 16, 0.57, 0.19, 0.19, 6),
+                   graphgen.config_er_dense()):
+        o = oracle.count(rp, ci)
+        with gcb.Graph(rp, ci) as g:
+            for _ in range(3):
+                pe = np.zeros((g.m, 13), np.uint64)
+                assert g.count(pe) == o["X"]
+                np.testing.assert_array_equal(pe, o["per_edge"])
+            assert g.work_counts()["t_triangles"] == g.work_counts()["k_local_edges"]
+    rp, ci = graphgen.er(1200, 0.92, 41)  # out-degrees up to ~1100
+    with gcb.Graph(rp, ci) as g:
+        pe1 = np.zeros((g.m, 13), np.uint64)
+        X1 = g.count(pe1)
+        pe2 = np.zeros((g.m, 13), np.uint64)
+        X2 = g.count(pe2)
+    assert X1 == X2
+    np.testing.assert_array_equal(pe1, pe2)
+
+
 def test_device_output_and_repeat():
     import torch
     rp, ci = graphgen.rmat(12, 16, 0.57, 0.19, 0.19, 23)
