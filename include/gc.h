@@ -151,8 +151,9 @@ gc_status gc_graph_phase_ms(gc_graph g, double* ms);
  *   9 pass C: lower neighbours swept, summed over the blocks of the hub units
  *  10 pass T: out-list entries scanned
  *  11 pass T: triangles (each once)
+ *  12 pass C: wedges of the units counted in a shared-memory hash
  * Used to turn kernel times into algorithmic bytes per second. */
-#define GC_NUM_WORK 12
+#define GC_NUM_WORK 13
 gc_status gc_graph_work_counts(gc_graph g, uint64_t* out);
 
 /* Release the graph and all its device memory. NULL is accepted. */

@@ -38,7 +38,7 @@ EXPORTED = ["gc_last_error", "gc_graph_upload", "gc_graph_info", "gc_graph_edges
             "gc_batch_flush", "gc_batch_poll", "gc_batch_destroy", "gc_edge_triangles_noalloc",
             "gc_graph_work_counts", "gc_batch_submit_many"]
 WORK_NAMES = ["t_members", "c_wedges", "k_members", "k_scan", "k_local_edges", "k_words", "finish_edges", "launches",
-              "c_heavy_wedges", "c_heavy_sweeps", "t_scan", "t_triangles"]
+              "c_heavy_wedges", "c_heavy_sweeps", "t_scan", "t_triangles", "c_hash_wedges"]
 
 
 class GcError(RuntimeError):

@@ -476,6 +476,9 @@ gc_status gc_count_edge_graphlets(gc_graph g, uint64_t* per_edge_out, uint64_t* 
   ku.units = g->prep.kunits;
   ku.cunits = g->prep.cunits;
   ku.n_cheavy = g->prep.n_cheavy;
+  ku.chash_w = g->prep.chash_w;
+  ku.n_chash = g->prep.n_chash;
+  ku.n_cunits = g->prep.n_cunits;
   for (int t = 0; t <= kNumTiers; ++t) ku.tier_off[t] = g->prep.ktier_off[t];
   if ((st = run_count(dg, g->prep.units, g->prep.n_units, ku, pe_dev, g->d_csum, g->d_x, &g->sc, s, g->ev)) != GC_OK)
     return st;

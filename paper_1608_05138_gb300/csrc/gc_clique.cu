@@ -269,10 +269,8 @@ __global__ void __launch_bounds__(kThreads, 65536 / (kThreads * 64)) k_pass_k(De
               if (lane == 0) base_h = atomicAdd(&s_nhit, __popc(hit));
               base_h = __shfl_sync(kFull, base_h, 0);
               const int32_t slot = base_h + __popc(hit & ((1u << lane) - 1u));
-              if (j >= 0 && slot < a.hitcap) {
-                hits[2 * (size_t)slot] = (int32_t)(((uint32_t)i << 16) | (uint32_t)j);
-                hits[2 * (size_t)slot + 1] = q;
-              }
+              if (j >= 0 && slot < a.hitcap)
+                reinterpret_cast<int2*>(hits)[slot] = make_int2((int32_t)(((uint32_t)i << 16) | (uint32_t)j), q);
             }
           } else if (hit) {
             int32_t base_h = 0;
@@ -282,10 +280,8 @@ __global__ void __launch_bounds__(kThreads, 65536 / (kThreads * 64)) k_pass_k(De
               atomicOr(&rows[i * S + (j >> 5)], 1u << (j & 31));
               atomicOr(&rows[j * S + (i >> 5)], 1u << (i & 31));
               const int32_t slot = base_h + __popc(hit & ((1u << lane) - 1u));
-              if (slot < a.hitcap) {
-                hits[2 * (size_t)slot] = (int32_t)(((uint32_t)i << 16) | (uint32_t)j);  // read only when k <= 65535
-                hits[2 * (size_t)slot + 1] = q;
-              }
+              if (slot < a.hitcap)  // read only when k <= 65535
+                reinterpret_cast<int2*>(hits)[slot] = make_int2((int32_t)(((uint32_t)i << 16) | (uint32_t)j), q);
             }
           }
         }
@@ -312,7 +308,7 @@ __global__ void __launch_bounds__(kThreads, 65536 / (kThreads * 64)) k_pass_k(De
         const long long off = s_loff;
         if (off >= 0)
           for (int32_t e = threadIdx.x; e < nh; e += kThreads)
-            a.tlist[off + e] = make_int2(hits[2 * (size_t)e], hits[2 * (size_t)e + 1]);
+            a.tlist[off + e] = reinterpret_cast<const int2*>(hits)[e];
       }
       continue;
     }
@@ -323,7 +319,8 @@ __global__ void __launch_bounds__(kThreads, 65536 / (kThreads * 64)) k_pass_k(De
       for (int32_t e0 = warp * 32; e0 < nhit; e0 += kThreads) {
         const int32_t e = e0 + lane;
         if (e < nhit) {
-          const int32_t ij = hits[2 * (size_t)e], q = hits[2 * (size_t)e + 1];
+          const int2 en = reinterpret_cast<const int2*>(hits)[e];
+          const int32_t ij = en.x, q = en.y;
           const int32_t i = (int32_t)((uint32_t)ij >> 16), j = ij & 0xffff;
           const uint32_t* ri = rows + i * S;
           const uint32_t* rj = rows + j * S;
@@ -557,12 +554,23 @@ __global__ void __launch_bounds__(kWBlock) k_pass_k_warp(DevGraph g, CountArgs a
         }
         off = __shfl_sync(kFull, off, 0);
         if (off >= 0) {
-          long long pos = off + (incl - c);
-          unsigned f = found;
-          while (f) {
-            const int j = __ffs(f) - 1;
-            f &= f - 1;
-            a.tlist[pos++] = make_int2((int32_t)(((uint32_t)lane << 16) | (uint32_t)j), qs[lane * 32 + j]);
+          // entry e of the unit's list, lane per entry: its row r is the
+          // number of rows whose inclusive prefix is <= e, its column the
+          // (e - exclusive prefix of r)-th set bit of found_r
+          for (int32_t e0 = 0; e0 < total; e0 += 32) {  // warp-uniform trip count
+            const int32_t e = e0 + lane;
+            int r = 0;
+#pragma unroll
+            for (int step = 16; step; step >>= 1)
+              if (__shfl_sync(kFull, incl, r + step - 1) <= e) r += step;
+            const unsigned fr = __shfl_sync(kFull, found, r);
+            const int ir = __shfl_sync(kFull, incl, r);
+            if (e < total) {
+              unsigned f = fr;
+              for (int t = e - (ir - __popc(fr)); t > 0; --t) f &= f - 1;
+              const int j = __ffs(f) - 1;
+              a.tlist[off + e] = make_int2((int32_t)(((uint32_t)r << 16) | (uint32_t)j), qs[r * 32 + j]);
+            }
           }
         }
         __syncwarp();

@@ -180,14 +180,7 @@ __global__ void __launch_bounds__(kBlock) k_pass_c(DevGraph g, CountArgs a) {
         if (!rank_less(g.deg, x, h)) continue;
         const int32_t xb = g.rp[x];
         int32_t xe = g.rp[x + 1];
-        if (g.ranked) {
-          int32_t lo = xb, hi = xe;
-          while (lo < hi) {
-            const int32_t mid = (lo + hi) >> 1;
-            if (g.ci[mid] < h) lo = mid + 1; else hi = mid;
-          }
-          xe = lo;
-        }
+        if (g.ranked) xe = min(max(g.rev[p], xb), xe);  // Gamma(x) below the slot of (x, h) is < h
         unsigned long long s = 0;
         if (pass == 0 && lane == 0) w_wedge += xe - xb;
         for (int32_t q = xb + lane; q < xe; q += 32) {
@@ -334,11 +327,7 @@ __global__ void __launch_bounds__(kHeavyBlock, 1) k_pass_c_heavy(DevGraph g, Cou
     for (int32_t i = threadIdx.x; i < nx; i += kHeavyBlock) {
       const int32_t x = g.ci[hb + i];
       const int32_t xb = g.rp[x];
-      int32_t lo = xb, hi = g.rp[x + 1];
-      while (lo < hi) {
-        const int32_t mid = (lo + hi) >> 1;
-        if (g.ci[mid] < h) lo = mid + 1; else hi = mid;
-      }
+      const int32_t lo = min(max(g.rev[hb + i], xb), g.rp[x + 1]);  // Gamma(x) below the slot of (x, h) is < h
       cur[i] = xb;
       endp[i] = lo;
       w_wedge += lo - xb;
@@ -514,6 +503,120 @@ __global__ void __launch_bounds__(kHeavyBlock, 1) k_pass_c_heavy(DevGraph g, Cou
   if (threadIdx.x == 0 && w_blocks) atomicAdd(a.work + kWorkCBlocks, (unsigned long long)w_blocks);
 }
 
+// ---------------- pass C for units of at most kHashMaxW wedges ----------------
+// The same wedges and attribution as k_pass_c, with cnt_h(o) in a
+// shared-memory hash keyed by o instead of a vertex-indexed table in DRAM
+// (open addressing, linear probing; sized per unit to at least twice its
+// wedges, so at most half full; 16-bit counts, since cnt_h(o) <= wedges).
+// A warp takes one lower neighbour x of h at a time, its lanes the run
+// {o in Gamma(x) : o < h}, which ends at the slot of (x, h) (ids are ranks
+// and rows ascend).
+constexpr int kHashBlock = 512;
+constexpr int kHashSlots = 2 * kHashMaxW;
+
+__device__ __forceinline__ uint32_t o_hash(int32_t o, int bits) {
+  return ((uint32_t)o * 0x9E3779B1u) >> (32 - bits);  // Fibonacci hashing
+}
+// slot of o (inserted if absent), or -1 if the table is full
+__device__ __forceinline__ int32_t hash_insert(int32_t* keys, int32_t o, uint32_t mask, int bits) {
+  uint32_t sl = o_hash(o, bits);
+  for (uint32_t t = 0; t <= mask; ++t) {
+    const int32_t kk = *reinterpret_cast<volatile int32_t*>(&keys[sl]);
+    if (kk == o) return (int32_t)sl;
+    if (kk == -1) {
+      const int32_t prev = atomicCAS(&keys[sl], -1, o);
+      if (prev == -1 || prev == o) return (int32_t)sl;
+    }
+    sl = (sl + 1) & mask;
+  }
+  return -1;
+}
+// slot of o, or -1 if absent
+__device__ __forceinline__ int32_t hash_find(const int32_t* keys, int32_t o, uint32_t mask, int bits) {
+  uint32_t sl = o_hash(o, bits);
+  for (uint32_t t = 0; t <= mask; ++t) {
+    const int32_t kk = keys[sl];
+    if (kk == o) return (int32_t)sl;
+    if (kk == -1) return -1;
+    sl = (sl + 1) & mask;
+  }
+  return -1;
+}
+
+__global__ void __launch_bounds__(kHashBlock, kCtasPerSm) k_pass_c_hash(DevGraph g, CountArgs a) {
+  extern __shared__ int32_t hkeys[];                                  // [kHashSlots] o, or -1
+  uint32_t* hcnt = reinterpret_cast<uint32_t*>(hkeys + kHashSlots);   // [kHashSlots / 2] two counts
+  __shared__ int32_t s_unit, s_next[2];
+  const int lane = threadIdx.x & 31;
+  long long w_wedge = 0;  // lane 0
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_unit = atomicAdd(a.cursor + 9, 1);
+    __syncthreads();
+    const int32_t k = s_unit;
+    if (k >= a.n_chash) break;
+    const int32_t h = a.cunits[a.n_cheavy + k];
+    const int32_t wk = min(a.chash_w[k], (int32_t)kHashMaxW);
+    int bits = 6;
+    while ((1 << bits) < 2 * wk) ++bits;  // at most log2(kHashSlots)
+    const uint32_t mask = (1u << bits) - 1u;
+    const int32_t hb = g.rp[h], he = g.rp[h + 1];
+    for (int32_t i = threadIdx.x; i <= (int32_t)mask; i += kHashBlock) hkeys[i] = -1;
+    for (int32_t i = threadIdx.x; i <= (int32_t)(mask >> 1); i += kHashBlock) hcnt[i] = 0u;
+    if (threadIdx.x < 2) s_next[threadIdx.x] = hb;
+    __syncthreads();
+    // pass 0 counts cnt_h(o); pass 1 attributes cnt_h(o) - 1 to the slots
+    // (x, o) and, summed over the run, to (h, x)
+    for (int pass = 0; pass < 2; ++pass) {
+      for (;;) {
+        int32_t p = 0;
+        if (lane == 0) p = atomicAdd(&s_next[pass], 1);
+        p = __shfl_sync(0xffffffffu, p, 0);
+        if (p >= he) break;
+        const int32_t x = g.ci[p];
+        if (x >= h) break;  // the lower neighbours are a prefix of Gamma(h)
+        const int32_t xb = g.rp[x];
+        const int32_t xe = min(max(g.rev[p], xb), g.rp[x + 1]);  // Gamma(x) below the slot of (x, h)
+        if (pass == 0 && lane == 0) w_wedge += xe - xb;
+        uint32_t sx = 0u;
+        for (int32_t q0 = xb; q0 < xe; q0 += 128) {  // four windows of 32 in flight
+          int32_t o[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int32_t q = q0 + 32 * j + lane;
+            o[j] = q < xe ? g.ci[q] : -1;
+          }
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            if (o[j] < 0) continue;
+            if (pass == 0) {
+              const int32_t sl = hash_insert(hkeys, o[j], mask, bits);
+              if (sl >= 0) atomicAdd(&hcnt[sl >> 1], 1u << ((sl & 1) << 4));
+              else atomicOr(a.status, (int32_t)kSpillOverflow);  // more distinct o than wedges: invalid input
+            } else {
+              const int32_t sl = hash_find(hkeys, o[j], mask, bits);
+              const uint32_t c = sl >= 0 ? ((hcnt[sl >> 1] >> ((sl & 1) << 4)) & 0xffffu) - 1u : 0u;
+              if (c) {
+                atomicAdd(&a.P[q0 + 32 * j + lane], (unsigned long long)c);  // slot (x, o)
+                sx += c;
+              }
+            }
+          }
+        }
+        if (pass == 1) {
+          for (int off = 16; off; off >>= 1) sx += __shfl_xor_sync(0xffffffffu, sx, off);
+          if (lane == 0 && sx) atomicAdd(&a.P[p], (unsigned long long)sx);  // slot (h, x)
+        }
+      }
+      __syncthreads();
+    }
+  }
+  if (lane == 0 && w_wedge) {
+    atomicAdd(a.work + kWorkCWedge, (unsigned long long)w_wedge);
+    atomicAdd(a.work + kWorkCHashWedge, (unsigned long long)w_wedge);
+  }
+}
+
 // ---------------- derive X_1..X_17 per graph ----------------
 __device__ __forceinline__ bool div_exact(u128 num, u128 den, u128* q) {
   if (num % den != 0) return false;
@@ -611,6 +714,18 @@ gc_status run_pass_c_heavy(const DevGraph& g, const CountArgs& a, cudaStream_t s
   k_pass_c_heavy<<<grid, kHeavyBlock, smem, s>>>(g, a);
   e = cudaGetLastError();
   return e == cudaSuccess ? GC_OK : cuda_fail(e, "k_pass_c_heavy");
+}
+
+gc_status run_pass_c_hash(const DevGraph& g, const CountArgs& a, cudaStream_t s) {
+  if (a.n_chash <= 0) return GC_OK;
+  const size_t smem = sizeof(int32_t) * kHashSlots + sizeof(uint32_t) * (kHashSlots / 2);
+  cudaError_t e = cudaFuncSetAttribute(k_pass_c_hash, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return cuda_fail(e, "k_pass_c_hash");
+  int grid = count_grid_size();
+  if (grid > a.n_chash) grid = a.n_chash;
+  k_pass_c_hash<<<grid, kHashBlock, smem, s>>>(g, a);
+  e = cudaGetLastError();
+  return e == cudaSuccess ? GC_OK : cuda_fail(e, "k_pass_c_hash");
 }
 
 gc_status run_finish(const DevGraph& g, const CountArgs& a, cudaStream_t s) {

@@ -48,8 +48,10 @@ constexpr int kTierCap[kNumTiers] = {0, 1024, 512, 256, 32};
 struct CountArgs {
   const int32_t* units;    // pass C: v-groups (high endpoints), heaviest bin first
   int32_t n_units;
-  const int32_t* cunits;   // pass C: hub units first (blocked kernel), then the others
+  const int32_t* cunits;   // pass C: hub units (blocked kernel), hashed units, then the others
   int32_t n_cheavy;        // hub units of pass C (cunits[0 .. n_cheavy))
+  const int32_t* chash_w;  // wedges of the hashed units cunits[n_cheavy .. n_cheavy + n_chash)
+  int32_t n_chash;
   int32_t* cbuf;           // pass C hub kernel: per-CTA cursors (cbuf_ctas x 3 x cbuf_nx ints)
   int32_t cbuf_nx;
   const int32_t* kunits;   // pass K: lowest vertices a with |out(a)| >= 2, tiers in KTier order
@@ -98,6 +100,7 @@ enum Work {
   kWorkCBlocks,        // pass C: lower neighbours swept, summed over the blocks of the hub units
   kWorkTScan,          // pass T: out-list entries scanned
   kWorkTTriangles,     // pass T: triangles (each once)
+  kWorkCHashWedge,     // pass C: wedges of the units counted in a shared-memory hash
   kNumWork
 };
 
@@ -150,8 +153,11 @@ void scratch_free(Scratch* sc, cudaStream_t s);
 struct KUnits {
   const int32_t* units;
   int32_t tier_off[kNumTiers + 1];
-  const int32_t* cunits;   // pass C units, hub units first
+  const int32_t* cunits;   // pass C units: hubs, hashed units, the others
   int32_t n_cheavy;
+  const int32_t* chash_w;
+  int32_t n_chash;
+  int32_t n_cunits;        // pass C units in all (units without wedges are left out)
 };
 gc_status run_count(const DevGraph& g, const int32_t* units, int32_t n_units, const KUnits& ku,
                     uint64_t* per_edge, unsigned long long* csum, unsigned long long* x, Scratch* sc,
@@ -187,8 +193,12 @@ struct PrepBuffers {
   int32_t* kunits = nullptr;  // pass K units (see CountArgs::kunits)
   int32_t ktier_off[kNumTiers + 1] = {0, 0, 0, 0, 0, 0};
   int32_t kmax = 0;         // largest out-degree
-  int32_t* cunits = nullptr;  // pass C units: hub units (heaviest first), then the rest in unit order
+  int32_t* cunits = nullptr;  // pass C units: hub units (heaviest first), hashed units (heaviest
+                              // first), then the rest in unit order
   int32_t n_cheavy = 0;
+  int32_t* chash_w = nullptr;  // wedges of each hashed unit
+  int32_t n_chash = 0;
+  int32_t n_cunits = 0;
   int32_t cnx_max = 0;      // most lower neighbours of a hub unit
 };
 // Builds degrees, edge ids, the edge list, degree-oriented out-lists and the
@@ -200,8 +210,10 @@ gc_status prepare_graph(int32_t n, int32_t m, const int32_t* d_rp, const int32_t
                         const int32_t* d_vgid, int32_t* d_eid_given, const int32_t* d_perm,
                         PrepBuffers* out, cudaStream_t stream);
 // Splits the pass-C units of a ranked graph (ids = ranks, rows ascending)
-// into hub units for the blocked kernel and the rest (fills cunits,
-// n_cheavy, cnx_max; without hubs cunits is a copy of units).
+// into hub units for the blocked kernel, units of at most kHashMaxW wedges
+// for the hashed kernel and the rest, leaving out units without wedges
+// (fills cunits, n_cheavy, chash_w, n_chash, n_cunits, cnx_max; otherwise
+// cunits is a copy of units).
 gc_status classify_c_units(int32_t n, const int32_t* d_rp, const int32_t* d_ci, bool ranked, PrepBuffers* p,
                            cudaStream_t stream);
 void free_prep(PrepBuffers* p, cudaStream_t s);
@@ -222,6 +234,11 @@ int count_grid_size();
 gc_status run_pass_c(const DevGraph& g, const CountArgs& a, cudaStream_t s);
 gc_status run_pass_c_heavy(const DevGraph& g, const CountArgs& a, cudaStream_t s);
 constexpr int kHeavyTab = 49152;  // o-range block of the hub kernel of pass C (entries in shared memory)
+// Units of pass C with at most kHashMaxW wedges count in a shared-memory
+// hash of 2 kHashMaxW keys (at most half full: a unit has no more distinct
+// o than wedges).
+constexpr int kHashMaxW = 8192;
+gc_status run_pass_c_hash(const DevGraph& g, const CountArgs& a, cudaStream_t s);
 gc_status run_derive(const DevGraph& g, const unsigned long long* csum, unsigned long long* x,
                      int32_t* status, cudaStream_t s);
 gc_status run_pass_t(const DevGraph& g, const CountArgs& a, cudaStream_t s, int* launches);

@@ -372,6 +372,8 @@ gc_status classify_c_units(int32_t n, const int32_t* d_rp, const int32_t* d_ci, 
   cudaError_t e = cudaMallocAsync(&p->cunits, sizeof(int32_t) * (nu > 0 ? nu : 1), s);
   if (e != cudaSuccess) return cuda_fail(e, "alloc cunits");
   p->n_cheavy = 0;
+  p->n_chash = 0;
+  p->n_cunits = nu;
   p->cnx_max = 0;
   if (!ranked || n <= kSmemTableMax || nu == 0) {
     e = nu > 0 ? cudaMemcpyAsync(p->cunits, p->units, sizeof(int32_t) * nu, cudaMemcpyDeviceToDevice, s) : cudaSuccess;
@@ -415,10 +417,28 @@ gc_status classify_c_units(int32_t n, const int32_t* d_rp, const int32_t* d_ci, 
     is_heavy[k] = 1;
     if (NX[k] > p->cnx_max) p->cnx_max = NX[k];
   }
+  // Units of at most kHashMaxW wedges: the hashed kernel, heaviest first.
+  // Units without wedges add nothing to P and are left out.
+  std::vector<int32_t> hashed;
   for (int32_t k = 0; k < nu; ++k)
-    if (!is_heavy[k]) out.push_back(U[k]);
+    if (!is_heavy[k] && W[k] > 0 && W[k] <= kHashMaxW) hashed.push_back(k);
+  std::sort(hashed.begin(), hashed.end(), [&](int32_t a, int32_t b) { return W[a] > W[b]; });
+  std::vector<int32_t> hw;
+  hw.reserve(hashed.size());
+  for (int32_t k : hashed) {
+    out.push_back(U[k]);
+    hw.push_back((int32_t)W[k]);
+  }
+  for (int32_t k = 0; k < nu; ++k)
+    if (!is_heavy[k] && W[k] > kHashMaxW) out.push_back(U[k]);
   p->n_cheavy = (int32_t)heavy.size();
-  e = cudaMemcpyAsync(p->cunits, out.data(), sizeof(int32_t) * nu, cudaMemcpyHostToDevice, s);
+  p->n_chash = (int32_t)hashed.size();
+  p->n_cunits = (int32_t)out.size();
+  if (!out.empty()) e = cudaMemcpyAsync(p->cunits, out.data(), sizeof(int32_t) * out.size(), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && !hw.empty()) {
+    e = cudaMallocAsync(&p->chash_w, sizeof(int32_t) * hw.size(), s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p->chash_w, hw.data(), sizeof(int32_t) * hw.size(), cudaMemcpyHostToDevice, s);
+  }
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   return e == cudaSuccess ? GC_OK : cuda_fail(e, "copy cunits");
 }
@@ -455,6 +475,7 @@ void free_prep(PrepBuffers* p, cudaStream_t s) {
   if (p->ocsr) cudaFreeAsync(p->ocsr, s);
   if (p->kunits) cudaFreeAsync(p->kunits, s);
   if (p->cunits) cudaFreeAsync(p->cunits, s);
+  if (p->chash_w) cudaFreeAsync(p->chash_w, s);
   *p = PrepBuffers();
 }
 

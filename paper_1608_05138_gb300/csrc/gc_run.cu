@@ -106,10 +106,12 @@ gc_status run_count(const DevGraph& g, const int32_t* units, int32_t n_units, co
   a.kunits = ku.units;
   a.cunits = ku.cunits;
   a.n_cheavy = ku.n_cheavy;
+  a.chash_w = ku.chash_w;
+  a.n_chash = ku.n_chash;
   a.cbuf = sc->cbuf;
   a.cbuf_nx = sc->cbuf_nx;
   for (int t = 0; t <= kNumTiers; ++t) a.ktier_off[t] = ku.tier_off[t];
-  a.cursor = sc->misc;  // [0] pass C, [2 + tier] pass K, [8] pass C hubs, [10 + tier] pass T
+  a.cursor = sc->misc;  // [0] pass C, [2 + tier] pass K, [8] pass C hubs, [9] pass C hashed, [10 + tier] pass T
   a.status = sc->misc + 1;
   a.tables = g.table_n > kSmemTableMax ? sc->tables : nullptr;
   a.trio = sc->trio;
@@ -168,15 +170,20 @@ gc_status run_count(const DevGraph& g, const int32_t* units, int32_t n_units, co
   if ((st = run_pass_t(g, a, s, &t_launches)) != GC_OK) return st;
   launches += t_launches;
   GR_EVENT(kPhasePassC);
-  if (n_units > 0) {
+  const int32_t n_cunits = ku.n_cunits;  // pass C units: hubs, hashed units, the others
+  if (n_cunits > 0) {
     if (a.n_cheavy > 0) {
       if ((st = run_pass_c_heavy(g, a, s)) != GC_OK) return st;
       launches += 1;
     }
-    if (n_units > a.n_cheavy) {
+    if (a.n_chash > 0) {
+      if ((st = run_pass_c_hash(g, a, s)) != GC_OK) return st;
+      launches += 1;
+    }
+    if (n_cunits > a.n_cheavy + a.n_chash) {
       CountArgs al = a;  // the remaining units on the vertex-indexed tables
-      al.units = a.cunits + a.n_cheavy;
-      al.n_units = n_units - a.n_cheavy;
+      al.units = a.cunits + a.n_cheavy + a.n_chash;
+      al.n_units = n_cunits - a.n_cheavy - a.n_chash;
       GR_TRY(cudaMemsetAsync(a.cursor, 0, sizeof(int32_t), s), "reset cursor");
       if ((st = run_pass_c(g, al, s)) != GC_OK) return st;
       launches += 1;

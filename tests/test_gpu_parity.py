@@ -143,6 +143,93 @@ def test_hub_units_of_the_cycle_pass():
     assert_parity(*graphgen.chung_lu(120000, 600000, 2.1, 1.2e6, 4000.0, 7))
 
 
+def wedges_by_highest_vertex(rp, ci):
+    """Wedges h-x-o with x and o both below h in the (degree, id) order,
+    summed per h (numpy; independent of the library)."""
+    n = len(rp) - 1
+    deg = np.diff(rp).astype(np.int64)
+    key = deg * (n + 1) + np.arange(n)  # (degree, id) order
+    rows = np.repeat(np.arange(n), deg)
+    cols = ci.astype(np.int64)
+    below = key[cols] < key[rows]  # slot (r, c) with c below r
+    nb = np.bincount(rows[below], minlength=n)  # neighbours below each vertex
+    # for h and x below h: the o in Gamma(x) below h (o != h automatically)
+    W = np.zeros(n, np.int64)
+    for r, c in zip(rows[below], cols[below]):
+        nbr = ci[rp[c]:rp[c + 1]].astype(np.int64)
+        W[r] += int(np.count_nonzero(key[nbr] < key[r]))
+    return W, nb
+
+
+def test_hashed_units_of_the_cycle_pass():
+    # A unit h with 160 lower neighbours x of 50 lower neighbours o each
+    # (8000 wedges, hash at its full 16384 slots), the o drawn from a pool
+    # of 2000 so that cnt_h(o) > 1 often; a 2400-cycle so that n exceeds the
+    # shared-memory table size and the graph is ranked.
+    rng = np.random.default_rng(3)
+    h = 0
+    xs = np.arange(1, 161)
+    pool = np.arange(161, 2161)
+    E = [(h, int(x)) for x in xs]
+    for x in xs:
+        for o in rng.choice(pool, 50, replace=False):
+            E.append((int(x), int(o)))
+    filler = np.arange(2161, 4561)
+    E += [(int(a), int(b)) for a, b in zip(filler, np.roll(filler, 1))]
+    rp, ci = graphs.csr(4561, E)
+    W, _ = wedges_by_highest_vertex(rp, ci)
+    assert W.max() == 8000 and W.sum() > 8000
+    with gcb.Graph(rp, ci) as g:
+        pe = np.zeros((g.m, 13), np.uint64)
+        X = g.count(pe)
+        w = g.work_counts()
+    o = oracle.count(rp, ci)
+    np.testing.assert_array_equal(pe, o["per_edge"])
+    assert X == o["X"]
+    assert w["c_wedges"] == W.sum() and w["c_heavy_wedges"] == 0 and w["c_hash_wedges"] == W.sum()
+
+
+def test_cycle_pass_unit_kinds_on_a_power_law_graph():
+    # hubs (shared-memory blocks), hashed units (at most 8192 wedges) and
+    # vertex-indexed tables take part; the wedge counters add up to the
+    # wedges counted on the host
+    rp, ci = graphgen.chung_lu(60000, 400000, 2.1, 8e5, 3000.0, 11)
+    W, _ = wedges_by_highest_vertex(rp, ci)
+    with gcb.Graph(rp, ci) as g:
+        g.count(None)
+        w = g.work_counts()
+    assert w["c_wedges"] == W.sum()
+    assert 0 < w["c_heavy_wedges"] and w["c_hash_wedges"] == W[W <= 8192].sum()
+    assert w["c_heavy_wedges"] + w["c_hash_wedges"] < w["c_wedges"]
+    assert_parity(rp, ci)
+
+
+def test_table_units_of_the_cycle_pass():
+    # A unit of 20000 wedges (above the hash) whose rank spans 21 blocks of
+    # the hub kernel's o-range: counted on the vertex-indexed tables. The
+    # 2M vertices are mostly isolated.
+    rng = np.random.default_rng(4)
+    n = 2_000_000
+    h = 0
+    xs = np.arange(1, 201)
+    pool = np.arange(201, 8201)
+    E = [(h, int(x)) for x in xs]
+    for x in xs:
+        for o in rng.choice(pool, 100, replace=False):
+            E.append((int(x), int(o)))
+    rp, ci = graphs.csr(n, E)
+    W, _ = wedges_by_highest_vertex(rp, ci)
+    assert W.max() == 20000
+    with gcb.Graph(rp, ci) as g:
+        pe = np.zeros((g.m, 13), np.uint64)
+        X = g.count(pe)
+        w = g.work_counts()
+    o = oracle.count(rp, ci)
+    np.testing.assert_array_equal(pe, o["per_edge"])
+    assert X == o["X"]
+    assert w["c_wedges"] == W.sum() and w["c_heavy_wedges"] == 0 and w["c_hash_wedges"] == W.sum() - 20000
+
+
 def test_clique_pass_rescan_when_edge_list_is_full():
     # pass K keeps the edges of each H_a in a per-CTA list; a unit whose list
     # overflows scans its out-lists again. Force that with a 64-entry list.
