@@ -98,7 +98,10 @@ gc_status gc_graph_edges(gc_graph g, int32_t* uv);
  * Count every 2/3/4-node graphlet (Problem 1) by the per-edge method.
  *   per_edge_out  NULL (skip), or a host or device pointer (detected with
  *                 cudaPointerGetAttributes) to m x GC_EDGE_COLS uint64, row e
- *                 for edge id e, columns (T, S_u, S_v of Fig. 2; D_e as in
+ *                 for edge id e. Device, managed and pinned host memory are
+ *                 written by the device directly; pageable host memory
+ *                 through a device staging buffer (kept with the graph) and
+ *                 one copy. Columns (T, S_u, S_v of Fig. 2; D_e as in
  *                 Sec. 4.5):
  *                   0 x3  = |T|                     (triangles on e)
  *                   1 x4  = |S_u| + |S_v|           (2-stars on e)

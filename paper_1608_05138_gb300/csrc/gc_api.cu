@@ -399,6 +399,7 @@ gc_status gc_graph_upload(int32_t n, const int32_t* row_ptr, const int32_t* col_
   {
     gc_status st2 = scratch_init(&g->sc, g->m, n, g->prep.kmax, g->prep.cnx_max, s);
     if (st2 != GC_OK) return fail(st2);
+    scratch_guess_tlist(&g->sc, g->m);
   }
   for (auto& ev : g->ev) GC_CHECK(cudaEventCreate(&ev), "event create");
   GC_CHECK(cudaStreamSynchronize(s), "sync upload");
@@ -423,13 +424,23 @@ gc_status gc_graph_edges(gc_graph g, int32_t* uv) {
   return e == cudaSuccess ? GC_OK : cuda_fail(e, "copy edges");
 }
 
-static bool is_device_pointer(const void* p) {
+// The address by which the device writes the per-edge rows at p: p itself
+// for device or managed memory, the mapped address for pinned host memory
+// (the finish kernel then writes the rows over the host link, with no staging
+// buffer and no copy; *host = true), nullptr for pageable host memory.
+static uint64_t* device_view(uint64_t* p, bool* host) {
+  *host = false;
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
-    return false;
+    return nullptr;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return p;
+  if (a.type == cudaMemoryTypeHost && a.devicePointer) {
+    *host = true;
+    return static_cast<uint64_t*>(a.devicePointer);
+  }
+  return nullptr;
 }
 
 gc_status gc_count_edge_graphlets(gc_graph g, uint64_t* per_edge_out, uint64_t* global_out,
@@ -445,10 +456,10 @@ gc_status gc_count_edge_graphlets(gc_graph g, uint64_t* per_edge_out, uint64_t* 
   } while (0)
   uint64_t* pe_dev = nullptr;
   const bool want_pe = per_edge_out != nullptr && g->m > 0;
+  bool staged = false, pe_host = false;
   if (want_pe) {
-    if (is_device_pointer(per_edge_out)) {
-      pe_dev = per_edge_out;
-    } else {
+    if ((pe_dev = device_view(per_edge_out, &pe_host)) == nullptr) {
+      staged = true;
       if (!g->d_pe_tmp)
         GC_CHECK(cudaMalloc(&g->d_pe_tmp, sizeof(uint64_t) * 13 * (size_t)g->m), "alloc per-edge staging");
       pe_dev = g->d_pe_tmp;
@@ -464,6 +475,7 @@ gc_status gc_count_edge_graphlets(gc_graph g, uint64_t* per_edge_out, uint64_t* 
   dg.out_ptr = g->prep.out_ptr;
   dg.out_idx = g->prep.out_idx;
   dg.ocsr = g->prep.ocsr;
+  dg.e2o = g->prep.e2o;
   dg.rev = g->prep.rev;
   dg.G = 1;
   dg.vgid = nullptr;
@@ -480,7 +492,8 @@ gc_status gc_count_edge_graphlets(gc_graph g, uint64_t* per_edge_out, uint64_t* 
   ku.n_chash = g->prep.n_chash;
   ku.n_cunits = g->prep.n_cunits;
   for (int t = 0; t <= kNumTiers; ++t) ku.tier_off[t] = g->prep.ktier_off[t];
-  if ((st = run_count(dg, g->prep.units, g->prep.n_units, ku, pe_dev, g->d_csum, g->d_x, &g->sc, s, g->ev)) != GC_OK)
+  if ((st = run_count(dg, g->prep.units, g->prep.n_units, ku, pe_dev, g->d_csum, g->d_x, &g->sc, s, g->ev, pe_host)) !=
+      GC_OK)
     return st;
   unsigned long long hx[17 * 2 + 13 * 2];
   int32_t hstatus = 0;
@@ -489,7 +502,7 @@ gc_status gc_count_edge_graphlets(gc_graph g, uint64_t* per_edge_out, uint64_t* 
            "copy C");
   GC_CHECK(cudaMemcpyAsync(&hstatus, g->sc.misc + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, s), "copy status");
   GC_CHECK(cudaMemcpyAsync(g->work, g->sc.work, sizeof(g->work), cudaMemcpyDeviceToHost, s), "copy work");
-  if (want_pe && pe_dev != per_edge_out)
+  if (staged)
     GC_CHECK(cudaMemcpyAsync(per_edge_out, pe_dev, sizeof(uint64_t) * 13 * (size_t)g->m, cudaMemcpyDeviceToHost, s),
              "copy per-edge");
   GC_CHECK(cudaEventRecord(g->ev[kNumPhases], s), "event");

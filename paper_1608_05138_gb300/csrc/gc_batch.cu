@@ -196,6 +196,7 @@ gc_status run_union(std::vector<PendingGraph*>& graphs, cudaStream_t s, Launch* 
     dg.out_ptr = prep.out_ptr;
     dg.out_idx = prep.out_idx;
     dg.ocsr = prep.ocsr;
+    dg.e2o = prep.e2o;
     dg.rev = prep.rev;
     dg.G = G;
     dg.vgid = d_vgid;

@@ -83,32 +83,41 @@ __device__ __forceinline__ uint32_t* table_of(const DevGraph& g, const CountArgs
 }
 
 // ---------------- finish: x10, per-edge columns, sums ----------------
-// One warp per 32 consecutive out-slots. Each lane computes the 13 columns of
-// its edge into shared memory; the rows then leave one edge at a time (13
-// lanes, one 104-byte store), and lane k < 13 adds column csum_column(k) of
-// every row to its 128-bit running sum, flushed whenever the graph changes.
+// One warp per 32 consecutive edges. Each lane computes the 13 columns of its
+// edge into shared memory, and lane k < 13 adds column csum_column(k) of every
+// row to its 128-bit running sum, flushed whenever the graph changes.
+// kByEdge: the warp's edges are 32 consecutive edge ids, whose rows leave as
+// one contiguous block of 416 words (13 coalesced stores of the warp) -- the
+// order for rows written over the host link into pinned host memory.
+// Otherwise: 32 consecutive out-slots (coalesced reads of the pass results),
+// whose rows leave one at a time (13 lanes, one 104-byte store) -- the order
+// for rows in device memory.
 constexpr int kFinBlock = 256;
+template <bool kByEdge>
 __global__ void __launch_bounds__(kFinBlock) k_finish(DevGraph g, CountArgs a) {
   __shared__ unsigned long long st[kFinBlock / 32][32][13];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   unsigned long long(*rowv)[13] = st[warp];
+  const unsigned long long* flat = &st[warp][0][0];
   u128 acc = 0;
   int32_t cur_g = -1;
   long long w_edges = 0;
   const int64_t stride = (int64_t)gridDim.x * (kFinBlock / 32) * 32;
-  for (int64_t o0 = ((int64_t)blockIdx.x * (kFinBlock / 32) + warp) * 32; o0 < g.m; o0 += stride) {
-    const int64_t o = o0 + lane;
-    int32_t e = 0, gid = 0;
-    if (o < g.m) {
+  for (int64_t e0 = ((int64_t)blockIdx.x * (kFinBlock / 32) + warp) * 32; e0 < g.m; e0 += stride) {
+    const int64_t i0 = e0 + lane;  // edge id (kByEdge) or out-slot
+    int32_t gid = 0, eid = 0;
+    if (i0 < g.m) {
+      int32_t o = kByEdge ? g.e2o[i0] : (int32_t)i0;
+      if ((uint32_t)o >= (uint32_t)g.m) o = 0;  // only for invalid input
       const int32_t p = g.ocsr[o];
+      if (!kByEdge) eid = g.eid[p];
       const int32_t r = g.rev[p];
-      e = g.eid[p];
       const int32_t u = g.ci[r], v = g.ci[p];
       gid = g.vgid ? g.vgid[u] : 0;
       const int64_t du = g.deg[u], dv = g.deg[v];
       const int64_t t = a.trio[o];
-      const int64_t x7 = (int64_t)a.xc[2 * o];
-      const int64_t x10 = (int64_t)(a.P[p] + a.P[r]) - (int64_t)a.xc[2 * o + 1] + 2 * x7;
+      const int64_t x7 = (int64_t)a.xc[2 * (size_t)o];
+      const int64_t x10 = (int64_t)(a.P[p] + a.P[r]) - (int64_t)a.xc[2 * (size_t)o + 1] + 2 * x7;
       const int64_t su = du - t - 1, sv = dv - t - 1;
       const int64_t n_g = g.gn[gid], m_g = g.gm[gid];
       const int64_t D = n_g - 2 - t - su - sv;
@@ -116,12 +125,16 @@ __global__ void __launch_bounds__(kFinBlock) k_finish(DevGraph g, CountArgs a) {
       for (int c = 0; c < 13; ++c) rowv[lane][c] = edge_column(c, t, su, sv, D, x7, x10, m_g, du, dv);
     }
     __syncwarp();
-    const int rows = (int)min((int64_t)32, (int64_t)g.m - o0);
+    const int rows = (int)min((int64_t)32, (int64_t)g.m - e0);
+    if (kByEdge && a.per_edge) {
+      unsigned long long* dst = reinterpret_cast<unsigned long long*>(a.per_edge) + (size_t)e0 * 13;
+      for (int i = lane; i < rows * 13; i += 32) dst[i] = flat[i];
+    }
     for (int r = 0; r < rows; ++r) {
-      const int32_t er = __shfl_sync(0xffffffffu, e, r);
       const int32_t gr = __shfl_sync(0xffffffffu, gid, r);
+      const int32_t er = __shfl_sync(0xffffffffu, eid, r);
       if (lane < 13) {
-        if (a.per_edge) a.per_edge[(size_t)er * 13 + lane] = rowv[r][lane];
+        if (!kByEdge && a.per_edge) a.per_edge[(size_t)er * 13 + lane] = rowv[r][lane];
         if (gr != cur_g) {
           if (cur_g >= 0) atomic_add_u128(a.csum + ((size_t)cur_g * 13 + lane) * 2, acc);
           acc = 0;
@@ -731,7 +744,8 @@ gc_status run_pass_c_hash(const DevGraph& g, const CountArgs& a, cudaStream_t s)
 gc_status run_finish(const DevGraph& g, const CountArgs& a, cudaStream_t s) {
   if (g.m == 0) return GC_OK;
   int blocks = (int)min((int64_t)count_grid_size() * 4, ((int64_t)g.m + kFinBlock - 1) / kFinBlock);
-  k_finish<<<blocks, kFinBlock, 0, s>>>(g, a);
+  if (a.per_edge_host) k_finish<true><<<blocks, kFinBlock, 0, s>>>(g, a);
+  else k_finish<false><<<blocks, kFinBlock, 0, s>>>(g, a);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? GC_OK : cuda_fail(e, "k_finish");
 }

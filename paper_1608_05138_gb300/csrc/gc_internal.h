@@ -27,6 +27,7 @@ struct DevGraph {
   const int32_t* out_ptr;  // [n + 1] degree-oriented out-lists (P3 orientation)
   const int32_t* out_idx;  // [m] ascending ids within each list; position = out-slot
   const int32_t* ocsr;     // [m] out-slot -> CSR slot of the same direction (row of the owner)
+  const int32_t* e2o;      // [m] edge id -> out-slot
   const int32_t* rev;      // [2m] slot of (y, x) for the slot of (x, y)
   int32_t G;               // graphs in the union (>= 1)
   const int32_t* vgid;     // [n] graph of each vertex, or nullptr when G == 1
@@ -80,6 +81,7 @@ struct CountArgs {
   long long* tl_off;
   int32_t* tl_cnt;
   uint64_t* per_edge;      // [m][13] device pointer or nullptr
+  bool per_edge_host;      // per_edge maps pinned host memory
   unsigned long long* csum;  // [G][13][2] 128-bit unrestricted counts (lo, hi)
   int32_t* status;         // device status word (0 = ok)
   unsigned long long* work;  // [kNumWork] work counters of this count
@@ -135,7 +137,7 @@ struct Scratch {
   int32_t hitbuf_ctas = 0;
   int2* tlist = nullptr;             // edges of all H_a, from pass T to pass K
   long long tlist_cap = 0;           // entries
-  long long tlist_want = 0;          // triangles of the last count: the size to keep
+  long long tlist_want = 0;          // triangles of the last count (or a first guess): the size to keep
   long long* tl_off = nullptr;       // [units of pass K]
   int32_t* tl_cnt = nullptr;
   int32_t tl_units = 0;
@@ -147,6 +149,9 @@ struct Scratch {
 // vertices and largest out-degree kmax (stream-ordered).
 gc_status scratch_init(Scratch* sc, int32_t m, int32_t table_n, int32_t kmax, int32_t cnx_max, cudaStream_t s);
 void scratch_free(Scratch* sc, cudaStream_t s);
+// Size of pass T's edge lists for the first count of a whole graph with m
+// edges: 32 m entries within the list budget (units past it scan again).
+void scratch_guess_tlist(Scratch* sc, int64_t m);
 // The whole count: passes T, C, K, finish, derive. csum [G][13][2] and
 // x [G][17][2] are device arrays; ev (optional) receives kNumPhases + 1
 // events. Returns after the derive is queued (no host synchronisation).
@@ -161,7 +166,7 @@ struct KUnits {
 };
 gc_status run_count(const DevGraph& g, const int32_t* units, int32_t n_units, const KUnits& ku,
                     uint64_t* per_edge, unsigned long long* csum, unsigned long long* x, Scratch* sc,
-                    cudaStream_t s, cudaEvent_t* ev);
+                    cudaStream_t s, cudaEvent_t* ev, bool per_edge_host = false);
 
 // ---- host helpers (gc_api.cu) ----
 void set_error(const std::string& msg);
@@ -190,6 +195,7 @@ struct PrepBuffers {
   long long* S = nullptr;  // [n] sum of neighbour degrees (Psi build cost of a v-group)
   int32_t* rev = nullptr;  // [2m] slot of the reverse direction of every slot
   int32_t* ocsr = nullptr;  // [m] out-slot -> CSR slot
+  int32_t* e2o = nullptr;   // [m] edge id -> out-slot
   int32_t* kunits = nullptr;  // pass K units (see CountArgs::kunits)
   int32_t ktier_off[kNumTiers + 1] = {0, 0, 0, 0, 0, 0};
   int32_t kmax = 0;         // largest out-degree

@@ -82,13 +82,14 @@ __global__ void k_out_cnt(int32_t n, const int32_t* __restrict__ rp, const int32
   }
 }
 
-// Warp per vertex: edge ids of every slot, edge list, out-lists.
-__global__ void k_edges(int32_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+// Warp per vertex: edge ids of every slot, edge list, out-lists, and the
+// out-slot of every edge id.
+__global__ void k_edges(int32_t n, int32_t m, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                         const int32_t* __restrict__ deg, const int32_t* __restrict__ up,
                         const int32_t* __restrict__ upoff, const int32_t* __restrict__ out_ptr,
                         int32_t* __restrict__ eid, int32_t* __restrict__ uv,
                         int32_t* __restrict__ out_idx, int32_t* __restrict__ ocsr, int32_t* __restrict__ rev,
-                        bool write_ids) {
+                        int32_t* __restrict__ e2o, bool write_ids) {
   const int lane = threadIdx.x & 31;
   const int warps = (gridDim.x * blockDim.x) >> 5;
   for (int32_t x = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < n; x += warps) {
@@ -105,8 +106,8 @@ __global__ void k_edges(int32_t n, const int32_t* __restrict__ rp, const int32_t
         const int32_t q = lower_bound_i32(ci, yb, ye, x);
         rev[p] = (q < ye && ci[q] == x) ? q : p;  // p itself only for invalid input
       }
+      int32_t id = 0;
       if (valid && write_ids) {
-        int32_t id;
         if (y > x) {
           id = upoff[x] + (p - first_up);
           uv[2 * (int64_t)id] = x;
@@ -123,6 +124,8 @@ __global__ void k_edges(int32_t n, const int32_t* __restrict__ rp, const int32_t
         const int32_t os = o + __popc(mask & ((1u << lane) - 1u));
         out_idx[os] = y;
         ocsr[os] = p;
+        const int32_t ide = write_ids ? id : eid[p];
+        if ((uint32_t)ide < (uint32_t)m) e2o[ide] = os;  // out of range only for invalid input
       }
       o += __popc(mask);
     }
@@ -473,6 +476,7 @@ void free_prep(PrepBuffers* p, cudaStream_t s) {
   if (p->S) cudaFreeAsync(p->S, s);
   if (p->rev) cudaFreeAsync(p->rev, s);
   if (p->ocsr) cudaFreeAsync(p->ocsr, s);
+  if (p->e2o) cudaFreeAsync(p->e2o, s);
   if (p->kunits) cudaFreeAsync(p->kunits, s);
   if (p->cunits) cudaFreeAsync(p->cunits, s);
   if (p->chash_w) cudaFreeAsync(p->chash_w, s);
@@ -506,6 +510,8 @@ gc_status prepare_graph(int32_t n, int32_t m, const int32_t* d_rp, const int32_t
   GC_TRY(cudaMallocAsync(&P.out_idx, sizeof(int32_t) * (m > 0 ? m : 1), s), "alloc out_idx");
   GC_TRY(cudaMallocAsync(&P.units, sizeof(int32_t) * (n > 0 ? n : 1), s), "alloc units");
   GC_TRY(cudaMallocAsync(&P.ocsr, sizeof(int32_t) * (m > 0 ? m : 1), s), "alloc ocsr");
+  GC_TRY(cudaMallocAsync(&P.e2o, sizeof(int32_t) * (m > 0 ? m : 1), s), "alloc e2o");
+  GC_TRY(cudaMemsetAsync(P.e2o, 0, sizeof(int32_t) * (m > 0 ? m : 1), s), "memset e2o");  // in range whatever the input
   GC_TRY(cudaMallocAsync(&P.kunits, sizeof(int32_t) * (n > 0 ? n : 1), s), "alloc kunits");
   GC_TRY(cudaMallocAsync(&up, sizeof(int32_t) * (n > 0 ? n : 1), s), "alloc up");
   GC_TRY(cudaMallocAsync(&upoff, sizeof(int32_t) * ((int64_t)n + 1), s), "alloc upoff");
@@ -523,9 +529,9 @@ gc_status prepare_graph(int32_t n, int32_t m, const int32_t* d_rp, const int32_t
     k_out_cnt<<<grid_for((int64_t)n * 32, 256), 256, 0, s>>>(n, d_rp, d_ci, P.deg, out_cnt, S, dmax, dmax + 65);
     GC_TRY(cudaGetLastError(), "k_out_cnt");
     if ((st = exclusive_scan(n, out_cnt, P.out_ptr, s)) != GC_OK) goto fail;
-    k_edges<<<grid_for((int64_t)n * 32, 256), 256, 0, s>>>(n, d_rp, d_ci, P.deg, up, upoff,
+    k_edges<<<grid_for((int64_t)n * 32, 256), 256, 0, s>>>(n, m, d_rp, d_ci, P.deg, up, upoff,
                                                             P.out_ptr, P.eid, P.uv, P.out_idx, P.ocsr, P.rev,
-                                                            d_eid_given == nullptr);
+                                                            P.e2o, d_eid_given == nullptr);
     GC_TRY(cudaGetLastError(), "k_edges");
     if (d_eid_given) {
       k_uv_perm<<<grid_for((int64_t)n * 32, 256), 256, 0, s>>>(n, d_rp, d_ci, P.eid, d_perm, P.uv);

@@ -33,6 +33,17 @@ long long k_list_cap() {
   }();
   return v;
 }
+// Bound on the entries of pass T's edge lists from the environment's
+// GC_T_LIST_CAP (>= 1; units past it scan again in pass K), read once per
+// process; 0: not set.
+long long t_list_cap_knob() {
+  static long long v = [] {
+    const char* e = getenv("GC_T_LIST_CAP");
+    const long long x = e ? atoll(e) : 0;
+    return e ? (x < 1 ? 1LL : x) : 0LL;
+  }();
+  return v;
+}
 }  // namespace
 
 void scratch_free(Scratch* sc, cudaStream_t s) {
@@ -86,11 +97,16 @@ gc_status scratch_init(Scratch* sc, int32_t m, int32_t table_n, int32_t kmax, in
   return GC_OK;
 }
 
+void scratch_guess_tlist(Scratch* sc, int64_t m) {
+  const long long cap = kTListBudget / (long long)sizeof(int2);
+  sc->tlist_want = 32 * m < cap ? 32 * m : cap;
+}
+
 static int32_t ku_total(const KUnits& ku) { return ku.tier_off[kNumTiers]; }
 
 gc_status run_count(const DevGraph& g, const int32_t* units, int32_t n_units, const KUnits& ku,
                     uint64_t* per_edge, unsigned long long* csum, unsigned long long* x, Scratch* sc,
-                    cudaStream_t s, cudaEvent_t* ev) {
+                    cudaStream_t s, cudaEvent_t* ev, bool per_edge_host) {
   cudaError_t e = cudaSuccess;
   gc_status st = GC_OK;
 #define GR_TRY(call, what)                  \
@@ -124,17 +140,20 @@ gc_status run_count(const DevGraph& g, const int32_t* units, int32_t n_units, co
   a.hitbuf = sc->hitbuf;
   a.hitcap = sc->hitcap;
   a.hitbuf_ctas = sc->hitbuf_ctas;
-  // Pass T keeps the edges of the H_a for pass K when the triangles of the
-  // previous count (of this scratch) fit the budget; the first count scans twice.
+  // Pass T keeps the edges of the H_a for pass K, in a list sized by the
+  // triangles of the previous count of this scratch (or by a first guess);
+  // units that do not fit scan their out-lists again in pass K.
   {
     const int32_t nku = ku_total(ku);
     const long long want = sc->tlist_want;
     if (want > 0 && want * (long long)sizeof(int2) <= kTListBudget && nku > 0) {
-      if (want > sc->tlist_cap) {
+      long long need = want + want / 16 + 1024;
+      if (t_list_cap_knob() && need > t_list_cap_knob()) need = t_list_cap_knob();
+      if (need > sc->tlist_cap) {
         if (sc->tlist) cudaFreeAsync(sc->tlist, s);
         sc->tlist = nullptr;
         sc->tlist_cap = 0;
-        const long long cap = want + want / 16 + 1024;
+        const long long cap = need;
         if (cudaMallocAsync(&sc->tlist, sizeof(int2) * (size_t)cap, s) == cudaSuccess) sc->tlist_cap = cap;
         else cudaGetLastError();  // no list: pass K scans
       }
@@ -155,6 +174,7 @@ gc_status run_count(const DevGraph& g, const int32_t* units, int32_t n_units, co
   a.tl_cnt = sc->tl_cnt;
   if (a.tlist) GR_TRY(cudaMemsetAsync(sc->tl_fill, 0, sizeof(unsigned long long), s), "zero list fill");
   a.per_edge = per_edge;
+  a.per_edge_host = per_edge != nullptr && per_edge_host;
   a.csum = csum;
   a.work = sc->work;
   const size_t m1 = (size_t)(g.m > 0 ? g.m : 1);

@@ -248,6 +248,33 @@ def test_clique_pass_rescan_when_edge_list_is_full():
     assert r.returncode == 0 and "ok" in r.stdout, r.stdout + r.stderr
 
 
+def _run_with_env(code, env_extra):
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, PYTHONPATH=root, **env_extra)
+    r = subprocess.run([sys.executable, "-c", code], env=env, cwd=root, capture_output=True, text=True, timeout=900)
+    assert r.returncode == 0 and "ok" in r.stdout, r.stdout + r.stderr
+
+
+_TWICE = ("import numpy as np, graphgen, oracle, paper_1608_05138_gb300 as gcb\n"
+          "for rp, ci in (graphgen.rmat(13, 16, 0.57, 0.19, 0.19, 31), graphgen.config_er_dense(),\n"
+          "               graphgen.chung_lu(20000, 150000, 2.1, 3e5, 2000.0, 8)):\n"
+          "    o = oracle.count(rp, ci)\n"
+          "    with gcb.Graph(rp, ci) as g:\n"
+          "        for _ in range(2):\n"
+          "            pe = np.zeros((g.m, 13), np.uint64); X = g.count(pe)\n"
+          "            assert X == o['X'] and (pe == o['per_edge']).all()\n"
+          "print('ok')\n")
+
+
+def test_triangle_lists_that_do_not_fit():
+    # a list of 5000 entries: almost every unit of pass T finds it full and
+    # pass K scans its out-lists again
+    _run_with_env(_TWICE, {"GC_T_LIST_CAP": "5000"})
+
+
 def test_relabelling_is_metamorphic():
     rp, ci = graphgen.chung_lu(2000, 12000, 2.1, 24000.0, 500.0, 22)
     n = len(rp) - 1
@@ -297,10 +324,15 @@ def test_device_output_and_repeat():
         dev = torch.zeros((g.m, 13), dtype=torch.int64, device="cuda")
         X2 = g.count(dev)
         X3 = g.count()
-        assert X1 == X2 == X3
+        # pinned host memory: the rows are written by the device directly
+        pinned = torch.zeros((g.m, 13), dtype=torch.int64, pin_memory=True)
+        X4 = g.count(pinned.numpy().view(np.uint64))
+        assert X1 == X2 == X3 == X4
         np.testing.assert_array_equal(dev.cpu().numpy().view(np.uint64), host)
+        np.testing.assert_array_equal(pinned.numpy().view(np.uint64), host)
         ms = g.phase_ms()
         assert set(ms) == set(gcb.gc_phase_names()) and all(v >= 0 for v in ms.values())
+    np.testing.assert_array_equal(host, oracle.count(rp, ci)["per_edge"])
 
 
 def _sampled_check(rp, ci, k=1500, seed=0):
