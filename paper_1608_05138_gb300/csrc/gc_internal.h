@@ -239,7 +239,7 @@ gc_status run_small_graphs(const int32_t* rp, const int64_t* voff, const int32_t
 int count_grid_size();
 gc_status run_pass_c(const DevGraph& g, const CountArgs& a, cudaStream_t s);
 gc_status run_pass_c_heavy(const DevGraph& g, const CountArgs& a, cudaStream_t s);
-constexpr int kHeavyTab = 49152;  // o-range block of the hub kernel of pass C (entries in shared memory)
+constexpr int kHeavyTab = 53248;  // o-range block of the hub kernel of pass C (entries in shared memory)
 // Units of pass C with at most kHashMaxW wedges count in a shared-memory
 // hash of 2 kHashMaxW keys (at most half full: a unit has no more distinct
 // o than wedges).
