@@ -305,6 +305,7 @@ __global__ void __launch_bounds__(kHeavyBlock, 1) k_pass_c_heavy(DevGraph g, Cou
   extern __shared__ uint32_t tab[];  // kHeavyTab counters
   __shared__ int32_t s_unit, s_nx, s_chunk[2];
   __shared__ unsigned long long s_sx[kHeavyWarps][32];
+  __shared__ uint32_t s_sx32[kHeavyWarps][32];  // the short runs' part (< 32 entries x counts < 2^26)
   __shared__ int32_t s_comp[kHeavyWarps][32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int32_t* beg = a.cbuf + (size_t)blockIdx.x * 3 * (size_t)a.cbuf_nx;
@@ -427,6 +428,7 @@ __global__ void __launch_bounds__(kHeavyBlock, 1) k_pass_c_heavy(DevGraph g, Cou
           L = cur[i] - st;
         }
         s_sx[warp][lane] = 0ull;  // per x of the chunk: sum of its wedges' counts
+        s_sx32[warp][lane] = 0u;
         __syncwarp();
         // runs of 32 or more entries: the whole warp, one run at a time
         unsigned lm = __ballot_sync(0xffffffffu, L >= 32);
@@ -461,46 +463,32 @@ __global__ void __launch_bounds__(kHeavyBlock, 1) k_pass_c_heavy(DevGraph g, Cou
         const int32_t Ls = L < 32 ? L : 0;
         const Deal d = deal_setup(Ls, comp, lane);
         for (int32_t k0 = 0; k0 < d.total; k0 += 128) {
-          int32_t q[4], ol[4], ej[4], lj[4];
+          int32_t q[4], ol[4];
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
             ol[j] = deal_owner(d, Ls, k0 + 32 * j, comp, lane);
             const int32_t kk = k0 + 32 * j + lane;
             const int32_t sj = __shfl_sync(0xffffffffu, st, ol[j]);
-            ej[j] = __shfl_sync(0xffffffffu, d.excl, ol[j]);
-            lj[j] = __shfl_sync(0xffffffffu, Ls, ol[j]);
-            q[j] = kk < d.total ? sj + (kk - ej[j]) : -1;
+            const int32_t ej = __shfl_sync(0xffffffffu, d.excl, ol[j]);
+            q[j] = kk < d.total ? sj + (kk - ej) : -1;
           }
           int32_t o[4];
 #pragma unroll
           for (int j = 0; j < 4; ++j) o[j] = q[j] >= 0 ? g.ci[q[j]] : lo_id;
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
-            uint32_t cnt = 0u;
             if (q[j] >= 0) {
-              cnt = read_count(tab, o[j] - lo_id, half) - 1u;
-              if (cnt) atomicAdd(&a.P[q[j]], (unsigned long long)cnt);  // slot (x, o)
+              const uint32_t cnt = read_count(tab, o[j] - lo_id, half) - 1u;
+              if (cnt) {
+                atomicAdd(&a.P[q[j]], (unsigned long long)cnt);  // slot (x, o)
+                atomicAdd(&s_sx32[warp][ol[j]], cnt);           // the owner's sum
+              }
             }
-            // per-owner sums of this window: a prefix sum over the lanes, read
-            // at the last lane of each owner's segment
-            uint32_t S = cnt;
-            for (int off = 1; off < 32; off <<= 1) {
-              const uint32_t y = __shfl_up_sync(0xffffffffu, S, off);
-              if (lane >= off) S += y;
-            }
-            const int32_t kb = k0 + 32 * j;
-            const int head = max(ej[j] - kb, 0);
-            const uint32_t before = __shfl_sync(0xffffffffu, S, head > 0 ? head - 1 : 0);
-            const int32_t kk = kb + lane;
-            const bool tail = q[j] >= 0 && (lane == 31 || kk + 1 == ej[j] + lj[j]);
-            const uint32_t seg = S - (head > 0 ? before : 0u);
-            // tails of one window belong to distinct owners
-            if (tail && seg) s_sx[warp][ol[j]] += seg;
-            __syncwarp();
           }
         }
+        __syncwarp();
         if (i < nx) {
-          const unsigned long long sx = s_sx[warp][lane];
+          const unsigned long long sx = s_sx[warp][lane] + s_sx32[warp][lane];
           if (sx) atomicAdd(&a.P[hb + i], sx);  // slot (h, x)
         }
         __syncwarp();
