@@ -291,13 +291,16 @@ __device__ __forceinline__ Deal deal_setup(int32_t L, int32_t* comp, int lane) {
   return d;
 }
 // Owner lane of position k0 + lane (k0 a multiple of 32, call with the whole
-// warp): the runs starting in the window mark a 32-bit mask, and the owner is
-// the last non-empty run starting at or before the position.
-__device__ __forceinline__ int deal_owner(const Deal& d, int32_t L, int32_t k0, const int32_t* comp, int lane) {
+// warp, for the windows k0 = 0, 32, 64, ... in order): the runs starting in
+// the window mark a 32-bit mask, and the owner is the last non-empty run
+// starting at or before the position. `before` counts the non-empty runs that
+// start before the window (0 for the first) and is advanced past it.
+__device__ __forceinline__ int deal_owner(const Deal& d, int32_t L, int32_t k0, const int32_t* comp, int lane,
+                                          int& before) {
   const bool in_win = L > 0 && d.excl >= k0 && d.excl < k0 + 32;
   const unsigned M = __reduce_or_sync(0xffffffffu, in_win ? 1u << (d.excl - k0) : 0u);
-  const int before = __popc(__ballot_sync(0xffffffffu, L > 0 && d.excl < k0));
   const int r = before + __popc(M & (0xffffffffu >> (31 - lane))) - 1;
+  before += __popc(M);
   return comp[r < 0 ? 0 : r];
 }
 
@@ -395,15 +398,16 @@ __global__ void __launch_bounds__(kHeavyBlock, 1) k_pass_c_heavy(DevGraph g, Cou
         // shorter runs dealt to the lanes end to end
         const int32_t Ls = L < 32 ? L : 0;
         const Deal d = deal_setup(Ls, comp, lane);
+        const int32_t sb = st - d.excl;  // slot of position kk of this lane's run: sb + kk
+        int before = 0;
         for (int32_t k0 = 0; k0 < d.total; k0 += 128) {
           int32_t q[4];
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
-            const int ol = deal_owner(d, Ls, k0 + 32 * j, comp, lane);
+            const int ol = deal_owner(d, Ls, k0 + 32 * j, comp, lane, before);
             const int32_t kk = k0 + 32 * j + lane;
-            const int32_t sj = __shfl_sync(0xffffffffu, st, ol);
-            const int32_t ej = __shfl_sync(0xffffffffu, d.excl, ol);
-            q[j] = kk < d.total ? sj + (kk - ej) : -1;
+            const int32_t bj = __shfl_sync(0xffffffffu, sb, ol);
+            q[j] = kk < d.total ? bj + kk : -1;
           }
           int32_t o[4];
 #pragma unroll
@@ -462,15 +466,16 @@ __global__ void __launch_bounds__(kHeavyBlock, 1) k_pass_c_heavy(DevGraph g, Cou
         // shorter runs dealt to the lanes end to end
         const int32_t Ls = L < 32 ? L : 0;
         const Deal d = deal_setup(Ls, comp, lane);
+        const int32_t sb = st - d.excl;  // slot of position kk of this lane's run: sb + kk
+        int before = 0;
         for (int32_t k0 = 0; k0 < d.total; k0 += 128) {
           int32_t q[4], ol[4];
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
-            ol[j] = deal_owner(d, Ls, k0 + 32 * j, comp, lane);
+            ol[j] = deal_owner(d, Ls, k0 + 32 * j, comp, lane, before);
             const int32_t kk = k0 + 32 * j + lane;
-            const int32_t sj = __shfl_sync(0xffffffffu, st, ol[j]);
-            const int32_t ej = __shfl_sync(0xffffffffu, d.excl, ol[j]);
-            q[j] = kk < d.total ? sj + (kk - ej) : -1;
+            const int32_t bj = __shfl_sync(0xffffffffu, sb, ol[j]);
+            q[j] = kk < d.total ? bj + kk : -1;
           }
           int32_t o[4];
 #pragma unroll
