@@ -95,7 +95,7 @@ template <int kCap, int kThreads, bool kTri>
 __global__ void __launch_bounds__(kThreads, 65536 / (kThreads * 64)) k_pass_k(DevGraph g, CountArgs a, int tier) {
   constexpr int kW = kThreads / 32;
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ int32_t s_unit, s_cur1, s_cur2, s_nhit, s_lcnt;
+  __shared__ int32_t s_unit, s_cur1, s_cur2, s_nhit;
   __shared__ long long s_loff;
   __shared__ int32_t s_qj[kW][64], s_qq[kW][64];
 

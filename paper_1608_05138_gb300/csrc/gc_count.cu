@@ -235,9 +235,13 @@ __global__ void __launch_bounds__(kBlock) k_pass_c(DevGraph g, CountArgs a) {
 // once over all blocks; the end of the run is found by galloping search),
 // then the wedges of the block are attributed with the block's counts.
 // In both phases a warp takes 32 x's at a time (heaviest chunk first, from a
-// shared counter) and deals their runs to its lanes end to end, so that run
+// shared counter): runs of 32 or more entries are taken by the whole warp one
+// at a time, the shorter ones are dealt to its lanes end to end, so that run
 // lengths, however skewed, do not leave lanes idle, and the P atomics of
-// consecutive lanes hit consecutive slots.
+// consecutive lanes hit consecutive slots. The per-x sums of the attribution
+// collect in shared memory (warp sums for long runs, shared atomics for
+// short ones). The block fills shared memory: the longer the runs per block,
+// the more wedges take the whole-warp path.
 constexpr int kHeavyBlock = 1024;
 constexpr int kHeavyWarps = kHeavyBlock / 32;
 
