@@ -178,6 +178,23 @@ def cpu_baseline(rp, ci, m, target_s=12.0, seed=0):
             "sample": f"{len(ids)} uniformly drawn edges of the same graph, per-edge rows only, {dt:.1f} s"}
 
 
+def max_over_ranks(ms: float, dist, device) -> float:
+    """The slowest rank's time per step (every rank gets it); the time itself
+    when there is no process group."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world: int, units_per_rank: int, step_ms: float) -> float:
+    """Whole-job throughput: every rank processes its own units (replicas,
+    weak scaling) in at most the slowest rank's time."""
+    return world * units_per_rank / (step_ms / 1000.0)
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -429,12 +446,8 @@ def main():
         work = g.work_counts()
         ev1.record(stream)
         torch.cuda.synchronize()
-    step_ms = ev0.elapsed_time(ev1) / args.steps
-    if dist:
-        t = torch.tensor([step_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        step_ms = float(t.item())
-    value = world * m / (step_ms / 1000.0)
+    step_ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, dist, "cuda")
+    value = job_value(world, m, step_ms)
 
     e2e = None
     if not args.no_e2e and rank == 0:
