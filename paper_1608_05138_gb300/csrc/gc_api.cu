@@ -510,7 +510,7 @@ gc_status gc_count_edge_graphlets(gc_graph g, uint64_t* per_edge_out, uint64_t* 
   g->sc.tlist_want = (long long)g->work[kWorkTTriangles];  // the next count keeps pass T's edge lists
 #undef GC_CHECK
   if (hstatus & kSpillOverflow) {
-    set_error("internal: a pass-K unit exceeded its tier");
+    set_error("internal: a unit outgrew its tier, cursor buffer or hash (only for input that skipped validation)");
     return GC_ERR_CUDA;
   }
   if (hstatus & kInexact) {

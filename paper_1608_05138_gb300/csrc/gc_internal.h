@@ -106,6 +106,9 @@ enum Work {
   kNumWork
 };
 
+// Device status bits. kSpillOverflow: a unit outgrew what it was binned for
+// (a pass-T/K tier, the hub cursors, the hashed pass-C table); it cannot
+// happen for a validated graph.
 enum Status : int32_t { kOk = 0, kSpillOverflow = 1, kInexact = 2, kTimeout = 4 };
 
 constexpr int kBlock = 512;            // threads per CTA of passes A and C
