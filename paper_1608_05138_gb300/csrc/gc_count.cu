@@ -387,15 +387,15 @@ __global__ void __launch_bounds__(kHeavyBlock, 1) k_pass_c_heavy(DevGraph g, Cou
           lm &= lm - 1;
           const int32_t s0 = __shfl_sync(0xffffffffu, st, src);
           const int32_t n0 = __shfl_sync(0xffffffffu, L, src);
-          for (int32_t k0 = 0; k0 < n0; k0 += 128) {
-            int32_t o[4];
+          for (int32_t k0 = 0; k0 < n0; k0 += 256) {  // eight windows of loads in flight
+            int32_t o[8];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
+            for (int j = 0; j < 8; ++j) {
               const int32_t kk = k0 + 32 * j + lane;
               o[j] = kk < n0 ? g.ci[s0 + kk] : -1;
             }
 #pragma unroll
-            for (int j = 0; j < 4; ++j)
+            for (int j = 0; j < 8; ++j)
               if (o[j] >= 0) add_count(tab, o[j] - lo_id, half);
           }
         }
@@ -446,15 +446,15 @@ __global__ void __launch_bounds__(kHeavyBlock, 1) k_pass_c_heavy(DevGraph g, Cou
           const int32_t s0 = __shfl_sync(0xffffffffu, st, src);
           const int32_t n0 = __shfl_sync(0xffffffffu, L, src);
           unsigned long long acc = 0ull;
-          for (int32_t k0 = 0; k0 < n0; k0 += 128) {
-            int32_t o[4];
+          for (int32_t k0 = 0; k0 < n0; k0 += 256) {  // eight windows of loads in flight
+            int32_t o[8];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
+            for (int j = 0; j < 8; ++j) {
               const int32_t kk = k0 + 32 * j + lane;
               o[j] = kk < n0 ? g.ci[s0 + kk] : -1;
             }
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
+            for (int j = 0; j < 8; ++j) {
               if (o[j] < 0) continue;
               const uint32_t cnt = read_count(tab, o[j] - lo_id, half) - 1u;
               if (cnt) {
