@@ -13,6 +13,15 @@ per step). e2e = the same metric for the user's host-buffer call sequence
 copies included. The CSR (R-MAT-22: 530 MB) plus the Psi tables exceed the
 129 MB L2, so no extra flush is done between steps.
 
+The default run (R-MAT-22) also measures, on rank 0, the other workloads of
+the method and puts them into the same JSON line: "chung_lu" (n = 1M,
+m = 10M), "er_dense" (1K vertices, 150K edges), "batched" (100 000 small
+graphs in one submission vs the plain per-graph loop) and "serving" (a
+Poisson stream of Chung-Lu requests at 0.5x, 0.9x and 1.2x of the plain
+loop's capacity, p50/p99 latency). Each reports its own timing, clocks and
+parity against the oracle's stored results (tests/golden/large_configs.json,
+written by tests/golden/make_large_digests.py) and against the plain loop.
+
 --impl reference times the CPU oracle (the paper's Alg. 1/5/6 on the host
 cores) on a bounded random sample of edges per step.
 Under torchrun (N > 1) every rank counts its own replica of the graph
@@ -21,6 +30,7 @@ Under torchrun (N > 1) every rank counts its own replica of the graph
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -35,6 +45,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "per-edge 4-node graphlet counts: edges/s at R-MAT-22"
+GOLDEN = os.path.join(ROOT, "tests", "golden", "large_configs.json")
 
 
 def load_workload(name: str, scale: int):
@@ -54,6 +65,27 @@ def load_workload(name: str, scale: int):
     else:
         raise SystemExit(f"unknown workload {name}")
     return rp, ci, desc
+
+
+def golden(name: str):
+    """The oracle's stored results for a workload, or None."""
+    if not os.path.exists(GOLDEN):
+        return None
+    with open(GOLDEN) as f:
+        return json.load(f).get(name)
+
+
+def sha(*arrays) -> str:
+    """SHA-256 of the little-endian bytes of the arrays (the digest of the
+    stored oracle results)."""
+    h = hashlib.sha256()
+    for a in arrays:
+        h.update(np.ascontiguousarray(a).astype(a.dtype.newbyteorder("<"), copy=False).tobytes())
+    return h.hexdigest()
+
+
+def lohi(xs) -> np.ndarray:
+    return np.array([[x & (2**64 - 1), x >> 64] for x in xs], np.uint64).reshape(-1, 2)
 
 
 def algorithmic_bytes(work: dict) -> dict:
@@ -78,11 +110,14 @@ def algorithmic_bytes(work: dict) -> dict:
     }
 
 
+PHASE_OF = {"k_pass_t": "pass_t_triangles", "k_pass_c": "pass_c_cycles", "k_pass_k": "pass_k_cliques",
+            "k_finish": "finish_columns"}
+
+
 def measured_traffic(phase: str, workload: str, scale: int):
     """DRAM bytes per count of a phase from the committed ncu launch list
     (profiles/roofline_traffic_rmat22.txt), or None when the workload differs
     or the kernel sources changed since the counters were taken."""
-    import hashlib
     path = os.path.join(ROOT, "profiles", "roofline_traffic_rmat22.txt")
     if workload != "rmat22" or scale != 22 or not os.path.exists(path):
         return None
@@ -110,6 +145,15 @@ def paper_method_bytes(rp, ci):
     low = (deg[rows] < deg[cols]) | ((deg[rows] == deg[cols]) & (rows < cols))
     du, dv = deg[rows[low]], deg[cols[low]]
     return int(4 * (du.sum() + dv.sum() + (S[rows[low]] - dv).sum()) + 120 * len(du))
+
+
+def peak_hbm():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
 
 
 class ClockSampler:
@@ -195,6 +239,36 @@ def job_value(world: int, units_per_rank: int, step_ms: float) -> float:
     return world * units_per_rank / (step_ms / 1000.0)
 
 
+def roofline(work: dict, phases: dict, peak: float, peak_src: str, traffic_of=None) -> dict:
+    """Roofline of the dominant counting kernel (the phase with the most
+    device time). achieved/frac: the algorithmic bytes of the implemented
+    method (gc_graph_work_counts x the per-unit figures of algorithmic_bytes)
+    per second of kernel time; they count the 8-byte read-modify-write of
+    every wedge's 4-cycle counter, which L2 mostly serves, as HBM bytes.
+    achieved_dram/frac_dram: the DRAM bytes ncu measured for the same phase
+    (traffic, per count) per second of kernel time -- the fraction of the
+    HBM roofline the kernel actually uses."""
+    kernel_ms = {k: phases[ph] for k, ph in PHASE_OF.items()}
+    ab = algorithmic_bytes(work)
+    total = sum(kernel_ms.values()) or 1.0
+    kernels = {k: {"ms": kernel_ms[k], "algorithmic_bytes": ab[k],
+                   "gbs": ab[k] / (kernel_ms[k] / 1000.0) / 1e9 if kernel_ms[k] > 0 else None,
+                   "share": kernel_ms[k] / total} for k in kernel_ms}
+    dom = max(kernel_ms, key=kernel_ms.get)
+    achieved = kernels[dom]["gbs"] or 0.0
+    traffic = traffic_of(PHASE_OF[dom]) if traffic_of else None
+    a_dram = traffic / (kernel_ms[dom] / 1000.0) / 1e9 if traffic and kernel_ms[dom] > 0 else None
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "basis": "algorithmic bytes of the implemented method per kernel second (an 8-byte atomic per "
+                     "wedge counted as HBM traffic, though L2 serves most of it)",
+            "achieved_dram": a_dram, "frac_dram": a_dram / peak if a_dram else None,
+            "basis_dram": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the phase per kernel second",
+            "peak_source": peak_src, "kernel": dom, "phase": PHASE_OF[dom], "kernel_ms": kernel_ms[dom],
+            "algorithmic_bytes": ab[dom], "traffic": traffic,
+            "traffic_source": "profiles/launches_rmat22_count.md (ncu dram__bytes_read+write per count)",
+            "kernels": kernels}
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -231,12 +305,58 @@ def _pct(xs, q):
     return xs[min(len(xs) - 1, int(round(q * (len(xs) - 1))))] if xs else None
 
 
-def run_batched(args):
-    """Batched form: many small graphs in one launch of the batch runtime
+# ---------------- whole-graph counts of the other workloads ----------------
+
+def timed_counts(name: str, steps: int, warmup: int, gpu_index: int = 0) -> dict:
+    """Whole-graph counts of one workload through the C ABI (per-edge rows to
+    device memory), timed with CUDA events on the graph's stream, and the
+    result compared with the oracle's stored digests."""
+    import torch
+    import paper_1608_05138_gb300 as gcb
+    rp, ci, desc = load_workload(name, 22)
+    m = len(ci) // 2
+    stream = torch.cuda.current_stream()
+    peak, peak_src = peak_hbm()
+    with gcb.Graph(rp, ci, stream=stream) as g:
+        pe = torch.empty((m, 13), dtype=torch.int64, device="cuda")
+        for _ in range(warmup):
+            X = g.count(pe)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        phases = []
+        with ClockSampler(gpu_index) as clk:
+            ev0.record(stream)
+            for _ in range(steps):
+                X = g.count(pe)
+                phases.append(g.phase_ms())
+            ev1.record(stream)
+            torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1) / steps
+        work = g.work_counts()
+        csums = g.csums()
+        host = pe.cpu().numpy().view(np.uint64)
+    ph_ms = {k: statistics.mean(p[k] for p in phases) for k in phases[0]}
+    gold = golden(name)
+    parity = {"reference": "oracle results stored in tests/golden/large_configs.json"}
+    if gold:
+        parity.update({"csr_equal": sha(rp, ci) == gold["csr_sha256"],
+                       "per_edge_rows_equal": sha(host) == gold["per_edge_sha256"],
+                       "X_equal": X == gold["X"], "csums_equal": csums == gold["csum"]})
+    else:
+        parity["missing"] = True
+    return {"workload": desc, "n": len(rp) - 1, "m": m, "edges_per_s": m / (ms / 1000.0), "ms_per_count": ms,
+            "steps": steps, "warmup": warmup, "phases_ms": ph_ms, "clocks": clk.summary(),
+            "roofline": roofline(work, ph_ms, peak, peak_src), "gpu_launches": int(work["launches"]) * steps,
+            "parity": parity}
+
+
+# ---------------- batched form ----------------
+
+def run_batched(args, standalone: bool = True):
+    """Batched form: many small graphs in one submission to the batch runtime
     (gc_batch_*), against the plain per-graph loop (upload, count, free).
     Wall-clock through the C ABI from host CSR to host results."""
     import graphgen
-    import oracle
     import paper_1608_05138_gb300 as gcb
     from paper_1608_05138_gb300 import build as gcbuild
     gcbuild.build()
@@ -251,44 +371,55 @@ def run_batched(args):
         with gcb.Graph(*B.graph(i)) as g:
             plain[i] = g.count()
     plain_gps = len(idx) / (time.perf_counter() - t0)
-    times, res = [], None
-    for step in range(args.warmup + args.steps):
-        b = gcb.gc_batch_create(200 << 30, gcb.GC_BATCH_MANUAL)
-        t0 = time.perf_counter()
-        tickets = [int(t) for t in gcb.gc_batch_submit_many(b, B.nvert, B.voff, B.eoff, B.row_ptr, B.col_idx)]
-        t1 = time.perf_counter()
-        gcb.gc_batch_flush(b)
-        t2 = time.perf_counter()
-        out = [gcb.gc_batch_poll(b, t, timeout_us=-1) for t in tickets]
-        dt = time.perf_counter() - t0
-        gcb.gc_batch_destroy(b)
-        if step >= args.warmup:
-            times.append(dt)
-            split = {"submit_s": t1 - t0, "flush_s": t2 - t1, "poll_s": t0 + dt - t2}
-        res = out
+    times, res, split = [], None, {}
+    steps, warmup = (args.steps, args.warmup) if standalone else (min(args.steps, 3), 1)
+    with ClockSampler(0) as clk:
+        for step in range(warmup + steps):
+            b = gcb.gc_batch_create(200 << 30, gcb.GC_BATCH_MANUAL)
+            t0 = time.perf_counter()
+            tickets = [int(t) for t in gcb.gc_batch_submit_many(b, B.nvert, B.voff, B.eoff, B.row_ptr, B.col_idx)]
+            t1 = time.perf_counter()
+            gcb.gc_batch_flush(b)
+            t2 = time.perf_counter()
+            out = [gcb.gc_batch_poll(b, t, timeout_us=-1) for t in tickets]
+            dt = time.perf_counter() - t0
+            gcb.gc_batch_destroy(b)
+            if step >= warmup:
+                times.append(dt)
+                split = {"submit_s": t1 - t0, "flush_s": t2 - t1, "poll_s": t0 + dt - t2}
+            res = out
     mism = sum(res[i] != plain[i] for i in idx)
-    orc = list(range(0, G, max(1, G // 20)))
-    omis = sum(res[i] != oracle.count(*B.graph(i), per_edge=False)["X"] for i in orc)
+    parity = {"vs_plain_sample": f"{len(idx) - mism}/{len(idx)} equal"}
+    gold = golden("batched") if G == 100_000 else None
+    if gold:
+        X = np.stack([lohi(x) for x in res])
+        chunks = [sha(X[c:c + gold["chunk"]]) for c in range(0, G, gold["chunk"])]
+        parity["vs_oracle"] = (f"{sum(a == b for a, b in zip(chunks, gold['chunk_sha256']))}/{len(chunks)} chunks of "
+                               f"{gold['chunk']} graphs equal; all {G}: {sha(X) == gold['X_sha256']}")
+        parity["csr_equal"] = sha(B.nvert, B.voff, B.eoff, B.row_ptr, B.col_idx) == gold["csr_sha256"]
     dt = statistics.mean(times)
     line = {"metric": "batched form: graphs/s, 100k small graphs in one launch vs the plain per-graph loop",
-            "value": G / dt, "unit": "graphs/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "value": G / dt, "unit": "graphs/s", "n_gpus": 1, "steps": steps, "warmup": warmup,
             "ms_per_step": 1000 * dt, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "int64", "data": "synthetic",
             "config": {"workload": f"{G} graphs, n uniform in [20, 500], half ER p in [0.05, 0.5], half "
                                    "Chung-Lu gamma in [2, 3]", "edges": edges},
             "edges_per_s": edges / dt, "plain_loop_graphs_per_s": plain_gps, "time_split": split,
-            "speedup_vs_plain_loop": (G / dt) / plain_gps,
-            "parity": {"vs_plain_sample": f"{len(idx) - mism}/{len(idx)} equal",
-                       "vs_oracle_sample": f"{len(orc) - omis}/{len(orc)} equal"},
+            "speedup_vs_plain_loop": (G / dt) / plain_gps, "clocks": clk.summary(), "parity": parity,
             "e2e": {"value": G / dt, "unit": "graphs/s", "h2d_bytes_per_step": int(B.row_ptr.nbytes + B.col_idx.nbytes),
                     "d2h_bytes_per_step": G * 17 * 16, "includes": "validation, copy-in, count, results to host"}}
-    print(json.dumps(line))
+    if standalone:
+        print(json.dumps(line))
+    return line
 
 
-def run_serving(args):
+# ---------------- serving form ----------------
+
+def run_serving(args, standalone: bool = True):
     """Serving form: a Poisson stream of Chung-Lu graphs (m log-uniform in
     [1e3, 2e6]) served by the continuous-batching runtime (120 GB budget),
-    against the plain per-request loop; latency = arrival -> result."""
+    against the plain per-request loop; latency = arrival -> result. The
+    arrival rate is swept over --rate-factors x the plain loop's capacity."""
     import threading as th
     import graphgen
     import paper_1608_05138_gb300 as gcb
@@ -298,14 +429,12 @@ def run_serving(args):
     params = graphgen.serving_params(R)
     graphs = [graphgen.serving_graph(params, r) for r in range(R)]
     sizes = [len(c) // 2 for _, c in graphs]
-    # warm up the device and the library
-    with gcb.Graph(*graphs[0]) as g:
+    with gcb.Graph(*graphs[0]) as g:  # warm up the device and the library
         g.count()
 
     def plain_serve(arrivals):
-        lat, done = [], []
+        lat, done, res = [], [], []
         t0 = time.perf_counter()
-        res = []
         for r in range(R):
             now = time.perf_counter() - t0
             if arrivals[r] > now:
@@ -319,9 +448,7 @@ def run_serving(args):
 
     def batched_serve(arrivals):
         b = gcb.gc_batch_create(120 << 30, 0)
-        tickets = [None] * R
-        fin = [None] * R
-        res = [None] * R
+        tickets, fin, res = [None] * R, [None] * R, [None] * R
         t0 = time.perf_counter()
 
         def submitter():
@@ -351,35 +478,63 @@ def run_serving(args):
             time.sleep(0.0002)
         sub.join()
         gcb.gc_batch_destroy(b)
-        lat = [fin[r] - arrivals[r] for r in range(R)]
-        return lat, max(fin), res
+        return [fin[r] - arrivals[r] for r in range(R)], max(fin), res
 
-    zero = [0.0] * R
-    _, t_plain_cap, res_plain = plain_serve(zero)
-    cap_plain = R / t_plain_cap
-    _, t_batch_cap, res_batch = batched_serve(zero)
-    cap_batch = R / t_batch_cap
-    rate = args.rate_factor * cap_plain
-    gaps = np.asarray(params["gap"], np.float64) / rate
-    arrivals = list(np.cumsum(gaps) - gaps[0])
-    lat_p, span_p, _ = plain_serve(arrivals)
-    lat_b, span_b, res_b2 = batched_serve(arrivals)
-    same = sum(a == b for a, b in zip(res_plain, res_batch)) + sum(a == b for a, b in zip(res_plain, res_b2))
+    with ClockSampler(0) as clk:
+        zero = [0.0] * R
+        _, t_plain_cap, res_plain = plain_serve(zero)
+        cap_plain = R / t_plain_cap
+        _, t_batch_cap, res_batch = batched_serve(zero)
+        cap_batch = R / t_batch_cap
+        same, total = sum(a == b for a, b in zip(res_plain, res_batch)), R
+        sweep = []
+        for f in args.rate_factors:
+            rate = f * cap_plain
+            gaps = np.asarray(params["gap"], np.float64) / rate
+            arrivals = list(np.cumsum(gaps) - gaps[0])
+            lat_p, span_p, _ = plain_serve(arrivals)
+            lat_b, span_b, res_b = batched_serve(arrivals)
+            same += sum(a == b for a, b in zip(res_plain, res_b))
+            total += R
+            sweep.append({"rate_factor": f, "arrival_rate_graphs_per_s": rate,
+                          "served": {"graphs_per_s": R / span_b, "edges_per_s": sum(sizes) / span_b,
+                                     "p50_ms": 1000 * _pct(lat_b, 0.5), "p99_ms": 1000 * _pct(lat_b, 0.99)},
+                          "plain_loop": {"graphs_per_s": R / span_p, "edges_per_s": sum(sizes) / span_p,
+                                         "p50_ms": 1000 * _pct(lat_p, 0.5), "p99_ms": 1000 * _pct(lat_p, 0.99)}})
+    parity = {"vs_plain_loop": f"{same}/{total} served results equal to the plain loop's"}
+    gold = golden("serving")
+    if gold and gold["requests"] == R:
+        ok = sum(res_batch[q["request"]] == q["X"] and res_plain[q["request"]] == q["X"] for q in gold["graphs"])
+        parity["vs_oracle"] = f"{ok}/{len(gold['graphs'])} requests of >= {gold['min_edges']} edges equal"
+    main_pt = min(sweep, key=lambda s: abs(s["rate_factor"] - 0.9))
     line = {"metric": "serving form: graphs/s and p50/p99 latency (ms), Poisson stream, continuous batching",
-            "value": R / span_b, "unit": "graphs/s", "n_gpus": 1, "steps": 1, "warmup": 1,
-            "ms_per_step": 1000 * span_b, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "int64", "data": "synthetic",
+            "value": main_pt["served"]["graphs_per_s"], "unit": "graphs/s", "n_gpus": 1, "steps": 1, "warmup": 1,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic",
             "config": {"workload": f"{R} Chung-Lu requests, m log-uniform in [1e3, 2e6], gamma in [2.1, 2.5], "
-                                   "n = max(64, m/8), budget 120 GB", "edges": int(sum(sizes)),
-                       "arrival_rate_graphs_per_s": rate},
-            "served": {"graphs_per_s": R / span_b, "edges_per_s": sum(sizes) / span_b,
-                       "p50_ms": 1000 * _pct(lat_b, 0.5), "p99_ms": 1000 * _pct(lat_b, 0.99)},
-            "plain_loop": {"graphs_per_s": R / span_p, "edges_per_s": sum(sizes) / span_p,
-                           "p50_ms": 1000 * _pct(lat_p, 0.5), "p99_ms": 1000 * _pct(lat_p, 0.99)},
+                                   "n = max(64, m/8), budget 120 GB", "edges": int(sum(sizes))},
             "capacity": {"plain_loop_graphs_per_s": cap_plain, "batched_graphs_per_s": cap_batch,
                          "speedup": cap_batch / cap_plain},
-            "parity": f"{same}/{2 * R} results equal to the plain loop's"}
-    print(json.dumps(line))
+            "sweep": sweep, "clocks": clk.summary(), "parity": parity}
+    if standalone:
+        print(json.dumps(line))
+    return line
+
+
+def run_extras(args) -> dict:
+    """The other workloads of the default run (rank 0, one GPU)."""
+    out = {}
+    for name, fn in (("chung_lu", lambda: timed_counts("chung_lu", 10, 3)),
+                     ("er_dense", lambda: timed_counts("er_dense", 10, 3)),
+                     ("batched", lambda: run_batched(args, standalone=False)),
+                     ("serving", lambda: run_serving(args, standalone=False))):
+        t0 = time.perf_counter()
+        try:
+            out[name] = fn()
+        except Exception as exc:  # reported in the line; the headline stands
+            out[name] = {"error": f"{type(exc).__name__}: {exc}"}
+        out[name]["wall_s"] = round(time.perf_counter() - t0, 1)
+    return out
 
 
 def main():
@@ -392,10 +547,12 @@ def main():
                                                               "serving"])
     ap.add_argument("--graphs", type=int, default=100_000, help="batched: number of graphs")
     ap.add_argument("--requests", type=int, default=300, help="serving: number of requests")
-    ap.add_argument("--rate-factor", type=float, default=0.9, help="serving: arrival rate / plain-loop capacity")
+    ap.add_argument("--rate-factors", type=lambda s: [float(x) for x in s.split(",")], default=[0.5, 0.9, 1.2],
+                    help="serving: arrival rates as multiples of the plain loop's capacity")
     ap.add_argument("--scale", type=int, default=22)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="R-MAT line only (no other workloads)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -474,6 +631,7 @@ def main():
                "ms": 1000 * dt, "includes": "validation, upload, preparation, count, per-edge rows to host",
                "split_ms": {"upload": 1000 * (t1 - t0), "count_with_rows_to_host": 1000 * (t2 - t1),
                             "free": 1000 * (t0 + dt - t2)}}
+        del host_pe
     else:
         g.close()
 
@@ -481,30 +639,11 @@ def main():
         if dist:
             dist.destroy_process_group()
         return
-    with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) if os.path.exists(
-            os.path.join(ROOT, "MEASURED_PEAKS.json")) else open(os.devnull) as f:
-        try:
-            peaks = json.load(f)
-            peak, peak_src = float(peaks["hbm_gbs"]), "measured"
-        except Exception:
-            peak, peak_src = 6800.0, "fallback"
+    peak, peak_src = peak_hbm()
     ph_ms = {k: statistics.mean(p[k] for p in phases) for k in phases[0]}
-    phase_of = {"k_pass_t": "pass_t_triangles", "k_pass_c": "pass_c_cycles", "k_pass_k": "pass_k_cliques",
-                "k_finish": "finish_columns"}
-    kernel_ms = {k: ph_ms[ph] for k, ph in phase_of.items()}
-    ab = algorithmic_bytes(work)
-    kernels = {k: {"ms": kernel_ms[k], "algorithmic_bytes": ab[k],
-                   "gbs": ab[k] / (kernel_ms[k] / 1000.0) / 1e9 if kernel_ms[k] > 0 else None,
-                   "share": kernel_ms[k] / sum(kernel_ms.values())} for k in kernel_ms}
-    dom = max(kernel_ms, key=kernel_ms.get)
-    achieved = kernels[dom]["gbs"]
-    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "peak_source": peak_src, "kernel": dom, "phase": phase_of[dom], "kernel_ms": kernel_ms[dom],
-            "algorithmic_bytes": ab[dom],
-            "traffic": measured_traffic(phase_of[dom], args.workload, args.scale),
-            "traffic_source": "profiles/launches_rmat22_count.md (ncu dram__bytes_read+write per count)",
-            "kernels": kernels,
-            "logical_paper_method_gbs": paper_method_bytes(rp, ci) / (step_ms / 1000.0) / 1e9}
+    roof = roofline(work, ph_ms, peak, peak_src,
+                    traffic_of=lambda ph: measured_traffic(ph, args.workload, args.scale))
+    roof["logical_paper_method_gbs"] = paper_method_bytes(rp, ci) / (step_ms / 1000.0) / 1e9
     line = {"metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int64", "data": "synthetic",
@@ -515,6 +654,9 @@ def main():
             "e2e": e2e}
     if not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(rp, ci, m)
+    if world == 1 and args.workload == "rmat22" and args.scale == 22 and not args.no_extra:
+        del rp, ci
+        line.update(run_extras(args))
     print(json.dumps(line))
     if dist:
         dist.destroy_process_group()

@@ -83,8 +83,31 @@ static void* gg_rs_scatter(void* a) {
   return NULL;
 }
 
+/* Small arrays (the graphs of a batch): 8-bit digits with the histogram on
+ * the stack, so that many threads sorting small arrays at once do not
+ * allocate and clear large histograms. Same sorted output. */
+static int gg_radix_sort_small(uint64_t* a, int64_t n, int key_bits) {
+  uint64_t* tmp = (uint64_t*)malloc((size_t)n * sizeof(uint64_t));
+  if (!tmp) return -1;
+  uint64_t* src = a; uint64_t* dst = tmp;
+  int64_t cnt[256];
+  for (int shift = 0; shift < key_bits; shift += 8) {
+    memset(cnt, 0, sizeof(cnt));
+    for (int64_t i = 0; i < n; ++i) cnt[(src[i] >> shift) & 0xFF]++;
+    if (cnt[(src[0] >> shift) & 0xFF] == n) continue;  /* one digit value: order unchanged */
+    int64_t s = 0;
+    for (int d = 0; d < 256; ++d) { int64_t c = cnt[d]; cnt[d] = s; s += c; }
+    for (int64_t i = 0; i < n; ++i) dst[cnt[(src[i] >> shift) & 0xFF]++] = src[i];
+    uint64_t* x = src; src = dst; dst = x;
+  }
+  if (src != a) memcpy(a, src, (size_t)n * sizeof(uint64_t));
+  free(tmp);
+  return 0;
+}
+
 static int gg_radix_sort_u64(uint64_t* a, int64_t n, int key_bits) {
   if (n <= 1) return 0;
+  if (n < (1 << 16)) return gg_radix_sort_small(a, n, key_bits);
   int T = gg_threads();
   if (n < (1 << 20)) T = 1;
   uint64_t* tmp = (uint64_t*)malloc((size_t)n * sizeof(uint64_t));
@@ -154,16 +177,21 @@ static int gg_csr_from_pairs(int32_t n, const uint64_t* keys, int64_t m,
 
 static int gg_bits(uint64_t x) { int b = 0; while (x) { ++b; x >>= 1; } return b; }
 
-/* keys: canonical (min << 32 | max); sort + unique + CSR */
-static int gg_finish(int32_t n, uint64_t* keys, int64_t k, int64_t* m_out,
-                     int32_t** rp, int32_t** ci) {
+/* keys: canonical (min << 32 | max); sort + unique + CSR. sorted: the keys
+ * are already strictly ascending (Erdos-Renyi draws pairs in lexicographic
+ * order), so the sort is skipped -- the same result. */
+static int gg_finish_keys(int32_t n, uint64_t* keys, int64_t k, int sorted, int64_t* m_out,
+                          int32_t** rp, int32_t** ci) {
   int bits = 32 + gg_bits((uint64_t)(n > 0 ? n - 1 : 0));
-  if (gg_radix_sort_u64(keys, k, bits) != 0) return -1;
+  if (!sorted && gg_radix_sort_u64(keys, k, bits) != 0) return -1;
   int64_t m = gg_unique_sorted(keys, k);
   while (m > 0 && keys[m - 1] == 0xFFFFFFFFFFFFFFFFULL) --m;  /* dropped self-loops sort last */
   int rc = gg_csr_from_pairs(n, keys, m, rp, ci);
   if (rc == 0) *m_out = m;
   return rc;
+}
+static int gg_finish(int32_t n, uint64_t* keys, int64_t k, int64_t* m_out, int32_t** rp, int32_t** ci) {
+  return gg_finish_keys(n, keys, k, 0, m_out, rp, ci);
 }
 
 /* ---------------- Erdos-Renyi G(n, p) ---------------- */
@@ -404,7 +432,7 @@ static void* gg_batch_worker(void* arg) {
       uint64_t* keys = (uint64_t*)malloc((size_t)(pairs > 0 ? pairs : 1) * sizeof(uint64_t));
       if (!keys) { j->rc = -1; break; }
       int64_t k = gg_er_keys(bp.n, bp.p_or_gamma, gg_key(bp.seed2, 1), keys);
-      rc = gg_finish(bp.n, keys, k, &m, &j->rps[g], &j->cis[g]);
+      rc = gg_finish_keys(bp.n, keys, k, 1, &m, &j->rps[g], &j->cis[g]);
       free(keys);
     } else {
       int64_t mt = (int64_t)((double)bp.n * bp.dbar / 2.0 + 0.5);

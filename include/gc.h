@@ -55,7 +55,8 @@ enum {
   GC_ERR_NOMEM = -7,       /* device or host allocation failed */
   GC_ERR_CUDA = -8,        /* a CUDA call failed (message has the CUDA error) */
   GC_ERR_OVERFLOW = -9,    /* 2m >= 2^31, or a high word is needed but global_hi is NULL */
-  GC_ERR_TIMEOUT = -10,    /* a bounded device wait gave up (device status word set) */
+  GC_ERR_TIMEOUT = -10,    /* reserved: no call returns it (no kernel of this library waits
+                              on another CTA, stream or device) */
   GC_ERR_BUSY = -11        /* gc_batch_submit: the device-memory budget is full */
 };
 
@@ -182,7 +183,7 @@ gc_status gc_graph_free(gc_graph g);
  *   forever) for the ticket. GC_OK: global_out/global_hi (17 words each, hi
  *   may be NULL as above) hold X_1..X_17 and the ticket is retired; GC_PENDING:
  *   not finished; GC_ERR_ARG: unknown or already retired ticket;
- *   GC_ERR_TIMEOUT: the device reported a bounded wait that gave up.
+ *   GC_ERR_CUDA: the launch that held the ticket failed (message says how).
  * gc_batch_destroy: waits for outstanding work and frees everything.
  */
 #define GC_BATCH_MANUAL 0x1u
@@ -206,15 +207,16 @@ gc_status gc_batch_destroy(gc_batch b);
 /*
  * Triangle counts per CSR slot without any memory allocation.
  *
- * For callers that cannot allocate device memory (a fixed arena, a stream
- * under capture, an allocator callback, a budget that forbids growth). The
+ * For callers that cannot allocate device memory (a fixed arena, an
+ * allocator callback, a budget that forbids growth). The
  * paper has no counterpart: it is a variant of the triangle step that reads
  * the caller's device CSR in place and uses, as its only scratch, a 32 MiB
  * file-scope device array (256 bitmaps of 2^20 bits) that every GPU loading
  * libgc.so holds until the process exits.
  *   n        vertices, 0 <= n <= 1,048,576; larger n returns GC_ERR_OVERFLOW
  *   row_ptr  device pointer, n + 1 int32 (same CSR rules as gc_graph_upload;
- *            not validated here)
+ *            not validated here: a column index outside [0, n) is skipped,
+ *            and a slot whose column is outside gets 0)
  *   col_idx  device pointer, row_ptr[n] int32
  *   tri_out  device pointer, row_ptr[n] int32: tri_out[p] = |Gamma(x) ∩ Gamma(y)|
  *            for the slot p = (x, y) (both directions of an edge get its |T|)
@@ -222,6 +224,8 @@ gc_status gc_batch_destroy(gc_batch b);
  * Asynchronous on `stream`; calls no cudaMalloc/cudaFree. The first call on a
  * device, with that device current, looks up the array's device address
  * (cudaGetSymbolAddress) -- make that first call before any stream capture.
+ * The address is kept per device ordinal for the life of the process: it
+ * assumes the runtime's primary context and no cudaDeviceReset afterwards.
  * All calls share the array and each call clears it first: calls whose
  * kernels overlap on the GPU (other streams, other threads) race and give
  * wrong results.

@@ -295,10 +295,39 @@ def gc_batch_destroy(b):
 
 # ---------------- allocation-free triangle step ----------------
 
+def _noalloc_args(row_ptr, col_idx, tri_out):
+    """The C entry point takes raw device pointers and cannot see sizes or
+    types, so a wrong tensor here would make its kernel read or write past a
+    buffer: every check happens before the call. Returns n."""
+    import torch
+    named = (("row_ptr", row_ptr), ("col_idx", col_idx), ("tri_out", tri_out))
+    for name, t in named:
+        if not isinstance(t, torch.Tensor):
+            raise ValueError(f"{name} must be a torch tensor")
+        if t.dtype != torch.int32:
+            raise ValueError(f"{name} must be int32, not {t.dtype}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+    if row_ptr.dim() != 1 or row_ptr.numel() < 1:
+        raise ValueError("row_ptr must be a 1-D tensor of n + 1 >= 1 entries")
+    if tri_out.numel() < col_idx.numel():
+        raise ValueError(f"tri_out holds {tri_out.numel()} entries, fewer than the {col_idx.numel()} slots of col_idx")
+    devs = {t.device for _, t in named}
+    if len(devs) != 1 or next(iter(devs)).type != "cuda":
+        raise ValueError("row_ptr, col_idx and tri_out must be on the same CUDA device")
+    nnz = int(row_ptr[-1].item())  # one 4-byte read back; allocates no device memory
+    if nnz < 0 or nnz > col_idx.numel():
+        raise ValueError(f"row_ptr[n] = {nnz} does not fit col_idx of {col_idx.numel()} entries")
+    return row_ptr.numel() - 1
+
+
 def gc_edge_triangles_noalloc(row_ptr, col_idx, tri_out, stream=None):
     """Per-slot triangle counts from a device CSR into a device int32 buffer,
     with no memory allocation (see include/gc.h). row_ptr, col_idx and
-    tri_out are contiguous int32 CUDA tensors; runs asynchronously."""
-    n = row_ptr.numel() - 1
+    tri_out are contiguous int32 tensors on one CUDA device, tri_out with at
+    least col_idx.numel() entries (ValueError otherwise); the library reads
+    row_ptr[n] entries of col_idx, so row_ptr must describe col_idx. Runs
+    asynchronously on `stream`."""
+    n = _noalloc_args(row_ptr, col_idx, tri_out)
     _check(lib().gc_edge_triangles_noalloc(n, _ptr(row_ptr), _ptr(col_idx), _ptr(tri_out),
                                            _stream_handle(stream)), "gc_edge_triangles_noalloc")

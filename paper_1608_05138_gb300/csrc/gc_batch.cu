@@ -378,7 +378,7 @@ void retire_locked(gc_batch b) {
       if (L->launch_status == GC_OK) {
         std::memcpy(r.x, L->h_x + 34 * (size_t)L->slot[k], sizeof(r.x));
         int32_t dst = *L->h_status;
-        r.status = dst == 0 ? GC_OK : ((dst & kTimeout) ? GC_ERR_TIMEOUT : GC_ERR_CUDA);
+        r.status = dst == 0 ? GC_OK : GC_ERR_CUDA;
       } else {
         std::memset(r.x, 0, sizeof(r.x));
         r.status = L->launch_status;

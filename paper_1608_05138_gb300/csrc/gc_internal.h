@@ -109,7 +109,7 @@ enum Work {
 // Device status bits. kSpillOverflow: a unit outgrew what it was binned for
 // (a pass-T/K tier, the hub cursors, the hashed pass-C table); it cannot
 // happen for a validated graph.
-enum Status : int32_t { kOk = 0, kSpillOverflow = 1, kInexact = 2, kTimeout = 4 };
+enum Status : int32_t { kOk = 0, kSpillOverflow = 1, kInexact = 2 };
 
 constexpr int kBlock = 512;            // threads per CTA of passes A and C
 constexpr int kCtasPerSm = 2;          // resident CTAs per SM of the persistent grids

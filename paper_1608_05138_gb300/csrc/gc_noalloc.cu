@@ -1,17 +1,17 @@
 // gc_noalloc.cu -- a triangle-count entry point that allocates no memory.
 //
 // Callers that own a fixed memory arena, or that run where a device
-// allocation may not happen at all (inside a stream that is being captured,
-// inside another allocator's callback, under a hard budget that forbids
-// growth), cannot use gc_graph_upload: it allocates the CSR copy, the
-// preparation arrays and the per-CTA tables. This entry point is a variant
+// allocation may not happen at all (inside another allocator's callback,
+// under a hard budget that forbids growth), cannot use gc_graph_upload: it
+// allocates the CSR copy, the preparation arrays and the per-CTA tables. This entry point is a variant
 // of the triangle step (Alg. 1: a Psi bitmap of Gamma(x), probed with the
 // neighbours of each neighbour) that works directly on the caller's device
 // CSR and writes the caller's device output. Its only scratch -- one bitmap
 // per CTA marking Gamma(x) -- lives in a file-scope __device__ array that
 // every GPU loading the library holds until the process exits:
 //   kNoAllocCtas bitmaps x kNoAllocMaxN bits = 256 x 1,048,576 bits = 32 MiB.
-// Graphs with more than kNoAllocMaxN vertices are rejected.
+// Graphs with more than kNoAllocMaxN vertices are rejected. A column index
+// outside [0, n) is skipped (it would otherwise touch another CTA's bitmap).
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -29,7 +29,10 @@ constexpr int kNoAllocBlock = 512;
 
 static __device__ __align__(256) uint32_t g_noalloc_scratch[(size_t)kNoAllocCtas * kNoAllocWords];
 
-// Device address of g_noalloc_scratch, looked up once per device.
+// Device address of g_noalloc_scratch, looked up once per device ordinal and
+// kept for the life of the process: this assumes the device's primary context
+// (the one the CUDA runtime uses) and no cudaDeviceReset in between, after
+// which the cached address would name memory of a context that is gone.
 constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
 uint32_t* g_noalloc_ptr[kMaxDevices] = {};
@@ -52,21 +55,28 @@ __global__ void __launch_bounds__(kNoAllocBlock) k_triangles_noalloc(int32_t n, 
     const int32_t xb = rp[x], xe = rp[x + 1];
     for (int32_t p = xb + threadIdx.x; p < xe; p += kNoAllocBlock) {
       const int32_t w = ci[p];
-      atomicOr(&bm[w >> 5], 1u << (w & 31));
+      if ((uint32_t)w < (uint32_t)n) atomicOr(&bm[w >> 5], 1u << (w & 31));
     }
     __syncthreads();
     for (int32_t p = xb + warp; p < xe; p += warps) {
       const int32_t y = ci[p];
       int c = 0;
+      if ((uint32_t)y >= (uint32_t)n) {  // not a vertex: no row to scan
+        if (lane == 0) tri[p] = 0;
+        continue;
+      }
       for (int32_t q = rp[y] + lane; q < rp[y + 1]; q += 32) {
         const int32_t w = ci[q];
-        c += (bm[w >> 5] >> (w & 31)) & 1u;
+        if ((uint32_t)w < (uint32_t)n) c += (bm[w >> 5] >> (w & 31)) & 1u;
       }
       for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
       if (lane == 0) tri[p] = c;
     }
     __syncthreads();
-    for (int32_t p = xb + threadIdx.x; p < xe; p += kNoAllocBlock) bm[ci[p] >> 5] = 0u;
+    for (int32_t p = xb + threadIdx.x; p < xe; p += kNoAllocBlock) {
+      const int32_t w = ci[p];
+      if ((uint32_t)w < (uint32_t)n) bm[w >> 5] = 0u;
+    }
     __syncthreads();
   }
 }

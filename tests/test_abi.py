@@ -82,3 +82,26 @@ def test_no_fallback_when_library_missing(monkeypatch, tmp_path):
     monkeypatch.setattr(gcb, "_lib", None)
     with pytest.raises(RuntimeError):
         gcb.lib()
+
+
+def test_noalloc_wrapper_rejects_bad_tensors_before_the_call():
+    # the C entry point takes raw device pointers, so the binding checks
+    # type, contiguity, sizes and device before calling it (no GPU needed:
+    # every case below is refused before the library is touched)
+    import torch
+    rp = torch.tensor([0, 1, 2], dtype=torch.int32)
+    ci = torch.tensor([1, 0], dtype=torch.int32)
+    out = torch.zeros(2, dtype=torch.int32)
+    cases = [
+        ((rp.numpy(), ci, out), "torch tensor"),
+        ((rp.long(), ci, out), "int32"),
+        ((rp, ci.long(), out), "int32"),
+        ((rp, ci, out.long()), "int32"),
+        ((rp, torch.zeros(4, dtype=torch.int32)[::2], out), "contiguous"),
+        ((torch.zeros(0, dtype=torch.int32), ci, out), "n + 1"),
+        ((rp, ci, torch.zeros(1, dtype=torch.int32)), "fewer than"),
+        ((rp, ci, out), "same CUDA device"),
+    ]
+    for args, words in cases:
+        with pytest.raises(ValueError, match=re.escape(words)):
+            gcb.gc_edge_triangles_noalloc(*args)
