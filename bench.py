@@ -371,33 +371,43 @@ def run_batched(args, standalone: bool = True):
         with gcb.Graph(*B.graph(i)) as g:
             plain[i] = g.count()
     plain_gps = len(idx) / (time.perf_counter() - t0)
-    times, res, split = [], None, {}
-    steps, warmup = (args.steps, args.warmup) if standalone else (min(args.steps, 3), 1)
-    with ClockSampler(0) as clk:
-        for step in range(warmup + steps):
-            b = gcb.gc_batch_create(200 << 30, gcb.GC_BATCH_MANUAL)
-            t0 = time.perf_counter()
-            tickets = [int(t) for t in gcb.gc_batch_submit_many(b, B.nvert, B.voff, B.eoff, B.row_ptr, B.col_idx)]
-            t1 = time.perf_counter()
-            gcb.gc_batch_flush(b)
-            t2 = time.perf_counter()
-            out = [gcb.gc_batch_poll(b, t, timeout_us=-1) for t in tickets]
-            dt = time.perf_counter() - t0
-            gcb.gc_batch_destroy(b)
-            if step >= warmup:
-                times.append(dt)
-                split = {"submit_s": t1 - t0, "flush_s": t2 - t1, "poll_s": t0 + dt - t2}
-            res = out
-    mism = sum(res[i] != plain[i] for i in idx)
+    times, dev_ms, res, split = [], [], None, {}
+    steps, warmup = (args.steps, args.warmup) if standalone else (min(args.steps, 3), 2)
+    # one runtime for all steps, as a serving process keeps it: its buffers
+    # and its captured launch stay warm (the first steps are the warm-up)
+    b = gcb.gc_batch_create(200 << 30, gcb.GC_BATCH_MANUAL)
+    config = gcb.gc_batch_config(b)
+    try:
+        with ClockSampler(0) as clk:
+            for step in range(warmup + steps):
+                t0 = time.perf_counter()
+                tickets = gcb.gc_batch_submit_many(b, B.nvert, B.voff, B.eoff, B.row_ptr, B.col_idx)
+                t1 = time.perf_counter()
+                gcb.gc_batch_flush(b)
+                t2 = time.perf_counter()
+                out = gcb.gc_batch_poll_many(b, tickets, timeout_us=-1)  # [G][17] (lo, hi)
+                dt = time.perf_counter() - t0
+                stats = gcb.gc_batch_last_stats(b)
+                if step >= warmup:
+                    times.append(dt)
+                    dev_ms.append(stats["small_sequence_ms"] + stats["union_ms"])
+                    split = {"submit_s": t1 - t0, "flush_s": t2 - t1, "poll_s": t0 + dt - t2}
+                res = out
+    finally:
+        gcb.gc_batch_destroy(b)
+    X = res
+    mism = sum(not np.array_equal(X[i], lohi(plain[i])) for i in idx)
     parity = {"vs_plain_sample": f"{len(idx) - mism}/{len(idx)} equal"}
     gold = golden("batched") if G == 100_000 else None
     if gold:
-        X = np.stack([lohi(x) for x in res])
         chunks = [sha(X[c:c + gold["chunk"]]) for c in range(0, G, gold["chunk"])]
         parity["vs_oracle"] = (f"{sum(a == b for a, b in zip(chunks, gold['chunk_sha256']))}/{len(chunks)} chunks of "
                                f"{gold['chunk']} graphs equal; all {G}: {sha(X) == gold['X_sha256']}")
         parity["csr_equal"] = sha(B.nvert, B.voff, B.eoff, B.row_ptr, B.col_idx) == gold["csr_sha256"]
     dt = statistics.mean(times)
+    dms = statistics.mean(dev_ms)
+    csr_bytes = int(B.row_ptr.nbytes + B.col_idx.nbytes)
+    peak, peak_src = peak_hbm()
     line = {"metric": "batched form: graphs/s, 100k small graphs in one launch vs the plain per-graph loop",
             "value": G / dt, "unit": "graphs/s", "n_gpus": 1, "steps": steps, "warmup": warmup,
             "ms_per_step": 1000 * dt, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -406,6 +416,14 @@ def run_batched(args, standalone: bool = True):
                                    "Chung-Lu gamma in [2, 3]", "edges": edges},
             "edges_per_s": edges / dt, "plain_loop_graphs_per_s": plain_gps, "time_split": split,
             "speedup_vs_plain_loop": (G / dt) / plain_gps, "clocks": clk.summary(), "parity": parity,
+            "runtime_config": config, "last_launch": stats,
+            "device": {"ms": dms, "graphs_per_s": G / (dms / 1000.0), "edges_per_s": edges / (dms / 1000.0),
+                       "includes": "copy-in of the packed CSR, bitmatrix kernels, Sec. 4.6 derivation, copy-out"},
+            "roofline": {"bound": "shared memory / issue (bit rows on chip)", "traffic_algorithmic": csr_bytes,
+                         "achieved": csr_bytes / (dms / 1000.0) / 1e9, "peak": peak, "unit": "GB/s",
+                         "frac": csr_bytes / (dms / 1000.0) / 1e9 / peak, "peak_source": peak_src,
+                         "note": "compulsory HBM bytes (the CSR, read once) per device second; the kernels work "
+                                 "on shared-memory bit rows, so this fraction is small by design"},
             "e2e": {"value": G / dt, "unit": "graphs/s", "h2d_bytes_per_step": int(B.row_ptr.nbytes + B.col_idx.nbytes),
                     "d2h_bytes_per_step": G * 17 * 16, "includes": "validation, copy-in, count, results to host"}}
     if standalone:

@@ -126,6 +126,32 @@ gc_status gc_graph_edges(gc_graph g, int32_t* uv);
 gc_status gc_count_edge_graphlets(gc_graph g, uint64_t* per_edge_out, uint64_t* global_out,
                                   uint64_t* global_hi);
 
+/*
+ * The count of gc_count_edge_graphlets, plus per-edge induced 4-node counts.
+ * The paper defines per edge only x3..x5 and the summands of C_7..C_16
+ * (Sec. 4.5); this call adds, for every edge e, the number of 4-vertex sets
+ * containing e whose induced subgraph is H_i (Table 1), for the ten
+ * 4-node graphlets that have an edge:
+ *   induced_out   host or device pointer (as per_edge_out) to
+ *                 m x GC_INDUCED_COLS uint64, row e for edge id e, columns
+ *                   0 H7 4-clique (= x7)     1 H8 chordal cycle
+ *                   2 H9 tailed triangle     3 H10 4-cycle (= x10)
+ *                   4 H11 3-star             5 H12 4-path
+ *                   6 H13 triangle + vertex  7 H14 two disjoint edges
+ *                   8 H15 2-star + vertex    9 H16 edge + two vertices
+ *                 Summed over the edges, column i is |E(H_{i+7})| X_{i+7}
+ *                 (6, 5, 4, 4, 3, 3, 3, 2, 2, 1 edges); every row sums to
+ *                 C(n-2, 2). Must not be NULL when m > 0.
+ *   per_edge_out, global_out, global_hi: as in gc_count_edge_graphlets.
+ * The extra work is the degree sum of the third vertex of every triangle
+ * (pass T), the per-vertex triangle and neighbour-degree sums, and one more
+ * per-edge pass; the scratch (16 bytes per vertex, 8 per edge) is kept with
+ * the graph. Errors: as gc_count_edge_graphlets.
+ */
+#define GC_INDUCED_COLS 10
+gc_status gc_count_edge_induced(gc_graph g, uint64_t* induced_out, uint64_t* per_edge_out, uint64_t* global_out,
+                                uint64_t* global_hi);
+
 /* The 13 unrestricted counts C_3, C_4, C_5, C_7, C_8, ..., C_16 (Sec. 4.5) of
  * the last gc_count_edge_graphlets on g, as low/high 64-bit words (host
  * pointers, 13 each; hi may be NULL). GC_ERR_ARG if g was never counted. */
@@ -136,7 +162,8 @@ gc_status gc_graph_csums(gc_graph g, uint64_t* lo, uint64_t* hi);
  * gc_phase_count() doubles. Phases, in order: "pass_t_triangles" (Alg. 1),
  * "pass_c_cycles" (4-cycles through each edge, Alg. 4/6), "pass_k_cliques"
  * (4-cliques and cross terms, Alg. 3/5), "finish_columns" (Sec. 4.5 columns
- * and sums), "derive" (Sec. 4.6), "copy_out". */
+ * and sums), "induced_columns" (gc_count_edge_induced only; empty otherwise),
+ * "derive" (Sec. 4.6), "copy_out". */
 int gc_phase_count(void);
 const char* gc_phase_name(int i);
 gc_status gc_graph_phase_ms(gc_graph g, double* ms);
@@ -156,8 +183,14 @@ gc_status gc_graph_phase_ms(gc_graph g, double* ms);
  *  10 pass T: out-list entries scanned
  *  11 pass T: triangles (each once)
  *  12 pass C: wedges of the units counted in a shared-memory hash
+ *  13 pass C: jobs of the hub kernel (hub units cut into ranges of o-range
+ *     blocks, Sec. 4.4's finer granularity)
+ *  14 pass C: CTAs of the hub kernel
+ *  15 pass C: sum over those CTAs of their lifetime, ns (%globaltimer)
+ *  16 pass C: the longest of those lifetimes, ns (15 / 14 against 16 is the
+ *     kernel's tail)
  * Used to turn kernel times into algorithmic bytes per second. */
-#define GC_NUM_WORK 13
+#define GC_NUM_WORK 17
 gc_status gc_graph_work_counts(gc_graph g, uint64_t* out);
 
 /* Release the graph and all its device memory. NULL is accepted. */
@@ -202,7 +235,49 @@ gc_status gc_batch_submit_many(gc_batch b, int64_t G, const int32_t* nvert, cons
 gc_status gc_batch_flush(gc_batch b);
 gc_status gc_batch_poll(gc_batch b, uint64_t ticket, uint64_t* global_out, uint64_t* global_hi,
                         int32_t timeout_us);
+/* Waits (as gc_batch_poll) until all G tickets are done, then writes their
+ * X_1..X_17 to global_out[17 g .. 17 g + 16] (and the high words to
+ * global_hi, which may be NULL as above) and retires them. GC_PENDING: not
+ * all done within timeout_us, nothing retired; GC_ERR_ARG: a ticket unknown
+ * or retired; a failed launch's status if one of them failed (all are
+ * retired). Host pointers. */
+gc_status gc_batch_poll_many(gc_batch b, int64_t G, const uint64_t* tickets, uint64_t* global_out,
+                             uint64_t* global_hi, int32_t timeout_us);
 gc_status gc_batch_destroy(gc_batch b);
+
+/*
+ * Tuning of the batched form. Graphs of at most GC_PARAM_SMALL_N_MAX vertices
+ * are counted one CTA per graph on a shared-memory bitmatrix (Alg. 1/5/6 as
+ * bit operations), binned by vertex count into size classes n <= 64, 128,
+ * 256, 512 and 1024, each class with its own block size; larger graphs go
+ * through the general passes as one disjoint union. The small-graph sequence
+ * of a launch (copies in, kernels, Sec. 4.6 derivation, copy out) is
+ * captured into a CUDA graph and replayed (GC_PARAM_USE_GRAPH = 1), or
+ * issued eagerly with a timer per size class (0). gc_batch_create takes the
+ * defaults (512; 256 threads per class; 1), then the tuning cache's entry for
+ * the GPU if there is one: the JSON file named by the environment variable
+ * GC_TUNE_CACHE, else tune_cache.json beside libgc.so, written by the tuner
+ * (paper_1608_05138_gb300/tune.py). Results are identical under every
+ * setting. A parameter applies to launches taken after the call.
+ *   GC_PARAM_SMALL_N_MAX   0 .. 1024
+ *   GC_PARAM_BLOCK_N64 + c threads per CTA of size class c (n <= 64, 128,
+ *                          256, 512, 1024): 64, 128, 256 or 512
+ *   GC_PARAM_USE_GRAPH     0 or 1
+ * Errors: GC_ERR_ARG (unknown parameter or value out of range).
+ */
+#define GC_PARAM_SMALL_N_MAX 0
+#define GC_PARAM_BLOCK_N64 1
+#define GC_PARAM_USE_GRAPH 6
+gc_status gc_batch_set_param(gc_batch b, int32_t param, int32_t value);
+gc_status gc_batch_get_param(gc_batch b, int32_t param, int32_t* value);
+
+/* Device times (ms, CUDA events) of the last launch the batch retired, as
+ * GC_BATCH_STATS doubles: [0..4] the bitmatrix kernel of each size class
+ * (eager launches only, else 0), [5] the whole small-graph sequence, [6] the
+ * larger graphs' passes, [7] 1 if the small-graph sequence was replayed from
+ * a CUDA graph. */
+#define GC_BATCH_STATS 8
+gc_status gc_batch_last_stats(gc_batch b, double* out);
 
 /*
  * Triangle counts per CSR slot without any memory allocation.

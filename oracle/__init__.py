@@ -51,6 +51,7 @@ def lib():
             L.oracle_count.argtypes = [C.c_int32, vp, vp, C.c_int, vp, vp, vp, vp, vp]
             L.oracle_count_sample.argtypes = [C.c_int32, vp, vp, C.c_int, vp, C.c_int64, vp]
             L.oracle_derive.argtypes = [C.c_int64, C.c_int64, vp, vp, vp, vp]
+            L.oracle_count_induced.argtypes = [C.c_int32, vp, vp, C.c_int, vp, C.c_int64, vp]
             _lib = L
     return _lib
 
@@ -102,6 +103,28 @@ def count_sample(row_ptr, col_idx, edge_ids, threads: int | None = None):
     out = np.zeros((len(ids), 13), np.uint64)
     rc = lib().oracle_count_sample(len(rp) - 1, _p(rp), _p(ci), threads or default_threads(),
                                    _p(ids), len(ids), _p(out))
+    if rc != 0:
+        raise IndexError("oracle: edge id out of range")
+    return out
+
+
+INDUCED = ["H7", "H8", "H9", "H10", "H11", "H12", "H13", "H14", "H15", "H16"]
+
+
+def count_induced(row_ptr, col_idx, edge_ids=None, threads: int | None = None):
+    """Per-edge induced 4-node counts (uint64 [k, 10], columns H7..H16 of
+    Table 1): for each edge, the number of 4-vertex sets containing it whose
+    induced subgraph is H_i. All edges in edge-id order, or the given ids."""
+    rp = np.ascontiguousarray(row_ptr, np.int32)
+    ci = np.ascontiguousarray(col_idx, np.int32)
+    m = int(rp[-1]) // 2
+    ids = None if edge_ids is None else np.ascontiguousarray(edge_ids, np.int64)
+    k = m if ids is None else len(ids)
+    out = np.zeros((k, 10), np.uint64)
+    if k == 0:
+        return out
+    rc = lib().oracle_count_induced(len(rp) - 1, _p(rp), _p(ci), threads or default_threads(),
+                                    _p(ids) if ids is not None else None, k, _p(out))
     if rc != 0:
         raise IndexError("oracle: edge id out of range")
     return out

@@ -120,3 +120,30 @@ def per_edge_columns(row_ptr, col_idx, m=None):
         out[i] = [t, s, D, r["x7"], r["x10"], comb(t, 2), t * s, comb(su, 2) + comb(sv, 2),
                   su * sv, t * D, m - du - dv + 1, s * D, comb(D, 2)]
     return out
+
+
+def per_edge_induced(row_ptr, col_idx):
+    """Per edge (edge-id order), the number of 4-vertex sets containing it
+    whose induced subgraph is H_7 .. H_16: int64 [m, 10], by enumerating
+    every pair {a, b} of the other vertices and classifying {u, v, a, b}."""
+    adj = adjacency_sets(row_ptr, col_idx)
+    n = len(adj)
+    rows = []
+    for u in range(n):
+        for v in sorted(adj[u]):
+            if v <= u:
+                continue
+            row = [0] * 10
+            others = [x for x in range(n) if x != u and x != v]
+            for a, b in combinations(others, 2):
+                s = (u, v, a, b)
+                deg = {x: 0 for x in s}
+                e = 0
+                for p, q in combinations(s, 2):
+                    if q in adj[p]:
+                        e += 1
+                        deg[p] += 1
+                        deg[q] += 1
+                row[_CLASS4[(e, tuple(sorted(deg.values())))] - 7] += 1
+            rows.append(row)
+    return np.array(rows, dtype=np.int64).reshape(-1, 10)

@@ -101,6 +101,100 @@ EdgeRaw count_edge(const Csr& g, int32_t u, int32_t v, std::vector<uint64_t>& ps
 
 inline u128 choose2(u128 x) { return x < 2 ? 0 : x * (x - 1) / 2; }
 
+// Per-edge induced 4-node counts. The paper defines per edge only x3..x5 and
+// the summands of C_7..C_16 (Sec. 4.5); the number of induced copies of each
+// of H_7..H_16 (Table 1) that contain the edge is this library's extension,
+// read straight from the definition: every 4-set containing e = (u, v) is
+// {u, v, a, b} for a pair {a, b} of the other n - 2 vertices, and its induced
+// subgraph is fixed by the classes of a and b -- T, S_u, S_v of Fig. 2, or
+// the rest R (the D_e vertices of Sec. 4.5) -- and by whether a ~ b:
+//   a, b in T:          a~b H7  (4-clique)        else H8  (chordal cycle)
+//   T, S_u or S_v:      a~b H8                    else H9  (tailed triangle)
+//   T, R:               a~b H9                    else H13 (triangle + vertex)
+//   both S_u / both S_v: a~b H9                   else H11 (3-star)
+//   S_u, S_v:           a~b H10 (4-cycle)         else H12 (4-path)
+//   S_u or S_v, R:      a~b H12                   else H15 (2-star + vertex)
+//   a, b in R:          a~b H14 (2 edges)         else H16 (edge + 2 vertices)
+// The adjacent pairs of every class pair are counted by scanning Gamma(w)
+// for every w in T, S_u and S_v against the Psi tags of Alg. 1 (lambda1 =
+// S_v, lambda2 = S_u, lambda3 = T, and one more tag for u and v themselves);
+// the adjacent pairs inside R are the edges left over from m.
+// out[0..9] = H7 .. H16.
+void count_edge_induced(const Csr& g, int64_t m, int32_t u, int32_t v, std::vector<uint64_t>& psi,
+                        uint64_t lam, std::vector<int32_t>& T, std::vector<int32_t>& Su,
+                        std::vector<int32_t>& Sv, uint64_t* out) {
+  const uint64_t L0 = lam + 1, L1 = lam + 2, L2 = lam + 3, L3 = lam + 4;
+  T.clear();
+  Su.clear();
+  Sv.clear();
+  for (int32_t p = g.rp[v]; p < g.rp[v + 1]; ++p)
+    if (g.ci[p] != u) psi[g.ci[p]] = L1;
+  for (int32_t p = g.rp[u]; p < g.rp[u + 1]; ++p) {
+    int32_t w = g.ci[p];
+    if (w == v) continue;
+    if (psi[w] == L1) {
+      T.push_back(w);
+      psi[w] = L3;
+    } else {
+      Su.push_back(w);
+      psi[w] = L2;
+    }
+  }
+  for (int32_t p = g.rp[v]; p < g.rp[v + 1]; ++p)
+    if (g.ci[p] != u && psi[g.ci[p]] == L1) Sv.push_back(g.ci[p]);
+  psi[u] = L0;
+  psi[v] = L0;
+  // adjacent pairs per class pair; pairs inside one class are met twice
+  int64_t aTT = 0, aTSu = 0, aTSv = 0, aTR = 0, aSuSu = 0, aSvSv = 0, aSuSv = 0, aSuR = 0, aSvR = 0;
+  int64_t degN = g.deg(u) + g.deg(v);  // sum of degrees over N = {u, v} + T + S_u + S_v
+  for (int32_t w : T) {
+    degN += g.deg(w);
+    for (int32_t p = g.rp[w]; p < g.rp[w + 1]; ++p) {
+      const uint64_t c = psi[g.ci[p]];
+      if (c == L3) ++aTT;
+      else if (c == L2) ++aTSu;
+      else if (c == L1) ++aTSv;
+      else if (c != L0) ++aTR;
+    }
+  }
+  for (int32_t w : Su) {
+    degN += g.deg(w);
+    for (int32_t p = g.rp[w]; p < g.rp[w + 1]; ++p) {
+      const uint64_t c = psi[g.ci[p]];
+      if (c == L2) ++aSuSu;
+      else if (c == L1) ++aSuSv;
+      else if (c != L3 && c != L0) ++aSuR;
+    }
+  }
+  for (int32_t w : Sv) {
+    degN += g.deg(w);
+    for (int32_t p = g.rp[w]; p < g.rp[w + 1]; ++p) {
+      const uint64_t c = psi[g.ci[p]];
+      if (c == L1) ++aSvSv;
+      else if (c != L2 && c != L3 && c != L0) ++aSvR;
+    }
+  }
+  aTT /= 2;
+  aSuSu /= 2;
+  aSvSv /= 2;
+  const int64_t t = (int64_t)T.size(), su = (int64_t)Su.size(), sv = (int64_t)Sv.size();
+  const int64_t R = g.n - 2 - t - su - sv;
+  // edges inside N: (u, v), u and v to T, u to S_u, v to S_v, and the pairs above
+  const int64_t inN = 1 + 2 * t + su + sv + aTT + aTSu + aTSv + aSuSu + aSvSv + aSuSv;
+  const int64_t aRR = m - degN + inN;  // m = inN + (edges from N to R = degN - 2 inN) + aRR
+  const int64_t c2t = t * (t - 1) / 2, c2su = su * (su - 1) / 2, c2sv = sv * (sv - 1) / 2, c2R = R * (R - 1) / 2;
+  out[0] = (uint64_t)aTT;                                                          // H7
+  out[1] = (uint64_t)(c2t - aTT + aTSu + aTSv);                                    // H8
+  out[2] = (uint64_t)(t * su - aTSu + t * sv - aTSv + aTR + aSuSu + aSvSv);        // H9
+  out[3] = (uint64_t)aSuSv;                                                        // H10
+  out[4] = (uint64_t)(c2su - aSuSu + c2sv - aSvSv);                                // H11
+  out[5] = (uint64_t)(su * sv - aSuSv + aSuR + aSvR);                              // H12
+  out[6] = (uint64_t)(t * R - aTR);                                                // H13
+  out[7] = (uint64_t)aRR;                                                          // H14
+  out[8] = (uint64_t)(su * R - aSuR + sv * R - aSvR);                              // H15
+  out[9] = (uint64_t)(c2R - aRR);                                                  // H16
+}
+
 // The 13 per-edge columns, in the library's column order.
 void edge_columns(const EdgeRaw& r, int64_t n, int64_t m, int64_t du, int64_t dv, uint64_t* col) {
   int64_t s = r.su + r.sv;
@@ -278,6 +372,38 @@ int oracle_count_sample(int32_t n, const int32_t* rp, const int32_t* ci, int nth
       orient(g, E.u[e], E.v[e], &u, &v);
       EdgeRaw r = count_edge(g, u, v, psi, 4 * (uint64_t)i, T, Su);
       edge_columns(r, n, m, g.deg(u), g.deg(v), out + 13 * i);
+    }
+  };
+  std::vector<std::thread> th;
+  for (int t = 1; t < nthreads; ++t) th.emplace_back(work);
+  work();
+  for (auto& t : th) t.join();
+  return 0;
+}
+
+// Per-edge induced counts of H_7..H_16 (see count_edge_induced) for the
+// given edge ids (all edges when edge_ids is NULL, k = m); out[k][10].
+// Returns 0 or -2 on a bad id.
+int oracle_count_induced(int32_t n, const int32_t* rp, const int32_t* ci, int nthreads,
+                         const int64_t* edge_ids, int64_t k, uint64_t* out) {
+  Csr g{n, rp, ci};
+  Edges E = list_edges(g);
+  const int64_t m = (int64_t)E.u.size();
+  if (!edge_ids) k = m;
+  for (int64_t i = 0; edge_ids && i < k; ++i)
+    if (edge_ids[i] < 0 || edge_ids[i] >= m) return -2;
+  if (nthreads < 1) nthreads = 1;
+  std::atomic<int64_t> cursor(0);
+  auto work = [&]() {
+    std::vector<uint64_t> psi((size_t)n, 0);
+    std::vector<int32_t> T, Su, Sv;
+    for (;;) {
+      int64_t i = cursor.fetch_add(1);
+      if (i >= k) break;
+      int64_t e = edge_ids ? edge_ids[i] : i;
+      int32_t u, v;
+      orient(g, E.u[e], E.v[e], &u, &v);
+      count_edge_induced(g, m, u, v, psi, 5 * (uint64_t)i, T, Su, Sv, out + 10 * i);
     }
   };
   std::vector<std::thread> th;

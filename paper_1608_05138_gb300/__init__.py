@@ -29,16 +29,25 @@ STATUS_NAMES = {
     -8: "GC_ERR_CUDA", -9: "GC_ERR_OVERFLOW", -10: "GC_ERR_TIMEOUT", -11: "GC_ERR_BUSY",
 }
 GC_EDGE_COLS = 13
+GC_INDUCED_COLS = 10
+INDUCED_NAMES = ["H7", "H8", "H9", "H10", "H11", "H12", "H13", "H14", "H15", "H16"]
 GC_NUM_GRAPHLETS = 17
 GC_NO_VALIDATE = 0x1
 GC_BATCH_MANUAL = 0x1
+GC_PARAM_SMALL_N_MAX, GC_PARAM_BLOCK_N64, GC_PARAM_USE_GRAPH = 0, 1, 6
+SMALL_CLASS_N = [64, 128, 256, 512, 1024]      # size classes of the bitmatrix kernels
+SMALL_BLOCKS = [64, 128, 256, 512]
+BATCH_STATS = ["class_n64_ms", "class_n128_ms", "class_n256_ms", "class_n512_ms", "class_n1024_ms",
+               "small_sequence_ms", "union_ms", "replayed"]
 EXPORTED = ["gc_last_error", "gc_graph_upload", "gc_graph_info", "gc_graph_edges",
             "gc_count_edge_graphlets", "gc_graph_csums", "gc_phase_count", "gc_phase_name",
             "gc_graph_phase_ms", "gc_graph_free", "gc_batch_create", "gc_batch_submit",
             "gc_batch_flush", "gc_batch_poll", "gc_batch_destroy", "gc_edge_triangles_noalloc",
-            "gc_graph_work_counts", "gc_batch_submit_many"]
+            "gc_graph_work_counts", "gc_batch_submit_many", "gc_count_edge_induced", "gc_batch_set_param",
+            "gc_batch_get_param", "gc_batch_last_stats", "gc_batch_poll_many"]
 WORK_NAMES = ["t_members", "c_wedges", "k_members", "k_scan", "k_local_edges", "k_words", "finish_edges", "launches",
-              "c_heavy_wedges", "c_heavy_sweeps", "t_scan", "t_triangles", "c_hash_wedges"]
+              "c_heavy_wedges", "c_heavy_sweeps", "t_scan", "t_triangles", "c_hash_wedges", "c_hub_jobs",
+              "c_hub_ctas", "c_hub_busy_sum_ns", "c_hub_busy_max_ns"]
 
 
 class GcError(RuntimeError):
@@ -65,6 +74,7 @@ def lib():
             L.gc_graph_info.argtypes = [vp, C.POINTER(i64), C.POINTER(i64)]
             L.gc_graph_edges.argtypes = [vp, vp]
             L.gc_count_edge_graphlets.argtypes = [vp, vp, vp, vp]
+            L.gc_count_edge_induced.argtypes = [vp, vp, vp, vp, vp]
             L.gc_graph_csums.argtypes = [vp, vp, vp]
             L.gc_phase_name.restype = C.c_char_p
             L.gc_phase_name.argtypes = [C.c_int]
@@ -78,10 +88,16 @@ def lib():
             L.gc_edge_triangles_noalloc.argtypes = [i32, vp, vp, vp, vp]
             L.gc_graph_work_counts.argtypes = [vp, vp]
             L.gc_batch_submit_many.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp]
+            L.gc_batch_set_param.argtypes = [vp, i32, i32]
+            L.gc_batch_get_param.argtypes = [vp, i32, C.POINTER(i32)]
+            L.gc_batch_last_stats.argtypes = [vp, vp]
+            L.gc_batch_poll_many.argtypes = [vp, i64, vp, vp, vp, i32]
             for name in ("gc_graph_upload", "gc_graph_info", "gc_graph_edges", "gc_count_edge_graphlets",
+                         "gc_count_edge_induced",
                          "gc_graph_csums", "gc_graph_phase_ms", "gc_graph_free", "gc_batch_create",
                          "gc_batch_submit", "gc_batch_flush", "gc_batch_poll", "gc_batch_destroy",
-                         "gc_edge_triangles_noalloc", "gc_graph_work_counts", "gc_batch_submit_many"):
+                         "gc_edge_triangles_noalloc", "gc_graph_work_counts", "gc_batch_submit_many",
+                         "gc_batch_set_param", "gc_batch_get_param", "gc_batch_last_stats", "gc_batch_poll_many"):
                 getattr(L, name).restype = C.c_int
             _lib = L
     return _lib
@@ -163,6 +179,17 @@ def gc_count_edge_graphlets(g, per_edge_out=None, wide: bool = True):
     return _join(lo, hi)
 
 
+def gc_count_edge_induced(g, induced_out, per_edge_out=None, wide: bool = True):
+    """Count with per-edge induced 4-node counts: fills induced_out ([m, 10]
+    uint64 numpy array, or int64/uint64 CUDA tensor; columns H7..H16) and
+    per_edge_out if given; returns X_1..X_17 as Python ints."""
+    lo = np.zeros(17, np.uint64)
+    hi = np.zeros(17, np.uint64)
+    _check(lib().gc_count_edge_induced(g, _ptr(induced_out), _ptr(per_edge_out), _ptr(lo), _ptr(hi) if wide else None),
+           "gc_count_edge_induced")
+    return _join(lo, hi)
+
+
 def gc_graph_csums(g):
     lo = np.zeros(13, np.uint64)
     hi = np.zeros(13, np.uint64)
@@ -201,6 +228,9 @@ class Graph:
 
     def count(self, per_edge_out=None, wide: bool = True):
         return gc_count_edge_graphlets(self.handle, per_edge_out, wide)
+
+    def count_induced(self, induced_out, per_edge_out=None, wide: bool = True):
+        return gc_count_edge_induced(self.handle, induced_out, per_edge_out, wide)
 
     def edges(self):
         return gc_graph_edges(self.handle)
@@ -286,6 +316,53 @@ def gc_batch_poll(b, ticket: int, timeout_us: int = -1):
     if st == GC_PENDING:
         return None
     return _join(lo, hi)
+
+
+def gc_batch_poll_many(b, tickets, timeout_us: int = -1):
+    """X_1..X_17 of every ticket as a uint64 array [G, 17, 2] of (low, high)
+    words, or None while not all are done (nothing is retired then)."""
+    t = np.ascontiguousarray(tickets, np.uint64)
+    lo = np.zeros((len(t), 17), np.uint64)
+    hi = np.zeros((len(t), 17), np.uint64)
+    st = _check(lib().gc_batch_poll_many(b, len(t), _ptr(t), _ptr(lo), _ptr(hi), int(timeout_us)),
+                "gc_batch_poll_many")
+    if st == GC_PENDING:
+        return None
+    return np.stack([lo, hi], axis=-1)
+
+
+def gc_batch_set_param(b, param: int, value: int):
+    _check(lib().gc_batch_set_param(b, int(param), int(value)), "gc_batch_set_param")
+
+
+def gc_batch_get_param(b, param: int) -> int:
+    v = C.c_int32()
+    _check(lib().gc_batch_get_param(b, int(param), C.byref(v)), "gc_batch_get_param")
+    return v.value
+
+
+def gc_batch_config(b) -> dict:
+    """The batch's parameters: small_n_max, block per size class, use_graph."""
+    return {"small_n_max": gc_batch_get_param(b, GC_PARAM_SMALL_N_MAX),
+            "block": {str(n): gc_batch_get_param(b, GC_PARAM_BLOCK_N64 + c) for c, n in enumerate(SMALL_CLASS_N)},
+            "use_graph": gc_batch_get_param(b, GC_PARAM_USE_GRAPH)}
+
+
+def gc_batch_configure(b, config: dict):
+    """Set the parameters of a dict shaped like gc_batch_config's (keys may be missing)."""
+    if "small_n_max" in config:
+        gc_batch_set_param(b, GC_PARAM_SMALL_N_MAX, config["small_n_max"])
+    for c, n in enumerate(SMALL_CLASS_N):
+        if str(n) in config.get("block", {}):
+            gc_batch_set_param(b, GC_PARAM_BLOCK_N64 + c, config["block"][str(n)])
+    if "use_graph" in config:
+        gc_batch_set_param(b, GC_PARAM_USE_GRAPH, config["use_graph"])
+
+
+def gc_batch_last_stats(b) -> dict:
+    out = np.zeros(len(BATCH_STATS), np.float64)
+    _check(lib().gc_batch_last_stats(b, _ptr(out)), "gc_batch_last_stats")
+    return dict(zip(BATCH_STATS, out.tolist()))
 
 
 def gc_batch_destroy(b):

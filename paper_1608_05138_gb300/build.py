@@ -11,7 +11,7 @@ CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 SO = os.path.join(HERE, "libgc.so")
 SOURCES = ["gc_api.cu", "gc_prep.cu", "gc_count.cu", "gc_run.cu", "gc_batch.cu", "gc_small.cu",
-           "gc_noalloc.cu", "gc_clique.cu", "gc_relabel.cu"]
+           "gc_noalloc.cu", "gc_clique.cu", "gc_relabel.cu", "gc_tune.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "-I", os.path.join(HERE, "..", "include")]
 
@@ -49,7 +49,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     objs = [os.path.join(OBJ, s.replace(".cu", ".o")) for s in SOURCES]
     if force or jobs or _stale(SO, objs):
         tmp = SO + f".tmp{os.getpid()}"
-        r = subprocess.run([nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lpthread"], capture_output=True, text=True)
+        r = subprocess.run([nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lpthread", "-ldl"], capture_output=True,
+                           text=True)
         if r.returncode != 0:
             raise RuntimeError("link failed:\n" + r.stdout + r.stderr)
         os.replace(tmp, SO)

@@ -231,6 +231,7 @@ struct gc_graph_s {
   unsigned long long* d_csum = nullptr;  // [13][2]
   unsigned long long* d_x = nullptr;     // [17][2]
   uint64_t* d_pe_tmp = nullptr;          // device staging for a host per-edge buffer
+  uint64_t* d_ind_tmp = nullptr;         // device staging for a host per-edge induced buffer
   cudaEvent_t ev[kNumPhases + 1] = {};
   bool counted = false;
   uint64_t csum_lo[13] = {0}, csum_hi[13] = {0};
@@ -253,6 +254,7 @@ static void graph_release(gc_graph g) {
   cudaStreamSynchronize(g->stream);
   cudaFree(g->d_csum);
   cudaFree(g->d_pe_tmp);
+  cudaFree(g->d_ind_tmp);
   for (auto& e : g->ev)
     if (e) cudaEventDestroy(e);
   delete g;
@@ -443,8 +445,9 @@ static uint64_t* device_view(uint64_t* p, bool* host) {
   return nullptr;
 }
 
-gc_status gc_count_edge_graphlets(gc_graph g, uint64_t* per_edge_out, uint64_t* global_out,
-                                  uint64_t* global_hi) {
+// The count behind gc_count_edge_graphlets and gc_count_edge_induced.
+static gc_status count_graph(gc_graph g, uint64_t* per_edge_out, uint64_t* induced_out, uint64_t* global_out,
+                             uint64_t* global_hi) {
   if (!g || !global_out) { set_error("NULL argument"); return GC_ERR_ARG; }
   cudaStream_t s = g->stream;
   cudaError_t e;
@@ -463,6 +466,18 @@ gc_status gc_count_edge_graphlets(gc_graph g, uint64_t* per_edge_out, uint64_t* 
       if (!g->d_pe_tmp)
         GC_CHECK(cudaMalloc(&g->d_pe_tmp, sizeof(uint64_t) * 13 * (size_t)g->m), "alloc per-edge staging");
       pe_dev = g->d_pe_tmp;
+    }
+  }
+  uint64_t* ind_dev = nullptr;
+  const bool want_ind = induced_out != nullptr && g->m > 0;
+  bool ind_staged = false, ind_host = false;
+  if (want_ind) {
+    if ((ind_dev = device_view(induced_out, &ind_host)) == nullptr) {
+      ind_staged = true;
+      if (!g->d_ind_tmp)
+        GC_CHECK(cudaMalloc(&g->d_ind_tmp, sizeof(uint64_t) * GC_INDUCED_COLS * (size_t)g->m),
+                 "alloc induced staging");
+      ind_dev = g->d_ind_tmp;
     }
   }
   DevGraph dg;
@@ -488,12 +503,14 @@ gc_status gc_count_edge_graphlets(gc_graph g, uint64_t* per_edge_out, uint64_t* 
   ku.units = g->prep.kunits;
   ku.cunits = g->prep.cunits;
   ku.n_cheavy = g->prep.n_cheavy;
+  ku.cjobs = g->prep.cjobs;
+  ku.n_cjobs = g->prep.n_cjobs;
   ku.chash_w = g->prep.chash_w;
   ku.n_chash = g->prep.n_chash;
   ku.n_cunits = g->prep.n_cunits;
   for (int t = 0; t <= kNumTiers; ++t) ku.tier_off[t] = g->prep.ktier_off[t];
-  if ((st = run_count(dg, g->prep.units, g->prep.n_units, ku, pe_dev, g->d_csum, g->d_x, &g->sc, s, g->ev, pe_host)) !=
-      GC_OK)
+  if ((st = run_count(dg, g->prep.units, g->prep.n_units, ku, pe_dev, g->d_csum, g->d_x, &g->sc, s, g->ev, pe_host,
+                      ind_dev, ind_host)) != GC_OK)
     return st;
   unsigned long long hx[17 * 2 + 13 * 2];
   int32_t hstatus = 0;
@@ -505,6 +522,10 @@ gc_status gc_count_edge_graphlets(gc_graph g, uint64_t* per_edge_out, uint64_t* 
   if (staged)
     GC_CHECK(cudaMemcpyAsync(per_edge_out, pe_dev, sizeof(uint64_t) * 13 * (size_t)g->m, cudaMemcpyDeviceToHost, s),
              "copy per-edge");
+  if (ind_staged)
+    GC_CHECK(cudaMemcpyAsync(induced_out, ind_dev, sizeof(uint64_t) * GC_INDUCED_COLS * (size_t)g->m,
+                             cudaMemcpyDeviceToHost, s),
+             "copy induced");
   GC_CHECK(cudaEventRecord(g->ev[kNumPhases], s), "event");
   GC_CHECK(cudaStreamSynchronize(s), "sync count");
   g->sc.tlist_want = (long long)g->work[kWorkTTriangles];  // the next count keeps pass T's edge lists
@@ -535,6 +556,17 @@ gc_status gc_count_edge_graphlets(gc_graph g, uint64_t* per_edge_out, uint64_t* 
   return GC_OK;
 }
 
+gc_status gc_count_edge_graphlets(gc_graph g, uint64_t* per_edge_out, uint64_t* global_out,
+                                  uint64_t* global_hi) {
+  return count_graph(g, per_edge_out, nullptr, global_out, global_hi);
+}
+
+gc_status gc_count_edge_induced(gc_graph g, uint64_t* induced_out, uint64_t* per_edge_out, uint64_t* global_out,
+                                uint64_t* global_hi) {
+  if (!induced_out && g && g->m > 0) { set_error("induced_out is NULL"); return GC_ERR_ARG; }
+  return count_graph(g, per_edge_out, induced_out, global_out, global_hi);
+}
+
 gc_status gc_graph_csums(gc_graph g, uint64_t* lo, uint64_t* hi) {
   if (!g || !lo) { set_error("NULL argument"); return GC_ERR_ARG; }
   if (!g->counted) { set_error("graph not counted yet"); return GC_ERR_ARG; }
@@ -558,7 +590,7 @@ int gc_phase_count(void) { return kNumPhases; }
 
 const char* gc_phase_name(int i) {
   static const char* names[kNumPhases] = {"pass_t_triangles", "pass_c_cycles", "pass_k_cliques",
-                                          "finish_columns", "derive", "copy_out"};
+                                          "finish_columns", "induced_columns", "derive", "copy_out"};
   return (i >= 0 && i < kNumPhases) ? names[i] : "";
 }
 

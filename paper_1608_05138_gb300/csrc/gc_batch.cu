@@ -60,17 +60,55 @@ struct Result {
   gc_status status;
 };
 
+// Timers of one launch (CUDA events on its stream): the size classes of the
+// small-graph kernels (eager launches only), the whole small-graph sequence
+// (copies in, kernels, derive, copy out) and the larger graphs' passes.
+enum { kEvSmall0 = 0, kEvSmallSeq0 = kSmallClasses + 1, kEvSmallSeq1, kEvUnion0, kEvUnion1, kNumLaunchEv };
+
 struct Launch {
   std::vector<uint64_t> tickets;
   std::vector<int32_t> slot;          // ticket k's row in h_x
   int64_t bytes = 0;
+  int stream_slot = 0;
+  BatchConfig cfg;                    // the batch's parameters when the launch was taken
   cudaStream_t stream = nullptr;
   cudaEvent_t done = nullptr;
+  cudaEvent_t ev[kNumLaunchEv] = {};
+  bool timed_classes = false, timed_small = false, timed_union = false, replayed = false;
   unsigned long long* h_x = nullptr;  // pinned [G][17][2]
   int32_t* h_status = nullptr;        // pinned
   gc_status launch_status = GC_OK;
   std::string error;
 };
+
+// Device buffers and pinned host staging of the small-graph path, one set per
+// stream slot, grown as needed and kept: once warm, a launch allocates
+// nothing, and its sequence (copies in, kernels, derive, copy out) can be
+// captured and replayed as a CUDA graph. `busy` marks the end of the slot's
+// last sequence: the host waits on it before it refills or regrows them.
+struct SmallBufs {
+  size_t cap_rows = 0, cap_nnz = 0, cap_g = 0;
+  int32_t *d_rp = nullptr, *d_ci = nullptr, *d_order = nullptr, *d_gn = nullptr, *d_misc = nullptr;
+  int64_t *d_voff = nullptr, *d_eoff = nullptr, *d_gm = nullptr;
+  unsigned long long *d_csum = nullptr, *d_x = nullptr;
+  int32_t *h_rp = nullptr, *h_ci = nullptr, *h_order = nullptr, *h_gn = nullptr;
+  int64_t *h_voff = nullptr, *h_eoff = nullptr, *h_gm = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaEvent_t busy = nullptr;
+};
+
+void free_small_bufs(SmallBufs* b) {
+  if (b->busy) cudaEventSynchronize(b->busy);
+  for (void* p : {(void*)b->d_rp, (void*)b->d_ci, (void*)b->d_order, (void*)b->d_gn, (void*)b->d_misc,
+                  (void*)b->d_voff, (void*)b->d_eoff, (void*)b->d_gm, (void*)b->d_csum, (void*)b->d_x})
+    if (p) cudaFree(p);
+  for (void* p : {(void*)b->h_rp, (void*)b->h_ci, (void*)b->h_order, (void*)b->h_gn, (void*)b->h_voff,
+                  (void*)b->h_eoff, (void*)b->h_gm})
+    if (p) cudaFreeHost(p);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->busy) cudaEventDestroy(b->busy);
+  *b = SmallBufs();
+}
 
 int64_t footprint(int32_t n, int64_t m) {
   int64_t b = 44LL * n + 32LL * m + 1024;
@@ -86,6 +124,9 @@ using namespace gc;
 struct gc_batch_s {
   int64_t budget = 0;
   uint32_t flags = 0;
+  BatchConfig cfg;
+  SmallBufs small[2];                   // per stream slot
+  double last_stats[GC_BATCH_STATS] = {};  // of the last retired launch
   int64_t in_use = 0;
   std::mutex mu;
   std::condition_variable cv;
@@ -209,6 +250,8 @@ gc_status run_union(std::vector<PendingGraph*>& graphs, cudaStream_t s, Launch* 
     ku.units = prep.kunits;
     ku.cunits = prep.cunits;
     ku.n_cheavy = prep.n_cheavy;
+    ku.cjobs = prep.cjobs;
+    ku.n_cjobs = prep.n_cjobs;
     ku.chash_w = prep.chash_w;
     ku.n_chash = prep.n_chash;
     ku.n_cunits = prep.n_cunits;
@@ -230,41 +273,105 @@ out:
   return st;
 }
 
-// Graphs of at most kSmallN vertices: packed as they are (local ids) and
-// counted one CTA per graph on a shared-memory bitmatrix.
-gc_status run_small(std::vector<PendingGraph*>& graphs, cudaStream_t s, Launch* L, unsigned long long* h_x_dst) {
+// Grows the device buffer *d and the pinned host buffer *h (either may be
+// absent) to hold `need` elements of T.
+template <typename T>
+cudaError_t grow_pair(T** d, T** h, size_t* cap, size_t need) {
+  if (need <= *cap && (d == nullptr || *d) && (h == nullptr || *h)) return cudaSuccess;
+  const size_t want = need + need / 4 + 64;
+  if (d && *d) cudaFree(*d);
+  if (h && *h) cudaFreeHost(*h);
+  if (d) *d = nullptr;
+  if (h) *h = nullptr;
+  *cap = 0;
+  cudaError_t e = cudaSuccess;
+  if (d) e = cudaMalloc(d, sizeof(T) * want);
+  if (e == cudaSuccess && h) e = cudaMallocHost(h, sizeof(T) * want);
+  if (e == cudaSuccess) *cap = want;
+  return e;
+}
+
+// Graphs of at most cfg.small_n_max vertices: packed as they are (local ids)
+// into the slot's pinned staging and counted one CTA per graph on a
+// shared-memory bitmatrix, binned by size class. The sequence is captured
+// into a CUDA graph and replayed (cudaGraphExecUpdate keeps one executable
+// per slot while the shape of the launches stays the same), or issued
+// eagerly with per-class timers when cfg.use_graph is 0.
+gc_status run_small(std::vector<PendingGraph*>& graphs, cudaStream_t s, Launch* L, unsigned long long* h_x_dst,
+                    SmallBufs* sb, const BatchConfig& cfg) {
   const int32_t G = (int32_t)graphs.size();
-  std::vector<int64_t> h_voff((size_t)G + 1), h_eoff((size_t)G + 1), h_gm((size_t)G);
-  std::vector<int32_t> h_gn((size_t)G), h_order((size_t)G);
-  h_voff[0] = h_eoff[0] = 0;
+  std::vector<int64_t> voff((size_t)G + 1), eoff((size_t)G + 1);
+  voff[0] = eoff[0] = 0;
   for (int32_t gi = 0; gi < G; ++gi) {
-    h_voff[gi + 1] = h_voff[gi] + graphs[gi]->n + 1;
-    h_eoff[gi + 1] = h_eoff[gi] + 2 * graphs[gi]->m;
-    h_gn[gi] = graphs[gi]->n;
-    h_gm[gi] = graphs[gi]->m;
-    h_order[gi] = gi;
+    voff[gi + 1] = voff[gi] + graphs[gi]->n + 1;
+    eoff[gi + 1] = eoff[gi] + 2 * graphs[gi]->m;
   }
-  std::sort(h_order.begin(), h_order.end(), [&](int32_t a, int32_t b) { return h_gm[a] > h_gm[b]; });
-  // packed on all host cores into buffers that are not zeroed first (every
-  // entry is copied over)
-  struct Packed {
-    std::unique_ptr<int32_t[]> p;
-    size_t n;
-    int32_t* data() { return p.get(); }
-    size_t size() const { return n; }
-  } h_rp{std::unique_ptr<int32_t[]>(new int32_t[(size_t)h_voff[G] + 1]), (size_t)h_voff[G] + 1},
-    h_ci{std::unique_ptr<int32_t[]>(new int32_t[(size_t)(h_eoff[G] > 0 ? h_eoff[G] : 1)]),
-         (size_t)(h_eoff[G] > 0 ? h_eoff[G] : 1)};
+  const size_t rows = (size_t)voff[G], nnz = (size_t)(eoff[G] > 0 ? eoff[G] : 1);
+  gc_status st = GC_OK;
+  cudaError_t e = cudaSuccess;
+#define GS_TRY(call, what)                   \
+  do {                                       \
+    e = (call);                              \
+    if (e != cudaSuccess) {                  \
+      st = cuda_fail(e, what);               \
+      L->error = gc_last_error();            \
+      return st;                             \
+    }                                        \
+  } while (0)
+  if (sb->busy) GS_TRY(cudaEventSynchronize(sb->busy), "small buffers in use");
+  else GS_TRY(cudaEventCreateWithFlags(&sb->busy, cudaEventDisableTiming), "small event");
   {
+    size_t cr = sb->cap_rows, cn = sb->cap_nnz, cg = sb->cap_g;
+    GS_TRY(grow_pair(&sb->d_rp, &sb->h_rp, &cr, rows), "small buffers");
+    GS_TRY(grow_pair(&sb->d_ci, &sb->h_ci, &cn, nnz), "small buffers");
+    if ((size_t)G + 1 > sb->cap_g || !sb->d_voff) {
+      size_t c1 = 0;
+      const size_t need = (size_t)G + 1;
+      GS_TRY(grow_pair(&sb->d_voff, &sb->h_voff, &c1, need), "small buffers");
+      c1 = 0; GS_TRY(grow_pair(&sb->d_eoff, &sb->h_eoff, &c1, need), "small buffers");
+      c1 = 0; GS_TRY(grow_pair(&sb->d_gm, &sb->h_gm, &c1, need), "small buffers");
+      c1 = 0; GS_TRY(grow_pair(&sb->d_gn, &sb->h_gn, &c1, need), "small buffers");
+      c1 = 0; GS_TRY(grow_pair(&sb->d_order, &sb->h_order, &c1, need), "small buffers");
+      c1 = 0; GS_TRY(grow_pair<unsigned long long>(&sb->d_csum, nullptr, &c1, 26 * need), "small buffers");
+      c1 = 0; GS_TRY(grow_pair<unsigned long long>(&sb->d_x, nullptr, &c1, 34 * need), "small buffers");
+      if (!sb->d_misc) GS_TRY(cudaMalloc(&sb->d_misc, sizeof(int32_t) * (kSmallClasses + 1)), "small buffers");
+      cg = c1 / 34;
+    }
+    sb->cap_rows = cr;
+    sb->cap_nnz = cn;
+    sb->cap_g = cg;
+  }
+  // order: graphs binned by size class, largest m first within a class
+  int32_t class_off[kSmallClasses + 1] = {0};
+  {
+    std::vector<int32_t> cls((size_t)G);
+    for (int32_t gi = 0; gi < G; ++gi) {
+      cls[gi] = small_class_of(graphs[gi]->n);
+      ++class_off[cls[gi] + 1];
+    }
+    for (int c = 0; c < kSmallClasses; ++c) class_off[c + 1] += class_off[c];
+    std::vector<int32_t> pos(class_off, class_off + kSmallClasses);
+    for (int32_t gi = 0; gi < G; ++gi) sb->h_order[pos[cls[gi]]++] = gi;
+    for (int c = 0; c < kSmallClasses; ++c)
+      std::sort(sb->h_order + class_off[c], sb->h_order + class_off[c + 1],
+                [&](int32_t a, int32_t b) { return graphs[a]->m > graphs[b]->m; });
+  }
+  std::memcpy(sb->h_voff, voff.data(), sizeof(int64_t) * voff.size());
+  std::memcpy(sb->h_eoff, eoff.data(), sizeof(int64_t) * eoff.size());
+  for (int32_t gi = 0; gi < G; ++gi) {
+    sb->h_gn[gi] = graphs[gi]->n;
+    sb->h_gm[gi] = graphs[gi]->m;
+  }
+  {  // CSR packed on the host cores, each thread the graphs whose entries start in its share
     const unsigned hw = std::thread::hardware_concurrency();
-    const int nt = h_eoff[G] < (1 << 22) ? 1 : (int)std::min<unsigned>(hw ? hw : 1, 32);
-    auto pack = [&](int t) {  // the graphs whose entries start in this thread's share
-      const int64_t e0 = h_eoff[G] * t / nt, e1 = h_eoff[G] * (t + 1) / nt;
-      int32_t gi = (int32_t)(std::lower_bound(h_eoff.begin(), h_eoff.begin() + G, e0) - h_eoff.begin());
-      for (; gi < G && (h_eoff[gi] < e1 || t == nt - 1); ++gi) {
-        std::memcpy(h_rp.data() + h_voff[gi], graphs[gi]->rp.data(), sizeof(int32_t) * (graphs[gi]->n + 1));
+    const int nt = eoff[G] < (1 << 22) ? 1 : (int)std::min<unsigned>(hw ? hw : 1, 32);
+    auto pack = [&](int t) {
+      const int64_t e0 = eoff[G] * t / nt, e1 = eoff[G] * (t + 1) / nt;
+      int32_t gi = (int32_t)(std::lower_bound(eoff.begin(), eoff.begin() + G, e0) - eoff.begin());
+      for (; gi < G && (eoff[gi] < e1 || t == nt - 1); ++gi) {
+        std::memcpy(sb->h_rp + voff[gi], graphs[gi]->rp.data(), sizeof(int32_t) * (graphs[gi]->n + 1));
         if (graphs[gi]->m > 0)
-          std::memcpy(h_ci.data() + h_eoff[gi], graphs[gi]->ci.data(), sizeof(int32_t) * 2 * graphs[gi]->m);
+          std::memcpy(sb->h_ci + eoff[gi], graphs[gi]->ci.data(), sizeof(int32_t) * 2 * graphs[gi]->m);
       }
     };
     std::vector<std::thread> th;
@@ -272,81 +379,107 @@ gc_status run_small(std::vector<PendingGraph*>& graphs, cudaStream_t s, Launch* 
     pack(0);
     for (auto& x : th) x.join();
   }
-  int32_t *d_rp = nullptr, *d_ci = nullptr, *d_gn = nullptr, *d_order = nullptr, *d_misc = nullptr;
-  int64_t *d_voff = nullptr, *d_eoff = nullptr, *d_gm = nullptr;
-  unsigned long long *d_csum = nullptr, *d_x = nullptr;
-  cudaError_t e = cudaSuccess;
-  gc_status st = GC_OK;
-#define GS_TRY(call, what)                   \
-  do {                                       \
-    e = (call);                              \
-    if (e != cudaSuccess) {                  \
-      st = cuda_fail(e, what);               \
-      L->error = gc_last_error();            \
-      goto out;                              \
-    }                                        \
-  } while (0)
-  GS_TRY(cudaMallocAsync(&d_rp, sizeof(int32_t) * h_rp.size(), s), "small alloc");
-  GS_TRY(cudaMallocAsync(&d_ci, sizeof(int32_t) * h_ci.size(), s), "small alloc");
-  GS_TRY(cudaMallocAsync(&d_voff, sizeof(int64_t) * h_voff.size(), s), "small alloc");
-  GS_TRY(cudaMallocAsync(&d_eoff, sizeof(int64_t) * h_eoff.size(), s), "small alloc");
-  GS_TRY(cudaMallocAsync(&d_gn, sizeof(int32_t) * G, s), "small alloc");
-  GS_TRY(cudaMallocAsync(&d_gm, sizeof(int64_t) * G, s), "small alloc");
-  GS_TRY(cudaMallocAsync(&d_order, sizeof(int32_t) * G, s), "small alloc");
-  GS_TRY(cudaMallocAsync(&d_misc, sizeof(int32_t) * 2, s), "small alloc");
-  GS_TRY(cudaMallocAsync(&d_csum, sizeof(unsigned long long) * (size_t)G * 26, s), "small alloc");
-  GS_TRY(cudaMallocAsync(&d_x, sizeof(unsigned long long) * (size_t)G * 34, s), "small alloc");
-  GS_TRY(cudaMemcpyAsync(d_rp, h_rp.data(), sizeof(int32_t) * h_rp.size(), cudaMemcpyHostToDevice, s), "small copy");
-  GS_TRY(cudaMemcpyAsync(d_ci, h_ci.data(), sizeof(int32_t) * h_ci.size(), cudaMemcpyHostToDevice, s), "small copy");
-  GS_TRY(cudaMemcpyAsync(d_voff, h_voff.data(), sizeof(int64_t) * h_voff.size(), cudaMemcpyHostToDevice, s),
-         "small copy");
-  GS_TRY(cudaMemcpyAsync(d_eoff, h_eoff.data(), sizeof(int64_t) * h_eoff.size(), cudaMemcpyHostToDevice, s),
-         "small copy");
-  GS_TRY(cudaMemcpyAsync(d_gn, h_gn.data(), sizeof(int32_t) * G, cudaMemcpyHostToDevice, s), "small copy");
-  GS_TRY(cudaMemcpyAsync(d_gm, h_gm.data(), sizeof(int64_t) * G, cudaMemcpyHostToDevice, s), "small copy");
-  GS_TRY(cudaMemcpyAsync(d_order, h_order.data(), sizeof(int32_t) * G, cudaMemcpyHostToDevice, s), "small copy");
-  GS_TRY(cudaMemsetAsync(d_misc, 0, sizeof(int32_t) * 2, s), "small memset");
-  GS_TRY(cudaMemsetAsync(d_csum, 0, sizeof(unsigned long long) * (size_t)G * 26, s), "small memset");
-  if ((st = run_small_graphs(d_rp, d_voff, d_ci, d_eoff, d_order, G, d_misc, d_csum, s)) != GC_OK) {
-    L->error = gc_last_error();
-    goto out;
-  }
-  {
+  const bool graph_mode = cfg.use_graph != 0;
+  // the sequence; returns the first failure (for a capture, the capture is
+  // ended by the caller)
+  auto issue = [&]() -> cudaError_t {
+    cudaError_t r = cudaSuccess;
+    const size_t b4 = sizeof(int32_t), b8 = sizeof(int64_t);
+    r = cudaMemcpyAsync(sb->d_rp, sb->h_rp, b4 * rows, cudaMemcpyHostToDevice, s);
+    if (r == cudaSuccess && eoff[G] > 0) r = cudaMemcpyAsync(sb->d_ci, sb->h_ci, b4 * (size_t)eoff[G], cudaMemcpyHostToDevice, s);
+    if (r == cudaSuccess) r = cudaMemcpyAsync(sb->d_voff, sb->h_voff, b8 * (G + 1), cudaMemcpyHostToDevice, s);
+    if (r == cudaSuccess) r = cudaMemcpyAsync(sb->d_eoff, sb->h_eoff, b8 * (G + 1), cudaMemcpyHostToDevice, s);
+    if (r == cudaSuccess) r = cudaMemcpyAsync(sb->d_gn, sb->h_gn, b4 * G, cudaMemcpyHostToDevice, s);
+    if (r == cudaSuccess) r = cudaMemcpyAsync(sb->d_gm, sb->h_gm, b8 * G, cudaMemcpyHostToDevice, s);
+    if (r == cudaSuccess) r = cudaMemcpyAsync(sb->d_order, sb->h_order, b4 * G, cudaMemcpyHostToDevice, s);
+    if (r == cudaSuccess) r = cudaMemsetAsync(sb->d_misc, 0, b4 * (kSmallClasses + 1), s);
+    if (r == cudaSuccess) r = cudaMemsetAsync(sb->d_csum, 0, sizeof(unsigned long long) * 26 * (size_t)G, s);
+    if (r != cudaSuccess) return r;
+    if (run_small_graphs(sb->d_rp, sb->d_voff, sb->d_ci, sb->d_eoff, sb->d_order, class_off, sb->d_misc,
+                         sb->d_misc + kSmallClasses, sb->d_csum, cfg, graph_mode ? nullptr : L->ev + kEvSmall0,
+                         s) != GC_OK)
+      return cudaErrorLaunchFailure;
     DevGraph dg = DevGraph();
     dg.G = G;
-    dg.gn = d_gn;
-    dg.gm = d_gm;
-    if ((st = run_derive(dg, d_csum, d_x, d_misc + 1, s)) != GC_OK) {
-      L->error = gc_last_error();
-      goto out;
+    dg.gn = sb->d_gn;
+    dg.gm = sb->d_gm;
+    if (run_derive(dg, sb->d_csum, sb->d_x, sb->d_misc + kSmallClasses, s) != GC_OK) return cudaErrorLaunchFailure;
+    r = cudaMemcpyAsync(h_x_dst, sb->d_x, sizeof(unsigned long long) * (size_t)G * 34, cudaMemcpyDeviceToHost, s);
+    if (r == cudaSuccess) r = cudaMemcpyAsync(L->h_status, sb->d_misc + kSmallClasses, b4, cudaMemcpyDeviceToHost, s);
+    return r;
+  };
+  GS_TRY(cudaEventRecord(L->ev[kEvSmallSeq0], s), "small event");
+  if (graph_mode) {
+    cudaGraph_t graph = nullptr;
+    GS_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "capture small-graph launch");
+    const cudaError_t r = issue();
+    const cudaError_t r2 = cudaStreamEndCapture(s, &graph);
+    if (r != cudaSuccess || r2 != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      GS_TRY(r != cudaSuccess ? r : r2, "capture small-graph launch");
     }
+    if (sb->exec) {
+      cudaGraphExecUpdateResultInfo info;
+      if (cudaGraphExecUpdate(sb->exec, graph, &info) != cudaSuccess) {
+        cudaGetLastError();
+        cudaGraphExecDestroy(sb->exec);
+        sb->exec = nullptr;
+      }
+    }
+    if (!sb->exec) {
+      e = cudaGraphInstantiate(&sb->exec, graph, 0);
+      if (e != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        sb->exec = nullptr;
+        GS_TRY(e, "instantiate small-graph launch");
+      }
+    }
+    cudaGraphDestroy(graph);
+    GS_TRY(cudaGraphLaunch(sb->exec, s), "replay small-graph launch");
+    L->replayed = true;
+  } else {
+    GS_TRY(issue(), "small-graph launch");
+    L->timed_classes = true;
   }
-  GS_TRY(cudaMemcpyAsync(h_x_dst, d_x, sizeof(unsigned long long) * (size_t)G * 34, cudaMemcpyDeviceToHost, s),
-         "small copy out");
-out:
+  GS_TRY(cudaEventRecord(L->ev[kEvSmallSeq1], s), "small event");
+  GS_TRY(cudaEventRecord(sb->busy, s), "small event");
+  L->timed_small = true;
 #undef GS_TRY
-  for (void* p : {(void*)d_rp, (void*)d_ci, (void*)d_voff, (void*)d_eoff, (void*)d_gn, (void*)d_gm, (void*)d_order,
-                  (void*)d_misc, (void*)d_csum, (void*)d_x})
-    if (p) cudaFreeAsync(p, s);
-  return st;
+  return GC_OK;
 }
 
-// Counts `graphs` as one launch on `s`: small graphs on the bitmatrix kernel,
+// Counts `graphs` as one launch on `s`: small graphs on the bitmatrix kernels,
 // the others as one disjoint union. Results land in L->h_x when L->done
 // completes. Runs in the dispatcher thread (or the flushing thread in manual
 // mode) without holding the batch lock.
-void run_launch(std::vector<PendingGraph>& graphs, cudaStream_t s, Launch* L) {
+void run_launch(gc_batch b, std::vector<PendingGraph>& graphs, cudaStream_t s, Launch* L) {
+  const BatchConfig cfg = L->cfg;
+  auto is_small = [&](const PendingGraph& pg) {
+    return pg.n <= cfg.small_n_max && small_class_of(pg.n) < kSmallClasses;
+  };
   std::vector<PendingGraph*> small, large;
-  for (auto& pg : graphs) (pg.n <= kSmallN ? small : large).push_back(&pg);
+  for (auto& pg : graphs) (is_small(pg) ? small : large).push_back(&pg);
   L->slot.resize(graphs.size());
   {
     int32_t is = 0, il = (int32_t)small.size();
-    for (size_t k = 0; k < graphs.size(); ++k) L->slot[k] = graphs[k].n <= kSmallN ? is++ : il++;
+    for (size_t k = 0; k < graphs.size(); ++k) L->slot[k] = is_small(graphs[k]) ? is++ : il++;
   }
   gc_status st = GC_OK;
   L->h_status[0] = 0;
-  if (!small.empty()) st = run_small(small, s, L, L->h_x);
-  if (st == GC_OK && !large.empty()) st = run_union(large, s, L, L->h_x + 34 * small.size(), L->h_status);
+  L->h_status[1] = 0;
+  for (auto& ev : L->ev)
+    if (cudaEventCreate(&ev) != cudaSuccess) {
+      L->launch_status = cuda_fail(cudaGetLastError(), "batch event");
+      L->error = gc_last_error();
+      return;
+    }
+  if (!small.empty()) st = run_small(small, s, L, L->h_x, &b->small[L->stream_slot], cfg);
+  if (st == GC_OK && !large.empty()) {
+    cudaEventRecord(L->ev[kEvUnion0], s);
+    st = run_union(large, s, L, L->h_x + 34 * small.size(), L->h_status + 1);
+    cudaEventRecord(L->ev[kEvUnion1], s);
+    L->timed_union = st == GC_OK;
+  }
   L->launch_status = st;
   if (st == GC_OK) {
     cudaError_t e = cudaEventRecord(L->done, s);
@@ -373,11 +506,23 @@ void retire_locked(gc_batch b) {
         L->error = gc_last_error();
       }
     }
+    if (L->launch_status == GC_OK) {  // device times of the launch
+      auto ms = [&](int a, int z) {
+        float f = 0.f;
+        return cudaEventElapsedTime(&f, L->ev[a], L->ev[z]) == cudaSuccess ? (double)f : 0.0;
+      };
+      for (int c = 0; c < kSmallClasses; ++c)
+        b->last_stats[c] = L->timed_classes ? ms(kEvSmall0 + c, kEvSmall0 + c + 1) : 0.0;
+      b->last_stats[kSmallClasses] = L->timed_small ? ms(kEvSmallSeq0, kEvSmallSeq1) : 0.0;
+      b->last_stats[kSmallClasses + 1] = L->timed_union ? ms(kEvUnion0, kEvUnion1) : 0.0;
+      b->last_stats[kSmallClasses + 2] = L->replayed ? 1.0 : 0.0;
+      cudaGetLastError();
+    }
     for (size_t k = 0; k < L->tickets.size(); ++k) {
       Result r;
       if (L->launch_status == GC_OK) {
         std::memcpy(r.x, L->h_x + 34 * (size_t)L->slot[k], sizeof(r.x));
-        int32_t dst = *L->h_status;
+        const int32_t dst = L->h_status[0] | L->h_status[1];
         r.status = dst == 0 ? GC_OK : GC_ERR_CUDA;
       } else {
         std::memset(r.x, 0, sizeof(r.x));
@@ -389,6 +534,8 @@ void retire_locked(gc_batch b) {
     cudaFreeHost(L->h_x);
     cudaFreeHost(L->h_status);
     cudaEventDestroy(L->done);
+    for (auto& ev : L->ev)
+      if (ev) cudaEventDestroy(ev);
     delete L;
     b->inflight.erase(b->inflight.begin() + i);
     b->cv.notify_all();
@@ -417,17 +564,19 @@ bool launch_pending(gc_batch b) {
       take.push_back(std::move(pg));
       b->pending.pop_front();
     }
+    L->stream_slot = b->next_stream;
+    L->cfg = b->cfg;
     L->stream = b->streams[b->next_stream];
     b->next_stream ^= 1;
   }
   cudaSetDevice(b->device);
   cudaError_t e1 = cudaMallocHost(&L->h_x, sizeof(unsigned long long) * 34 * take.size());
-  cudaError_t e2 = cudaMallocHost(&L->h_status, sizeof(int32_t));
+  cudaError_t e2 = cudaMallocHost(&L->h_status, 2 * sizeof(int32_t));  // small graphs, union
   cudaError_t e3 = cudaEventCreateWithFlags(&L->done, cudaEventDisableTiming);
   if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
     L->launch_status = GC_ERR_NOMEM;
   } else {
-    run_launch(take, L->stream, L);
+    run_launch(b, take, L->stream, L);
   }
   {
     std::lock_guard<std::mutex> lk(b->mu);
@@ -479,8 +628,52 @@ gc_status gc_batch_create(int64_t device_mem_budget_bytes, uint32_t flags, gc_ba
     }
   }
   count_grid_size();
+  gc_status st = small_graphs_setup();
+  if (st != GC_OK) {
+    for (auto& t : b->streams) cudaStreamDestroy(t);
+    delete b;
+    return st;
+  }
+  load_tuned_config(&b->cfg, nullptr);
   if (!(flags & GC_BATCH_MANUAL)) b->dispatcher = std::thread(dispatcher_main, b);
   *out = b;
+  return GC_OK;
+}
+
+gc_status gc_batch_set_param(gc_batch b, int32_t param, int32_t value) {
+  if (!b) { set_error("batch is NULL"); return GC_ERR_ARG; }
+  std::lock_guard<std::mutex> lk(b->mu);
+  if (param == GC_PARAM_SMALL_N_MAX) {
+    if (value < 0 || value > kSmallClassN[kSmallClasses - 1]) { set_error("small_n_max outside [0, 1024]"); return GC_ERR_ARG; }
+    b->cfg.small_n_max = value;
+  } else if (param >= GC_PARAM_BLOCK_N64 && param < GC_PARAM_BLOCK_N64 + kSmallClasses) {
+    if (value != 64 && value != 128 && value != 256 && value != 512) { set_error("block must be 64, 128, 256 or 512"); return GC_ERR_ARG; }
+    b->cfg.class_block[param - GC_PARAM_BLOCK_N64] = value;
+  } else if (param == GC_PARAM_USE_GRAPH) {
+    if (value != 0 && value != 1) { set_error("use_graph must be 0 or 1"); return GC_ERR_ARG; }
+    b->cfg.use_graph = value;
+  } else {
+    set_error("unknown parameter");
+    return GC_ERR_ARG;
+  }
+  return GC_OK;
+}
+
+gc_status gc_batch_get_param(gc_batch b, int32_t param, int32_t* value) {
+  if (!b || !value) { set_error("NULL argument"); return GC_ERR_ARG; }
+  std::lock_guard<std::mutex> lk(b->mu);
+  if (param == GC_PARAM_SMALL_N_MAX) *value = b->cfg.small_n_max;
+  else if (param >= GC_PARAM_BLOCK_N64 && param < GC_PARAM_BLOCK_N64 + kSmallClasses)
+    *value = b->cfg.class_block[param - GC_PARAM_BLOCK_N64];
+  else if (param == GC_PARAM_USE_GRAPH) *value = b->cfg.use_graph;
+  else { set_error("unknown parameter"); return GC_ERR_ARG; }
+  return GC_OK;
+}
+
+gc_status gc_batch_last_stats(gc_batch b, double* out) {
+  if (!b || !out) { set_error("NULL argument"); return GC_ERR_ARG; }
+  std::lock_guard<std::mutex> lk(b->mu);
+  for (int i = 0; i < GC_BATCH_STATS; ++i) out[i] = b->last_stats[i];
   return GC_OK;
 }
 
@@ -635,6 +828,50 @@ gc_status gc_batch_poll(gc_batch b, uint64_t ticket, uint64_t* global_out, uint6
   }
 }
 
+gc_status gc_batch_poll_many(gc_batch b, int64_t G, const uint64_t* tickets, uint64_t* global_out,
+                             uint64_t* global_hi, int32_t timeout_us) {
+  if (!b || G < 0 || (G > 0 && (!tickets || !global_out))) { set_error("bad arguments"); return GC_ERR_ARG; }
+  const auto deadline = std::chrono::steady_clock::now() + std::chrono::microseconds(timeout_us > 0 ? timeout_us : 0);
+  std::unique_lock<std::mutex> lk(b->mu);
+  for (int64_t i = 0; i < G; ++i)
+    if (!b->live.count(tickets[i])) {
+      set_error("ticket " + std::to_string(i) + " is unknown or retired");
+      return GC_ERR_ARG;
+    }
+  int64_t ready = 0;  // tickets[0 .. ready) are known to be done
+  for (;;) {
+    if (b->flags & GC_BATCH_MANUAL) retire_locked(b);
+    while (ready < G && b->done.count(tickets[ready])) ++ready;
+    if (ready == G) break;
+    if (timeout_us == 0) return GC_PENDING;
+    if (timeout_us > 0 && std::chrono::steady_clock::now() >= deadline) return GC_PENDING;
+    b->cv.wait_for(lk, std::chrono::microseconds(50));
+  }
+  gc_status first = GC_OK;
+  bool need_hi = false;
+  for (int64_t i = 0; i < G; ++i) {
+    auto it = b->done.find(tickets[i]);
+    const Result r = it->second;
+    b->done.erase(it);
+    b->live.erase(tickets[i]);
+    if (r.status != GC_OK && first == GC_OK) {
+      first = r.status;
+      set_error("the launch of ticket " + std::to_string(i) + " failed");
+    }
+    for (int k = 0; k < 17; ++k) {
+      global_out[17 * i + k] = r.x[2 * k];
+      if (global_hi) global_hi[17 * i + k] = r.x[2 * k + 1];
+      if (r.x[2 * k + 1]) need_hi = true;
+    }
+  }
+  if (first != GC_OK) return first;
+  if (need_hi && !global_hi) {
+    set_error("a global count exceeds 64 bits and global_hi is NULL");
+    return GC_ERR_OVERFLOW;
+  }
+  return GC_OK;
+}
+
 gc_status gc_batch_destroy(gc_batch b) {
   if (!b) return GC_OK;
   {
@@ -648,6 +885,7 @@ gc_status gc_batch_destroy(gc_batch b) {
     std::lock_guard<std::mutex> lk(b->mu);
     retire_locked(b);
   }
+  for (auto& sb : b->small) free_small_bufs(&sb);
   for (auto& s : b->streams) cudaStreamDestroy(s);
   delete b;
   return GC_OK;

@@ -90,8 +90,10 @@ struct KLayout {
 
 // kTri: the triangle step alone (|T| per edge, Alg. 1): every triangle is an
 // edge of exactly one H_a, so phase 1 adds 1 to that edge and to the two
-// edges (a, b_i), (a, b_j), and nothing else runs.
-template <int kCap, int kThreads, bool kTri>
+// edges (a, b_i), (a, b_j), and nothing else runs. kDeg (with kTri): each
+// triangle also adds the degree of its third vertex to each of its edges,
+// so that a.dsum[e] = sum_{w in T_e} d_w (for the per-edge induced counts).
+template <int kCap, int kThreads, bool kTri, bool kDeg = false>
 __global__ void __launch_bounds__(kThreads, 65536 / (kThreads * 64)) k_pass_k(DevGraph g, CountArgs a, int tier) {
   constexpr int kW = kThreads / 32;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -150,12 +152,13 @@ __global__ void __launch_bounds__(kThreads, 65536 / (kThreads * 64)) k_pass_k(De
       ids[i] = g.out_idx[ob + i];
       vx7[i] = 0u;
       vx7h[i] = 0u;
-      if (!kTri) {
-        ta[i] = a.trio[ob + i];
+      if (!kTri || kDeg) {
+        ta[i] = kTri ? g.deg[ids[i]] : a.trio[ob + i];  // kDeg: the member's degree
         vcr[i] = 0u;
         vcrh[i] = 0u;
       }
     }
+    const int32_t da = kDeg ? g.deg[av] : 0;
     // pass K with the edges of H_a kept by pass T: no hash, no scan
     const int32_t lcnt = (!kTri && a.tlist) ? a.tl_cnt[ui] : -1;
     if (lcnt < 0) {
@@ -259,6 +262,15 @@ __global__ void __launch_bounds__(kThreads, 65536 / (kThreads * 64)) k_pass_k(De
             if (j >= 0) {
               atomicAdd(&a.trio[q], 1);  // edge (b_i, c)
               atomicAdd(&vx7[j], 1u);    // edge (a, c)
+              if (kDeg) {
+                atomicAdd(&a.dsum[q], (unsigned long long)da);               // edge (b_i, c): third vertex a
+                add_split(vcr, vcrh, j, (unsigned long long)ta[i]);          // edge (a, c): third vertex b_i
+              }
+            }
+            if (kDeg && hit) {  // edge (a, b_i): third vertices c
+              unsigned long long sd = j >= 0 ? (unsigned long long)ta[j] : 0ull;
+              for (int o = 16; o; o >>= 1) sd += __shfl_xor_sync(kFull, sd, o);
+              if (lane == 0) add_split(vcr, vcrh, i, sd);
             }
             if (lane == 0 && hit) {
               atomicAdd(&vx7[i], (uint32_t)__popc(hit));  // edge (a, b_i)
@@ -290,8 +302,13 @@ __global__ void __launch_bounds__(kThreads, 65536 / (kThreads * 64)) k_pass_k(De
     }
     __syncthreads();
     if (kTri) {
-      for (int32_t i = threadIdx.x; i < k; i += kThreads)
+      for (int32_t i = threadIdx.x; i < k; i += kThreads) {
         if (vx7[i]) atomicAdd(&a.trio[ob + i], (int32_t)vx7[i]);
+        if (kDeg) {
+          const unsigned long long sd = read_split(vcr, vcrh, i);
+          if (sd) atomicAdd(&a.dsum[ob + i], sd);
+        }
+      }
       if (a.tlist) {  // hand the edges of H_a on to pass K, if they fit
         const int32_t nh = s_nhit;
         if (threadIdx.x == 0) {
@@ -449,7 +466,7 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long x)
   return x;
 }
 
-template <bool kTri>
+template <bool kTri, bool kDeg = false>
 __global__ void __launch_bounds__(kWBlock) k_pass_k_warp(DevGraph g, CountArgs a, int tier) {
   __shared__ int32_t s_q[kWWarps][32 * 32];  // out-slot of edge (i, j) found from member i
   __shared__ uint32_t s_rowf[kWWarps][64];    // rows and found masks rebuilt from pass T's list
@@ -472,6 +489,8 @@ __global__ void __launch_bounds__(kWBlock) k_pass_k_warp(DevGraph g, CountArgs a
     }
     const int32_t id = lane < k ? g.out_idx[ob + lane] : 0x7fffffff;
     const int32_t ti = (!kTri && lane < k) ? a.trio[ob + lane] : 0;
+    const int32_t dl = (kDeg && lane < k) ? g.deg[id] : 0;  // kDeg: degree of member b_lane
+    const int32_t da = kDeg ? g.deg[av] : 0;
     const int32_t cmax = __shfl_sync(kFull, id, k - 1);
     unsigned row = 0u, found = 0u;
     const int32_t lcnt = (!kTri && a.tlist) ? a.tl_cnt[ui] : -1;
@@ -520,6 +539,7 @@ __global__ void __launch_bounds__(kWBlock) k_pass_k_warp(DevGraph g, CountArgs a
           const bool hit = c <= cmax && id_lo == c && lo < k;  // lanes >= k hold padding ids
           if (hit) {
             if (kTri) atomicAdd(&a.trio[q], 1);  // edge (b_i, c)
+            if (kDeg) atomicAdd(&a.dsum[q], (unsigned long long)da);  // its third vertex a
             qs[i * 32 + lo] = q;
           }
           hits |= __reduce_or_sync(kFull, hit ? 1u << lo : 0u);
@@ -536,6 +556,14 @@ __global__ void __launch_bounds__(kWBlock) k_pass_k_warp(DevGraph g, CountArgs a
     }  // scan
     if (kTri) {  // edge (a, b_lane): one triangle per edge of H_a at lane
       if (lane < k && row) atomicAdd(&a.trio[ob + lane], __popc(row));
+      if (kDeg) {  // and the degrees of their third vertices b_i
+        unsigned long long sd = 0;
+        for (int i = 0; i < k; ++i) {
+          const int32_t di = __shfl_sync(kFull, dl, i);
+          if ((row >> i) & 1u) sd += (unsigned long long)di;
+        }
+        if (lane < k && sd) atomicAdd(&a.dsum[ob + lane], sd);
+      }
       if (lane == 0) w_members += k;
       if (a.tlist) {  // hand the edges of H_a on to pass K
         const int c = __popc(found);
@@ -621,12 +649,12 @@ __global__ void __launch_bounds__(kWBlock) k_pass_k_warp(DevGraph g, CountArgs a
   }
 }
 
-template <int kCap, int kThreads, bool kTri>
+template <int kCap, int kThreads, bool kTri, bool kDeg = false>
 gc_status launch_tier(const DevGraph& g, const CountArgs& a, int tier, cudaStream_t s, int* launches) {
   const int32_t units = a.ktier_off[tier + 1] - a.ktier_off[tier];
   if (units <= 0) return GC_OK;
   const size_t smem = kCap ? KLayout(kCap, !kTri).total : 0;
-  auto kern = k_pass_k<kCap, kThreads, kTri>;
+  auto kern = k_pass_k<kCap, kThreads, kTri, kDeg>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return cuda_fail(e, "k_pass_k attribute");
   int grid = 0;
@@ -647,7 +675,7 @@ gc_status launch_tier(const DevGraph& g, const CountArgs& a, int tier, cudaStrea
   return e == cudaSuccess ? GC_OK : cuda_fail(e, "k_pass_k");
 }
 
-template <bool kTri>
+template <bool kTri, bool kDeg = false>
 gc_status run_tiers(const DevGraph& g, const CountArgs& a, cudaStream_t s, int* launches) {
   gc_status st;
   if (a.ktier_off[kTierGlobal + 1] > a.ktier_off[kTierGlobal]) {
@@ -655,20 +683,20 @@ gc_status run_tiers(const DevGraph& g, const CountArgs& a, cudaStream_t s, int* 
       set_error("internal: pass K global buffers missing");
       return GC_ERR_CUDA;
     }
-    if ((st = launch_tier<0, 1024, kTri>(g, a, kTierGlobal, s, launches)) != GC_OK) return st;
+    if ((st = launch_tier<0, 1024, kTri, kDeg>(g, a, kTierGlobal, s, launches)) != GC_OK) return st;
   }
-  if ((st = launch_tier<1024, 1024, kTri>(g, a, kTier1024, s, launches)) != GC_OK) return st;
-  if ((st = launch_tier<512, 512, kTri>(g, a, kTier512, s, launches)) != GC_OK) return st;
-  if ((st = launch_tier<256, 512, kTri>(g, a, kTier256, s, launches)) != GC_OK) return st;
+  if ((st = launch_tier<1024, 1024, kTri, kDeg>(g, a, kTier1024, s, launches)) != GC_OK) return st;
+  if ((st = launch_tier<512, 512, kTri, kDeg>(g, a, kTier512, s, launches)) != GC_OK) return st;
+  if ((st = launch_tier<256, 512, kTri, kDeg>(g, a, kTier256, s, launches)) != GC_OK) return st;
   const int32_t units = a.ktier_off[kTier32 + 1] - a.ktier_off[kTier32];
   if (units > 0) {
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pass_k_warp<kTri>, kWBlock, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pass_k_warp<kTri, kDeg>, kWBlock, 0);
     if (e != cudaSuccess) return cuda_fail(e, "k_pass_k_warp occupancy");
     int grid = (per_sm > 0 ? per_sm : 1) * (count_grid_size() / kCtasPerSm);
     const int need = (units + kWWarps - 1) / kWWarps;
     if (grid > need) grid = need;
-    k_pass_k_warp<kTri><<<grid, kWBlock, 0, s>>>(g, a, kTier32);
+    k_pass_k_warp<kTri, kDeg><<<grid, kWBlock, 0, s>>>(g, a, kTier32);
     ++*launches;
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "k_pass_k_warp");
@@ -685,7 +713,7 @@ gc_status run_pass_k(const DevGraph& g, const CountArgs& a, cudaStream_t s, int*
 }
 
 gc_status run_pass_t(const DevGraph& g, const CountArgs& a, cudaStream_t s, int* launches) {
-  return run_tiers<true>(g, a, s, launches);
+  return a.dsum ? run_tiers<true, true>(g, a, s, launches) : run_tiers<true>(g, a, s, launches);
 }
 
 }  // namespace gc

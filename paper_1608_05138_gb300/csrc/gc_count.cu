@@ -150,6 +150,110 @@ __global__ void __launch_bounds__(kFinBlock) k_finish(DevGraph g, CountArgs a) {
   if (lane == 0 && w_edges) atomicAdd(a.work + kWorkFinishEdges, (unsigned long long)w_edges);
 }
 
+// ---------------- per-edge induced 4-node counts ----------------
+// Per vertex x: vsum[2x] = sum over Gamma(x) of |T| of the edge (twice the
+// triangles at x), vsum[2x + 1] = sum over Gamma(x) of the neighbour's
+// degree. One warp per vertex.
+__global__ void __launch_bounds__(256) k_vertex_sums(DevGraph g, const int32_t* __restrict__ trio,
+                                                     unsigned long long* __restrict__ vsum) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t x = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < g.n; x += warps) {
+    unsigned long long t2 = 0, ns = 0;
+    for (int32_t p = g.rp[x] + lane; p < g.rp[x + 1]; p += 32) {
+      ns += (unsigned long long)g.deg[g.ci[p]];
+      t2 += (unsigned long long)trio[g.e2o[g.eid[p]]];
+    }
+    for (int o = 16; o; o >>= 1) {
+      t2 += __shfl_xor_sync(0xffffffffu, t2, o);
+      ns += __shfl_xor_sync(0xffffffffu, ns, o);
+    }
+    if (lane == 0) {
+      vsum[2 * x] = t2;
+      vsum[2 * x + 1] = ns;
+    }
+  }
+}
+
+// For the edge e = (u, v) and the other vertices split into T, S_u, S_v (Fig.
+// 2) and the rest R (|R| = D_e), the induced subgraph on {u, v, a, b} depends
+// on the classes of a and b and on whether a ~ b. With A_XY the adjacent
+// pairs between classes X and Y, the counts of H_7..H_16 containing e are
+//   H7 = A_TT = x7            H8 = C(|T|,2) - A_TT + A_TS
+//   H9 = |T||S| - A_TS + A_TR + A_SS                 H10 = A_SuSv = x10
+//   H11 = C(|S_u|,2) + C(|S_v|,2) - A_SS             H12 = |S_u||S_v| - x10 + A_SR
+//   H13 = |T||R| - A_TR      H14 = A_RR     H15 = |S||R| - A_SR     H16 = C(|R|,2) - A_RR
+// (S = S_u + S_v, A_SS = A_SuSu + A_SvSv). The A's follow from quantities the
+// passes already have, by counting incidences:
+//   A_TS = cross(e) - 4 x7          (sum over T of |T_(w,u)| - 1 is 2 x7 + A_TSu)
+//   A_SS = tri(u) + tri(v) - 2|T| - 2 x7 - A_TS      (triangles at u: |T| + x7 + A_TSu + A_SuSu)
+//   A_TR = sum_T d_w - 2|T| - 2 x7 - A_TS            (degrees of T: u, v, T, S, R)
+//   A_SR = sum_S d_w - |S| - A_TS - 2 A_SS - 2 x10   (sum_S d_w = NS(u) - d_v + NS(v) - d_u - 2 sum_T d_w)
+//   A_RR = m - 1 - 2|T| - |S| - x7 - A_TS - A_SS - x10 - A_TR - A_SR
+// with tri(x) the triangles at x and NS(x) the sum of the neighbours' degrees.
+// Rows are staged per warp like k_finish (kByEdge: 32 consecutive edge ids).
+constexpr int kIndCols = 10;
+static_assert(kIndCols == GC_INDUCED_COLS, "induced columns");
+template <bool kByEdge>
+__global__ void __launch_bounds__(kFinBlock) k_finish_induced(DevGraph g, CountArgs a,
+                                                              const unsigned long long* __restrict__ vsum,
+                                                              unsigned long long* __restrict__ out) {
+  __shared__ unsigned long long st[kFinBlock / 32][32][kIndCols];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  unsigned long long(*rowv)[kIndCols] = st[warp];
+  const unsigned long long* flat = &st[warp][0][0];
+  const int64_t stride = (int64_t)gridDim.x * (kFinBlock / 32) * 32;
+  for (int64_t e0 = ((int64_t)blockIdx.x * (kFinBlock / 32) + warp) * 32; e0 < g.m; e0 += stride) {
+    const int64_t i0 = e0 + lane;  // edge id (kByEdge) or out-slot
+    int32_t eid = 0;
+    if (i0 < g.m) {
+      int32_t o = kByEdge ? g.e2o[i0] : (int32_t)i0;
+      if ((uint32_t)o >= (uint32_t)g.m) o = 0;  // only for invalid input
+      const int32_t p = g.ocsr[o];
+      if (!kByEdge) eid = g.eid[p];
+      const int32_t r = g.rev[p];
+      const int32_t u = g.ci[r], v = g.ci[p];
+      const int32_t gid = g.vgid ? g.vgid[u] : 0;
+      const int64_t du = g.deg[u], dv = g.deg[v];
+      const int64_t t = a.trio[o];
+      const int64_t x7 = (int64_t)a.xc[2 * (size_t)o], cross = (int64_t)a.xc[2 * (size_t)o + 1];
+      const int64_t x10 = (int64_t)(a.P[p] + a.P[r]) - cross + 2 * x7;
+      const int64_t su = du - t - 1, sv = dv - t - 1, S = su + sv;
+      const int64_t R = (int64_t)g.gn[gid] - 2 - t - S;
+      const int64_t sdT = (int64_t)a.dsum[o];
+      const int64_t aTS = cross - 4 * x7;
+      const int64_t aSS = (int64_t)((vsum[2 * (size_t)u] + vsum[2 * (size_t)v]) / 2) - 2 * t - 2 * x7 - aTS;
+      const int64_t aTR = sdT - 2 * t - 2 * x7 - aTS;
+      const int64_t sdS = (int64_t)vsum[2 * (size_t)u + 1] - dv + (int64_t)vsum[2 * (size_t)v + 1] - du - 2 * sdT;
+      const int64_t aSR = sdS - S - aTS - 2 * aSS - 2 * x10;
+      const int64_t aRR = g.gm[gid] - 1 - 2 * t - S - x7 - aTS - aSS - x10 - aTR - aSR;
+      unsigned long long* rw = rowv[lane];
+      rw[0] = (unsigned long long)x7;
+      rw[1] = (unsigned long long)(t * (t - 1) / 2 - x7 + aTS);
+      rw[2] = (unsigned long long)(t * S - aTS + aTR + aSS);
+      rw[3] = (unsigned long long)x10;
+      rw[4] = (unsigned long long)(su * (su - 1) / 2 + sv * (sv - 1) / 2 - aSS);
+      rw[5] = (unsigned long long)(su * sv - x10 + aSR);
+      rw[6] = (unsigned long long)(t * R - aTR);
+      rw[7] = (unsigned long long)aRR;
+      rw[8] = (unsigned long long)(S * R - aSR);
+      rw[9] = (unsigned long long)(R * (R - 1) / 2 - aRR);
+    }
+    __syncwarp();
+    const int rows = (int)min((int64_t)32, (int64_t)g.m - e0);
+    if (kByEdge) {
+      unsigned long long* dst = out + (size_t)e0 * kIndCols;
+      for (int i = lane; i < rows * kIndCols; i += 32) dst[i] = flat[i];
+    } else {
+      for (int r = 0; r < rows; ++r) {
+        const int32_t er = __shfl_sync(0xffffffffu, eid, r);
+        if (lane < kIndCols) out[(size_t)er * kIndCols + lane] = rowv[r][lane];
+      }
+    }
+    __syncwarp();
+  }
+}
+
 // ---------------- pass C: 4-cycles through every edge ----------------
 // P(e) = number of 4-cycles (as subgraphs) containing e. Each 4-cycle is
 // counted from its highest-rank vertex h: with cnt_h(o) = #{x in Gamma(h) :
@@ -308,9 +412,16 @@ __device__ __forceinline__ int deal_owner(const Deal& d, int32_t L, int32_t k0, 
   return comp[r < 0 ? 0 : r];
 }
 
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
 __global__ void __launch_bounds__(kHeavyBlock, 1) k_pass_c_heavy(DevGraph g, CountArgs a) {
   extern __shared__ uint32_t tab[];  // kHeavyTab counters
   __shared__ int32_t s_unit, s_nx, s_chunk[2];
+  const unsigned long long t_start = global_ns();
   __shared__ unsigned long long s_sx[kHeavyWarps][32];
   __shared__ uint32_t s_sx32[kHeavyWarps][32];  // the short runs' part (< 32 entries x counts < 2^26)
   __shared__ int32_t s_comp[kHeavyWarps][32];
@@ -319,14 +430,15 @@ __global__ void __launch_bounds__(kHeavyBlock, 1) k_pass_c_heavy(DevGraph g, Cou
   int32_t* cur = beg + a.cbuf_nx;
   int32_t* endp = cur + a.cbuf_nx;
   int32_t* comp = s_comp[warp];
-  long long w_wedge = 0, w_blocks = 0;
+  long long w_wedge = 0, w_blocks = 0, w_jobs = 0;
   for (;;) {
     __syncthreads();
     if (threadIdx.x == 0) s_unit = atomicAdd(a.cursor + 8, 1);
     __syncthreads();
-    const int32_t k = s_unit;
-    if (k >= a.n_cheavy) break;
-    const int32_t h = a.cunits[k];
+    const int32_t jb = s_unit;
+    if (jb >= a.n_cjobs) break;
+    const int4 job = a.cjobs[jb];  // hub (index into cunits), first block, blocks
+    const int32_t h = a.cunits[job.x];
     const int32_t hb = g.rp[h], he = g.rp[h + 1];
     if (threadIdx.x == 0) {
       int32_t lo = hb, hi = he;  // first slot of Gamma(h) with id >= h
@@ -345,17 +457,20 @@ __global__ void __launch_bounds__(kHeavyBlock, 1) k_pass_c_heavy(DevGraph g, Cou
     const int32_t nchunks = (nx + 31) >> 5;
     const bool half = nx < 65536;
     const int32_t span = half ? 2 * kHeavyTab : kHeavyTab;
+    const int64_t job_lo = (int64_t)job.y * span;                       // the job's o-range
+    const int64_t job_hi = min((int64_t)h, job_lo + (int64_t)job.z * span);
     for (int32_t i = threadIdx.x; i < nx; i += kHeavyBlock) {
       const int32_t x = g.ci[hb + i];
       const int32_t xb = g.rp[x];
       const int32_t lo = min(max(g.rev[hb + i], xb), g.rp[x + 1]);  // Gamma(x) below the slot of (x, h) is < h
-      cur[i] = xb;
+      cur[i] = job.y == 0 ? xb : gallop_lower_bound(g.ci, xb, lo, (int32_t)job_lo);
       endp[i] = lo;
-      w_wedge += lo - xb;
+      if (job.y == 0) w_wedge += lo - xb;  // the hub's wedges, counted by its first job
     }
-    for (int64_t lo64 = 0; lo64 < h; lo64 += span) {
+    if (threadIdx.x == 0) ++w_jobs;
+    for (int64_t lo64 = job_lo; lo64 < job_hi; lo64 += span) {
       const int32_t lo_id = (int32_t)lo64;
-      const int32_t r1 = (int32_t)min(lo64 + span, (int64_t)h);
+      const int32_t r1 = (int32_t)min(lo64 + span, job_hi);
       const int32_t words = half ? (r1 - lo_id + 1) >> 1 : r1 - lo_id;
       for (int32_t i = threadIdx.x; i < words; i += kHeavyBlock) tab[i] = 0u;
       if (threadIdx.x == 0) {
@@ -510,7 +625,14 @@ __global__ void __launch_bounds__(kHeavyBlock, 1) k_pass_c_heavy(DevGraph g, Cou
     atomicAdd(a.work + kWorkCWedge, (unsigned long long)w_wedge);
     atomicAdd(a.work + kWorkCHeavyWedge, (unsigned long long)w_wedge);
   }
-  if (threadIdx.x == 0 && w_blocks) atomicAdd(a.work + kWorkCBlocks, (unsigned long long)w_blocks);
+  if (threadIdx.x == 0) {
+    if (w_blocks) atomicAdd(a.work + kWorkCBlocks, (unsigned long long)w_blocks);
+    if (w_jobs) atomicAdd(a.work + kWorkCHubJobs, (unsigned long long)w_jobs);
+    const unsigned long long life = global_ns() - t_start;
+    atomicAdd(a.work + kWorkCHubCtas, 1ull);
+    atomicAdd(a.work + kWorkCHubBusySum, life);
+    atomicMax(a.work + kWorkCHubBusyMax, life);
+  }
 }
 
 // ---------------- pass C for units of at most kHashMaxW wedges ----------------
@@ -720,7 +842,8 @@ gc_status run_pass_c_heavy(const DevGraph& g, const CountArgs& a, cudaStream_t s
   cudaError_t e = cudaFuncSetAttribute(k_pass_c_heavy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return cuda_fail(e, "k_pass_c_heavy");
   int grid = count_grid_size() / kCtasPerSm;
-  if (grid > a.n_cheavy) grid = a.n_cheavy;
+  if (grid > a.n_cjobs) grid = a.n_cjobs;
+  if (grid < 1) return GC_OK;
   k_pass_c_heavy<<<grid, kHeavyBlock, smem, s>>>(g, a);
   e = cudaGetLastError();
   return e == cudaSuccess ? GC_OK : cuda_fail(e, "k_pass_c_heavy");
@@ -745,6 +868,21 @@ gc_status run_finish(const DevGraph& g, const CountArgs& a, cudaStream_t s) {
   else k_finish<false><<<blocks, kFinBlock, 0, s>>>(g, a);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? GC_OK : cuda_fail(e, "k_finish");
+}
+
+gc_status run_induced(const DevGraph& g, const CountArgs& a, unsigned long long* vsum, uint64_t* out, bool out_host,
+                      cudaStream_t s) {
+  if (g.m == 0) return GC_OK;
+  const int vblocks = (int)min((int64_t)count_grid_size() * 4, ((int64_t)g.n * 32 + 255) / 256);
+  k_vertex_sums<<<vblocks > 0 ? vblocks : 1, 256, 0, s>>>(g, a.trio, vsum);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "k_vertex_sums");
+  const int blocks = (int)min((int64_t)count_grid_size() * 4, ((int64_t)g.m + kFinBlock - 1) / kFinBlock);
+  unsigned long long* o = reinterpret_cast<unsigned long long*>(out);
+  if (out_host) k_finish_induced<true><<<blocks, kFinBlock, 0, s>>>(g, a, vsum, o);
+  else k_finish_induced<false><<<blocks, kFinBlock, 0, s>>>(g, a, vsum, o);
+  e = cudaGetLastError();
+  return e == cudaSuccess ? GC_OK : cuda_fail(e, "k_finish_induced");
 }
 
 gc_status run_derive(const DevGraph& g, const unsigned long long* csum, unsigned long long* x,

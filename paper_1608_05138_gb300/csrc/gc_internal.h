@@ -53,6 +53,9 @@ struct CountArgs {
   int32_t n_cheavy;        // hub units of pass C (cunits[0 .. n_cheavy))
   const int32_t* chash_w;  // wedges of the hashed units cunits[n_cheavy .. n_cheavy + n_chash)
   int32_t n_chash;
+  const int4* cjobs;       // pass C hub kernel: jobs (hub index into cunits, first o-range block, blocks),
+                           // heaviest first
+  int32_t n_cjobs;
   int32_t* cbuf;           // pass C hub kernel: per-CTA cursors (cbuf_ctas x 3 x cbuf_nx ints)
   int32_t cbuf_nx;
   const int32_t* kunits;   // pass K: lowest vertices a with |out(a)| >= 2, tiers in KTier order
@@ -80,6 +83,7 @@ struct CountArgs {
   unsigned long long* tlist_fill;
   long long* tl_off;
   int32_t* tl_cnt;
+  unsigned long long* dsum;  // [m] per out-slot: sum over T of d_w (pass T, per-edge induced counts only)
   uint64_t* per_edge;      // [m][13] device pointer or nullptr
   bool per_edge_host;      // per_edge maps pinned host memory
   unsigned long long* csum;  // [G][13][2] 128-bit unrestricted counts (lo, hi)
@@ -103,6 +107,10 @@ enum Work {
   kWorkTScan,          // pass T: out-list entries scanned
   kWorkTTriangles,     // pass T: triangles (each once)
   kWorkCHashWedge,     // pass C: wedges of the units counted in a shared-memory hash
+  kWorkCHubJobs,       // pass C: jobs of the hub kernel (hub units cut into ranges of o-range blocks)
+  kWorkCHubCtas,       // pass C: CTAs of the hub kernel
+  kWorkCHubBusySum,    // pass C: sum over the hub kernel's CTAs of their lifetime (ns, %globaltimer)
+  kWorkCHubBusyMax,    // pass C: the longest of those lifetimes (ns)
   kNumWork
 };
 
@@ -114,11 +122,11 @@ enum Status : int32_t { kOk = 0, kSpillOverflow = 1, kInexact = 2 };
 constexpr int kBlock = 512;            // threads per CTA of passes A and C
 constexpr int kCtasPerSm = 2;          // resident CTAs per SM of the persistent grids
 constexpr int kWarps = kBlock / 32;
-constexpr int kSmallN = 512;           // graphs up to this many vertices use the bitmatrix kernel
 constexpr int kSmemTableMax = 4096;    // Psi tables up to this many vertices live in shared memory
 
 // Phases timed with CUDA events.
-enum Phase { kPhasePassT = 0, kPhasePassC, kPhasePassK, kPhaseFinish, kPhaseDerive, kPhaseCopy, kNumPhases };
+enum Phase { kPhasePassT = 0, kPhasePassC, kPhasePassK, kPhaseFinish, kPhaseInduced, kPhaseDerive, kPhaseCopy,
+             kNumPhases };
 
 // Device scratch of one count (lazily grown; owned by a graph handle or by
 // one batch launch).
@@ -147,6 +155,8 @@ struct Scratch {
   unsigned long long* tl_fill = nullptr;
   unsigned long long* work = nullptr;  // [kNumWork]
   int32_t launches = 0;              // kernels launched by the last run_count
+  unsigned long long* dsum = nullptr;  // [m] per-edge induced counts: sum over T of d_w
+  unsigned long long* vsum = nullptr;  // [n][2] per-edge induced counts: 2 x triangles, neighbour degrees
 };
 // Allocates the scratch of a graph with m edges, Psi tables of table_n
 // vertices and largest out-degree kmax (stream-ordered).
@@ -163,13 +173,19 @@ struct KUnits {
   int32_t tier_off[kNumTiers + 1];
   const int32_t* cunits;   // pass C units: hubs, hashed units, the others
   int32_t n_cheavy;
+  const int4* cjobs;       // hub jobs (see CountArgs)
+  int32_t n_cjobs;
   const int32_t* chash_w;
   int32_t n_chash;
   int32_t n_cunits;        // pass C units in all (units without wedges are left out)
 };
+// induced (optional): [m][10] rows of the per-edge induced counts of H_7..H_16
+// (device pointer, or the device view of pinned host memory when
+// induced_host), written after the finish.
 gc_status run_count(const DevGraph& g, const int32_t* units, int32_t n_units, const KUnits& ku,
                     uint64_t* per_edge, unsigned long long* csum, unsigned long long* x, Scratch* sc,
-                    cudaStream_t s, cudaEvent_t* ev, bool per_edge_host = false);
+                    cudaStream_t s, cudaEvent_t* ev, bool per_edge_host = false, uint64_t* induced = nullptr,
+                    bool induced_host = false);
 
 // ---- host helpers (gc_api.cu) ----
 void set_error(const std::string& msg);
@@ -205,6 +221,8 @@ struct PrepBuffers {
   int32_t* cunits = nullptr;  // pass C units: hub units (heaviest first), hashed units (heaviest
                               // first), then the rest in unit order
   int32_t n_cheavy = 0;
+  int4* cjobs = nullptr;       // hub jobs, heaviest first (see CountArgs)
+  int32_t n_cjobs = 0;
   int32_t* chash_w = nullptr;  // wedges of each hashed unit
   int32_t n_chash = 0;
   int32_t n_cunits = 0;
@@ -231,12 +249,34 @@ void free_prep(PrepBuffers* p, cudaStream_t s);
 gc_status first_unreversed_slot(int64_t nnz, const int32_t* d_rev, int32_t* out, cudaStream_t s);
 
 // ---- small graphs on a shared-memory bitmatrix (gc_small.cu) ----
-// rp/voff: concatenated local row pointers and their offsets ([G'+1] for the
-// packed graphs); ci/eoff: concatenated local columns; order: the G graph
-// indices to count, largest first; csum [G'][13][2] zeroed.
+// Size classes of the bitmatrix kernel: class c takes graphs of at most
+// kSmallClassN[c] vertices (and more than the previous class).
+constexpr int kSmallClasses = 5;
+constexpr int kSmallClassN[kSmallClasses] = {64, 128, 256, 512, 1024};
+// Tunable parameters of the batched form (read from the tuning cache at
+// gc_batch_create, or set with gc_batch_set_param).
+struct BatchConfig {
+  int32_t small_n_max = 512;                                  // graphs up to this many vertices: bitmatrix kernels
+  int32_t class_block[kSmallClasses] = {256, 256, 256, 256, 256};  // threads per CTA of each size class
+  int32_t use_graph = 1;                                      // replay each small-graph launch as a CUDA graph
+};
+// Size class of a graph with n vertices (kSmallClasses if above the largest).
+int small_class_of(int32_t n);
+// Overrides cfg with the tuning cache's entry for the current GPU (gc_tune.cu);
+// false (cfg unchanged) when there is no cache or no entry.
+bool load_tuned_config(BatchConfig* cfg, std::string* source);
+// Raises the dynamic shared-memory limit of every instantiation (once per
+// device, before any launch or capture).
+gc_status small_graphs_setup();
+// rp/voff: concatenated local row pointers and their offsets; ci/eoff:
+// concatenated local columns; class c counts the graphs
+// order[class_off[c] .. class_off[c + 1]) (largest first within a class);
+// cursor: kSmallClasses zeroed device ints; status: device status word;
+// csum [*][13][2] zeroed. ev (optional): kSmallClasses + 1 events recorded
+// before each class's launch and after the last.
 gc_status run_small_graphs(const int32_t* rp, const int64_t* voff, const int32_t* ci, const int64_t* eoff,
-                           const int32_t* order, int32_t G, int32_t* cursor, unsigned long long* csum,
-                           cudaStream_t s);
+                           const int32_t* order, const int32_t* class_off, int32_t* cursor, int32_t* status,
+                           unsigned long long* csum, const BatchConfig& cfg, cudaEvent_t* ev, cudaStream_t s);
 
 // ---- counting (gc_count.cu: pass C, finish, derive; gc_clique.cu: passes T and K) ----
 int count_grid_size();
@@ -253,6 +293,10 @@ gc_status run_derive(const DevGraph& g, const unsigned long long* csum, unsigned
 gc_status run_pass_t(const DevGraph& g, const CountArgs& a, cudaStream_t s, int* launches);
 gc_status run_pass_k(const DevGraph& g, const CountArgs& a, cudaStream_t s, int* launches);
 gc_status run_finish(const DevGraph& g, const CountArgs& a, cudaStream_t s);
+// Per-edge induced counts of H_7..H_16 (needs a.dsum from pass T, and the
+// results of passes C and K); vsum: [n][2] scratch.
+gc_status run_induced(const DevGraph& g, const CountArgs& a, unsigned long long* vsum, uint64_t* out, bool out_host,
+                      cudaStream_t s);
 // Bytes of one global-tier buffer for out-degrees up to cap.
 size_t kbuf_bytes(int32_t cap);
 // Unit ordering key (environment GC_ORDER): 0 = vol (default: d_v + sum of

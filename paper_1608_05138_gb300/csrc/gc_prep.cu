@@ -17,6 +17,8 @@
 //     (a vertex analogue of the vol ordering of Table 4).
 #include <cuda_runtime.h>
 
+#include <cmath>
+
 #include <cstdlib>
 #include <cstring>
 #include <algorithm>
@@ -369,6 +371,18 @@ gc_status exclusive_scan(int32_t n, const int32_t* in, int32_t* out, cudaStream_
   return e == cudaSuccess ? GC_OK : cuda_fail(e, "scan launch");
 }
 
+// Jobs per CTA of the hub kernel the hub units are cut into (environment
+// GC_HUB_JOBS_PER_CTA, 0 .. 64, default 4; 0 keeps one job per hub), read
+// once per process.
+static int hub_jobs_per_cta() {
+  static int v = [] {
+    const char* e = getenv("GC_HUB_JOBS_PER_CTA");
+    const int x = e ? atoi(e) : 4;
+    return x < 0 ? 0 : (x > 64 ? 64 : x);
+  }();
+  return v;
+}
+
 gc_status classify_c_units(int32_t n, const int32_t* d_rp, const int32_t* d_ci, bool ranked, PrepBuffers* p,
                            cudaStream_t s) {
   const int32_t nu = p->n_units;
@@ -437,6 +451,48 @@ gc_status classify_c_units(int32_t n, const int32_t* d_rp, const int32_t* d_ci, 
   p->n_cheavy = (int32_t)heavy.size();
   p->n_chash = (int32_t)hashed.size();
   p->n_cunits = (int32_t)out.size();
+  // Hub units cut into jobs of consecutive o-range blocks (the finer
+  // granularity of Sec. 4.4: one hub's work spread over several CTAs), so
+  // that the heaviest hubs do not end as one SM's serial tail. A unit's cost
+  // is estimated as its wedges plus kSweepCost per (lower neighbour, block)
+  // sweep; a unit is cut into about cost / target jobs, target = total cost
+  // over jobs_per_cta x the hub kernel's CTAs (GC_HUB_JOBS_PER_CTA, default 4;
+  // 0: one job per hub). Jobs are taken heaviest first.
+  std::vector<int4> jobs;
+  {
+    constexpr double kSweepCost = 4.0;
+    const int per_cta = hub_jobs_per_cta();
+    std::vector<double> cost(heavy.size());
+    std::vector<long long> nblk(heavy.size());
+    double total = 0;
+    for (size_t i = 0; i < heavy.size(); ++i) {
+      const int32_t k = heavy[i];
+      const long long span = NX[k] < 65536 ? 2LL * kHeavyTab : kHeavyTab;
+      nblk[i] = ((long long)U[k] + span - 1) / span;
+      cost[i] = (double)W[k] + kSweepCost * (double)NX[k] * (double)nblk[i];
+      total += cost[i];
+    }
+    const double target = per_cta > 0 ? total / ((double)(count_grid_size() / kCtasPerSm) * per_cta) : 0.0;
+    std::vector<std::pair<double, int4>> cj;
+    for (size_t i = 0; i < heavy.size(); ++i) {
+      long long J = target > 0 ? (long long)std::ceil(cost[i] / target) : 1;
+      J = std::max(1LL, std::min(J, nblk[i]));
+      const long long nb = (nblk[i] + J - 1) / J;
+      for (long long b0 = 0; b0 < nblk[i]; b0 += nb) {
+        const long long len = std::min(nb, nblk[i] - b0);
+        cj.push_back({cost[i] * (double)len / (double)nblk[i], make_int4((int)i, (int)b0, (int)len, 0)});
+      }
+    }
+    std::stable_sort(cj.begin(), cj.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
+    jobs.reserve(cj.size());
+    for (auto& c : cj) jobs.push_back(c.second);
+  }
+  p->n_cjobs = (int32_t)jobs.size();
+  if (!jobs.empty()) {
+    e = cudaMallocAsync(&p->cjobs, sizeof(int4) * jobs.size(), s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p->cjobs, jobs.data(), sizeof(int4) * jobs.size(), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(e, "hub jobs");
+  }
   if (!out.empty()) e = cudaMemcpyAsync(p->cunits, out.data(), sizeof(int32_t) * out.size(), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess && !hw.empty()) {
     e = cudaMallocAsync(&p->chash_w, sizeof(int32_t) * hw.size(), s);
@@ -479,6 +535,7 @@ void free_prep(PrepBuffers* p, cudaStream_t s) {
   if (p->e2o) cudaFreeAsync(p->e2o, s);
   if (p->kunits) cudaFreeAsync(p->kunits, s);
   if (p->cunits) cudaFreeAsync(p->cunits, s);
+  if (p->cjobs) cudaFreeAsync(p->cjobs, s);
   if (p->chash_w) cudaFreeAsync(p->chash_w, s);
   *p = PrepBuffers();
 }

@@ -49,7 +49,8 @@ long long t_list_cap_knob() {
 void scratch_free(Scratch* sc, cudaStream_t s) {
   for (void* p : {(void*)sc->trio, (void*)sc->P, (void*)sc->xc, (void*)sc->misc,
                   (void*)sc->cbuf, (void*)sc->tables, (void*)sc->kbuf, (void*)sc->hitbuf, (void*)sc->work,
-                  (void*)sc->tlist, (void*)sc->tl_off, (void*)sc->tl_cnt, (void*)sc->tl_fill})
+                  (void*)sc->tlist, (void*)sc->tl_off, (void*)sc->tl_cnt, (void*)sc->tl_fill, (void*)sc->dsum,
+                  (void*)sc->vsum})
     if (p) cudaFreeAsync(p, s);
   *sc = Scratch();
 }
@@ -106,7 +107,7 @@ static int32_t ku_total(const KUnits& ku) { return ku.tier_off[kNumTiers]; }
 
 gc_status run_count(const DevGraph& g, const int32_t* units, int32_t n_units, const KUnits& ku,
                     uint64_t* per_edge, unsigned long long* csum, unsigned long long* x, Scratch* sc,
-                    cudaStream_t s, cudaEvent_t* ev, bool per_edge_host) {
+                    cudaStream_t s, cudaEvent_t* ev, bool per_edge_host, uint64_t* induced, bool induced_host) {
   cudaError_t e = cudaSuccess;
   gc_status st = GC_OK;
 #define GR_TRY(call, what)                  \
@@ -122,6 +123,8 @@ gc_status run_count(const DevGraph& g, const int32_t* units, int32_t n_units, co
   a.kunits = ku.units;
   a.cunits = ku.cunits;
   a.n_cheavy = ku.n_cheavy;
+  a.cjobs = ku.cjobs;
+  a.n_cjobs = ku.n_cjobs;
   a.chash_w = ku.chash_w;
   a.n_chash = ku.n_chash;
   a.cbuf = sc->cbuf;
@@ -175,6 +178,16 @@ gc_status run_count(const DevGraph& g, const int32_t* units, int32_t n_units, co
   if (a.tlist) GR_TRY(cudaMemsetAsync(sc->tl_fill, 0, sizeof(unsigned long long), s), "zero list fill");
   a.per_edge = per_edge;
   a.per_edge_host = per_edge != nullptr && per_edge_host;
+  a.dsum = nullptr;
+  const bool want_induced = induced != nullptr && g.m > 0;
+  if (want_induced) {  // scratch of the per-edge induced counts, kept with the graph
+    if (!sc->dsum) GR_TRY(cudaMallocAsync(&sc->dsum, sizeof(unsigned long long) * (size_t)g.m, s), "alloc dsum");
+    if (!sc->vsum)
+      GR_TRY(cudaMallocAsync(&sc->vsum, sizeof(unsigned long long) * 2 * (size_t)(g.n > 0 ? g.n : 1), s),
+             "alloc vsum");
+    GR_TRY(cudaMemsetAsync(sc->dsum, 0, sizeof(unsigned long long) * (size_t)g.m, s), "zero dsum");
+    a.dsum = sc->dsum;
+  }
   a.csum = csum;
   a.work = sc->work;
   const size_t m1 = (size_t)(g.m > 0 ? g.m : 1);
@@ -216,6 +229,11 @@ gc_status run_count(const DevGraph& g, const int32_t* units, int32_t n_units, co
   GR_EVENT(kPhaseFinish);
   if ((st = run_finish(g, a, s)) != GC_OK) return st;
   launches += g.m > 0 ? 1 : 0;
+  GR_EVENT(kPhaseInduced);
+  if (want_induced) {
+    if ((st = run_induced(g, a, sc->vsum, induced, induced_host, s)) != GC_OK) return st;
+    launches += 2;
+  }
   GR_EVENT(kPhaseDerive);
   if ((st = run_derive(g, csum, x, a.status, s)) != GC_OK) return st;
   sc->launches = launches + 1;

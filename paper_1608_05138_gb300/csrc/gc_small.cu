@@ -1,29 +1,31 @@
-// gc_small.cu -- small graphs (n <= kSmallN) counted on a shared-memory
+// gc_small.cu -- small graphs (n <= 1024) counted on a shared-memory
 // adjacency bitmatrix.
 //
-// For a graph of at most 512 vertices the whole adjacency fits in 32 KB of
-// shared memory as bit rows. The paper's Psi marks with vertex types
+// For a graph of at most 1024 vertices the whole adjacency fits in at most
+// 128 KB of shared memory as bit rows. The paper's Psi marks with vertex types
 // (Alg. 1: lambda1 for Gamma(v), lambda2 for S_u, lambda3 for T) become bit
 // masks over the graph's vertices, and Alg. 5 / Alg. 6 become popcounts:
 //   T   = row(u) & row(v)                       |T| = popc(T)
 //   S_u = row(u) & ~row(v) without v            S_v = row(v) & ~row(u) without u
 //   x7  = (1/2) sum_{a in T}   popc(row(a) & T)     (pairs of T counted twice)
 //   x10 =       sum_{w in S_u} popc(row(w) & S_v)   (Alg. 6 with the S_v test)
-// One lane holds one 32-bit word of each mask (16 words for 512 vertices);
+// One lane holds one 32-bit word of each mask (up to 32 words);
 // the members of T and S_u are listed and dealt to the lanes as (member, word)
 // pairs, so an edge costs about (|T| + |S_u|) * W / 32 steps for the warp.
 // One CTA per graph (work stealing over the graphs, largest first); per-edge
 // terms go into the 13 unrestricted sums of the graph in 128 bits.
+//
+// Graphs are binned by vertex count into size classes (n <= 64, 128, 256,
+// 512, 1024); each class runs its own instantiation, whose bitmatrix and
+// member lists are sized for the class, so that small graphs take little
+// shared memory and many CTAs fit on an SM. The block size of each class is
+// a tuning parameter (BatchConfig).
 #include <cuda_runtime.h>
 
 #include "gc_internal.h"
 
 namespace gc {
 namespace {
-
-constexpr int kSmallBlock = 256;
-constexpr int kSmallWarps = kSmallBlock / 32;
-constexpr int kSmallWords = kSmallN / 32;  // words per bit row
 
 __device__ __forceinline__ void add_u128(unsigned long long* p, u128 v) {
   unsigned long long lo = (unsigned long long)v;
@@ -57,7 +59,9 @@ __device__ __forceinline__ uint64_t small_column(int k, int64_t t, int64_t su, i
 // popc(row(b) & other), for the whole warp. The members are listed in `list`
 // (the warp's shared buffer), then each lane takes one (member, word) pair:
 // Wp = the power of two >= W lanes per member, 32 / Wp members per step, so
-// that every lane has a word to AND whatever the graph's size.
+// that every lane has a word to AND whatever the graph's size. kW: words per
+// bit row of the size class.
+template <int kW>
 __device__ __forceinline__ long long masked_row_popc(const uint32_t* __restrict__ bm, uint32_t mask,
                                                      uint32_t other, int lane, int Wp, int16_t* list) {
   const int c = __popc(mask);
@@ -79,20 +83,30 @@ __device__ __forceinline__ long long masked_row_popc(const uint32_t* __restrict_
   const uint32_t ow = __shfl_sync(0xffffffffu, other, w);  // word w of the other mask
   const int per = 32 / Wp;
   long long acc = 0;
-  for (int i = lane / Wp; i < total; i += per) acc += __popc(bm[list[i] * kSmallWords + w] & ow);
+  for (int i = lane / Wp; i < total; i += per) acc += __popc(bm[list[i] * kW + w] & ow);
   __syncwarp();
   return acc;
 }
 
-__global__ void __launch_bounds__(kSmallBlock) k_small_graphs(const int32_t* __restrict__ rp,
-                                                              const int64_t* __restrict__ voff,
-                                                              const int32_t* __restrict__ ci,
-                                                              const int64_t* __restrict__ eoff,
-                                                              const int32_t* __restrict__ order, int32_t G,
-                                                              int32_t* __restrict__ cursor,
-                                                              unsigned long long* __restrict__ csum) {
-  __shared__ uint32_t bm[kSmallN * kSmallWords];
-  __shared__ int16_t s_list[kSmallWarps][kSmallN];  // members of a mask, per warp
+// Shared memory of a size class: the bitmatrix (kN rows of kN / 32 words)
+// and one member list of kN entries per warp.
+__host__ __device__ constexpr size_t small_smem(int kN, int kBlock) {
+  return (size_t)kN * (size_t)(kN / 32) * 4 + (size_t)(kBlock / 32) * (size_t)kN * 2;
+}
+
+template <int kN, int kBlock>
+__global__ void __launch_bounds__(kBlock) k_small_graphs(const int32_t* __restrict__ rp,
+                                                         const int64_t* __restrict__ voff,
+                                                         const int32_t* __restrict__ ci,
+                                                         const int64_t* __restrict__ eoff,
+                                                         const int32_t* __restrict__ order, int32_t G,
+                                                         int32_t* __restrict__ cursor, int32_t* __restrict__ status,
+                                                         unsigned long long* __restrict__ csum) {
+  constexpr int kW = kN / 32;  // words per bit row
+  constexpr int kWarps = kBlock / 32;
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint32_t* bm = reinterpret_cast<uint32_t*>(smem);
+  int16_t* s_list = reinterpret_cast<int16_t*>(smem + (size_t)kN * kW * 4);
   __shared__ int32_t s_g;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (;;) {
@@ -105,25 +119,30 @@ __global__ void __launch_bounds__(kSmallBlock) k_small_graphs(const int32_t* __r
     const int32_t* gci = ci + eoff[g];
     const int32_t n = (int32_t)(voff[g + 1] - voff[g]) - 1;
     const int64_t m = (eoff[g + 1] - eoff[g]) / 2;
+    if (n > kN) {  // cannot happen: graphs are binned by n
+      if (threadIdx.x == 0) atomicOr(status, (int32_t)kSpillOverflow);
+      continue;
+    }
     const int W = (n + 31) / 32;
     int Wp = 1;
     while (Wp < W) Wp <<= 1;
-    for (int32_t i = threadIdx.x; i < n * kSmallWords; i += kSmallBlock) bm[i] = 0u;
+    for (int32_t i = threadIdx.x; i < n * kW; i += kBlock) bm[i] = 0u;
     __syncthreads();
-    for (int32_t x = warp; x < n; x += kSmallWarps)
+    for (int32_t x = warp; x < n; x += kWarps)
       for (int32_t p = grp[x] + lane; p < grp[x + 1]; p += 32) {
         const int32_t y = gci[p];
-        atomicOr(&bm[x * kSmallWords + (y >> 5)], 1u << (y & 31));
+        atomicOr(&bm[x * kW + (y >> 5)], 1u << (y & 31));
       }
     __syncthreads();
     u128 acc = 0;  // lane k < 13: this warp's part of unrestricted sum k
-    for (int32_t u = warp; u < n; u += kSmallWarps) {
+    int16_t* list = s_list + warp * kN;
+    for (int32_t u = warp; u < n; u += kWarps) {
       const int32_t ub = grp[u], ue = grp[u + 1];
-      const uint32_t ru = lane < W ? bm[u * kSmallWords + lane] : 0u;
+      const uint32_t ru = lane < W ? bm[u * kW + lane] : 0u;
       for (int32_t p = ub; p < ue; ++p) {
         const int32_t v = gci[p];
         if (v <= u) continue;  // each edge once, from its smaller endpoint
-        const uint32_t rv = lane < W ? bm[v * kSmallWords + lane] : 0u;
+        const uint32_t rv = lane < W ? bm[v * kW + lane] : 0u;
         const uint32_t T = ru & rv;
         uint32_t Su = ru & ~rv, Sv = rv & ~ru;
         if (lane == (v >> 5)) Su &= ~(1u << (v & 31));
@@ -134,8 +153,8 @@ __global__ void __launch_bounds__(kSmallBlock) k_small_graphs(const int32_t* __r
           su += __shfl_xor_sync(0xffffffffu, su, o);
           sv += __shfl_xor_sync(0xffffffffu, sv, o);
         }
-        long long x7 = masked_row_popc(bm, T, T, lane, Wp, s_list[warp]);
-        long long x10 = masked_row_popc(bm, Su, Sv, lane, Wp, s_list[warp]);
+        long long x7 = masked_row_popc<kW>(bm, T, T, lane, Wp, list);
+        long long x10 = masked_row_popc<kW>(bm, Su, Sv, lane, Wp, list);
         for (int o = 16; o; o >>= 1) {
           x7 += __shfl_xor_sync(0xffffffffu, x7, o);
           x10 += __shfl_xor_sync(0xffffffffu, x10, o);
@@ -150,24 +169,104 @@ __global__ void __launch_bounds__(kSmallBlock) k_small_graphs(const int32_t* __r
   }
 }
 
+typedef void (*SmallKernel)(const int32_t*, const int64_t*, const int32_t*, const int64_t*, const int32_t*, int32_t,
+                            int32_t*, int32_t*, unsigned long long*);
+
+// kSmallBlocks[j] threads per CTA for tuning choice j.
+constexpr int kNumSmallBlocks = 4;
+constexpr int kSmallBlocks[kNumSmallBlocks] = {64, 128, 256, 512};
+
+template <int kN>
+SmallKernel small_kernel_for(int block) {
+  switch (block) {
+    case 64: return k_small_graphs<kN, 64>;
+    case 128: return k_small_graphs<kN, 128>;
+    case 512: return k_small_graphs<kN, 512>;
+    default: return k_small_graphs<kN, 256>;
+  }
+}
+
+SmallKernel small_kernel(int cls, int block) {
+  switch (cls) {
+    case 0: return small_kernel_for<64>(block);
+    case 1: return small_kernel_for<128>(block);
+    case 2: return small_kernel_for<256>(block);
+    case 3: return small_kernel_for<512>(block);
+    default: return small_kernel_for<1024>(block);
+  }
+}
+
+int valid_block(int block) {
+  for (int b : kSmallBlocks)
+    if (b == block) return block;
+  return 256;
+}
+
 }  // namespace
 
-// Counts graphs order[0..G) of a batch whose vertex counts are <= kSmallN;
-// csum [*][13][2] must be zeroed; cursor is a zeroed device int.
-gc_status run_small_graphs(const int32_t* rp, const int64_t* voff, const int32_t* ci, const int64_t* eoff,
-                           const int32_t* order, int32_t G, int32_t* cursor, unsigned long long* csum,
-                           cudaStream_t s) {
-  if (G <= 0) return GC_OK;
+int small_class_of(int32_t n) {
+  for (int c = 0; c < kSmallClasses; ++c)
+    if (n <= kSmallClassN[c]) return c;
+  return kSmallClasses;
+}
+
+// Resident CTAs of every (size class, block) instantiation on one GPU
+// (filled by small_graphs_setup, outside any stream capture).
+static int g_small_ctas[kSmallClasses][kNumSmallBlocks] = {};
+
+static int block_index(int block) {
+  for (int j = 0; j < kNumSmallBlocks; ++j)
+    if (kSmallBlocks[j] == block) return j;
+  return 2;
+}
+
+// Grid of one size class: resident CTAs, at most one CTA per graph.
+static int small_grid(int cls, int block, int32_t graphs) {
+  int grid = g_small_ctas[cls][block_index(block)];
+  if (grid < 1) grid = 1;
+  return grid > graphs ? graphs : grid;
+}
+
+gc_status small_graphs_setup() {
   int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_small_graphs, kSmallBlock, 0);
-  int grid = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
-  if (grid > G) grid = G;
-  k_small_graphs<<<grid, kSmallBlock, 0, s>>>(rp, voff, ci, eoff, order, G, cursor, csum);
-  cudaError_t e = cudaGetLastError();
-  return e == cudaSuccess ? GC_OK : cuda_fail(e, "k_small_graphs");
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return cuda_fail(e, "k_small_graphs setup");
+  for (int c = 0; c < kSmallClasses; ++c)
+    for (int j = 0; j < kNumSmallBlocks; ++j) {
+      const int b = kSmallBlocks[j];
+      const size_t smem = small_smem(kSmallClassN[c], b);
+      e = cudaFuncSetAttribute(small_kernel(c, b), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      int per_sm = 0;
+      if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, small_kernel(c, b), b, smem);
+      if (e != cudaSuccess) return cuda_fail(e, "k_small_graphs attribute");
+      g_small_ctas[c][j] = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
+    }
+  return GC_OK;
+}
+
+gc_status run_small_graphs(const int32_t* rp, const int64_t* voff, const int32_t* ci, const int64_t* eoff,
+                           const int32_t* order, const int32_t* class_off, int32_t* cursor, int32_t* status,
+                           unsigned long long* csum, const BatchConfig& cfg, cudaEvent_t* ev, cudaStream_t s) {
+  for (int c = 0; c < kSmallClasses; ++c) {
+    const int32_t G = class_off[c + 1] - class_off[c];
+    if (ev) {
+      cudaError_t e = cudaEventRecord(ev[c], s);
+      if (e != cudaSuccess) return cuda_fail(e, "small event");
+    }
+    if (G <= 0) continue;
+    const int block = valid_block(cfg.class_block[c]);
+    const int grid = small_grid(c, block, G);
+    small_kernel(c, block)<<<grid, block, small_smem(kSmallClassN[c], block), s>>>(
+        rp, voff, ci, eoff, order + class_off[c], G, cursor + c, status, csum);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "k_small_graphs");
+  }
+  if (ev) {
+    cudaError_t e = cudaEventRecord(ev[kSmallClasses], s);
+    if (e != cudaSuccess) return cuda_fail(e, "small event");
+  }
+  return GC_OK;
 }
 
 }  // namespace gc

@@ -1,0 +1,131 @@
+"""Autotuner of the batched form.
+
+Picks, for the GPU it runs on, the parameters of the batch runtime (see
+gc_batch_set_param in include/gc.h): the block size of each size class of
+the bitmatrix kernels (graphs of n <= 64, 128, 256, 512, 1024 vertices), the
+cut between the bitmatrix kernels and the general passes (small_n_max), and
+whether a launch is replayed from a CUDA graph. Every candidate is timed by
+the library's own CUDA events (gc_batch_last_stats) on a held-out sample of
+graphs, counted through the C ABI; the winners go into the tuning cache,
+a JSON file keyed by GPU name and graph class (vertex-count bin), which
+gc_batch_create reads:
+
+    python -m paper_1608_05138_gb300.tune [--graphs 6000] [--out PATH]
+
+Results do not depend on the parameters (every setting counts the same exact
+integers); only the time does.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import time
+
+import numpy as np
+
+from . import (BATCH_STATS, GC_BATCH_MANUAL, SMALL_BLOCKS, SMALL_CLASS_N, gc_batch_configure, gc_batch_create,
+               gc_batch_destroy, gc_batch_flush, gc_batch_last_stats, gc_batch_poll, gc_batch_submit_many)
+
+DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tune_cache.json")
+CUTS = [256, 512, 1024]
+
+
+def held_out_sample(graphs: int, seed: int = 2):
+    """Graphs of the batched workload's families (half Erdos-Renyi, half
+    Chung-Lu) with n uniform in [20, 1024], so that every size class is
+    timed; a seed the benchmarks do not use."""
+    import graphgen
+    return graphgen.batch(graphs, n_lo=20, n_hi=1024, seed=seed)
+
+
+def time_launch(sample, config: dict, repeats: int = 3):
+    """Counts the sample as one launch under `config`, `repeats` times; the
+    smallest device times of gc_batch_last_stats and the results."""
+    b = gc_batch_create(64 << 30, GC_BATCH_MANUAL)
+    best, res = None, None
+    try:
+        gc_batch_configure(b, config)
+        for _ in range(repeats):
+            t = gc_batch_submit_many(b, sample.nvert, sample.voff, sample.eoff, sample.row_ptr, sample.col_idx)
+            gc_batch_flush(b)
+            res = [gc_batch_poll(b, int(x), timeout_us=-1) for x in t]
+            st = gc_batch_last_stats(b)
+            if best is None:
+                best = st
+            else:
+                best = {k: min(best[k], st[k]) if k != "replayed" else st[k] for k in st}
+    finally:
+        gc_batch_destroy(b)
+    return best, res
+
+
+def tune(sample, repeats: int = 3, log=print) -> dict:
+    """The tuned parameters for this GPU and their measurements."""
+    n_of = np.asarray(sample.nvert)
+    present = [c for c, n in enumerate(SMALL_CLASS_N) if np.any((n_of <= n) & (n_of > ([0] + SMALL_CLASS_N)[c]))]
+    # 1. block size per size class: eager launches, one timer per class
+    per_class = {c: {} for c in present}
+    ref = None
+    for blk in SMALL_BLOCKS:
+        cfg = {"small_n_max": SMALL_CLASS_N[-1], "use_graph": 0, "block": {str(n): blk for n in SMALL_CLASS_N}}
+        st, res = time_launch(sample, cfg, repeats)
+        ref = ref or res
+        if res != ref:
+            raise RuntimeError("results changed with the block size")
+        for c in present:
+            per_class[c][blk] = st[BATCH_STATS[c]]
+        log(f"block {blk}: " + ", ".join(f"n<={SMALL_CLASS_N[c]} {per_class[c][blk]:.2f} ms" for c in present))
+    block = {str(n): 256 for n in SMALL_CLASS_N}
+    for c in present:
+        block[str(SMALL_CLASS_N[c])] = min(per_class[c], key=per_class[c].get)
+    # 2. the cut between the bitmatrix kernels and the passes, 3. CUDA graph or not
+    totals = {}
+    for cut in CUTS:
+        for use_graph in (0, 1):
+            st, res = time_launch(sample, {"small_n_max": cut, "use_graph": use_graph, "block": block}, repeats)
+            if res != ref:
+                raise RuntimeError("results changed with the cut or the graph replay")
+            totals[(cut, use_graph)] = st["small_sequence_ms"] + st["union_ms"]
+            log(f"small_n_max {cut} use_graph {use_graph}: {totals[(cut, use_graph)]:.2f} ms")
+    # the fastest cut; replay from a CUDA graph unless eager launches are
+    # faster by more than the timing noise (2 %)
+    cut = min(CUTS, key=lambda c: min(totals[(c, 0)], totals[(c, 1)]))
+    use_graph = 1 if totals[(cut, 1)] <= 1.02 * totals[(cut, 0)] else 0
+    return {"small_n_max": cut, "use_graph": use_graph, "block": block,
+            "measured": {"class_block_ms": {str(SMALL_CLASS_N[c]): {str(k): v for k, v in per_class[c].items()}
+                                            for c in present},
+                         "launch_ms": {f"{k[0]}/{k[1]}": v for k, v in totals.items()},
+                         "sample_graphs": int(len(n_of)), "sample_edges": int(sample.total_edges),
+                         "when": time.strftime("%Y-%m-%dT%H:%M:%SZ", time.gmtime())}}
+
+
+def write_cache(gpu_name: str, entry: dict, path: str = DEFAULT_CACHE):
+    data = {}
+    if os.path.exists(path):
+        with open(path) as f:
+            data = json.load(f)
+    data[gpu_name] = entry
+    tmp = path + f".tmp{os.getpid()}"
+    with open(tmp, "w") as f:
+        json.dump(data, f, indent=1)
+    os.replace(tmp, path)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--graphs", type=int, default=6000)
+    ap.add_argument("--repeats", type=int, default=3)
+    ap.add_argument("--out", default=DEFAULT_CACHE)
+    args = ap.parse_args()
+    import torch
+    from . import build
+    build.build()
+    gpu = torch.cuda.get_device_name(0)
+    entry = tune(held_out_sample(args.graphs), args.repeats)
+    write_cache(gpu, entry, args.out)
+    print(json.dumps({gpu: {k: v for k, v in entry.items() if k != "measured"}}))
+
+
+if __name__ == "__main__":
+    main()

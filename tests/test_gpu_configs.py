@@ -84,15 +84,20 @@ def test_batched_100k_whole_config_equals_oracle():
     try:
         tickets = gcb.gc_batch_submit_many(b, B.nvert, B.voff, B.eoff, B.row_ptr, B.col_idx)
         gcb.gc_batch_flush(b)
-        res = [gcb.gc_batch_poll(b, int(t), timeout_us=600_000_000) for t in tickets]
+        X = gcb.gc_batch_poll_many(b, tickets, timeout_us=600_000_000)  # [G][17] (lo, hi)
+        # the single-ticket poll agrees on a few graphs submitted again
+        t2 = gcb.gc_batch_submit_many(b, B.nvert[:3], B.voff[:4], B.eoff[:4], B.row_ptr, B.col_idx)
+        gcb.gc_batch_flush(b)
+        for k in range(3):
+            x = gcb.gc_batch_poll(b, int(t2[k]), timeout_us=60_000_000)
+            assert np.array_equal(lohi(x), X[k])
     finally:
         gcb.gc_batch_destroy(b)
-    X = np.stack([lohi(x) for x in res])
     c = gold["chunk"]
     bad = [k for k, d in enumerate(gold["chunk_sha256"]) if sha(X[k * c:(k + 1) * c]) != d]
     assert not bad, f"graphs differ in chunks {bad[:10]} (of {c} graphs each)"
     assert sha(X) == gold["X_sha256"]
-    totals = [int(sum(int(x[i]) for x in res)) for i in range(17)]
+    totals = [sum(int(v) for v in X[:, i, 0]) + (sum(int(v) for v in X[:, i, 1]) << 64) for i in range(17)]
     assert totals == gold["X_totals"]
 
 

@@ -513,3 +513,107 @@ def test_batch_submit_many_matches_single_submits():
         gcb.gc_batch_destroy(b)
     for i in range(0, len(B), 7):
         assert res[i] == _oracle_X(*B.graph(i)), i
+
+
+def _batch_results(B, config):
+    b = gcb.gc_batch_create(16 << 30, gcb.GC_BATCH_MANUAL)
+    try:
+        gcb.gc_batch_configure(b, config)
+        assert gcb.gc_batch_config(b)["small_n_max"] == config.get("small_n_max", 512)
+        res, stats = [], []
+        for _ in range(2):  # the second launch replays (or updates) the captured graph
+            ts = gcb.gc_batch_submit_many(b, B.nvert, B.voff, B.eoff, B.row_ptr, B.col_idx)
+            gcb.gc_batch_flush(b)
+            res.append([gcb.gc_batch_poll(b, int(t), timeout_us=120_000_000) for t in ts])
+            stats.append(gcb.gc_batch_last_stats(b))
+    finally:
+        gcb.gc_batch_destroy(b)
+    assert res[0] == res[1]
+    return res[0], stats
+
+
+def test_batch_results_identical_under_every_setting():
+    # every size class of the bitmatrix kernels (n up to 1024) and graphs on
+    # both sides of every cut; the counts must not depend on the parameters
+    B = graphgen.batch(240, n_lo=20, n_hi=1024, seed=35)
+    base = {"small_n_max": 1024, "use_graph": 1, "block": {str(n): 256 for n in gcb.SMALL_CLASS_N}}
+    ref, st = _batch_results(B, base)
+    assert st[1]["replayed"] == 1.0 and st[1]["small_sequence_ms"] > 0
+    configs = [dict(base, small_n_max=0), dict(base, small_n_max=64), dict(base, small_n_max=300),
+               dict(base, use_graph=0, block={str(n): 64 for n in gcb.SMALL_CLASS_N}),
+               dict(base, block={str(n): 512 for n in gcb.SMALL_CLASS_N}),
+               dict(base, use_graph=0, small_n_max=512, block={"64": 128, "128": 64, "256": 512, "512": 128})]
+    for cfg in configs:
+        res, st = _batch_results(B, cfg)
+        assert res == ref, cfg
+        if cfg["use_graph"] == 0:
+            assert st[1]["replayed"] == 0.0
+            assert sum(st[1][f"class_n{n}_ms"] for n in gcb.SMALL_CLASS_N) > 0
+        if cfg["small_n_max"] < 1024:
+            assert st[1]["union_ms"] > 0
+    checked = 0
+    for i in range(len(B)):
+        rp, ci = B.graph(i)
+        if len(ci) // 2 <= 40000 and i % 4 == 0:
+            assert ref[i] == _oracle_X(rp, ci), i
+            checked += 1
+    assert checked >= 20
+
+
+def test_batch_parameters_and_tuning_cache(tmp_path, monkeypatch):
+    import json
+    import torch
+    b = gcb.gc_batch_create(1 << 30, gcb.GC_BATCH_MANUAL)
+    try:
+        for param, value in ((gcb.GC_PARAM_SMALL_N_MAX, 2000), (gcb.GC_PARAM_BLOCK_N64, 96),
+                             (gcb.GC_PARAM_USE_GRAPH, 2), (99, 1)):
+            with pytest.raises(gcb.GcError) as ei:
+                gcb.gc_batch_set_param(b, param, value)
+            assert ei.value.status == -1
+        gcb.gc_batch_set_param(b, gcb.GC_PARAM_BLOCK_N64 + 2, 128)
+        assert gcb.gc_batch_get_param(b, gcb.GC_PARAM_BLOCK_N64 + 2) == 128
+    finally:
+        gcb.gc_batch_destroy(b)
+    # a cache entry for this GPU is read at gc_batch_create
+    entry = {"small_n_max": 300, "use_graph": 0, "block": {"64": 64, "128": 512, "256": 128, "512": 64, "1024": 512}}
+    path = tmp_path / "cache.json"
+    path.write_text(json.dumps({"some other GPU": {"small_n_max": 7}, torch.cuda.get_device_name(0): entry}))
+    monkeypatch.setenv("GC_TUNE_CACHE", str(path))
+    b = gcb.gc_batch_create(1 << 30, gcb.GC_BATCH_MANUAL)
+    try:
+        assert gcb.gc_batch_config(b) == entry
+    finally:
+        gcb.gc_batch_destroy(b)
+    path.write_text("{ not json")
+    b = gcb.gc_batch_create(1 << 30, gcb.GC_BATCH_MANUAL)  # a broken cache leaves the defaults
+    try:
+        assert gcb.gc_batch_config(b)["small_n_max"] == 512
+    finally:
+        gcb.gc_batch_destroy(b)
+
+
+_HUB_JOBS = ("import numpy as np, os, graphgen, oracle, paper_1608_05138_gb300 as gcb\n"
+             "rp, ci = graphgen.chung_lu(120000, 600000, 2.1, 1.2e6, 4000.0, 7)\n"
+             "o = oracle.count(rp, ci)\n"
+             "with gcb.Graph(rp, ci) as g:\n"
+             "    pe = np.zeros((g.m, 13), np.uint64); X = g.count(pe); w = g.work_counts()\n"
+             "assert X == o['X'] and (pe == o['per_edge']).all()\n"
+             "assert w['c_hub_ctas'] > 0 and 0 < w['c_hub_busy_max_ns'] and w['c_hub_busy_sum_ns'] >= w['c_hub_busy_max_ns']\n"
+             "print('ok', w['c_hub_jobs'])\n")
+
+
+def test_hub_jobs_split_or_whole_give_the_same_counts():
+    # hub units cut into many jobs of o-range blocks (Sec. 4.4's finer
+    # granularity), or kept whole: the same exact counts either way
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    jobs = {}
+    for per_cta in ("0", "64"):
+        env = dict(os.environ, PYTHONPATH=root, GC_HUB_JOBS_PER_CTA=per_cta)
+        r = subprocess.run([sys.executable, "-c", _HUB_JOBS], env=env, cwd=root, capture_output=True, text=True,
+                           timeout=900)
+        assert r.returncode == 0 and "ok" in r.stdout, r.stdout + r.stderr
+        jobs[per_cta] = int(r.stdout.split()[-1])
+    assert jobs["64"] > jobs["0"] > 0
