@@ -100,6 +100,9 @@ __global__ void __launch_bounds__(kThreads, 65536 / (kThreads * 64)) k_pass_k(De
   __shared__ int32_t s_unit, s_cur1, s_cur2, s_nhit;
   __shared__ long long s_loff;
   __shared__ int32_t s_qj[kW][64], s_qq[kW][64];
+  // pass T: the warp's entries that passed the bit filter, waiting for a
+  // full warp of hash probes (fewer than 32 left over + 128 of a round)
+  __shared__ int32_t s_pc[kW][kTri ? 160 : 1], s_pq[kW][kTri ? 160 : 1];
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int cap = kCap ? kCap : a.kbuf_cap;
@@ -220,9 +223,11 @@ __global__ void __launch_bounds__(kThreads, 65536 / (kThreads * 64)) k_pass_k(De
     }
     __syncthreads();
     const int32_t cmax = ids[k - 1];
-    auto lookup = [&](int32_t c) -> int32_t {
+    auto filter_pass = [&](int32_t c) -> bool {
       const uint32_t f = fhash(c, fbits);
-      if (!((filt[f >> 5] >> (f & 31)) & 1u)) return -1;  // at most one bit in 16 set
+      return (filt[f >> 5] >> (f & 31)) & 1u;  // at most one bit in 16 set
+    };
+    auto probe = [&](int32_t c) -> int32_t {  // position of c in out(a), or -1
       uint32_t h = khash(c, hbits);
       for (;;) {
         const int32_t s = hash[h];
@@ -231,6 +236,7 @@ __global__ void __launch_bounds__(kThreads, 65536 / (kThreads * 64)) k_pass_k(De
         h = (h + 1) & hmask;
       }
     };
+    auto lookup = [&](int32_t c) -> int32_t { return filter_pass(c) ? probe(c) : -1; };
 
     // Phase 1: the edges of H_a, as symmetric bits.
     for (;;) {
@@ -240,9 +246,80 @@ __global__ void __launch_bounds__(kThreads, 65536 / (kThreads * 64)) k_pass_k(De
       if (i >= k) break;
       const int32_t b = ids[i];
       const int32_t bb = g.out_ptr[b], be = g.out_ptr[b + 1];
-      // four windows of 32 entries per round, so that four loads are in
-      // flight per lane; out(b) ascends, so the scan stops at the first round
-      // that reaches past max out(a)
+      if (kTri) {
+        // The triangle step: four windows of 32 entries per round (four loads
+        // in flight per lane); the entries that pass the bit filter are
+        // compacted into the warp's buffer and looked up in the hash 32 at a
+        // time, so that every lane of a probe has an entry (about one entry
+        // in seven passes the filter). out(b) ascends: the scan stops at the
+        // first round that reaches past max out(a).
+        int32_t* pc = s_pc[warp];
+        int32_t* pq = s_pq[warp];
+        int32_t pend = 0;  // warp-uniform
+        auto probe_batch = [&](int32_t take) {  // the last `take` buffered entries
+          const int32_t c = lane < take ? pc[pend - take + lane] : 0;
+          const int32_t q = lane < take ? pq[pend - take + lane] : 0;
+          const int32_t j = lane < take ? probe(c) : -1;
+          const unsigned hit = __ballot_sync(kFull, j >= 0);
+          if (j >= 0) {
+            atomicAdd(&a.trio[q], 1);  // edge (b_i, c)
+            atomicAdd(&vx7[j], 1u);    // edge (a, c)
+            if (kDeg) {
+              atomicAdd(&a.dsum[q], (unsigned long long)da);       // edge (b_i, c): third vertex a
+              add_split(vcr, vcrh, j, (unsigned long long)ta[i]);  // edge (a, c): third vertex b_i
+            }
+          }
+          if (kDeg && hit) {  // edge (a, b_i): third vertices c
+            unsigned long long sd = j >= 0 ? (unsigned long long)ta[j] : 0ull;
+            for (int o = 16; o; o >>= 1) sd += __shfl_xor_sync(kFull, sd, o);
+            if (lane == 0) add_split(vcr, vcrh, i, sd);
+          }
+          if (lane == 0 && hit) {
+            atomicAdd(&vx7[i], (uint32_t)__popc(hit));  // edge (a, b_i)
+            w_edges += __popc(hit);
+          }
+          if (hits && hit) {  // recorded for pass K
+            int32_t base_h = 0;
+            if (lane == 0) base_h = atomicAdd(&s_nhit, __popc(hit));
+            base_h = __shfl_sync(kFull, base_h, 0);
+            const int32_t slot = base_h + __popc(hit & ((1u << lane) - 1u));
+            if (j >= 0 && slot < a.hitcap)
+              reinterpret_cast<int2*>(hits)[slot] = make_int2((int32_t)(((uint32_t)i << 16) | (uint32_t)j), q);
+          }
+          pend -= take;
+          __syncwarp();  // the entries are read before the buffer is refilled
+        };
+        for (int32_t q0 = bb; q0 < be; q0 += 128) {
+          int32_t cw[4];
+#pragma unroll
+          for (int w4 = 0; w4 < 4; ++w4) {
+            const int32_t q = q0 + 32 * w4 + lane;
+            cw[w4] = q < be ? g.out_idx[q] : 0x7fffffff;
+          }
+          if (lane == 0) w_scan += min(128, be - q0);
+          const bool past = __shfl_sync(kFull, cw[3], 31) > cmax;
+#pragma unroll
+          for (int w4 = 0; w4 < 4; ++w4) {
+            const int32_t c = cw[w4];
+            const bool pass = c <= cmax && filter_pass(c);
+            const unsigned pm = __ballot_sync(kFull, pass);
+            if (pass) {
+              const int32_t pos = pend + __popc(pm & ((1u << lane) - 1u));
+              pc[pos] = c;
+              pq[pos] = q0 + 32 * w4 + lane;
+            }
+            pend += __popc(pm);
+          }
+          __syncwarp();
+          const bool last = past || q0 + 128 >= be;
+          while (pend >= 32) probe_batch(32);
+          if (last && pend > 0) probe_batch(pend);
+          if (past) break;
+        }
+        continue;
+      }
+      // pass K for a unit whose edges were not kept: four windows of 32
+      // entries per round, so that four loads are in flight per lane
       for (int32_t q0 = bb; q0 < be; q0 += 128) {
         int32_t cw[4];
 #pragma unroll
@@ -258,33 +335,7 @@ __global__ void __launch_bounds__(kThreads, 65536 / (kThreads * 64)) k_pass_k(De
           const int32_t c = cw[w4];
           const int32_t j = c <= cmax ? lookup(c) : -1;
           const unsigned hit = __ballot_sync(kFull, j >= 0);
-          if (kTri) {
-            if (j >= 0) {
-              atomicAdd(&a.trio[q], 1);  // edge (b_i, c)
-              atomicAdd(&vx7[j], 1u);    // edge (a, c)
-              if (kDeg) {
-                atomicAdd(&a.dsum[q], (unsigned long long)da);               // edge (b_i, c): third vertex a
-                add_split(vcr, vcrh, j, (unsigned long long)ta[i]);          // edge (a, c): third vertex b_i
-              }
-            }
-            if (kDeg && hit) {  // edge (a, b_i): third vertices c
-              unsigned long long sd = j >= 0 ? (unsigned long long)ta[j] : 0ull;
-              for (int o = 16; o; o >>= 1) sd += __shfl_xor_sync(kFull, sd, o);
-              if (lane == 0) add_split(vcr, vcrh, i, sd);
-            }
-            if (lane == 0 && hit) {
-              atomicAdd(&vx7[i], (uint32_t)__popc(hit));  // edge (a, b_i)
-              w_edges += __popc(hit);
-            }
-            if (hits && hit) {  // recorded for pass K
-              int32_t base_h = 0;
-              if (lane == 0) base_h = atomicAdd(&s_nhit, __popc(hit));
-              base_h = __shfl_sync(kFull, base_h, 0);
-              const int32_t slot = base_h + __popc(hit & ((1u << lane) - 1u));
-              if (j >= 0 && slot < a.hitcap)
-                reinterpret_cast<int2*>(hits)[slot] = make_int2((int32_t)(((uint32_t)i << 16) | (uint32_t)j), q);
-            }
-          } else if (hit) {
+          if (hit) {  // pass K scanning again: the edges of H_a as bits, and their list
             int32_t base_h = 0;
             if (lane == 0) base_h = atomicAdd(&s_nhit, __popc(hit));
             base_h = __shfl_sync(kFull, base_h, 0);

@@ -372,12 +372,16 @@ gc_status exclusive_scan(int32_t n, const int32_t* in, int32_t* out, cudaStream_
 }
 
 // Jobs per CTA of the hub kernel the hub units are cut into (environment
-// GC_HUB_JOBS_PER_CTA, 0 .. 64, default 4; 0 keeps one job per hub), read
-// once per process.
+// GC_HUB_JOBS_PER_CTA, 0 .. 64, default 1; 0 keeps one job per hub), read
+// once per process. With 1, only a hub that costs more than a whole CTA's
+// share of the work is cut: a new job has to seed every lower neighbour's
+// cursor with a galloping search (milliseconds for the largest hubs), and
+// heaviest-first stealing already balances hubs below that size (on R-MAT
+// scale 22 the CTAs' lifetimes differ by 0.1 %).
 static int hub_jobs_per_cta() {
   static int v = [] {
     const char* e = getenv("GC_HUB_JOBS_PER_CTA");
-    const int x = e ? atoi(e) : 4;
+    const int x = e ? atoi(e) : 1;
     return x < 0 ? 0 : (x > 64 ? 64 : x);
   }();
   return v;
@@ -456,7 +460,7 @@ gc_status classify_c_units(int32_t n, const int32_t* d_rp, const int32_t* d_ci, 
   // that the heaviest hubs do not end as one SM's serial tail. A unit's cost
   // is estimated as its wedges plus kSweepCost per (lower neighbour, block)
   // sweep; a unit is cut into about cost / target jobs, target = total cost
-  // over jobs_per_cta x the hub kernel's CTAs (GC_HUB_JOBS_PER_CTA, default 4;
+  // over jobs_per_cta x the hub kernel's CTAs (GC_HUB_JOBS_PER_CTA, default 1;
   // 0: one job per hub). Jobs are taken heaviest first.
   std::vector<int4> jobs;
   {

@@ -25,7 +25,7 @@ import time
 import numpy as np
 
 from . import (BATCH_STATS, GC_BATCH_MANUAL, SMALL_BLOCKS, SMALL_CLASS_N, gc_batch_configure, gc_batch_create,
-               gc_batch_destroy, gc_batch_flush, gc_batch_last_stats, gc_batch_poll, gc_batch_submit_many)
+               gc_batch_destroy, gc_batch_flush, gc_batch_last_stats, gc_batch_poll_many, gc_batch_submit_many)
 
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tune_cache.json")
 CUTS = [256, 512, 1024]
@@ -49,7 +49,7 @@ def time_launch(sample, config: dict, repeats: int = 3):
         for _ in range(repeats):
             t = gc_batch_submit_many(b, sample.nvert, sample.voff, sample.eoff, sample.row_ptr, sample.col_idx)
             gc_batch_flush(b)
-            res = [gc_batch_poll(b, int(x), timeout_us=-1) for x in t]
+            res = gc_batch_poll_many(b, t, timeout_us=-1)
             st = gc_batch_last_stats(b)
             if best is None:
                 best = st
@@ -70,8 +70,8 @@ def tune(sample, repeats: int = 3, log=print) -> dict:
     for blk in SMALL_BLOCKS:
         cfg = {"small_n_max": SMALL_CLASS_N[-1], "use_graph": 0, "block": {str(n): blk for n in SMALL_CLASS_N}}
         st, res = time_launch(sample, cfg, repeats)
-        ref = ref or res
-        if res != ref:
+        ref = res if ref is None else ref
+        if not np.array_equal(res, ref):
             raise RuntimeError("results changed with the block size")
         for c in present:
             per_class[c][blk] = st[BATCH_STATS[c]]
@@ -84,7 +84,7 @@ def tune(sample, repeats: int = 3, log=print) -> dict:
     for cut in CUTS:
         for use_graph in (0, 1):
             st, res = time_launch(sample, {"small_n_max": cut, "use_graph": use_graph, "block": block}, repeats)
-            if res != ref:
+            if not np.array_equal(res, ref):
                 raise RuntimeError("results changed with the cut or the graph replay")
             totals[(cut, use_graph)] = st["small_sequence_ms"] + st["union_ms"]
             log(f"small_n_max {cut} use_graph {use_graph}: {totals[(cut, use_graph)]:.2f} ms")
