@@ -624,6 +624,34 @@ def main():
     step_ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, dist, "cuda")
     value = job_value(world, m, step_ms)
 
+    induced = None
+    if rank == 0 and not args.no_extra:
+        # the same count with the per-edge induced 4-node counts (H7..H16 per
+        # edge, gc_count_edge_induced) written to device memory as well
+        ind = torch.empty((m, 10), dtype=torch.int64, device="cuda")
+        for _ in range(2):
+            Xi = g.count_induced(ind, per_edge)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ph_i = []
+        e0.record(stream)
+        for _ in range(3):
+            Xi = g.count_induced(ind, per_edge)
+            ph_i.append(g.phase_ms())
+        e1.record(stream)
+        torch.cuda.synchronize()
+        assert Xi == X
+        # exact invariants: column i sums to |E(H_i)| X_i
+        edges_of = [6, 5, 4, 4, 3, 3, 3, 2, 2, 1]
+        ok = all(sum(int(ind[j:j + (1 << 22), i].sum().item()) for j in range(0, m, 1 << 22)) == edges_of[i] * X[6 + i]
+                 for i in range(10))
+        ms_i = e0.elapsed_time(e1) / 3
+        induced = {"ms_per_count": ms_i, "edges_per_s": m / (ms_i / 1000.0), "extra_ms_vs_plain": ms_i - step_ms,
+                   "phases_ms": {k: statistics.mean(p[k] for p in ph_i) for k in ph_i[0]},
+                   "column_sums_equal_edges_times_X": ok,
+                   "note": "per-edge rows (13 columns) and induced rows (10 columns) both to device memory"}
+        del ind
+
     e2e = None
     if not args.no_e2e and rank == 0:
         g.close()
@@ -669,7 +697,7 @@ def main():
                        "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas{world}"},
             "phases_ms": ph_ms, "work": work,
             "roofline": roof, "clocks": clk.summary(), "gpu_launches": int(work["launches"]) * args.steps,
-            "e2e": e2e}
+            "e2e": e2e, "induced": induced}
     if not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(rp, ci, m)
     if world == 1 and args.workload == "rmat22" and args.scale == 22 and not args.no_extra:

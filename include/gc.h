@@ -189,8 +189,9 @@ gc_status gc_graph_phase_ms(gc_graph g, double* ms);
  *  15 pass C: sum over those CTAs of their lifetime, ns (%globaltimer)
  *  16 pass C: the longest of those lifetimes, ns (15 / 14 against 16 is the
  *     kernel's tail)
+ *  17 pass C: wedges of the units counted in the packed-key shared-memory hash
  * Used to turn kernel times into algorithmic bytes per second. */
-#define GC_NUM_WORK 17
+#define GC_NUM_WORK 18
 gc_status gc_graph_work_counts(gc_graph g, uint64_t* out);
 
 /* Release the graph and all its device memory. NULL is accepted. */

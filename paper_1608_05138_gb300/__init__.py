@@ -47,7 +47,7 @@ EXPORTED = ["gc_last_error", "gc_graph_upload", "gc_graph_info", "gc_graph_edges
             "gc_batch_get_param", "gc_batch_last_stats", "gc_batch_poll_many"]
 WORK_NAMES = ["t_members", "c_wedges", "k_members", "k_scan", "k_local_edges", "k_words", "finish_edges", "launches",
               "c_heavy_wedges", "c_heavy_sweeps", "t_scan", "t_triangles", "c_hash_wedges", "c_hub_jobs",
-              "c_hub_ctas", "c_hub_busy_sum_ns", "c_hub_busy_max_ns"]
+              "c_hub_ctas", "c_hub_busy_sum_ns", "c_hub_busy_max_ns", "c_hash2_wedges"]
 
 
 class GcError(RuntimeError):

@@ -749,6 +749,118 @@ __global__ void __launch_bounds__(kHashBlock, kCtasPerSm) k_pass_c_hash(DevGraph
   }
 }
 
+// ---------------- pass C for units of at most kHash2MaxW wedges ----------------
+// The same counting and attribution as k_pass_c_hash, for the units whose
+// wedges do not fit that hash: each slot is one 32-bit word holding the
+// vertex o (22 bits; graphs of at most 2^22 vertices) and cnt_h(o) (10 bits;
+// units of fewer than 1023 lower neighbours, so a count never reaches 1023
+// and a word is never all ones, the empty mark). kHash2Slots words fill the
+// shared memory of one 1024-thread CTA per SM; a unit uses the first
+// ceil(W / 0.72) of them, so the table is at most 72 % full, and the probe
+// position is a multiply-shift of the hash into that range.
+constexpr int kHash2Block = 1024;
+constexpr uint32_t kHash2Empty = 0xffffffffu;
+
+__device__ __forceinline__ uint32_t h2_start(int32_t o, uint32_t size) {
+  return (uint32_t)(((unsigned long long)((uint32_t)o * 0x9E3779B1u) * size) >> 32);
+}
+// adds 1 to the count of o (inserted with count 1 if absent); false if the
+// table is full (cannot happen for a unit sized as above)
+__device__ __forceinline__ bool h2_insert(uint32_t* tab, int32_t o, uint32_t size) {
+  uint32_t sl = h2_start(o, size);
+  for (uint32_t t = 0; t < size; ++t) {
+    uint32_t w = *reinterpret_cast<volatile uint32_t*>(&tab[sl]);
+    if (w == kHash2Empty) {
+      w = atomicCAS(&tab[sl], kHash2Empty, ((uint32_t)o << 10) | 1u);
+      if (w == kHash2Empty) return true;
+    }
+    if ((w >> 10) == (uint32_t)o) {
+      atomicAdd(&tab[sl], 1u);
+      return true;
+    }
+    sl = sl + 1 == size ? 0 : sl + 1;
+  }
+  return false;
+}
+__device__ __forceinline__ uint32_t h2_count(const uint32_t* tab, int32_t o, uint32_t size) {
+  uint32_t sl = h2_start(o, size);
+  for (uint32_t t = 0; t < size; ++t) {
+    const uint32_t w = tab[sl];
+    if (w == kHash2Empty) return 0u;
+    if ((w >> 10) == (uint32_t)o) return w & 1023u;
+    sl = sl + 1 == size ? 0 : sl + 1;
+  }
+  return 0u;
+}
+
+__global__ void __launch_bounds__(kHash2Block, 1) k_pass_c_hash2(DevGraph g, CountArgs a) {
+  extern __shared__ uint32_t htab[];  // kHash2Slots packed (o, count) words
+  __shared__ int32_t s_unit, s_next[2];
+  const int lane = threadIdx.x & 31;
+  long long w_wedge = 0;  // lane 0
+  const int32_t first = a.n_cheavy + a.n_chash;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_unit = atomicAdd(a.cursor + 15, 1);
+    __syncthreads();
+    const int32_t k = s_unit;
+    if (k >= a.n_chash2) break;
+    const int32_t h = a.cunits[first + k];
+    const int32_t wk = min(a.chash_w[a.n_chash + k], (int32_t)kHash2MaxW);
+    const uint32_t size = min((uint32_t)kHash2Slots, (uint32_t)(((long long)wk * 25 + 17) / 18) + 32u);
+    const int32_t hb = g.rp[h], he = g.rp[h + 1];
+    for (uint32_t i = threadIdx.x; i < size; i += kHash2Block) htab[i] = kHash2Empty;
+    if (threadIdx.x < 2) s_next[threadIdx.x] = hb;
+    __syncthreads();
+    // pass 0 counts cnt_h(o); pass 1 attributes cnt_h(o) - 1 to the slots
+    // (x, o) and, summed over the run, to (h, x)
+    for (int pass = 0; pass < 2; ++pass) {
+      for (;;) {
+        int32_t p = 0;
+        if (lane == 0) p = atomicAdd(&s_next[pass], 1);
+        p = __shfl_sync(0xffffffffu, p, 0);
+        if (p >= he) break;
+        const int32_t x = g.ci[p];
+        if (x >= h) break;  // the lower neighbours are a prefix of Gamma(h)
+        const int32_t xb = g.rp[x];
+        const int32_t xe = min(max(g.rev[p], xb), g.rp[x + 1]);  // Gamma(x) below the slot of (x, h)
+        if (pass == 0 && lane == 0) w_wedge += xe - xb;
+        unsigned long long sx = 0;
+        for (int32_t q0 = xb; q0 < xe; q0 += 128) {  // four windows of 32 in flight
+          int32_t o[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int32_t q = q0 + 32 * j + lane;
+            o[j] = q < xe ? g.ci[q] : -1;
+          }
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            if (o[j] < 0) continue;
+            if (pass == 0) {
+              if (!h2_insert(htab, o[j], size)) atomicOr(a.status, (int32_t)kSpillOverflow);
+            } else {
+              const uint32_t c = h2_count(htab, o[j], size) - 1u;
+              if (c && c < 1023u) {
+                atomicAdd(&a.P[q0 + 32 * j + lane], (unsigned long long)c);  // slot (x, o)
+                sx += c;
+              }
+            }
+          }
+        }
+        if (pass == 1) {
+          for (int off = 16; off; off >>= 1) sx += __shfl_xor_sync(0xffffffffu, sx, off);
+          if (lane == 0 && sx) atomicAdd(&a.P[p], sx);  // slot (h, x)
+        }
+      }
+      __syncthreads();
+    }
+  }
+  if (lane == 0 && w_wedge) {
+    atomicAdd(a.work + kWorkCWedge, (unsigned long long)w_wedge);
+    atomicAdd(a.work + kWorkCHash2Wedge, (unsigned long long)w_wedge);
+  }
+}
+
 // ---------------- derive X_1..X_17 per graph ----------------
 __device__ __forceinline__ bool div_exact(u128 num, u128 den, u128* q) {
   if (num % den != 0) return false;
@@ -859,6 +971,18 @@ gc_status run_pass_c_hash(const DevGraph& g, const CountArgs& a, cudaStream_t s)
   k_pass_c_hash<<<grid, kHashBlock, smem, s>>>(g, a);
   e = cudaGetLastError();
   return e == cudaSuccess ? GC_OK : cuda_fail(e, "k_pass_c_hash");
+}
+
+gc_status run_pass_c_hash2(const DevGraph& g, const CountArgs& a, cudaStream_t s) {
+  if (a.n_chash2 <= 0) return GC_OK;
+  const size_t smem = sizeof(uint32_t) * kHash2Slots;
+  cudaError_t e = cudaFuncSetAttribute(k_pass_c_hash2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return cuda_fail(e, "k_pass_c_hash2");
+  int grid = count_grid_size() / kCtasPerSm;
+  if (grid > a.n_chash2) grid = a.n_chash2;
+  k_pass_c_hash2<<<grid, kHash2Block, smem, s>>>(g, a);
+  e = cudaGetLastError();
+  return e == cudaSuccess ? GC_OK : cuda_fail(e, "k_pass_c_hash2");
 }
 
 gc_status run_finish(const DevGraph& g, const CountArgs& a, cudaStream_t s) {

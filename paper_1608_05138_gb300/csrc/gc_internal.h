@@ -51,8 +51,9 @@ struct CountArgs {
   int32_t n_units;
   const int32_t* cunits;   // pass C: hub units (blocked kernel), hashed units, then the others
   int32_t n_cheavy;        // hub units of pass C (cunits[0 .. n_cheavy))
-  const int32_t* chash_w;  // wedges of the hashed units cunits[n_cheavy .. n_cheavy + n_chash)
+  const int32_t* chash_w;  // wedges of the hashed units cunits[n_cheavy .. n_cheavy + n_chash + n_chash2)
   int32_t n_chash;
+  int32_t n_chash2;        // units of the packed-key hash tier, after the hashed units
   const int4* cjobs;       // pass C hub kernel: jobs (hub index into cunits, first o-range block, blocks),
                            // heaviest first
   int32_t n_cjobs;
@@ -111,6 +112,7 @@ enum Work {
   kWorkCHubCtas,       // pass C: CTAs of the hub kernel
   kWorkCHubBusySum,    // pass C: sum over the hub kernel's CTAs of their lifetime (ns, %globaltimer)
   kWorkCHubBusyMax,    // pass C: the longest of those lifetimes (ns)
+  kWorkCHash2Wedge,    // pass C: wedges of the units counted in the packed-key hash
   kNumWork
 };
 
@@ -177,6 +179,7 @@ struct KUnits {
   int32_t n_cjobs;
   const int32_t* chash_w;
   int32_t n_chash;
+  int32_t n_chash2;
   int32_t n_cunits;        // pass C units in all (units without wedges are left out)
 };
 // induced (optional): [m][10] rows of the per-edge induced counts of H_7..H_16
@@ -223,8 +226,9 @@ struct PrepBuffers {
   int32_t n_cheavy = 0;
   int4* cjobs = nullptr;       // hub jobs, heaviest first (see CountArgs)
   int32_t n_cjobs = 0;
-  int32_t* chash_w = nullptr;  // wedges of each hashed unit
+  int32_t* chash_w = nullptr;  // wedges of each hashed unit (both hash tiers)
   int32_t n_chash = 0;
+  int32_t n_chash2 = 0;        // units of the packed-key hash tier
   int32_t n_cunits = 0;
   int32_t cnx_max = 0;      // most lower neighbours of a hub unit
 };
@@ -288,6 +292,15 @@ constexpr int kHeavyTab = 53248;  // o-range block of the hub kernel of pass C (
 // o than wedges).
 constexpr int kHashMaxW = 8192;
 gc_status run_pass_c_hash(const DevGraph& g, const CountArgs& a, cudaStream_t s);
+// Units of more than kHashMaxW and at most kHash2MaxW wedges, with fewer than
+// kHash2MaxNx lower neighbours, in graphs of at most 2^22 vertices: a
+// shared-memory hash of kHash2Slots words, each a packed (22-bit vertex,
+// 10-bit count) pair, at most 72 % full.
+constexpr int kHash2Slots = 57344;
+constexpr int kHash2MaxW = 41287;
+constexpr int kHash2MaxNx = 1023;
+constexpr int32_t kHash2MaxN = 1 << 22;
+gc_status run_pass_c_hash2(const DevGraph& g, const CountArgs& a, cudaStream_t s);
 gc_status run_derive(const DevGraph& g, const unsigned long long* csum, unsigned long long* x,
                      int32_t* status, cudaStream_t s);
 gc_status run_pass_t(const DevGraph& g, const CountArgs& a, cudaStream_t s, int* launches);

@@ -394,6 +394,7 @@ gc_status classify_c_units(int32_t n, const int32_t* d_rp, const int32_t* d_ci, 
   if (e != cudaSuccess) return cuda_fail(e, "alloc cunits");
   p->n_cheavy = 0;
   p->n_chash = 0;
+  p->n_chash2 = 0;
   p->n_cunits = nu;
   p->cnx_max = 0;
   if (!ranked || n <= kSmemTableMax || nu == 0) {
@@ -450,10 +451,25 @@ gc_status classify_c_units(int32_t n, const int32_t* d_rp, const int32_t* d_ci, 
     out.push_back(U[k]);
     hw.push_back((int32_t)W[k]);
   }
+  // Units above it, with fewer than kHash2MaxNx lower neighbours (counts fit
+  // 10 bits) in a graph whose ids fit 22 bits: the packed-key hash, heaviest
+  // first. The rest stay on the vertex-indexed tables.
+  std::vector<int32_t> hashed2;
   for (int32_t k = 0; k < nu; ++k)
-    if (!is_heavy[k] && W[k] > kHashMaxW) out.push_back(U[k]);
+    if (!is_heavy[k] && W[k] > kHashMaxW && W[k] <= kHash2MaxW && NX[k] < kHash2MaxNx && n <= kHash2MaxN)
+      hashed2.push_back(k);
+  std::sort(hashed2.begin(), hashed2.end(), [&](int32_t a, int32_t b) { return W[a] > W[b]; });
+  std::vector<char> is_hashed2(nu, 0);
+  for (int32_t k : hashed2) {
+    out.push_back(U[k]);
+    hw.push_back((int32_t)W[k]);
+    is_hashed2[k] = 1;
+  }
+  for (int32_t k = 0; k < nu; ++k)
+    if (!is_heavy[k] && !is_hashed2[k] && W[k] > kHashMaxW) out.push_back(U[k]);
   p->n_cheavy = (int32_t)heavy.size();
   p->n_chash = (int32_t)hashed.size();
+  p->n_chash2 = (int32_t)hashed2.size();
   p->n_cunits = (int32_t)out.size();
   // Hub units cut into jobs of consecutive o-range blocks (the finer
   // granularity of Sec. 4.4: one hub's work spread over several CTAs), so

@@ -127,10 +127,12 @@ gc_status run_count(const DevGraph& g, const int32_t* units, int32_t n_units, co
   a.n_cjobs = ku.n_cjobs;
   a.chash_w = ku.chash_w;
   a.n_chash = ku.n_chash;
+  a.n_chash2 = ku.n_chash2;
   a.cbuf = sc->cbuf;
   a.cbuf_nx = sc->cbuf_nx;
   for (int t = 0; t <= kNumTiers; ++t) a.ktier_off[t] = ku.tier_off[t];
-  a.cursor = sc->misc;  // [0] pass C, [2 + tier] pass K, [8] pass C hubs, [9] pass C hashed, [10 + tier] pass T
+  a.cursor = sc->misc;  // [0] pass C, [2 + tier] pass K, [8] pass C hubs, [9] pass C hashed, [10 + tier] pass T,
+                        // [15] pass C packed-key hash
   a.status = sc->misc + 1;
   a.tables = g.table_n > kSmemTableMax ? sc->tables : nullptr;
   a.trio = sc->trio;
@@ -213,10 +215,15 @@ gc_status run_count(const DevGraph& g, const int32_t* units, int32_t n_units, co
       if ((st = run_pass_c_hash(g, a, s)) != GC_OK) return st;
       launches += 1;
     }
-    if (n_cunits > a.n_cheavy + a.n_chash) {
+    if (a.n_chash2 > 0) {
+      if ((st = run_pass_c_hash2(g, a, s)) != GC_OK) return st;
+      launches += 1;
+    }
+    const int32_t n_hashed = a.n_cheavy + a.n_chash + a.n_chash2;
+    if (n_cunits > n_hashed) {
       CountArgs al = a;  // the remaining units on the vertex-indexed tables
-      al.units = a.cunits + a.n_cheavy + a.n_chash;
-      al.n_units = n_cunits - a.n_cheavy - a.n_chash;
+      al.units = a.cunits + n_hashed;
+      al.n_units = n_cunits - n_hashed;
       GR_TRY(cudaMemsetAsync(a.cursor, 0, sizeof(int32_t), s), "reset cursor");
       if ((st = run_pass_c(g, al, s)) != GC_OK) return st;
       launches += 1;

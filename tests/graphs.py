@@ -59,3 +59,17 @@ def wheel(k):
 def edges_of(rp, ci):
     n = len(rp) - 1
     return [(u, int(v)) for u in range(n) for v in ci[rp[u]:rp[u + 1]] if v > u]
+
+
+def csr_large(n, edges):
+    """csr() for large n with few edges (numpy; no per-vertex Python objects)."""
+    e = np.asarray(list(edges), np.int64).reshape(-1, 2)
+    if len(e) and (e[:, 0] == e[:, 1]).any():
+        raise ValueError("self-loop")
+    a = np.concatenate([e[:, 0], e[:, 1]])
+    b = np.concatenate([e[:, 1], e[:, 0]])
+    key = np.unique(a * n + b)
+    rows, cols = key // n, key % n
+    rp = np.zeros(n + 1, np.int64)
+    np.add.at(rp, rows + 1, 1)
+    return np.cumsum(rp).astype(np.int32), cols.astype(np.int32)

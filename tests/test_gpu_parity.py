@@ -200,16 +200,16 @@ def test_cycle_pass_unit_kinds_on_a_power_law_graph():
         w = g.work_counts()
     assert w["c_wedges"] == W.sum()
     assert 0 < w["c_heavy_wedges"] and w["c_hash_wedges"] == W[W <= 8192].sum()
-    assert w["c_heavy_wedges"] + w["c_hash_wedges"] < w["c_wedges"]
+    assert 0 < w["c_hash2_wedges"] <= W[(W > 8192) & (W <= 41287)].sum()
+    assert w["c_heavy_wedges"] + w["c_hash_wedges"] + w["c_hash2_wedges"] <= w["c_wedges"]
     assert_parity(rp, ci)
 
 
-def test_table_units_of_the_cycle_pass():
-    # A unit of 18000 wedges (above the hash) whose rank spans 19 blocks of
-    # the hub kernel's o-range: counted on the vertex-indexed tables. The
-    # 2M vertices are mostly isolated.
+def _unit_of_18000_wedges(n):
+    # A unit of 18000 wedges (above the first hash) whose rank spans 19 or
+    # more blocks of the hub kernel's o-range (not a hub); the n vertices are
+    # mostly isolated.
     rng = np.random.default_rng(4)
-    n = 2_000_000
     h = 0
     xs = np.arange(1, 201)
     pool = np.arange(201, 8201)
@@ -217,9 +217,17 @@ def test_table_units_of_the_cycle_pass():
     for x in xs:
         for o in rng.choice(pool, 90, replace=False):
             E.append((int(x), int(o)))
-    rp, ci = graphs.csr(n, E)
-    W, _ = wedges_by_highest_vertex(rp, ci)
+    rp, ci = graphs.csr_large(n, E)
+    sub_rp, sub_ci = graphs.csr(8201, E)
+    W, _ = wedges_by_highest_vertex(sub_rp, sub_ci)
     assert W.max() == 18000
+    return rp, ci, W
+
+
+def test_packed_hash_units_of_the_cycle_pass():
+    # 2M vertices (ids fit 22 bits), 200 lower neighbours: the packed-key
+    # shared-memory hash counts the unit
+    rp, ci, W = _unit_of_18000_wedges(2_000_000)
     with gcb.Graph(rp, ci) as g:
         pe = np.zeros((g.m, 13), np.uint64)
         X = g.count(pe)
@@ -227,7 +235,23 @@ def test_table_units_of_the_cycle_pass():
     o = oracle.count(rp, ci)
     np.testing.assert_array_equal(pe, o["per_edge"])
     assert X == o["X"]
-    assert w["c_wedges"] == W.sum() and w["c_heavy_wedges"] == 0 and w["c_hash_wedges"] == W.sum() - 18000
+    assert w["c_wedges"] == W.sum() and w["c_heavy_wedges"] == 0
+    assert w["c_hash2_wedges"] == 18000 and w["c_hash_wedges"] == W.sum() - 18000
+
+
+def test_table_units_of_the_cycle_pass():
+    # the same unit among 4.4M vertices: ids above 2^22 do not fit the packed
+    # hash, so it is counted on the vertex-indexed tables
+    rp, ci, W = _unit_of_18000_wedges(4_400_000)
+    with gcb.Graph(rp, ci) as g:
+        pe = np.zeros((g.m, 13), np.uint64)
+        X = g.count(pe)
+        w = g.work_counts()
+    o = oracle.count(rp, ci)
+    np.testing.assert_array_equal(pe, o["per_edge"])
+    assert X == o["X"]
+    assert w["c_wedges"] == W.sum() and w["c_heavy_wedges"] == 0 and w["c_hash2_wedges"] == 0
+    assert w["c_hash_wedges"] == W.sum() - 18000
 
 
 def test_clique_pass_rescan_when_edge_list_is_full():
