@@ -641,10 +641,14 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         assert Xi == X
-        # exact invariants: column i sums to |E(H_i)| X_i
+        # exact invariants: column i sums to |E(H_i)| X_i (the high and low
+        # 32-bit halves summed apart, so that no int64 partial sum overflows)
         edges_of = [6, 5, 4, 4, 3, 3, 3, 2, 2, 1]
-        ok = all(sum(int(ind[j:j + (1 << 22), i].sum().item()) for j in range(0, m, 1 << 22)) == edges_of[i] * X[6 + i]
-                 for i in range(10))
+
+        def col_sum(c):
+            return (int((c >> 32).sum().item()) << 32) + int((c & 0xFFFFFFFF).sum().item())
+
+        ok = all(col_sum(ind[:, i]) == edges_of[i] * X[6 + i] for i in range(10))
         ms_i = e0.elapsed_time(e1) / 3
         induced = {"ms_per_count": ms_i, "edges_per_s": m / (ms_i / 1000.0), "extra_ms_vs_plain": ms_i - step_ms,
                    "phases_ms": {k: statistics.mean(p[k] for p in ph_i) for k in ph_i[0]},

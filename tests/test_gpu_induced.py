@@ -116,9 +116,9 @@ def _sampled_induced(rp, ci, k, seed):
         ids = np.unique(np.concatenate([np.random.default_rng(seed).integers(0, m, k), [0, m - 1]])).astype(np.int64)
         rows = dev[torch.from_numpy(ids).cuda()].cpu().numpy().view(np.uint64)
         np.testing.assert_array_equal(rows, oracle.count_induced(rp, ci, ids))
-        for i in range(10):  # exact column sums (int64 partial sums of at most 2^20 rows)
+        for i in range(10):  # exact column sums: the high and low 32-bit halves summed apart
             col = dev[:, i]
-            s = sum(int(col[j:j + (1 << 20)].sum().item()) for j in range(0, m, 1 << 20))
+            s = (int((col >> 32).sum().item()) << 32) + int((col & 0xFFFFFFFF).sum().item())
             assert s == EDGES_OF[i] * X[6 + i], i
         assert bool((dev.sum(1) == comb(n - 2, 2)).all().item())
 

@@ -641,3 +641,45 @@ def test_hub_jobs_split_or_whole_give_the_same_counts():
         assert r.returncode == 0 and "ok" in r.stdout, r.stdout + r.stderr
         jobs[per_cta] = int(r.stdout.split()[-1])
     assert jobs["64"] > jobs["0"] > 0
+
+
+def test_serving_under_a_nearly_full_budget():
+    # a budget that holds about three of the requests at once: submissions are
+    # refused (GC_ERR_BUSY) until earlier ones retire, and every result equals
+    # the graph's own whole-graph count
+    import time
+    params = graphgen.serving_params(16, m_lo=20000, m_hi=200000, seed=9)
+    gs = [graphgen.serving_graph(params, r) for r in range(16)]
+    expect = []
+    for g in gs:
+        with gcb.Graph(*g) as h:
+            expect.append(h.count())
+    grid = 2 * 152
+
+    def footprint(rp, ci):  # the runtime's estimate of a graph's device memory
+        n, m = len(rp) - 1, len(ci) // 2
+        return 44 * n + 32 * m + 1024 + (grid * n * 4 if n > 4096 else 0)
+
+    budget = 3 * max(footprint(*g) for g in gs)
+    b = gcb.gc_batch_create(budget, 0)
+    tickets, results, busy, nxt = {}, {}, 0, 0
+    t_end = time.time() + 300
+    try:
+        while len(results) < len(gs) and time.time() < t_end:
+            if nxt < len(gs):
+                t = gcb.gc_batch_try_submit(b, *gs[nxt])
+                if t is None:
+                    busy += 1
+                else:
+                    tickets[nxt] = t
+                    nxt += 1
+            for r, t in list(tickets.items()):
+                x = gcb.gc_batch_poll(b, t, timeout_us=0)
+                if x is not None:
+                    results[r] = x
+                    del tickets[r]
+            time.sleep(0.0005)
+    finally:
+        gcb.gc_batch_destroy(b)
+    assert busy > 0
+    assert [results.get(r) for r in range(len(gs))] == expect
