@@ -30,7 +30,6 @@
 #include <cuda_runtime.h>
 
 #include <cstdlib>
-#include <type_traits>
 
 #include "gc_internal.h"
 
@@ -353,14 +352,12 @@ constexpr int kHeavyWarps = kHeavyBlock / 32;
 // Counters of the block: 32-bit, or two 16-bit counters per word when the
 // unit has fewer than 65536 lower neighbours (no count can exceed that, so no
 // carry crosses into the other half) -- twice the o-range per block.
-template <bool kHalf>
-__device__ __forceinline__ void add_count(uint32_t* tab, int32_t slot) {
-  if (kHalf) atomicAdd(&tab[slot >> 1], 1u << ((slot & 1) << 4));
+__device__ __forceinline__ void add_count(uint32_t* tab, int32_t slot, bool half) {
+  if (half) atomicAdd(&tab[slot >> 1], 1u << ((slot & 1) << 4));
   else atomicAdd(&tab[slot], 1u);
 }
-template <bool kHalf>
-__device__ __forceinline__ uint32_t read_count(const uint32_t* tab, int32_t slot) {
-  return kHalf ? (tab[slot >> 1] >> ((slot & 1) << 4)) & 0xffffu : tab[slot];
+__device__ __forceinline__ uint32_t read_count(const uint32_t* tab, int32_t slot, bool half) {
+  return half ? (tab[slot >> 1] >> ((slot & 1) << 4)) & 0xffffu : tab[slot];
 }
 
 // first index in [p, e) with a[index] >= key; a ascending
@@ -471,182 +468,157 @@ __global__ void __launch_bounds__(kHeavyBlock, 1) k_pass_c_heavy(DevGraph g, Cou
       if (job.y == 0) w_wedge += lo - xb;  // the hub's wedges, counted by its first job
     }
     if (threadIdx.x == 0) ++w_jobs;
-    // the blocks of the job, with the counter width fixed at compile time
-    auto sweep_blocks = [&](auto half_tag) {
-      constexpr bool kHalf = decltype(half_tag)::value;
-      for (int64_t lo64 = job_lo; lo64 < job_hi; lo64 += span) {
-        const int32_t lo_id = (int32_t)lo64;
-        const int32_t r1 = (int32_t)min(lo64 + span, job_hi);
-        const int32_t words = kHalf ? (r1 - lo_id + 1) >> 1 : r1 - lo_id;
-        for (int32_t i = threadIdx.x; i < words; i += kHeavyBlock) tab[i] = 0u;
-        if (threadIdx.x == 0) {
-          w_blocks += nx;
-          s_chunk[0] = 0;
-          s_chunk[1] = 0;
-        }
-        __syncthreads();
-        // counts of the block
-        for (;;) {
-          int32_t c = 0;
-          if (lane == 0) c = atomicAdd(&s_chunk[0], 1);
-          c = __shfl_sync(0xffffffffu, c, 0);
-          if (c >= nchunks) break;
-          const int32_t i = (nchunks - 1 - c) * 32 + lane;  // X ascends by degree: heaviest chunk first
-          int32_t st = 0, L = 0;
-          if (i < nx) {
-            st = cur[i];
-            const int32_t en = gallop_lower_bound(g.ci, st, endp[i], r1);
-            L = en - st;
-            beg[i] = st;
-            cur[i] = en;
-          }
-          // runs of 32 or more entries (most of the wedges): the whole warp,
-          // one run at a time, consecutive entries over the lanes
-          unsigned lm = __ballot_sync(0xffffffffu, L >= 32);
-          while (lm) {
-            const int src = __ffs(lm) - 1;
-            lm &= lm - 1;
-            const int32_t s0 = __shfl_sync(0xffffffffu, st, src);
-            const int32_t n0 = __shfl_sync(0xffffffffu, L, src);
-            // 16-byte loads of four entries: the run's aligned middle as int4
-            // vectors (two in flight per lane), the unaligned head and tail
-            // (at most three entries each) by single lanes
-            const int32_t e0 = s0 + n0;
-            const int32_t a0 = min((s0 + 3) & ~3, e0);
-            const int32_t nv = (e0 - a0) >> 2;
-            const int32_t t0 = a0 + 4 * nv;
-            {
-              int32_t q = -1;
-              if (lane < a0 - s0) q = s0 + lane;
-              else if (lane >= 4 && lane - 4 < e0 - t0) q = t0 + lane - 4;
-              if (q >= 0) add_count<kHalf>(tab, g.ci[q] - lo_id);
-            }
-            const int4* vec = reinterpret_cast<const int4*>(g.ci + a0);  // cudaMalloc'd: 16-byte aligned
-            for (int32_t t = lane; t < nv; t += 64) {
-              const int4 A = vec[t];
-              const bool two = t + 32 < nv;
-              int4 B = A;
-              if (two) B = vec[t + 32];
-              add_count<kHalf>(tab, A.x - lo_id);
-              add_count<kHalf>(tab, A.y - lo_id);
-              add_count<kHalf>(tab, A.z - lo_id);
-              add_count<kHalf>(tab, A.w - lo_id);
-              if (two) {
-                add_count<kHalf>(tab, B.x - lo_id);
-                add_count<kHalf>(tab, B.y - lo_id);
-                add_count<kHalf>(tab, B.z - lo_id);
-                add_count<kHalf>(tab, B.w - lo_id);
-              }
-            }
-          }
-          // shorter runs dealt to the lanes end to end
-          const int32_t Ls = L < 32 ? L : 0;
-          const Deal d = deal_setup(Ls, comp, lane);
-          const int32_t sb = st - d.excl;  // slot of position kk of this lane's run: sb + kk
-          int before = 0;
-          for (int32_t k0 = 0; k0 < d.total; k0 += 128) {
-            int32_t q[4];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-              const int ol = deal_owner(d, Ls, k0 + 32 * j, comp, lane, before);
-              const int32_t kk = k0 + 32 * j + lane;
-              const int32_t bj = __shfl_sync(0xffffffffu, sb, ol);
-              q[j] = kk < d.total ? bj + kk : -1;
-            }
-            int32_t o[4];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) o[j] = q[j] >= 0 ? g.ci[q[j]] : lo_id;
-#pragma unroll
-            for (int j = 0; j < 4; ++j)
-              if (q[j] >= 0) add_count<kHalf>(tab, o[j] - lo_id);
-          }
-          __syncwarp();
-        }
-        __syncthreads();
-        // attribution of the block's wedges
-        for (;;) {
-          int32_t c = 0;
-          if (lane == 0) c = atomicAdd(&s_chunk[1], 1);
-          c = __shfl_sync(0xffffffffu, c, 0);
-          if (c >= nchunks) break;
-          const int32_t i = (nchunks - 1 - c) * 32 + lane;
-          int32_t st = 0, L = 0;
-          if (i < nx) {
-            st = beg[i];
-            L = cur[i] - st;
-          }
-          s_sx[warp][lane] = 0ull;  // per x of the chunk: sum of its wedges' counts
-          s_sx32[warp][lane] = 0u;
-          __syncwarp();
-          // runs of 32 or more entries: the whole warp, one run at a time
-          unsigned lm = __ballot_sync(0xffffffffu, L >= 32);
-          while (lm) {
-            const int src = __ffs(lm) - 1;
-            lm &= lm - 1;
-            const int32_t s0 = __shfl_sync(0xffffffffu, st, src);
-            const int32_t n0 = __shfl_sync(0xffffffffu, L, src);
-            unsigned long long acc = 0ull;
-            for (int32_t k0 = 0; k0 < n0; k0 += 256) {  // eight windows of loads in flight
-              int32_t o[8];
-#pragma unroll
-              for (int j = 0; j < 8; ++j) {
-                const int32_t kk = k0 + 32 * j + lane;
-                o[j] = kk < n0 ? g.ci[s0 + kk] : -1;
-              }
-#pragma unroll
-              for (int j = 0; j < 8; ++j) {
-                if (o[j] < 0) continue;
-                const uint32_t cnt = read_count<kHalf>(tab, o[j] - lo_id) - 1u;
-                if (cnt) {
-                  atomicAdd(&a.P[s0 + k0 + 32 * j + lane], (unsigned long long)cnt);  // slot (x, o)
-                  acc += cnt;
-                }
-              }
-            }
-            for (int off = 16; off; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-            if (lane == src) s_sx[warp][lane] += acc;
-          }
-          __syncwarp();
-          // shorter runs dealt to the lanes end to end
-          const int32_t Ls = L < 32 ? L : 0;
-          const Deal d = deal_setup(Ls, comp, lane);
-          const int32_t sb = st - d.excl;  // slot of position kk of this lane's run: sb + kk
-          int before = 0;
-          for (int32_t k0 = 0; k0 < d.total; k0 += 128) {
-            int32_t q[4], ol[4];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-              ol[j] = deal_owner(d, Ls, k0 + 32 * j, comp, lane, before);
-              const int32_t kk = k0 + 32 * j + lane;
-              const int32_t bj = __shfl_sync(0xffffffffu, sb, ol[j]);
-              q[j] = kk < d.total ? bj + kk : -1;
-            }
-            int32_t o[4];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) o[j] = q[j] >= 0 ? g.ci[q[j]] : lo_id;
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-              if (q[j] >= 0) {
-                const uint32_t cnt = read_count<kHalf>(tab, o[j] - lo_id) - 1u;
-                if (cnt) {
-                  atomicAdd(&a.P[q[j]], (unsigned long long)cnt);  // slot (x, o)
-                  atomicAdd(&s_sx32[warp][ol[j]], cnt);           // the owner's sum
-                }
-              }
-            }
-          }
-          __syncwarp();
-          if (i < nx) {
-            const unsigned long long sx = s_sx[warp][lane] + s_sx32[warp][lane];
-            if (sx) atomicAdd(&a.P[hb + i], sx);  // slot (h, x)
-          }
-          __syncwarp();
-        }
-        __syncthreads();
+    for (int64_t lo64 = job_lo; lo64 < job_hi; lo64 += span) {
+      const int32_t lo_id = (int32_t)lo64;
+      const int32_t r1 = (int32_t)min(lo64 + span, job_hi);
+      const int32_t words = half ? (r1 - lo_id + 1) >> 1 : r1 - lo_id;
+      for (int32_t i = threadIdx.x; i < words; i += kHeavyBlock) tab[i] = 0u;
+      if (threadIdx.x == 0) {
+        w_blocks += nx;
+        s_chunk[0] = 0;
+        s_chunk[1] = 0;
       }
-    };
-    if (half) sweep_blocks(std::true_type{});
-    else sweep_blocks(std::false_type{});
+      __syncthreads();
+      // counts of the block
+      for (;;) {
+        int32_t c = 0;
+        if (lane == 0) c = atomicAdd(&s_chunk[0], 1);
+        c = __shfl_sync(0xffffffffu, c, 0);
+        if (c >= nchunks) break;
+        const int32_t i = (nchunks - 1 - c) * 32 + lane;  // X ascends by degree: heaviest chunk first
+        int32_t st = 0, L = 0;
+        if (i < nx) {
+          st = cur[i];
+          const int32_t en = gallop_lower_bound(g.ci, st, endp[i], r1);
+          L = en - st;
+          beg[i] = st;
+          cur[i] = en;
+        }
+        // runs of 32 or more entries (most of the wedges): the whole warp,
+        // one run at a time, consecutive entries over the lanes
+        unsigned lm = __ballot_sync(0xffffffffu, L >= 32);
+        while (lm) {
+          const int src = __ffs(lm) - 1;
+          lm &= lm - 1;
+          const int32_t s0 = __shfl_sync(0xffffffffu, st, src);
+          const int32_t n0 = __shfl_sync(0xffffffffu, L, src);
+          for (int32_t k0 = 0; k0 < n0; k0 += 256) {  // eight windows of loads in flight
+            int32_t o[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              const int32_t kk = k0 + 32 * j + lane;
+              o[j] = kk < n0 ? g.ci[s0 + kk] : -1;
+            }
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+              if (o[j] >= 0) add_count(tab, o[j] - lo_id, half);
+          }
+        }
+        // shorter runs dealt to the lanes end to end
+        const int32_t Ls = L < 32 ? L : 0;
+        const Deal d = deal_setup(Ls, comp, lane);
+        const int32_t sb = st - d.excl;  // slot of position kk of this lane's run: sb + kk
+        int before = 0;
+        for (int32_t k0 = 0; k0 < d.total; k0 += 128) {
+          int32_t q[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int ol = deal_owner(d, Ls, k0 + 32 * j, comp, lane, before);
+            const int32_t kk = k0 + 32 * j + lane;
+            const int32_t bj = __shfl_sync(0xffffffffu, sb, ol);
+            q[j] = kk < d.total ? bj + kk : -1;
+          }
+          int32_t o[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) o[j] = q[j] >= 0 ? g.ci[q[j]] : lo_id;
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            if (q[j] >= 0) add_count(tab, o[j] - lo_id, half);
+        }
+        __syncwarp();
+      }
+      __syncthreads();
+      // attribution of the block's wedges
+      for (;;) {
+        int32_t c = 0;
+        if (lane == 0) c = atomicAdd(&s_chunk[1], 1);
+        c = __shfl_sync(0xffffffffu, c, 0);
+        if (c >= nchunks) break;
+        const int32_t i = (nchunks - 1 - c) * 32 + lane;
+        int32_t st = 0, L = 0;
+        if (i < nx) {
+          st = beg[i];
+          L = cur[i] - st;
+        }
+        s_sx[warp][lane] = 0ull;  // per x of the chunk: sum of its wedges' counts
+        s_sx32[warp][lane] = 0u;
+        __syncwarp();
+        // runs of 32 or more entries: the whole warp, one run at a time
+        unsigned lm = __ballot_sync(0xffffffffu, L >= 32);
+        while (lm) {
+          const int src = __ffs(lm) - 1;
+          lm &= lm - 1;
+          const int32_t s0 = __shfl_sync(0xffffffffu, st, src);
+          const int32_t n0 = __shfl_sync(0xffffffffu, L, src);
+          unsigned long long acc = 0ull;
+          for (int32_t k0 = 0; k0 < n0; k0 += 256) {  // eight windows of loads in flight
+            int32_t o[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              const int32_t kk = k0 + 32 * j + lane;
+              o[j] = kk < n0 ? g.ci[s0 + kk] : -1;
+            }
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              if (o[j] < 0) continue;
+              const uint32_t cnt = read_count(tab, o[j] - lo_id, half) - 1u;
+              if (cnt) {
+                atomicAdd(&a.P[s0 + k0 + 32 * j + lane], (unsigned long long)cnt);  // slot (x, o)
+                acc += cnt;
+              }
+            }
+          }
+          for (int off = 16; off; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+          if (lane == src) s_sx[warp][lane] += acc;
+        }
+        __syncwarp();
+        // shorter runs dealt to the lanes end to end
+        const int32_t Ls = L < 32 ? L : 0;
+        const Deal d = deal_setup(Ls, comp, lane);
+        const int32_t sb = st - d.excl;  // slot of position kk of this lane's run: sb + kk
+        int before = 0;
+        for (int32_t k0 = 0; k0 < d.total; k0 += 128) {
+          int32_t q[4], ol[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            ol[j] = deal_owner(d, Ls, k0 + 32 * j, comp, lane, before);
+            const int32_t kk = k0 + 32 * j + lane;
+            const int32_t bj = __shfl_sync(0xffffffffu, sb, ol[j]);
+            q[j] = kk < d.total ? bj + kk : -1;
+          }
+          int32_t o[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) o[j] = q[j] >= 0 ? g.ci[q[j]] : lo_id;
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            if (q[j] >= 0) {
+              const uint32_t cnt = read_count(tab, o[j] - lo_id, half) - 1u;
+              if (cnt) {
+                atomicAdd(&a.P[q[j]], (unsigned long long)cnt);  // slot (x, o)
+                atomicAdd(&s_sx32[warp][ol[j]], cnt);           // the owner's sum
+              }
+            }
+          }
+        }
+        __syncwarp();
+        if (i < nx) {
+          const unsigned long long sx = s_sx[warp][lane] + s_sx32[warp][lane];
+          if (sx) atomicAdd(&a.P[hb + i], sx);  // slot (h, x)
+        }
+        __syncwarp();
+      }
+      __syncthreads();
+    }
   }
   for (int o = 16; o; o >>= 1) w_wedge += __shfl_xor_sync(0xffffffffu, w_wedge, o);
   if (lane == 0 && w_wedge) {

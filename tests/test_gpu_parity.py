@@ -644,11 +644,11 @@ def test_hub_jobs_split_or_whole_give_the_same_counts():
 
 
 def test_serving_under_a_nearly_full_budget():
-    # a budget that holds about three of the requests at once: submissions are
+    # a budget that holds about two of the requests at once: submissions are
     # refused (GC_ERR_BUSY) until earlier ones retire, and every result equals
     # the graph's own whole-graph count
     import time
-    params = graphgen.serving_params(16, m_lo=20000, m_hi=200000, seed=9)
+    params = graphgen.serving_params(16, m_lo=200000, m_hi=800000, seed=9)
     gs = [graphgen.serving_graph(params, r) for r in range(16)]
     expect = []
     for g in gs:
@@ -660,19 +660,19 @@ def test_serving_under_a_nearly_full_budget():
         n, m = len(rp) - 1, len(ci) // 2
         return 44 * n + 32 * m + 1024 + (grid * n * 4 if n > 4096 else 0)
 
-    budget = 3 * max(footprint(*g) for g in gs)
+    budget = 2 * max(footprint(*g) for g in gs)
     b = gcb.gc_batch_create(budget, 0)
     tickets, results, busy, nxt = {}, {}, 0, 0
     t_end = time.time() + 300
     try:
         while len(results) < len(gs) and time.time() < t_end:
-            if nxt < len(gs):
+            while nxt < len(gs):  # submit until the runtime refuses
                 t = gcb.gc_batch_try_submit(b, *gs[nxt])
                 if t is None:
                     busy += 1
-                else:
-                    tickets[nxt] = t
-                    nxt += 1
+                    break
+                tickets[nxt] = t
+                nxt += 1
             for r, t in list(tickets.items()):
                 x = gcb.gc_batch_poll(b, t, timeout_us=0)
                 if x is not None:
