@@ -264,11 +264,15 @@ gc_status gc_batch_destroy(gc_batch b);
  *   GC_PARAM_BLOCK_N64 + c threads per CTA of size class c (n <= 64, 128,
  *                          256, 512, 1024): 64, 128, 256 or 512
  *   GC_PARAM_USE_GRAPH     0 or 1
+ *   GC_PARAM_MAX_INFLIGHT  1 .. 4: launches the dispatcher of a continuous
+ *                          batch keeps in flight, each on its own stream
+ *                          (default 2)
  * Errors: GC_ERR_ARG (unknown parameter or value out of range).
  */
 #define GC_PARAM_SMALL_N_MAX 0
 #define GC_PARAM_BLOCK_N64 1
 #define GC_PARAM_USE_GRAPH 6
+#define GC_PARAM_MAX_INFLIGHT 7
 gc_status gc_batch_set_param(gc_batch b, int32_t param, int32_t value);
 gc_status gc_batch_get_param(gc_batch b, int32_t param, int32_t* value);
 

@@ -34,7 +34,7 @@ INDUCED_NAMES = ["H7", "H8", "H9", "H10", "H11", "H12", "H13", "H14", "H15", "H1
 GC_NUM_GRAPHLETS = 17
 GC_NO_VALIDATE = 0x1
 GC_BATCH_MANUAL = 0x1
-GC_PARAM_SMALL_N_MAX, GC_PARAM_BLOCK_N64, GC_PARAM_USE_GRAPH = 0, 1, 6
+GC_PARAM_SMALL_N_MAX, GC_PARAM_BLOCK_N64, GC_PARAM_USE_GRAPH, GC_PARAM_MAX_INFLIGHT = 0, 1, 6, 7
 SMALL_CLASS_N = [64, 128, 256, 512, 1024]      # size classes of the bitmatrix kernels
 SMALL_BLOCKS = [64, 128, 256, 512]
 BATCH_STATS = ["class_n64_ms", "class_n128_ms", "class_n256_ms", "class_n512_ms", "class_n1024_ms",
@@ -345,7 +345,8 @@ def gc_batch_config(b) -> dict:
     """The batch's parameters: small_n_max, block per size class, use_graph."""
     return {"small_n_max": gc_batch_get_param(b, GC_PARAM_SMALL_N_MAX),
             "block": {str(n): gc_batch_get_param(b, GC_PARAM_BLOCK_N64 + c) for c, n in enumerate(SMALL_CLASS_N)},
-            "use_graph": gc_batch_get_param(b, GC_PARAM_USE_GRAPH)}
+            "use_graph": gc_batch_get_param(b, GC_PARAM_USE_GRAPH),
+            "max_inflight": gc_batch_get_param(b, GC_PARAM_MAX_INFLIGHT)}
 
 
 def gc_batch_configure(b, config: dict):
@@ -357,6 +358,8 @@ def gc_batch_configure(b, config: dict):
             gc_batch_set_param(b, GC_PARAM_BLOCK_N64 + c, config["block"][str(n)])
     if "use_graph" in config:
         gc_batch_set_param(b, GC_PARAM_USE_GRAPH, config["use_graph"])
+    if "max_inflight" in config:
+        gc_batch_set_param(b, GC_PARAM_MAX_INFLIGHT, config["max_inflight"])
 
 
 def gc_batch_last_stats(b) -> dict:

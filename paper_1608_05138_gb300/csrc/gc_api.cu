@@ -149,6 +149,43 @@ gc_status csr_symmetry(int32_t n, const int32_t* rp, const int32_t* ci, std::str
   return GC_OK;
 }
 
+// The same checks, in the same order and with the same codes, for one small
+// graph on the calling thread, with the caller's scratch for the symmetry
+// walk (no allocation once the scratch has grown): what a bulk submission of
+// many small graphs runs on each of its threads.
+gc_status validate_csr_small(int32_t n, const int32_t* rp, const int32_t* ci, std::vector<int32_t>* fill) {
+  if (n < 0) { set_error("n < 0"); return GC_ERR_ARG; }
+  if (rp[0] != 0) { set_error("row_ptr[0] != 0"); return GC_ERR_RANGE; }
+  for (int32_t x = 0; x < n; ++x)
+    if (rp[x + 1] < rp[x]) {
+      set_error("row_ptr decreases at row " + std::to_string(x));
+      return GC_ERR_UNSORTED;
+    }
+  if (rp[n] % 2 != 0) { set_error("row_ptr[n] is odd: the graph cannot be symmetric"); return GC_ERR_ASYMMETRIC; }
+  for (int32_t x = 0; x < n; ++x)
+    for (int32_t p = rp[x]; p < rp[x + 1]; ++p) {
+      const int32_t y = ci[p];
+      if (y < 0 || y >= n) { set_error("column " + std::to_string(y) + " out of range in row " + std::to_string(x)); return GC_ERR_RANGE; }
+      if (y == x) { set_error("self-loop at vertex " + std::to_string(x)); return GC_ERR_SELF_LOOP; }
+      if (p > rp[x] && ci[p - 1] == y) { set_error("duplicate neighbour " + std::to_string(y) + " in row " + std::to_string(x)); return GC_ERR_DUPLICATE; }
+      if (p > rp[x] && ci[p - 1] > y) { set_error("row " + std::to_string(x) + " not ascending"); return GC_ERR_UNSORTED; }
+    }
+  // symmetry: the k-th row (in order) that names y names it from the k-th entry of row y
+  if ((int64_t)fill->size() < (int64_t)n) fill->resize((size_t)n);
+  int32_t* f = fill->data();
+  for (int32_t y = 0; y < n; ++y) f[y] = rp[y];
+  for (int32_t x = 0; x < n; ++x)
+    for (int32_t p = rp[x]; p < rp[x + 1]; ++p) {
+      const int32_t y = ci[p];
+      const int32_t q = f[y]++;
+      if (q >= rp[y + 1] || ci[q] != x) {
+        set_error("edge (" + std::to_string(x) + "," + std::to_string(y) + ") has no reverse");
+        return GC_ERR_ASYMMETRIC;
+      }
+    }
+  return GC_OK;
+}
+
 gc_status validate_csr(int32_t n, const int32_t* rp, const int32_t* ci) {
   gc_status st = csr_linear_checks(n, rp, ci);
   if (st != GC_OK) return st;

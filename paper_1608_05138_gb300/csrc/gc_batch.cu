@@ -34,6 +34,7 @@
 
 namespace gc {
 gc_status validate_csr(int32_t n, const int32_t* rp, const int32_t* ci);
+gc_status validate_csr_small(int32_t n, const int32_t* rp, const int32_t* ci, std::vector<int32_t>* fill);
 
 namespace {
 
@@ -47,12 +48,19 @@ __global__ void k_globalize(int32_t n, const int32_t* __restrict__ rp, const int
   }
 }
 
+// A graph waiting for a launch. Its CSR is the library's own copy: rp (n + 1
+// entries starting at 0) and ci (2m entries) point into `owner` -- a copy of
+// one graph (gc_batch_submit), or one shared copy of a whole bulk submission
+// (gc_batch_submit_many: one allocation and two bulk copies instead of one
+// pair per graph).
 struct PendingGraph {
   uint64_t ticket;
   int32_t n;
   int64_t m;
   int64_t bytes;
-  std::vector<int32_t> rp, ci;
+  const int32_t* rp = nullptr;
+  const int32_t* ci = nullptr;
+  std::shared_ptr<std::vector<int32_t>> owner;
 };
 
 struct Result {
@@ -125,7 +133,7 @@ struct gc_batch_s {
   int64_t budget = 0;
   uint32_t flags = 0;
   BatchConfig cfg;
-  SmallBufs small[2];                   // per stream slot
+  SmallBufs small[kMaxInflight];        // per stream slot
   double last_stats[GC_BATCH_STATS] = {};  // of the last retired launch
   int64_t in_use = 0;
   std::mutex mu;
@@ -137,8 +145,8 @@ struct gc_batch_s {
   uint64_t next_ticket = 1;
   bool stop = false;
   std::thread dispatcher;
-  cudaStream_t streams[2] = {nullptr, nullptr};
-  int next_stream = 0;
+  cudaStream_t streams[kMaxInflight] = {};
+  int next_stream = 0;                  // manual mode: round-robin over the slots
   int device = 0;
 };
 
@@ -173,7 +181,7 @@ gc_status run_union(std::vector<PendingGraph*>& graphs, cudaStream_t s, Launch* 
         h_rp[vo + i] = (int32_t)(eo + pg.rp[i]);
         h_vgid[vo + i] = gi;
       }
-      if (pg.m > 0) std::memcpy(h_ci.data() + eo, pg.ci.data(), sizeof(int32_t) * 2 * pg.m);
+      if (pg.m > 0) std::memcpy(h_ci.data() + eo, pg.ci, sizeof(int32_t) * 2 * pg.m);
       h_desc[gi] = (int32_t)vo;
       h_desc[G + gi] = pg.n;
       h_gm[gi] = pg.m;
@@ -370,9 +378,9 @@ gc_status run_small(std::vector<PendingGraph*>& graphs, cudaStream_t s, Launch* 
       const int64_t e0 = eoff[G] * t / nt, e1 = eoff[G] * (t + 1) / nt;
       int32_t gi = (int32_t)(std::lower_bound(eoff.begin(), eoff.begin() + G, e0) - eoff.begin());
       for (; gi < G && (eoff[gi] < e1 || t == nt - 1); ++gi) {
-        std::memcpy(sb->h_rp + voff[gi], graphs[gi]->rp.data(), sizeof(int32_t) * (graphs[gi]->n + 1));
+        std::memcpy(sb->h_rp + voff[gi], graphs[gi]->rp, sizeof(int32_t) * (graphs[gi]->n + 1));
         if (graphs[gi]->m > 0)
-          std::memcpy(sb->h_ci + eoff[gi], graphs[gi]->ci.data(), sizeof(int32_t) * 2 * graphs[gi]->m);
+          std::memcpy(sb->h_ci + eoff[gi], graphs[gi]->ci, sizeof(int32_t) * 2 * graphs[gi]->m);
       }
     };
     std::vector<std::thread> th;
@@ -565,10 +573,22 @@ bool launch_pending(gc_batch b) {
       take.push_back(std::move(pg));
       b->pending.pop_front();
     }
-    L->stream_slot = b->next_stream;
+    // a stream slot no launch in flight holds (the dispatcher keeps fewer
+    // than max_inflight launches in flight); manual flushes take the slots in
+    // turn (a slot's buffers wait for their previous use)
+    int slot = -1;
+    for (int k = 0; k < b->cfg.max_inflight && slot < 0; ++k) {
+      bool used = false;
+      for (Launch* o : b->inflight) used |= o->stream_slot == k;
+      if (!used) slot = k;
+    }
+    if (slot < 0) {
+      slot = b->next_stream % b->cfg.max_inflight;
+      b->next_stream = slot + 1;
+    }
+    L->stream_slot = slot;
     L->cfg = b->cfg;
-    L->stream = b->streams[b->next_stream];
-    b->next_stream ^= 1;
+    L->stream = b->streams[slot];
   }
   cudaSetDevice(b->device);
   cudaError_t e1 = cudaMallocHost(&L->h_x, sizeof(unsigned long long) * 34 * take.size());
@@ -592,7 +612,7 @@ void dispatcher_main(gc_batch b) {
   std::unique_lock<std::mutex> lk(b->mu);
   while (!b->stop) {
     retire_locked(b);
-    if (!b->pending.empty() && b->inflight.size() < 2) {
+    if (!b->pending.empty() && (int)b->inflight.size() < b->cfg.max_inflight) {
       lk.unlock();
       launch_pending(b);
       lk.lock();
@@ -653,6 +673,9 @@ gc_status gc_batch_set_param(gc_batch b, int32_t param, int32_t value) {
   } else if (param == GC_PARAM_USE_GRAPH) {
     if (value != 0 && value != 1) { set_error("use_graph must be 0 or 1"); return GC_ERR_ARG; }
     b->cfg.use_graph = value;
+  } else if (param == GC_PARAM_MAX_INFLIGHT) {
+    if (value < 1 || value > kMaxInflight) { set_error("max_inflight must be 1 .. 4"); return GC_ERR_ARG; }
+    b->cfg.max_inflight = value;
   } else {
     set_error("unknown parameter");
     return GC_ERR_ARG;
@@ -667,6 +690,7 @@ gc_status gc_batch_get_param(gc_batch b, int32_t param, int32_t* value) {
   else if (param >= GC_PARAM_BLOCK_N64 && param < GC_PARAM_BLOCK_N64 + kSmallClasses)
     *value = b->cfg.class_block[param - GC_PARAM_BLOCK_N64];
   else if (param == GC_PARAM_USE_GRAPH) *value = b->cfg.use_graph;
+  else if (param == GC_PARAM_MAX_INFLIGHT) *value = b->cfg.max_inflight;
   else { set_error("unknown parameter"); return GC_ERR_ARG; }
   return GC_OK;
 }
@@ -693,8 +717,16 @@ gc_status gc_batch_submit(gc_batch b, int32_t n, const int32_t* row_ptr, const i
   pg.n = n;
   pg.m = m;
   pg.bytes = bytes;
-  pg.rp.assign(row_ptr, row_ptr + n + 1);
-  if (m > 0) pg.ci.assign(col_idx, col_idx + 2 * m);
+  try {
+    pg.owner = std::make_shared<std::vector<int32_t>>((size_t)n + 1 + 2 * (size_t)m);
+  } catch (...) {
+    set_error("host allocation failed");
+    return GC_ERR_NOMEM;
+  }
+  std::memcpy(pg.owner->data(), row_ptr, sizeof(int32_t) * ((size_t)n + 1));
+  if (m > 0) std::memcpy(pg.owner->data() + n + 1, col_idx, sizeof(int32_t) * 2 * (size_t)m);
+  pg.rp = pg.owner->data();
+  pg.ci = pg.owner->data() + n + 1;
   {
     std::lock_guard<std::mutex> lk(b->mu);
     if (b->in_use + bytes > b->budget) {
@@ -718,22 +750,48 @@ gc_status gc_batch_submit_many(gc_batch b, int64_t G, const int32_t* nvert, cons
     return GC_ERR_ARG;
   }
   if (G == 0) return GC_OK;
+  // the library's copy: one buffer for all graphs, rows then columns, each
+  // graph at its own offset (own_v, own_e), filled while validating
+  std::vector<int64_t> own_v((size_t)G + 1), own_e((size_t)G + 1);
+  own_v[0] = own_e[0] = 0;
+  for (int64_t g = 0; g < G; ++g) {
+    const int32_t n = nvert[g];
+    if (n < 0 || eoff[g + 1] < eoff[g]) {
+      set_error("graph " + std::to_string(g) + ": negative size or decreasing offsets");
+      return GC_ERR_ARG;
+    }
+    own_v[g + 1] = own_v[g] + n + 1;
+    own_e[g + 1] = own_e[g] + (eoff[g + 1] - eoff[g]);
+  }
+  std::shared_ptr<std::vector<int32_t>> owner;
+  try {
+    owner = std::make_shared<std::vector<int32_t>>((size_t)(own_v[G] + own_e[G]));
+  } catch (...) {
+    set_error("host allocation failed");
+    return GC_ERR_NOMEM;
+  }
+  int32_t* own_rp = owner->data();
+  int32_t* own_ci = owner->data() + own_v[G];
   std::vector<PendingGraph> pgs((size_t)G);
   unsigned hw = std::thread::hardware_concurrency();
   const int nt = (int)std::min<int64_t>(std::max(1u, std::min(hw, 32u)), G);
   std::vector<gc_status> res(nt, GC_OK);
   std::vector<std::string> msg(nt);
-  auto work = [&](int t) {
-    for (int64_t g = t; g < G; g += nt) {
+  auto work = [&](int t) {  // the graphs whose entries start in this thread's share
+    std::vector<int32_t> fill;  // symmetry-walk scratch of this thread
+    const int64_t e0 = own_e[G] * t / nt, e1 = own_e[G] * (t + 1) / nt;
+    int64_t g = std::lower_bound(own_e.begin(), own_e.begin() + G, e0) - own_e.begin();
+    for (; g < G && (own_e[g] < e1 || t == nt - 1); ++g) {
+      if (t > 0 && own_e[g] < e0) continue;
       const int32_t n = nvert[g];
       const int32_t* rp = row_ptr + voff[g];
       const int32_t* ci = col_idx ? col_idx + eoff[g] : nullptr;
-      if (n < 0 || (int64_t)rp[n] != eoff[g + 1] - eoff[g]) {
+      if ((int64_t)rp[n] != eoff[g + 1] - eoff[g]) {
         res[t] = GC_ERR_ARG;
         msg[t] = "graph " + std::to_string(g) + ": offsets disagree with row_ptr";
         return;
       }
-      gc_status st = validate_csr(n, rp, ci);
+      gc_status st = (int64_t)rp[n] < (1 << 20) ? validate_csr_small(n, rp, ci, &fill) : validate_csr(n, rp, ci);
       if (st != GC_OK) {
         res[t] = st;
         msg[t] = "graph " + std::to_string(g) + ": " + gc_last_error();
@@ -743,8 +801,11 @@ gc_status gc_batch_submit_many(gc_batch b, int64_t G, const int32_t* nvert, cons
       pg.n = n;
       pg.m = rp[n] / 2;
       pg.bytes = footprint(n, pg.m);
-      pg.rp.assign(rp, rp + n + 1);
-      if (pg.m > 0) pg.ci.assign(ci, ci + 2 * pg.m);
+      std::memcpy(own_rp + own_v[g], rp, sizeof(int32_t) * ((size_t)n + 1));
+      if (pg.m > 0) std::memcpy(own_ci + own_e[g], ci, sizeof(int32_t) * 2 * (size_t)pg.m);
+      pg.rp = own_rp + own_v[g];
+      pg.ci = own_ci + own_e[g];
+      pg.owner = owner;
     }
   };
   std::vector<std::thread> th;

@@ -263,7 +263,9 @@ struct BatchConfig {
   int32_t small_n_max = 512;                                  // graphs up to this many vertices: bitmatrix kernels
   int32_t class_block[kSmallClasses] = {256, 256, 256, 256, 256};  // threads per CTA of each size class
   int32_t use_graph = 1;                                      // replay each small-graph launch as a CUDA graph
+  int32_t max_inflight = 2;                                   // launches the dispatcher keeps in flight
 };
+constexpr int kMaxInflight = 4;                                 // stream slots of a batch runtime
 // Size class of a graph with n vertices (kSmallClasses if above the largest).
 int small_class_of(int32_t n);
 // Overrides cfg with the tuning cache's entry for the current GPU (gc_tune.cu);

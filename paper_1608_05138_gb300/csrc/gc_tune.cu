@@ -194,6 +194,8 @@ bool load_tuned_config(BatchConfig* cfg, std::string* source) {
       c.small_n_max = (int32_t)v->num;
   if (const JValue* v = member(gpu, "use_graph"))
     if (v->kind == JValue::kNumber) c.use_graph = v->num != 0;
+  if (const JValue* v = member(gpu, "max_inflight"))
+    if (v->kind == JValue::kNumber && v->num >= 1 && v->num <= kMaxInflight) c.max_inflight = (int32_t)v->num;
   if (const JValue* blk = member(gpu, "block"))
     for (int k = 0; k < kSmallClasses; ++k)
       if (const JValue* v = member(blk, std::to_string(kSmallClassN[k])))

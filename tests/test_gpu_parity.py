@@ -486,7 +486,8 @@ def test_batch_budget_and_tickets():
         gcb.gc_batch_destroy(b)
 
 
-def test_served_result_same_alone_and_in_mix():
+@pytest.mark.parametrize("inflight", [1, 2, 4])
+def test_served_result_same_alone_and_in_mix(inflight):
     params = graphgen.serving_params(12, m_lo=1000, m_hi=60000, seed=7)
     gs = [graphgen.serving_graph(params, r) for r in range(12)]
     alone = []
@@ -498,6 +499,8 @@ def test_served_result_same_alone_and_in_mix():
             gcb.gc_batch_destroy(b)
     b = gcb.gc_batch_create(4 << 30, 0)
     try:
+        gcb.gc_batch_set_param(b, gcb.GC_PARAM_MAX_INFLIGHT, inflight)
+        assert gcb.gc_batch_config(b)["max_inflight"] == inflight
         ts = [gcb.gc_batch_submit(b, *g) for g in gs]
         mix = [gcb.gc_batch_poll(b, t, timeout_us=120_000_000) for t in ts]
     finally:
@@ -590,7 +593,7 @@ def test_batch_parameters_and_tuning_cache(tmp_path, monkeypatch):
     b = gcb.gc_batch_create(1 << 30, gcb.GC_BATCH_MANUAL)
     try:
         for param, value in ((gcb.GC_PARAM_SMALL_N_MAX, 2000), (gcb.GC_PARAM_BLOCK_N64, 96),
-                             (gcb.GC_PARAM_USE_GRAPH, 2), (99, 1)):
+                             (gcb.GC_PARAM_USE_GRAPH, 2), (gcb.GC_PARAM_MAX_INFLIGHT, 5), (99, 1)):
             with pytest.raises(gcb.GcError) as ei:
                 gcb.gc_batch_set_param(b, param, value)
             assert ei.value.status == -1
@@ -599,7 +602,8 @@ def test_batch_parameters_and_tuning_cache(tmp_path, monkeypatch):
     finally:
         gcb.gc_batch_destroy(b)
     # a cache entry for this GPU is read at gc_batch_create
-    entry = {"small_n_max": 300, "use_graph": 0, "block": {"64": 64, "128": 512, "256": 128, "512": 64, "1024": 512}}
+    entry = {"small_n_max": 300, "use_graph": 0, "block": {"64": 64, "128": 512, "256": 128, "512": 64, "1024": 512},
+             "max_inflight": 3}
     path = tmp_path / "cache.json"
     path.write_text(json.dumps({"some other GPU": {"small_n_max": 7}, torch.cuda.get_device_name(0): entry}))
     monkeypatch.setenv("GC_TUNE_CACHE", str(path))
@@ -683,3 +687,29 @@ def test_serving_under_a_nearly_full_budget():
         gcb.gc_batch_destroy(b)
     assert busy > 0
     assert [results.get(r) for r in range(len(gs))] == expect
+
+
+def test_batch_submit_many_rejects_a_malformed_graph():
+    # the bulk path validates each graph on its own thread: the codes and
+    # messages are those of a single submission, and nothing is admitted
+    good = [graphgen.er(60, 0.2, 80 + i) for i in range(4)]
+    bad = {-5: (np.array([0, 2, 3, 4], np.int32), np.array([1, 2, 2, 0], np.int32)),   # (0,1) without (1,0)
+           -4: (np.array([0, 1, 2], np.int32), np.array([0, 0], np.int32)),             # self-loop
+           -3: (np.array([0, 2, 4], np.int32), np.array([1, 1, 0, 0], np.int32)),       # duplicate
+           -6: (np.array([0, 1, 2], np.int32), np.array([7, 0], np.int32))}             # out of range
+    for code, (brp, bci) in bad.items():
+        gs = good[:2] + [(brp, bci)] + good[2:]
+        nvert = np.array([len(r) - 1 for r, _ in gs], np.int32)
+        voff = np.concatenate([[0], np.cumsum([len(r) for r, _ in gs])]).astype(np.int64)
+        eoff = np.concatenate([[0], np.cumsum([len(c) for _, c in gs])]).astype(np.int64)
+        rp = np.concatenate([r for r, _ in gs]).astype(np.int32)
+        ci = np.concatenate([c for _, c in gs]).astype(np.int32)
+        b = gcb.gc_batch_create(1 << 30, gcb.GC_BATCH_MANUAL)
+        try:
+            with pytest.raises(gcb.GcError) as ei:
+                gcb.gc_batch_submit_many(b, nvert, voff, eoff, rp, ci)
+            assert ei.value.status == code and "graph 2" in str(ei.value)
+            x = gcb.gc_batch_poll_many(b, np.zeros(0, np.uint64), timeout_us=0)  # nothing was admitted
+            assert x is not None and x.shape == (0, 17, 2)
+        finally:
+            gcb.gc_batch_destroy(b)
