@@ -349,15 +349,30 @@ __global__ void __launch_bounds__(kBlock) k_pass_c(DevGraph g, CountArgs a) {
 constexpr int kHeavyBlock = 1024;
 constexpr int kHeavyWarps = kHeavyBlock / 32;
 
-// Counters of the block: 32-bit, or two 16-bit counters per word when the
-// unit has fewer than 65536 lower neighbours (no count can exceed that, so no
-// carry crosses into the other half) -- twice the o-range per block.
-__device__ __forceinline__ void add_count(uint32_t* tab, int32_t slot, bool half) {
-  if (half) atomicAdd(&tab[slot >> 1], 1u << ((slot & 1) << 4));
-  else atomicAdd(&tab[slot], 1u);
+// Counters of the block, kCpw to a word: one 32-bit counter; two 16-bit
+// counters when the unit has fewer than 65536 lower neighbours; three 10-bit
+// counters when it has fewer than 1023 (no count exceeds the number of lower
+// neighbours, so no carry crosses into the next field) -- twice or three
+// times the o-range per block.
+template <int kCpw>
+__device__ __forceinline__ void add_count(uint32_t* tab, int32_t slot) {
+  if (kCpw == 3) {
+    const uint32_t w = (uint32_t)slot / 3u;
+    atomicAdd(&tab[w], 1u << (((uint32_t)slot - 3u * w) * 10u));
+  } else if (kCpw == 2) {
+    atomicAdd(&tab[slot >> 1], 1u << ((slot & 1) << 4));
+  } else {
+    atomicAdd(&tab[slot], 1u);
+  }
 }
-__device__ __forceinline__ uint32_t read_count(const uint32_t* tab, int32_t slot, bool half) {
-  return half ? (tab[slot >> 1] >> ((slot & 1) << 4)) & 0xffffu : tab[slot];
+template <int kCpw>
+__device__ __forceinline__ uint32_t read_count(const uint32_t* tab, int32_t slot) {
+  if (kCpw == 3) {
+    const uint32_t w = (uint32_t)slot / 3u;
+    return (tab[w] >> (((uint32_t)slot - 3u * w) * 10u)) & 1023u;
+  }
+  if (kCpw == 2) return (tab[slot >> 1] >> ((slot & 1) << 4)) & 0xffffu;
+  return tab[slot];
 }
 
 // first index in [p, e) with a[index] >= key; a ascending
@@ -418,6 +433,155 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
+// One block [lo_id, r1) of a hub job: the counts of the block from each
+// x's run in it (found by galloping search from the x's cursor), then the
+// attribution of the block's wedges. Called by the whole CTA after the
+// table is zeroed and the chunk counters reset (and a barrier).
+template <int kCpw>
+__device__ __forceinline__ void hub_block(const DevGraph& g, const CountArgs& a, uint32_t* tab, int32_t* s_chunk,
+                                          unsigned long long* sx, uint32_t* sx32, int32_t* comp, int32_t* beg,
+                                          int32_t* cur, const int32_t* endp, int32_t nx, int32_t nchunks,
+                                          int32_t hb, int32_t lo_id, int32_t r1, int lane) {
+  // counts of the block
+  for (;;) {
+    int32_t c = 0;
+    if (lane == 0) c = atomicAdd(&s_chunk[0], 1);
+    c = __shfl_sync(0xffffffffu, c, 0);
+    if (c >= nchunks) break;
+    const int32_t i = (nchunks - 1 - c) * 32 + lane;  // X ascends by degree: heaviest chunk first
+    int32_t st = 0, L = 0;
+    if (i < nx) {
+      st = cur[i];
+      const int32_t en = gallop_lower_bound(g.ci, st, endp[i], r1);
+      L = en - st;
+      beg[i] = st;
+      cur[i] = en;
+    }
+    // runs of 32 or more entries (most of the wedges): the whole warp,
+    // one run at a time, consecutive entries over the lanes
+    unsigned lm = __ballot_sync(0xffffffffu, L >= 32);
+    while (lm) {
+      const int src = __ffs(lm) - 1;
+      lm &= lm - 1;
+      const int32_t s0 = __shfl_sync(0xffffffffu, st, src);
+      const int32_t n0 = __shfl_sync(0xffffffffu, L, src);
+      for (int32_t k0 = 0; k0 < n0; k0 += 256) {  // eight windows of loads in flight
+        int32_t o[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int32_t kk = k0 + 32 * j + lane;
+          o[j] = kk < n0 ? g.ci[s0 + kk] : -1;
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          if (o[j] >= 0) add_count<kCpw>(tab, o[j] - lo_id);
+      }
+    }
+    // shorter runs dealt to the lanes end to end
+    const int32_t Ls = L < 32 ? L : 0;
+    const Deal d = deal_setup(Ls, comp, lane);
+    const int32_t sb = st - d.excl;  // slot of position kk of this lane's run: sb + kk
+    int before = 0;
+    for (int32_t k0 = 0; k0 < d.total; k0 += 128) {
+      int32_t q[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int ol = deal_owner(d, Ls, k0 + 32 * j, comp, lane, before);
+        const int32_t kk = k0 + 32 * j + lane;
+        const int32_t bj = __shfl_sync(0xffffffffu, sb, ol);
+        q[j] = kk < d.total ? bj + kk : -1;
+      }
+      int32_t o[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) o[j] = q[j] >= 0 ? g.ci[q[j]] : lo_id;
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (q[j] >= 0) add_count<kCpw>(tab, o[j] - lo_id);
+    }
+    __syncwarp();
+  }
+  __syncthreads();
+  // attribution of the block's wedges
+  for (;;) {
+    int32_t c = 0;
+    if (lane == 0) c = atomicAdd(&s_chunk[1], 1);
+    c = __shfl_sync(0xffffffffu, c, 0);
+    if (c >= nchunks) break;
+    const int32_t i = (nchunks - 1 - c) * 32 + lane;
+    int32_t st = 0, L = 0;
+    if (i < nx) {
+      st = beg[i];
+      L = cur[i] - st;
+    }
+    sx[lane] = 0ull;  // per x of the chunk: sum of its wedges' counts
+    sx32[lane] = 0u;
+    __syncwarp();
+    // runs of 32 or more entries: the whole warp, one run at a time
+    unsigned lm = __ballot_sync(0xffffffffu, L >= 32);
+    while (lm) {
+      const int src = __ffs(lm) - 1;
+      lm &= lm - 1;
+      const int32_t s0 = __shfl_sync(0xffffffffu, st, src);
+      const int32_t n0 = __shfl_sync(0xffffffffu, L, src);
+      unsigned long long acc = 0ull;
+      for (int32_t k0 = 0; k0 < n0; k0 += 256) {  // eight windows of loads in flight
+        int32_t o[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int32_t kk = k0 + 32 * j + lane;
+          o[j] = kk < n0 ? g.ci[s0 + kk] : -1;
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          if (o[j] < 0) continue;
+          const uint32_t cnt = read_count<kCpw>(tab, o[j] - lo_id) - 1u;
+          if (cnt) {
+            atomicAdd(&a.P[s0 + k0 + 32 * j + lane], (unsigned long long)cnt);  // slot (x, o)
+            acc += cnt;
+          }
+        }
+      }
+      for (int off = 16; off; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+      if (lane == src) sx[lane] += acc;
+    }
+    __syncwarp();
+    // shorter runs dealt to the lanes end to end
+    const int32_t Ls = L < 32 ? L : 0;
+    const Deal d = deal_setup(Ls, comp, lane);
+    const int32_t sb = st - d.excl;  // slot of position kk of this lane's run: sb + kk
+    int before = 0;
+    for (int32_t k0 = 0; k0 < d.total; k0 += 128) {
+      int32_t q[4], ol[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        ol[j] = deal_owner(d, Ls, k0 + 32 * j, comp, lane, before);
+        const int32_t kk = k0 + 32 * j + lane;
+        const int32_t bj = __shfl_sync(0xffffffffu, sb, ol[j]);
+        q[j] = kk < d.total ? bj + kk : -1;
+      }
+      int32_t o[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) o[j] = q[j] >= 0 ? g.ci[q[j]] : lo_id;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        if (q[j] >= 0) {
+          const uint32_t cnt = read_count<kCpw>(tab, o[j] - lo_id) - 1u;
+          if (cnt) {
+            atomicAdd(&a.P[q[j]], (unsigned long long)cnt);  // slot (x, o)
+            atomicAdd(&sx32[ol[j]], cnt);                    // the owner's sum
+          }
+        }
+      }
+    }
+    __syncwarp();
+    if (i < nx) {
+      const unsigned long long sum = sx[lane] + sx32[lane];
+      if (sum) atomicAdd(&a.P[hb + i], sum);  // slot (h, x)
+    }
+    __syncwarp();
+  }
+}
+
 __global__ void __launch_bounds__(kHeavyBlock, 1) k_pass_c_heavy(DevGraph g, CountArgs a) {
   extern __shared__ uint32_t tab[];  // kHeavyTab counters
   __shared__ int32_t s_unit, s_nx, s_chunk[2];
@@ -455,8 +619,8 @@ __global__ void __launch_bounds__(kHeavyBlock, 1) k_pass_c_heavy(DevGraph g, Cou
       continue;
     }
     const int32_t nchunks = (nx + 31) >> 5;
-    const bool half = nx < 65536;
-    const int32_t span = half ? 2 * kHeavyTab : kHeavyTab;
+    const int cpw = hub_cpw(nx);
+    const int32_t span = cpw * kHeavyTab;
     const int64_t job_lo = (int64_t)job.y * span;                       // the job's o-range
     const int64_t job_hi = min((int64_t)h, job_lo + (int64_t)job.z * span);
     for (int32_t i = threadIdx.x; i < nx; i += kHeavyBlock) {
@@ -471,7 +635,7 @@ __global__ void __launch_bounds__(kHeavyBlock, 1) k_pass_c_heavy(DevGraph g, Cou
     for (int64_t lo64 = job_lo; lo64 < job_hi; lo64 += span) {
       const int32_t lo_id = (int32_t)lo64;
       const int32_t r1 = (int32_t)min(lo64 + span, job_hi);
-      const int32_t words = half ? (r1 - lo_id + 1) >> 1 : r1 - lo_id;
+      const int32_t words = (r1 - lo_id + cpw - 1) / cpw;
       for (int32_t i = threadIdx.x; i < words; i += kHeavyBlock) tab[i] = 0u;
       if (threadIdx.x == 0) {
         w_blocks += nx;
@@ -479,144 +643,15 @@ __global__ void __launch_bounds__(kHeavyBlock, 1) k_pass_c_heavy(DevGraph g, Cou
         s_chunk[1] = 0;
       }
       __syncthreads();
-      // counts of the block
-      for (;;) {
-        int32_t c = 0;
-        if (lane == 0) c = atomicAdd(&s_chunk[0], 1);
-        c = __shfl_sync(0xffffffffu, c, 0);
-        if (c >= nchunks) break;
-        const int32_t i = (nchunks - 1 - c) * 32 + lane;  // X ascends by degree: heaviest chunk first
-        int32_t st = 0, L = 0;
-        if (i < nx) {
-          st = cur[i];
-          const int32_t en = gallop_lower_bound(g.ci, st, endp[i], r1);
-          L = en - st;
-          beg[i] = st;
-          cur[i] = en;
-        }
-        // runs of 32 or more entries (most of the wedges): the whole warp,
-        // one run at a time, consecutive entries over the lanes
-        unsigned lm = __ballot_sync(0xffffffffu, L >= 32);
-        while (lm) {
-          const int src = __ffs(lm) - 1;
-          lm &= lm - 1;
-          const int32_t s0 = __shfl_sync(0xffffffffu, st, src);
-          const int32_t n0 = __shfl_sync(0xffffffffu, L, src);
-          for (int32_t k0 = 0; k0 < n0; k0 += 256) {  // eight windows of loads in flight
-            int32_t o[8];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-              const int32_t kk = k0 + 32 * j + lane;
-              o[j] = kk < n0 ? g.ci[s0 + kk] : -1;
-            }
-#pragma unroll
-            for (int j = 0; j < 8; ++j)
-              if (o[j] >= 0) add_count(tab, o[j] - lo_id, half);
-          }
-        }
-        // shorter runs dealt to the lanes end to end
-        const int32_t Ls = L < 32 ? L : 0;
-        const Deal d = deal_setup(Ls, comp, lane);
-        const int32_t sb = st - d.excl;  // slot of position kk of this lane's run: sb + kk
-        int before = 0;
-        for (int32_t k0 = 0; k0 < d.total; k0 += 128) {
-          int32_t q[4];
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const int ol = deal_owner(d, Ls, k0 + 32 * j, comp, lane, before);
-            const int32_t kk = k0 + 32 * j + lane;
-            const int32_t bj = __shfl_sync(0xffffffffu, sb, ol);
-            q[j] = kk < d.total ? bj + kk : -1;
-          }
-          int32_t o[4];
-#pragma unroll
-          for (int j = 0; j < 4; ++j) o[j] = q[j] >= 0 ? g.ci[q[j]] : lo_id;
-#pragma unroll
-          for (int j = 0; j < 4; ++j)
-            if (q[j] >= 0) add_count(tab, o[j] - lo_id, half);
-        }
-        __syncwarp();
-      }
-      __syncthreads();
-      // attribution of the block's wedges
-      for (;;) {
-        int32_t c = 0;
-        if (lane == 0) c = atomicAdd(&s_chunk[1], 1);
-        c = __shfl_sync(0xffffffffu, c, 0);
-        if (c >= nchunks) break;
-        const int32_t i = (nchunks - 1 - c) * 32 + lane;
-        int32_t st = 0, L = 0;
-        if (i < nx) {
-          st = beg[i];
-          L = cur[i] - st;
-        }
-        s_sx[warp][lane] = 0ull;  // per x of the chunk: sum of its wedges' counts
-        s_sx32[warp][lane] = 0u;
-        __syncwarp();
-        // runs of 32 or more entries: the whole warp, one run at a time
-        unsigned lm = __ballot_sync(0xffffffffu, L >= 32);
-        while (lm) {
-          const int src = __ffs(lm) - 1;
-          lm &= lm - 1;
-          const int32_t s0 = __shfl_sync(0xffffffffu, st, src);
-          const int32_t n0 = __shfl_sync(0xffffffffu, L, src);
-          unsigned long long acc = 0ull;
-          for (int32_t k0 = 0; k0 < n0; k0 += 256) {  // eight windows of loads in flight
-            int32_t o[8];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-              const int32_t kk = k0 + 32 * j + lane;
-              o[j] = kk < n0 ? g.ci[s0 + kk] : -1;
-            }
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-              if (o[j] < 0) continue;
-              const uint32_t cnt = read_count(tab, o[j] - lo_id, half) - 1u;
-              if (cnt) {
-                atomicAdd(&a.P[s0 + k0 + 32 * j + lane], (unsigned long long)cnt);  // slot (x, o)
-                acc += cnt;
-              }
-            }
-          }
-          for (int off = 16; off; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-          if (lane == src) s_sx[warp][lane] += acc;
-        }
-        __syncwarp();
-        // shorter runs dealt to the lanes end to end
-        const int32_t Ls = L < 32 ? L : 0;
-        const Deal d = deal_setup(Ls, comp, lane);
-        const int32_t sb = st - d.excl;  // slot of position kk of this lane's run: sb + kk
-        int before = 0;
-        for (int32_t k0 = 0; k0 < d.total; k0 += 128) {
-          int32_t q[4], ol[4];
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            ol[j] = deal_owner(d, Ls, k0 + 32 * j, comp, lane, before);
-            const int32_t kk = k0 + 32 * j + lane;
-            const int32_t bj = __shfl_sync(0xffffffffu, sb, ol[j]);
-            q[j] = kk < d.total ? bj + kk : -1;
-          }
-          int32_t o[4];
-#pragma unroll
-          for (int j = 0; j < 4; ++j) o[j] = q[j] >= 0 ? g.ci[q[j]] : lo_id;
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            if (q[j] >= 0) {
-              const uint32_t cnt = read_count(tab, o[j] - lo_id, half) - 1u;
-              if (cnt) {
-                atomicAdd(&a.P[q[j]], (unsigned long long)cnt);  // slot (x, o)
-                atomicAdd(&s_sx32[warp][ol[j]], cnt);           // the owner's sum
-              }
-            }
-          }
-        }
-        __syncwarp();
-        if (i < nx) {
-          const unsigned long long sx = s_sx[warp][lane] + s_sx32[warp][lane];
-          if (sx) atomicAdd(&a.P[hb + i], sx);  // slot (h, x)
-        }
-        __syncwarp();
-      }
+      if (cpw == 3)
+        hub_block<3>(g, a, tab, s_chunk, s_sx[warp], s_sx32[warp], comp, beg, cur, endp, nx, nchunks, hb, lo_id, r1,
+                     lane);
+      else if (cpw == 2)
+        hub_block<2>(g, a, tab, s_chunk, s_sx[warp], s_sx32[warp], comp, beg, cur, endp, nx, nchunks, hb, lo_id, r1,
+                     lane);
+      else
+        hub_block<1>(g, a, tab, s_chunk, s_sx[warp], s_sx32[warp], comp, beg, cur, endp, nx, nchunks, hb, lo_id, r1,
+                     lane);
       __syncthreads();
     }
   }

@@ -288,7 +288,11 @@ gc_status run_small_graphs(const int32_t* rp, const int64_t* voff, const int32_t
 int count_grid_size();
 gc_status run_pass_c(const DevGraph& g, const CountArgs& a, cudaStream_t s);
 gc_status run_pass_c_heavy(const DevGraph& g, const CountArgs& a, cudaStream_t s);
-constexpr int kHeavyTab = 53248;  // o-range block of the hub kernel of pass C (entries in shared memory)
+constexpr int kHeavyTab = 53248;  // o-range block of the hub kernel of pass C (words of shared memory)
+// Counters per word of the hub kernel for a unit of nx lower neighbours
+// (count fields of 32, 16 or 10 bits; no count exceeds nx): one block of
+// its o-range spans hub_cpw(nx) * kHeavyTab ids.
+__host__ __device__ __forceinline__ int hub_cpw(int64_t nx) { return nx < 1023 ? 3 : nx < 65536 ? 2 : 1; }
 // Units of pass C with at most kHashMaxW wedges count in a shared-memory
 // hash of 2 kHashMaxW keys (at most half full: a unit has no more distinct
 // o than wedges).

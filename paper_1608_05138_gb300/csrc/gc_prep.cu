@@ -424,10 +424,15 @@ gc_status classify_c_units(int32_t n, const int32_t* d_rp, const int32_t* d_ci, 
   // a CTA's worth of lower neighbours), against roughly 10 ns per wedge on an
   // SM for a wedge that goes through the vertex-indexed table in DRAM; the
   // hub kernel is taken when the wedges exceed blocks x max(1024, nx), about
-  // three times the break-even point.
+  // three times the break-even point. Units that fit the packed-key hash
+  // (below) stay there.
+  auto fits_hash2 = [&](int32_t k) {
+    return W[k] > kHashMaxW && W[k] <= kHash2MaxW && NX[k] < kHash2MaxNx && n <= kHash2MaxN;
+  };
   std::vector<int32_t> heavy;
   for (int32_t k = 0; k < nu; ++k) {
-    const long long span = NX[k] < 65536 ? 2LL * kHeavyTab : kHeavyTab;  // 16-bit counters below 65536
+    if (fits_hash2(k)) continue;
+    const long long span = (long long)hub_cpw(NX[k]) * kHeavyTab;
     const long long blocks = ((long long)U[k] + span - 1) / span;
     const long long per_block = NX[k] > 1024 ? NX[k] : 1024;
     if (W[k] >= 16384 && W[k] >= blocks * per_block && NX[k] < (1 << 26)) heavy.push_back(k);
@@ -456,8 +461,7 @@ gc_status classify_c_units(int32_t n, const int32_t* d_rp, const int32_t* d_ci, 
   // first. The rest stay on the vertex-indexed tables.
   std::vector<int32_t> hashed2;
   for (int32_t k = 0; k < nu; ++k)
-    if (!is_heavy[k] && W[k] > kHashMaxW && W[k] <= kHash2MaxW && NX[k] < kHash2MaxNx && n <= kHash2MaxN)
-      hashed2.push_back(k);
+    if (fits_hash2(k)) hashed2.push_back(k);
   std::sort(hashed2.begin(), hashed2.end(), [&](int32_t a, int32_t b) { return W[a] > W[b]; });
   std::vector<char> is_hashed2(nu, 0);
   for (int32_t k : hashed2) {
@@ -487,7 +491,7 @@ gc_status classify_c_units(int32_t n, const int32_t* d_rp, const int32_t* d_ci, 
     double total = 0;
     for (size_t i = 0; i < heavy.size(); ++i) {
       const int32_t k = heavy[i];
-      const long long span = NX[k] < 65536 ? 2LL * kHeavyTab : kHeavyTab;
+      const long long span = (long long)hub_cpw(NX[k]) * kHeavyTab;
       nblk[i] = ((long long)U[k] + span - 1) / span;
       cost[i] = (double)W[k] + kSweepCost * (double)NX[k] * (double)nblk[i];
       total += cost[i];

@@ -128,7 +128,7 @@ def test_serving_requests_of_a_million_edges_equal_oracle():
 
 K_TIERS = [(2, 32), (33, 256), (257, 512), (513, 1024), (1025, 1 << 30)]
 HASH_MAX_W = 8192          # pass-C units of at most this many wedges: shared-memory hash
-HUB_BLOCK = 53248          # o-range block of the hub kernel (two 16-bit counters per word below 65536)
+HUB_BLOCK = 53248          # words of an o-range block of the hub kernel (1, 2 or 3 counters a word)
 
 
 def unit_strata(rp, ci):
@@ -151,7 +151,7 @@ def unit_strata(rp, ci):
     up = Ys > Xs                                  # slot (x, h), h above x
     W = np.bincount(Ys[up], weights=pos[up], minlength=n).astype(np.int64)
     NX = np.bincount(Ys[up], minlength=n).astype(np.int64)   # lower neighbours of h
-    span = np.where(NX < 65536, 2 * HUB_BLOCK, HUB_BLOCK)
+    span = np.where(NX < 1023, 3 * HUB_BLOCK, np.where(NX < 65536, 2 * HUB_BLOCK, HUB_BLOCK))
     blocks = (np.arange(n) + span - 1) // span
     hub = (W >= 16384) & (W >= blocks * np.maximum(1024, NX))
     ckind = np.where(hub, 0, np.where(W == 0, 3, np.where(W <= HASH_MAX_W, 1, 2)))  # by rank

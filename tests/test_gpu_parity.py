@@ -190,19 +190,78 @@ def test_hashed_units_of_the_cycle_pass():
 
 
 def test_cycle_pass_unit_kinds_on_a_power_law_graph():
-    # hubs (shared-memory blocks), hashed units (at most 8192 wedges) and
-    # vertex-indexed tables take part; the wedge counters add up to the
-    # wedges counted on the host
+    # hubs (shared-memory blocks), hashed units (at most 8192 wedges), the
+    # packed-key hash and vertex-indexed tables take part; the wedge counters
+    # add up to the wedges counted on the host
     rp, ci = graphgen.chung_lu(60000, 400000, 2.1, 8e5, 3000.0, 11)
-    W, _ = wedges_by_highest_vertex(rp, ci)
     with gcb.Graph(rp, ci) as g:
         g.count(None)
         w = g.work_counts()
+    W, nb = wedges_by_highest_vertex(rp, ci)
     assert w["c_wedges"] == W.sum()
     assert 0 < w["c_heavy_wedges"] and w["c_hash_wedges"] == W[W <= 8192].sum()
     assert 0 < w["c_hash2_wedges"] <= W[(W > 8192) & (W <= 41287)].sum()
     assert w["c_heavy_wedges"] + w["c_hash_wedges"] + w["c_hash2_wedges"] <= w["c_wedges"]
     assert_parity(rp, ci)
+
+
+def _count_with_work(rp, ci):
+    with gcb.Graph(rp, ci) as g:
+        pe = np.zeros((g.m, 13), np.uint64)
+        X = g.count(pe)
+        w = g.work_counts()
+    o = oracle.count(rp, ci)
+    np.testing.assert_array_equal(pe, o["per_edge"])
+    assert X == o["X"]
+    return w
+
+
+def test_hub_counts_near_the_10_bit_field_limit():
+    # h joined to 900 vertices x and 50 pendant vertices; every x joined to the
+    # same 60 vertices o: 54000 wedges on 60 distinct o, each of count 900
+    # (a hub of fewer than 1023 lower neighbours keeps 10-bit counters); the o
+    # (degree 900) rank below h (degree 950) and are hubs of that kind too
+    n = 100_000
+    h, xs, os_, pend = 0, np.arange(1, 901), np.arange(901, 961), np.arange(961, 1011)
+    E = [(h, int(x)) for x in xs] + [(h, int(p)) for p in pend]
+    E += [(int(x), int(o)) for x in xs for o in os_]
+    rp, ci = graphs.csr_large(n, E)
+    W, nb = wedges_by_highest_vertex(rp, ci)
+    assert W[h] == 54000 and nb[h] == 950
+    w = _count_with_work(rp, ci)
+    assert w["c_heavy_wedges"] >= 54000 and w["c_wedges"] == W.sum()
+
+
+def test_hub_over_a_skewed_o_range():
+    # 3M vertices, almost all isolated (the lowest ranks): h has 620 lower
+    # neighbours, 600 of them with 150 o each, drawn with weights 1/(i + 100)
+    # from a pool of 50000, so the o crowd the top of [0, h): 19 blocks of
+    # the o-range, the wedges in the last one
+    rng = np.random.default_rng(17)
+    n = 3_000_000
+    h, xs = 0, np.arange(1, 601)
+    pool = np.arange(1000, 51000)
+    wt = 1.0 / (np.arange(len(pool)) + 100.0)
+    wt /= wt.sum()
+    E = [(h, int(x)) for x in xs] + [(h, int(p)) for p in range(601, 621)]
+    for x in xs:
+        for o in rng.choice(pool, 150, replace=False, p=wt):
+            E.append((int(x), int(o)))
+    rp, ci = graphs.csr_large(n, E)
+    W, nb = wedges_by_highest_vertex(rp, ci)
+    assert W[h] == 90000 and nb[h] == 620
+    w = _count_with_work(rp, ci)
+    assert w["c_heavy_wedges"] >= 90000 and w["c_wedges"] == W.sum()
+
+
+def test_hubs_of_few_lower_neighbours_rmat14():
+    # R-MAT scale 14: 91 hubs of more than 41287 wedges and fewer than 1023
+    # lower neighbours (10-bit counters), half of all wedges
+    rp, ci = graphgen.rmat(14, 16, 0.57, 0.19, 0.19, 1)
+    W, nb = wedges_by_highest_vertex(rp, ci)
+    few = (W > 41287) & (nb < 1023)
+    w = _count_with_work(rp, ci)
+    assert few.sum() == 91 and w["c_heavy_wedges"] >= W[few].sum()
 
 
 def _unit_of_18000_wedges(n):
