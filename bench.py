@@ -114,12 +114,18 @@ PHASE_OF = {"k_pass_t": "pass_t_triangles", "k_pass_c": "pass_c_cycles", "k_pass
             "k_finish": "finish_columns"}
 
 
+TRAFFIC_SCALE = 20  # R-MAT scale of the committed DRAM counters
+TRAFFIC_FILE = os.path.join("profiles", "roofline_traffic_rmat20.txt")
+
+
 def measured_traffic(phase: str, workload: str, scale: int):
-    """DRAM bytes per count of a phase from the committed ncu launch list
-    (profiles/roofline_traffic_rmat22.txt), or None when the workload differs
-    or the kernel sources changed since the counters were taken."""
-    path = os.path.join(ROOT, "profiles", "roofline_traffic_rmat22.txt")
-    if workload != "rmat22" or scale != 22 or not os.path.exists(path):
+    """DRAM bytes per count of a phase from the committed ncu counters
+    (profiles/roofline_traffic_rmat20.txt, R-MAT scale 20), or None when the
+    workload differs or the kernel sources changed since the counters were
+    taken. The bytes per wedge grow with the scale (1.36 at 19, 4.82 at 20
+    for the hub kernel), so they are not scaled to another size."""
+    path = os.path.join(ROOT, TRAFFIC_FILE)
+    if workload != "rmat22" or scale != TRAFFIC_SCALE or not os.path.exists(path):
         return None
     table, ok = {}, True
     for line in open(path):
@@ -265,8 +271,35 @@ def roofline(work: dict, phases: dict, peak: float, peak_src: str, traffic_of=No
             "basis_dram": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the phase per kernel second",
             "peak_source": peak_src, "kernel": dom, "phase": PHASE_OF[dom], "kernel_ms": kernel_ms[dom],
             "algorithmic_bytes": ab[dom], "traffic": traffic,
-            "traffic_source": "profiles/launches_rmat22_count.md (ncu dram__bytes_read+write per count)",
+            "traffic_source": TRAFFIC_FILE + " (ncu dram__bytes_read+write per count, R-MAT scale "
+                              + str(TRAFFIC_SCALE) + " only)",
             "kernels": kernels}
+
+
+def dram_small_case(stream, peak: float, peak_src: str) -> dict:
+    """The DRAM fraction where the counters were taken: pass C of R-MAT scale
+    20, timed here with CUDA events (phase events of the count), against the
+    committed ncu DRAM bytes of the same kernels."""
+    import torch
+    import paper_1608_05138_gb300 as gcb
+    rp, ci, desc = load_workload("rmat22", TRAFFIC_SCALE)
+    traffic = measured_traffic("pass_c_cycles", "rmat22", TRAFFIC_SCALE)
+    m = len(ci) // 2
+    with gcb.Graph(rp, ci, stream=stream) as g:
+        pe = torch.empty((m, 13), dtype=torch.int64, device="cuda")
+        for _ in range(3):
+            g.count(pe)
+        ms = []
+        for _ in range(5):
+            g.count(pe)
+            ms.append(g.phase_ms()["pass_c_cycles"])
+        work = g.work_counts()
+    pc = statistics.mean(ms)
+    ach = traffic / (pc / 1000.0) / 1e9 if traffic else None
+    return {"workload": desc, "m": m, "phase": "pass_c_cycles", "kernel_ms": pc, "traffic": traffic,
+            "traffic_per_wedge": traffic / work["c_wedges"] if traffic else None,
+            "achieved_dram": ach, "peak": peak, "frac_dram": ach / peak if ach else None, "peak_source": peak_src,
+            "source": TRAFFIC_FILE}
 
 
 def run_reference(args, rank, world):
@@ -694,6 +727,11 @@ def main():
     roof = roofline(work, ph_ms, peak, peak_src,
                     traffic_of=lambda ph: measured_traffic(ph, args.workload, args.scale))
     roof["logical_paper_method_gbs"] = paper_method_bytes(rp, ci) / (step_ms / 1000.0) / 1e9
+    if args.workload == "rmat22" and args.scale != TRAFFIC_SCALE and not args.no_extra:
+        roof["traffic_note"] = ("DRAM counters are taken at R-MAT scale 20 only (captures beyond the duration "
+                                "metric stay on a small case), and their bytes per wedge grow with the scale, so "
+                                "traffic is null here; dram_rmat20 gives the measured fraction at scale 20")
+        roof["dram_rmat20"] = dram_small_case(torch.cuda.current_stream(), peak, peak_src)
     line = {"metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int64", "data": "synthetic",
