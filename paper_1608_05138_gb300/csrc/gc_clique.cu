@@ -31,7 +31,13 @@
 //
 // Tiers by k: the bitmatrix (k * ((k+31)/32 | 1) words) stays in shared
 // memory for k <= 1024; above that the same code runs on a per-CTA global
-// buffer; units with k <= 32 run one per warp (k_pass_k_warp). Work per unit is about sum_{b in out(a)} |out(b)| (triangle
+// buffer; units with k <= 32 run one per warp (k_pass_k_warp). The 512-thread
+// CTAs run three to an SM (at most 40 registers a thread, a few bytes of
+// spill in two pass-K instances): the passes wait on loads, and the third
+// CTA hides more of that wait than the registers it costs (pass T 71.4 ->
+// 58.1 ms, pass K 46.3 -> 45.1 ms on R-MAT scale 22). Pass T's k <= 1024 tier
+// runs in 512-thread CTAs for the same reason; pass K's keeps 1024 threads,
+// since its bitmatrix leaves room for one CTA an SM. Work per unit is about sum_{b in out(a)} |out(b)| (triangle
 // listing) plus (#edges of H_a) * k / 32 words.
 #include <cuda_runtime.h>
 
@@ -94,7 +100,7 @@ struct KLayout {
 // triangle also adds the degree of its third vertex to each of its edges,
 // so that a.dsum[e] = sum_{w in T_e} d_w (for the per-edge induced counts).
 template <int kCap, int kThreads, bool kTri, bool kDeg = false>
-__global__ void __launch_bounds__(kThreads, 65536 / (kThreads * 64)) k_pass_k(DevGraph g, CountArgs a, int tier) {
+__global__ void __launch_bounds__(kThreads, kThreads == 512 ? 3 : 65536 / (kThreads * 64)) k_pass_k(DevGraph g, CountArgs a, int tier) {
   constexpr int kW = kThreads / 32;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int32_t s_unit, s_cur1, s_cur2, s_nhit;
@@ -736,7 +742,7 @@ gc_status run_tiers(const DevGraph& g, const CountArgs& a, cudaStream_t s, int* 
     }
     if ((st = launch_tier<0, 1024, kTri, kDeg>(g, a, kTierGlobal, s, launches)) != GC_OK) return st;
   }
-  if ((st = launch_tier<1024, 1024, kTri, kDeg>(g, a, kTier1024, s, launches)) != GC_OK) return st;
+  if ((st = launch_tier<1024, kTri ? 512 : 1024, kTri, kDeg>(g, a, kTier1024, s, launches)) != GC_OK) return st;
   if ((st = launch_tier<512, 512, kTri, kDeg>(g, a, kTier512, s, launches)) != GC_OK) return st;
   if ((st = launch_tier<256, 512, kTri, kDeg>(g, a, kTier256, s, launches)) != GC_OK) return st;
   const int32_t units = a.ktier_off[kTier32 + 1] - a.ktier_off[kTier32];
