@@ -334,7 +334,7 @@ __global__ void __launch_bounds__(kBlock) k_pass_c(DevGraph g, CountArgs a) {
 // otherwise hit a vertex-indexed table in DRAM at random. Ids are ranks, so
 // the lower-rank neighbours X of h are a prefix of Gamma(h) and, for x in X,
 // the o < h are a prefix of Gamma(x), ascending. The o-range [0, h) is swept
-// in blocks of kHeavyTab ids: cnt_h(o) for the block is built in shared
+// in blocks of a.hub_tab words: cnt_h(o) for the block is built in shared
 // memory from each x's run of o in the block (a per-x cursor walks Gamma(x)
 // once over all blocks; the end of the run is found by galloping search),
 // then the wedges of the block are attributed with the block's counts.
@@ -589,7 +589,7 @@ __device__ __forceinline__ void hub_block(const DevGraph& g, const CountArgs& a,
 }
 
 __global__ void __launch_bounds__(kHeavyBlock, 1) k_pass_c_heavy(DevGraph g, CountArgs a) {
-  extern __shared__ uint32_t tab[];  // kHeavyTab counters
+  extern __shared__ uint32_t tab[];  // a.hub_tab words of counters
   __shared__ int32_t s_unit, s_nx, s_chunk[2];
   const unsigned long long t_start = global_ns();
   __shared__ unsigned long long s_sx[kHeavyWarps][32];
@@ -628,7 +628,7 @@ __global__ void __launch_bounds__(kHeavyBlock, 1) k_pass_c_heavy(DevGraph g, Cou
     // them at 1024 too, the same in both readings); fewer: one per warp
     const int32_t nchunks = nx > kHeavyBlock ? (nx + 31) >> 5 : kHeavyWarps;
     const int cpw = hub_cpw(nx);
-    const int32_t span = cpw * kHeavyTab;
+    const int32_t span = cpw * a.hub_tab;
     const int64_t job_lo = (int64_t)job.y * span;                       // the job's o-range
     const int64_t job_hi = min((int64_t)h, job_lo + (int64_t)job.z * span);
     for (int32_t i = threadIdx.x; i < nx; i += kHeavyBlock) {
@@ -993,7 +993,7 @@ gc_status run_pass_c(const DevGraph& g, const CountArgs& a, cudaStream_t s) {
 
 gc_status run_pass_c_heavy(const DevGraph& g, const CountArgs& a, cudaStream_t s) {
   if (a.n_cheavy <= 0) return GC_OK;
-  const size_t smem = sizeof(uint32_t) * kHeavyTab;
+  const size_t smem = sizeof(uint32_t) * (size_t)a.hub_tab;
   cudaError_t e = cudaFuncSetAttribute(k_pass_c_heavy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return cuda_fail(e, "k_pass_c_heavy");
   int grid = count_grid_size() / kCtasPerSm;

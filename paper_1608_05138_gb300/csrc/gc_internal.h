@@ -59,6 +59,7 @@ struct CountArgs {
   int32_t n_cjobs;
   int32_t* cbuf;           // pass C hub kernel: per-CTA cursors (cbuf_ctas x 3 x cbuf_nx ints)
   int32_t cbuf_nx;
+  int32_t hub_tab;         // pass C hub kernel: words of the count block (hub_tab_words())
   const int32_t* kunits;   // pass K: lowest vertices a with |out(a)| >= 2, tiers in KTier order
   int32_t ktier_off[kNumTiers + 1];  // tier t = kunits[ktier_off[t] .. ktier_off[t + 1])
   int32_t* cursor;         // work-stealing cursors (device ints, zeroed before each launch)
@@ -288,10 +289,20 @@ gc_status run_small_graphs(const int32_t* rp, const int64_t* voff, const int32_t
 int count_grid_size();
 gc_status run_pass_c(const DevGraph& g, const CountArgs& a, cudaStream_t s);
 gc_status run_pass_c_heavy(const DevGraph& g, const CountArgs& a, cudaStream_t s);
-constexpr int kHeavyTab = 53248;  // o-range block of the hub kernel of pass C (words of shared memory)
+constexpr int kHeavyTab = 53248;  // largest o-range block of the hub kernel of pass C (words of shared memory)
+// Words of the hub kernel's count block (environment GC_HUB_TAB_WORDS, a
+// multiple of 1024 in [4096, kHeavyTab], else kHubTabDefault), read once per
+// process. The block and the SM's L1 cache share one array, split in steps
+// (the shared-memory carveout); kHubTabDefault is the largest block whose CTA
+// (block + 16.4 KB of static arrays + 1 KB reserved) fits the 196 KB step,
+// leaving about 60 KB of L1 for the rows and cursors instead of 28 KB with a
+// 208 KB block (R-MAT scale 22: pass C 228.4 ms at 53248 words, 205.0 at
+// 45056, 213.3 at 39936, 226.7 at 32768).
+constexpr int kHubTabDefault = 45056;
+int hub_tab_words();
 // Counters per word of the hub kernel for a unit of nx lower neighbours
 // (count fields of 32, 16 or 10 bits; no count exceeds nx): one block of
-// its o-range spans hub_cpw(nx) * kHeavyTab ids.
+// its o-range spans hub_cpw(nx) * hub_tab_words() ids.
 __host__ __device__ __forceinline__ int hub_cpw(int64_t nx) { return nx < 1023 ? 3 : nx < 65536 ? 2 : 1; }
 // Units of pass C with at most kHashMaxW wedges count in a shared-memory
 // hash of 2 kHashMaxW keys (at most half full: a unit has no more distinct

@@ -378,6 +378,15 @@ gc_status exclusive_scan(int32_t n, const int32_t* in, int32_t* out, cudaStream_
 // cursor with a galloping search (milliseconds for the largest hubs), and
 // heaviest-first stealing already balances hubs below that size (on R-MAT
 // scale 22 the CTAs' lifetimes differ by 0.1 %).
+int hub_tab_words() {
+  static int v = [] {
+    const char* e = getenv("GC_HUB_TAB_WORDS");
+    const int x = e ? atoi(e) : kHubTabDefault;
+    return (x >= 4096 && x <= kHeavyTab && x % 1024 == 0) ? x : kHubTabDefault;
+  }();
+  return v;
+}
+
 static int hub_jobs_per_cta() {
   static int v = [] {
     const char* e = getenv("GC_HUB_JOBS_PER_CTA");
@@ -432,7 +441,7 @@ gc_status classify_c_units(int32_t n, const int32_t* d_rp, const int32_t* d_ci, 
   std::vector<int32_t> heavy;
   for (int32_t k = 0; k < nu; ++k) {
     if (fits_hash2(k)) continue;
-    const long long span = (long long)hub_cpw(NX[k]) * kHeavyTab;
+    const long long span = (long long)hub_cpw(NX[k]) * hub_tab_words();
     const long long blocks = ((long long)U[k] + span - 1) / span;
     const long long per_block = NX[k] > 1024 ? NX[k] : 1024;
     if (W[k] >= 16384 && W[k] >= blocks * per_block && NX[k] < (1 << 26)) heavy.push_back(k);
@@ -491,7 +500,7 @@ gc_status classify_c_units(int32_t n, const int32_t* d_rp, const int32_t* d_ci, 
     double total = 0;
     for (size_t i = 0; i < heavy.size(); ++i) {
       const int32_t k = heavy[i];
-      const long long span = (long long)hub_cpw(NX[k]) * kHeavyTab;
+      const long long span = (long long)hub_cpw(NX[k]) * hub_tab_words();
       nblk[i] = ((long long)U[k] + span - 1) / span;
       cost[i] = (double)W[k] + kSweepCost * (double)NX[k] * (double)nblk[i];
       total += cost[i];

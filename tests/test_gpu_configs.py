@@ -128,7 +128,7 @@ def test_serving_requests_of_a_million_edges_equal_oracle():
 
 K_TIERS = [(2, 32), (33, 256), (257, 512), (513, 1024), (1025, 1 << 30)]
 HASH_MAX_W = 8192          # pass-C units of at most this many wedges: shared-memory hash
-HUB_BLOCK = 53248          # words of an o-range block of the hub kernel (1, 2 or 3 counters a word)
+HUB_BLOCK = 45056          # words of an o-range block of the hub kernel (1, 2 or 3 counters a word)
 
 
 def unit_strata(rp, ci):

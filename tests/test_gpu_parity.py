@@ -138,7 +138,7 @@ def test_global_psi_tables():
 
 
 def test_hub_units_of_the_cycle_pass():
-    # n > 2 x 53248 and ~100 hub vertices whose wedges are counted in
+    # n > 2 x 45056 and ~100 hub vertices whose wedges are counted in
     # shared-memory blocks of the vertex range (several blocks each)
     assert_parity(*graphgen.chung_lu(120000, 600000, 2.1, 1.2e6, 4000.0, 7))
 
