@@ -194,8 +194,19 @@ gc_status gc_graph_phase_ms(gc_graph g, double* ms);
 #define GC_NUM_WORK 18
 gc_status gc_graph_work_counts(gc_graph g, uint64_t* out);
 
-/* Release the graph and all its device memory. NULL is accepted. */
+/* Release the graph and all its device memory. NULL is accepted. The device
+ * buffers go back to the library's memory pool (freed in the graph's stream
+ * order), where later graphs, counts and batches reuse them; the pool keeps up
+ * to GC_POOL_KEEP_BYTES bytes (environment, read when the pool is created on
+ * first use; default a quarter of the device's memory) and returns the rest
+ * to the device. */
 gc_status gc_graph_free(gc_graph g);
+
+/* Return every unused block of the library's memory pool on the current
+ * device to the device (like a caching allocator's empty-cache call). Waits
+ * for all work on the device first (cudaDeviceSynchronize). Live graphs and
+ * batches keep their memory. Errors: GC_ERR_CUDA (no device). */
+gc_status gc_release_cached_memory(void);
 
 /*
  * Batched and served counting of many graphs (global counts only).

@@ -44,7 +44,7 @@ EXPORTED = ["gc_last_error", "gc_graph_upload", "gc_graph_info", "gc_graph_edges
             "gc_graph_phase_ms", "gc_graph_free", "gc_batch_create", "gc_batch_submit",
             "gc_batch_flush", "gc_batch_poll", "gc_batch_destroy", "gc_edge_triangles_noalloc",
             "gc_graph_work_counts", "gc_batch_submit_many", "gc_count_edge_induced", "gc_batch_set_param",
-            "gc_batch_get_param", "gc_batch_last_stats", "gc_batch_poll_many"]
+            "gc_batch_get_param", "gc_batch_last_stats", "gc_batch_poll_many", "gc_release_cached_memory"]
 WORK_NAMES = ["t_members", "c_wedges", "k_members", "k_scan", "k_local_edges", "k_words", "finish_edges", "launches",
               "c_heavy_wedges", "c_heavy_sweeps", "t_scan", "t_triangles", "c_hash_wedges", "c_hub_jobs",
               "c_hub_ctas", "c_hub_busy_sum_ns", "c_hub_busy_max_ns", "c_hash2_wedges"]
@@ -92,12 +92,14 @@ def lib():
             L.gc_batch_get_param.argtypes = [vp, i32, C.POINTER(i32)]
             L.gc_batch_last_stats.argtypes = [vp, vp]
             L.gc_batch_poll_many.argtypes = [vp, i64, vp, vp, vp, i32]
+            L.gc_release_cached_memory.argtypes = []
             for name in ("gc_graph_upload", "gc_graph_info", "gc_graph_edges", "gc_count_edge_graphlets",
                          "gc_count_edge_induced",
                          "gc_graph_csums", "gc_graph_phase_ms", "gc_graph_free", "gc_batch_create",
                          "gc_batch_submit", "gc_batch_flush", "gc_batch_poll", "gc_batch_destroy",
                          "gc_edge_triangles_noalloc", "gc_graph_work_counts", "gc_batch_submit_many",
-                         "gc_batch_set_param", "gc_batch_get_param", "gc_batch_last_stats", "gc_batch_poll_many"):
+                         "gc_batch_set_param", "gc_batch_get_param", "gc_batch_last_stats", "gc_batch_poll_many",
+                         "gc_release_cached_memory"):
                 getattr(L, name).restype = C.c_int
             _lib = L
     return _lib
@@ -366,6 +368,12 @@ def gc_batch_last_stats(b) -> dict:
     out = np.zeros(len(BATCH_STATS), np.float64)
     _check(lib().gc_batch_last_stats(b, _ptr(out)), "gc_batch_last_stats")
     return dict(zip(BATCH_STATS, out.tolist()))
+
+
+def gc_release_cached_memory():
+    """Return the unused blocks of the library's device memory pool to the
+    device (waits for all device work first)."""
+    _check(lib().gc_release_cached_memory(), "gc_release_cached_memory")
 
 
 def gc_batch_destroy(b):

@@ -8,9 +8,11 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <functional>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <thread>
 #include <vector>
@@ -27,6 +29,39 @@ gc_status cuda_fail(cudaError_t e, const char* what) {
   set_error(std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")");
   if (e == cudaErrorMemoryAllocation) return GC_ERR_NOMEM;
   return GC_ERR_CUDA;
+}
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_pool_mu;
+cudaMemPool_t g_pools[kMaxDevices] = {};
+}  // namespace
+
+cudaMemPool_t lib_pool() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  if (g_pools[dev]) return g_pools[dev];
+  cudaMemPoolProps props;
+  std::memset(&props, 0, sizeof(props));
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = dev;
+  cudaMemPool_t pool = nullptr;
+  if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) cudaGetLastError();
+  unsigned long long keep = (unsigned long long)total_b / 4;
+  if (const char* e = getenv("GC_POOL_KEEP_BYTES")) keep = strtoull(e, nullptr, 10);
+  if (cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess) cudaGetLastError();
+  g_pools[dev] = pool;
+  return pool;
 }
 
 namespace {
@@ -218,32 +253,82 @@ struct RelabelPlan {
 
 RelabelPlan plan_relabel(int32_t n, const int32_t* rp) {
   RelabelPlan R;
-  int32_t dmax = 0;
-  for (int32_t x = 0; x < n; ++x) dmax = std::max(dmax, rp[x + 1] - rp[x]);
-  std::vector<int32_t> cnt((size_t)dmax + 2, 0);
-  for (int32_t x = 0; x < n; ++x) cnt[rp[x + 1] - rp[x] + 1]++;
-  for (int32_t d = 0; d <= dmax; ++d) cnt[d + 1] += cnt[d];
   R.perm.resize((size_t)n);
   R.newid.resize((size_t)n);
-  for (int32_t x = 0; x < n; ++x) {
-    const int32_t i = cnt[rp[x + 1] - rp[x]]++;
-    R.perm[i] = x;
-    R.newid[x] = i;
-  }
   R.rp.resize((size_t)n + 1);
   R.rp[0] = 0;
-  for (int32_t i = 0; i < n; ++i) {
-    const int32_t d = rp[R.perm[i] + 1] - rp[R.perm[i]];
-    R.rp[i + 1] = R.rp[i] + d;
-    if (d > 4096) {
-      int64_t P = 4096;
-      while (P < d) P <<= 1;
-      R.longr.push_back(i);
-      R.long_off.push_back(R.tmp_len);
-      R.tmp_len += P;
-    } else if (d > 32) {
-      R.mid.push_back(i);
+  if (n == 0) return R;
+  // vertex chunks, one per thread (fewer threads when the per-thread degree
+  // histograms would pass 2^24 counters)
+  int nt = n >= (1 << 16) ? host_threads() : 1;
+  std::vector<int32_t> dmx((size_t)nt, 0);
+  auto chunk = [&](int t, int T) { return (int32_t)((int64_t)n * t / T); };
+  run_threads(nt, [&](int t) {
+    int32_t d = 0;
+    for (int32_t x = chunk(t, nt); x < chunk(t + 1, nt); ++x) d = std::max(d, rp[x + 1] - rp[x]);
+    dmx[(size_t)t] = d;
+  });
+  const int32_t dmax = *std::max_element(dmx.begin(), dmx.end());
+  const size_t D = (size_t)dmax + 1;
+  const int nt0 = nt;
+  while (nt > 1 && (size_t)nt * D > ((size_t)1 << 24)) nt >>= 1;
+  if (nt != nt0) dmx.assign((size_t)nt, 0);
+  // cnt[t][d]: vertices of degree d in chunk t, then the first rank each
+  // chunk gives its degree-d vertices: ranks ascend by degree, then by chunk,
+  // then by id within the chunk -- the (degree, id) order
+  std::vector<int32_t> cnt((size_t)nt * D, 0);
+  run_threads(nt, [&](int t) {
+    int32_t* c = cnt.data() + (size_t)t * D;
+    for (int32_t x = chunk(t, nt); x < chunk(t + 1, nt); ++x) c[rp[x + 1] - rp[x]]++;
+  });
+  std::vector<int32_t> base(D + 1);  // first rank of degree d
+  std::vector<int64_t> S(D + 1);     // first internal slot of degree d
+  {
+    int32_t r = 0;
+    int64_t sl = 0;
+    for (size_t d = 0; d < D; ++d) {
+      base[d] = r;
+      S[d] = sl;
+      int32_t tot = 0;
+      for (int t = 0; t < nt; ++t) {
+        int32_t& c = cnt[(size_t)t * D + d];
+        const int32_t k = c;
+        c = r + tot;  // chunk t's first rank of degree d
+        tot += k;
+      }
+      r += tot;
+      sl += (int64_t)tot * (int64_t)d;
     }
+    base[D] = r;
+    S[D] = sl;
+  }
+  run_threads(nt, [&](int t) {
+    int32_t* c = cnt.data() + (size_t)t * D;
+    for (int32_t x = chunk(t, nt); x < chunk(t + 1, nt); ++x) {
+      const int32_t i = c[rp[x + 1] - rp[x]]++;
+      R.perm[(size_t)i] = x;
+      R.newid[(size_t)x] = i;
+    }
+  });
+  // internal row pointers: every row of a degree bucket has that degree
+  run_threads(nt, [&](int t) {
+    for (int32_t i = chunk(t, nt); i < chunk(t + 1, nt); ++i) {
+      const int32_t x = R.perm[(size_t)i];
+      const int32_t d = rp[x + 1] - rp[x];
+      R.rp[(size_t)i + 1] = (int32_t)(S[(size_t)d] + (int64_t)(i + 1 - base[(size_t)d]) * d);
+    }
+  });
+  // rows of 33..4096 entries and longer ones: the last ranks, in two runs
+  const int32_t m0 = base[std::min<size_t>(33, D)], l0 = base[std::min<size_t>(4097, D)];
+  R.mid.resize((size_t)(l0 - m0));
+  for (int32_t i = m0; i < l0; ++i) R.mid[(size_t)(i - m0)] = i;
+  for (int32_t i = l0; i < n; ++i) {
+    const int32_t d = R.rp[(size_t)i + 1] - R.rp[(size_t)i];
+    int64_t P = 4096;
+    while (P < d) P <<= 1;
+    R.longr.push_back(i);
+    R.long_off.push_back(R.tmp_len);
+    R.tmp_len += P;
   }
   return R;
 }
@@ -281,17 +366,15 @@ const char* gc_last_error(void) { return t_err.c_str(); }
 
 static void graph_release(gc_graph g) {
   if (!g) return;
-  if (g->stream) cudaStreamSynchronize(g->stream);
-  cudaFree(g->d_rp);
-  cudaFree(g->d_ci);
-  free_prep(&g->prep, g->stream);
-  cudaStreamSynchronize(g->stream);
-  cudaFree(g->d_gbase);
-  scratch_free(&g->sc, g->stream);
-  cudaStreamSynchronize(g->stream);
-  cudaFree(g->d_csum);
-  cudaFree(g->d_pe_tmp);
-  cudaFree(g->d_ind_tmp);
+  // stream-ordered frees into the library pool (after the graph's queued
+  // work), then one synchronisation
+  const cudaStream_t s = g->stream;
+  for (void* p : {(void*)g->d_rp, (void*)g->d_ci, (void*)g->d_gbase, (void*)g->d_csum, (void*)g->d_pe_tmp,
+                  (void*)g->d_ind_tmp})
+    if (p) cudaFreeAsync(p, s);
+  free_prep(&g->prep, s);
+  scratch_free(&g->sc, s);
+  cudaStreamSynchronize(s);
   for (auto& e : g->ev)
     if (e) cudaEventDestroy(e);
   delete g;
@@ -369,17 +452,17 @@ gc_status gc_graph_upload(int32_t n, const int32_t* row_ptr, const int32_t* col_
   }
   const size_t nnz1 = (size_t)(nnz > 0 ? nnz : 1), n1 = (size_t)(n > 0 ? n : 1);
   const size_t n_lists = R.mid.size() + R.longr.size();
-  GC_CHECK(cudaMalloc(&g->d_rp, sizeof(int32_t) * ((size_t)n + 1)), "alloc row_ptr");
-  GC_CHECK(cudaMalloc(&g->d_ci, sizeof(int32_t) * nnz1), "alloc col_idx");
-  GC_CHECK(cudaMallocAsync(&d_eid, sizeof(int32_t) * nnz1, s), "alloc eid");
-  GC_CHECK(cudaMallocAsync(&d_perm, sizeof(int32_t) * n1, s), "alloc perm");
-  GC_CHECK(cudaMallocAsync(&d_newid, sizeof(int32_t) * n1, s), "alloc newid");
-  GC_CHECK(cudaMallocAsync(&d_rp0, sizeof(int32_t) * ((size_t)n + 1), s), "alloc caller row_ptr");
-  GC_CHECK(cudaMallocAsync(&d_ci0, sizeof(int32_t) * nnz1, s), "alloc caller col_idx");
-  GC_CHECK(cudaMallocAsync(&d_lists, sizeof(int32_t) * (n_lists > 0 ? n_lists : 1), s), "alloc row lists");
-  GC_CHECK(cudaMallocAsync(&d_loff, sizeof(int64_t) * (R.long_off.size() > 0 ? R.long_off.size() : 1), s),
+  GC_CHECK(pool_alloc(&g->d_rp, sizeof(int32_t) * ((size_t)n + 1), s), "alloc row_ptr");
+  GC_CHECK(pool_alloc(&g->d_ci, sizeof(int32_t) * nnz1, s), "alloc col_idx");
+  GC_CHECK(pool_alloc(&d_eid, sizeof(int32_t) * nnz1, s), "alloc eid");
+  GC_CHECK(pool_alloc(&d_perm, sizeof(int32_t) * n1, s), "alloc perm");
+  GC_CHECK(pool_alloc(&d_newid, sizeof(int32_t) * n1, s), "alloc newid");
+  GC_CHECK(pool_alloc(&d_rp0, sizeof(int32_t) * ((size_t)n + 1), s), "alloc caller row_ptr");
+  GC_CHECK(pool_alloc(&d_ci0, sizeof(int32_t) * nnz1, s), "alloc caller col_idx");
+  GC_CHECK(pool_alloc(&d_lists, sizeof(int32_t) * (n_lists > 0 ? n_lists : 1), s), "alloc row lists");
+  GC_CHECK(pool_alloc(&d_loff, sizeof(int64_t) * (R.long_off.size() > 0 ? R.long_off.size() : 1), s),
            "alloc row lists");
-  GC_CHECK(cudaMallocAsync(&d_tmp, sizeof(int32_t) * (size_t)(R.tmp_len > 0 ? R.tmp_len : 1), s), "alloc sort buffer");
+  GC_CHECK(pool_alloc(&d_tmp, sizeof(int32_t) * (size_t)(R.tmp_len > 0 ? R.tmp_len : 1), s), "alloc sort buffer");
   GC_CHECK(cudaMemcpyAsync(d_rp0, row_ptr, sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyHostToDevice, s),
            "copy row_ptr");
   if (nnz > 0)
@@ -423,7 +506,7 @@ gc_status gc_graph_upload(int32_t n, const int32_t* row_ptr, const int32_t* col_
   }
   cudaStreamSynchronize(s);  // the host arrays of the plan are released on return
   // single-graph descriptor block: gbase | gn | gm (gm 8-byte aligned)
-  GC_CHECK(cudaMalloc(&g->d_gbase, 32), "alloc descriptors");
+  GC_CHECK(pool_alloc(&g->d_gbase, 32, s), "alloc descriptors");
   {
     int32_t hb[4] = {0, n, 0, 0};
     int64_t hm = g->m;
@@ -433,7 +516,7 @@ gc_status gc_graph_upload(int32_t n, const int32_t* row_ptr, const int32_t* col_
     g->d_gn = g->d_gbase + 1;
     g->d_gm = reinterpret_cast<int64_t*>(reinterpret_cast<char*>(g->d_gbase) + 16);
   }
-  GC_CHECK(cudaMalloc(&g->d_csum, sizeof(unsigned long long) * (13 * 2 + 17 * 2)), "alloc sums");
+  GC_CHECK(pool_alloc(&g->d_csum, sizeof(unsigned long long) * (13 * 2 + 17 * 2), s), "alloc sums");
   g->d_x = g->d_csum + 13 * 2;
   {
     gc_status st2 = scratch_init(&g->sc, g->m, n, g->prep.kmax, g->prep.cnx_max, s);
@@ -501,7 +584,7 @@ static gc_status count_graph(gc_graph g, uint64_t* per_edge_out, uint64_t* induc
     if ((pe_dev = device_view(per_edge_out, &pe_host)) == nullptr) {
       staged = true;
       if (!g->d_pe_tmp)
-        GC_CHECK(cudaMalloc(&g->d_pe_tmp, sizeof(uint64_t) * 13 * (size_t)g->m), "alloc per-edge staging");
+        GC_CHECK(pool_alloc(&g->d_pe_tmp, sizeof(uint64_t) * 13 * (size_t)g->m, g->stream), "alloc per-edge staging");
       pe_dev = g->d_pe_tmp;
     }
   }
@@ -512,7 +595,7 @@ static gc_status count_graph(gc_graph g, uint64_t* per_edge_out, uint64_t* induc
     if ((ind_dev = device_view(induced_out, &ind_host)) == nullptr) {
       ind_staged = true;
       if (!g->d_ind_tmp)
-        GC_CHECK(cudaMalloc(&g->d_ind_tmp, sizeof(uint64_t) * GC_INDUCED_COLS * (size_t)g->m),
+        GC_CHECK(pool_alloc(&g->d_ind_tmp, sizeof(uint64_t) * GC_INDUCED_COLS * (size_t)g->m, g->stream),
                  "alloc induced staging");
       ind_dev = g->d_ind_tmp;
     }
@@ -647,6 +730,17 @@ gc_status gc_graph_phase_ms(gc_graph g, double* ms) {
 gc_status gc_graph_free(gc_graph g) {
   graph_release(g);
   return GC_OK;
+}
+
+gc_status gc_release_cached_memory(void) {
+  cudaMemPool_t pool = lib_pool();
+  if (!pool) {
+    set_error("gc_release_cached_memory: no CUDA device or pool");
+    return GC_ERR_CUDA;
+  }
+  cudaError_t e = cudaDeviceSynchronize();  // every stream-ordered free has reached the pool
+  if (e == cudaSuccess) e = cudaMemPoolTrimTo(pool, 0);
+  return e == cudaSuccess ? GC_OK : cuda_fail(e, "gc_release_cached_memory");
 }
 
 }  // extern "C"

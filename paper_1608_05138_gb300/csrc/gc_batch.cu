@@ -209,13 +209,13 @@ gc_status run_union(std::vector<PendingGraph*>& graphs, cudaStream_t s, Launch* 
       goto out;             \
     }                       \
   } while (0)
-  GB_TRY(cudaMallocAsync(&d_rp, sizeof(int32_t) * ((size_t)n + 1), s), "batch alloc");
-  GB_TRY(cudaMallocAsync(&d_ci, sizeof(int32_t) * h_ci.size(), s), "batch alloc");
-  GB_TRY(cudaMallocAsync(&d_vgid, sizeof(int32_t) * h_vgid.size(), s), "batch alloc");
-  GB_TRY(cudaMallocAsync(&d_desc, sizeof(int32_t) * h_desc.size(), s), "batch alloc");
-  GB_TRY(cudaMallocAsync(&d_gm, sizeof(int64_t) * G, s), "batch alloc");
-  GB_TRY(cudaMallocAsync(&d_csum, sizeof(unsigned long long) * (size_t)G * 26, s), "batch alloc");
-  GB_TRY(cudaMallocAsync(&d_x, sizeof(unsigned long long) * (size_t)G * 34, s), "batch alloc");
+  GB_TRY(pool_alloc(&d_rp, sizeof(int32_t) * ((size_t)n + 1), s), "batch alloc");
+  GB_TRY(pool_alloc(&d_ci, sizeof(int32_t) * h_ci.size(), s), "batch alloc");
+  GB_TRY(pool_alloc(&d_vgid, sizeof(int32_t) * h_vgid.size(), s), "batch alloc");
+  GB_TRY(pool_alloc(&d_desc, sizeof(int32_t) * h_desc.size(), s), "batch alloc");
+  GB_TRY(pool_alloc(&d_gm, sizeof(int64_t) * G, s), "batch alloc");
+  GB_TRY(pool_alloc(&d_csum, sizeof(unsigned long long) * (size_t)G * 26, s), "batch alloc");
+  GB_TRY(pool_alloc(&d_x, sizeof(unsigned long long) * (size_t)G * 34, s), "batch alloc");
   GB_TRY(cudaMemcpyAsync(d_rp, h_rp.data(), sizeof(int32_t) * h_rp.size(), cudaMemcpyHostToDevice, s), "batch copy");
   GB_TRY(cudaMemcpyAsync(d_ci, h_ci.data(), sizeof(int32_t) * h_ci.size(), cudaMemcpyHostToDevice, s), "batch copy");
   GB_TRY(cudaMemcpyAsync(d_vgid, h_vgid.data(), sizeof(int32_t) * h_vgid.size(), cudaMemcpyHostToDevice, s), "batch copy");

@@ -195,6 +195,21 @@ gc_status run_count(const DevGraph& g, const int32_t* units, int32_t n_units, co
 void set_error(const std::string& msg);
 gc_status cuda_fail(cudaError_t e, const char* what);
 
+// The library's stream-ordered memory pool on the current device (created on
+// first use). Freed blocks stay in it, up to a limit (environment
+// GC_POOL_KEEP_BYTES; default a quarter of the device's memory), so that a
+// later graph or count reuses them without mapping memory again and a free
+// does not unmap at the next synchronisation; gc_release_cached_memory hands
+// them back. Every device buffer of the library comes from it (pool_alloc),
+// and is returned with cudaFreeAsync.
+cudaMemPool_t lib_pool();
+template <class T>
+inline cudaError_t pool_alloc(T** p, size_t bytes, cudaStream_t s) {
+  cudaMemPool_t pool = lib_pool();
+  if (!pool) return cudaErrorMemoryAllocation;
+  return cudaMallocFromPoolAsync(reinterpret_cast<void**>(p), bytes, pool, s);
+}
+
 // ---- relabelling P1 on the device (gc_relabel.cu) ----
 // Internal row i = caller row perm[i] in internal ids (newid), sorted; eid:
 // caller's edge id of every internal slot. rp: internal row pointers (device);

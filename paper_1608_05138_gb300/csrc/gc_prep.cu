@@ -211,8 +211,14 @@ __global__ void k_kbin_scatter(int32_t n, const int32_t* __restrict__ out_cnt, i
 
 // Wedges of every pass-C unit h of a ranked graph: W_h = sum over the
 // lower-rank neighbours x of h of |{o in Gamma(x) : o < h}| (warp per unit).
+// Wedges W and lower neighbours NX of every pass-C unit h of a ranked graph.
+// Ids are ranks and rows ascend, so the o < h of Gamma(x) are the entries
+// before the slot of (x, h), the reverse of the slot of (h, x): no search per
+// lower neighbour (the reverse is clamped into the row, as the hub kernel does,
+// so that W is what the kernels count even before symmetry is checked).
 __global__ void k_cwork(int32_t n_units, const int32_t* __restrict__ units, const int32_t* __restrict__ rp,
-                        const int32_t* __restrict__ ci, long long* __restrict__ W, int32_t* __restrict__ NX) {
+                        const int32_t* __restrict__ ci, const int32_t* __restrict__ rev, long long* __restrict__ W,
+                        int32_t* __restrict__ NX) {
   const int lane = threadIdx.x & 31;
   const int warps = (gridDim.x * blockDim.x) >> 5;
   for (int32_t k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < n_units; k += warps) {
@@ -222,7 +228,8 @@ __global__ void k_cwork(int32_t n_units, const int32_t* __restrict__ units, cons
     long long w = 0;
     for (int32_t i = lane; i < nx; i += 32) {
       const int32_t x = ci[hb + i];
-      w += lower_bound_i32(ci, rp[x], rp[x + 1], h) - rp[x];
+      const int32_t xb = rp[x];
+      w += min(max(rev[hb + i], xb), rp[x + 1]) - xb;
     }
     for (int o = 16; o; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
     if (lane == 0) {
@@ -361,7 +368,7 @@ gc_status exclusive_scan(int32_t n, const int32_t* in, int32_t* out, cudaStream_
   }
   int32_t nb = (n + kScanTile - 1) / kScanTile;
   int32_t* sums = nullptr;
-  cudaError_t e = cudaMallocAsync(&sums, sizeof(int32_t) * nb, s);
+  cudaError_t e = pool_alloc(&sums, sizeof(int32_t) * nb, s);
   if (e != cudaSuccess) return cuda_fail(e, "scan alloc");
   k_scan_tile_sums<<<nb, 256, 0, s>>>(n, in, sums);
   k_scan_sums<<<1, 1024, 0, s>>>(nb, sums);
@@ -396,10 +403,26 @@ static int hub_jobs_per_cta() {
   return v;
 }
 
+// The units of v (wedge counts W[v[i]] in [1, wmax]) in descending W, equal W
+// in their order in v: a counting sort.
+static void sort_by_wedges_desc(std::vector<int32_t>* v, const std::vector<long long>& W, long long wmax) {
+  std::vector<int32_t> cnt((size_t)wmax + 2, 0);
+  for (int32_t k : *v) cnt[(size_t)(wmax - W[k])]++;
+  int32_t r = 0;
+  for (auto& c : cnt) {
+    const int32_t x = c;
+    c = r;
+    r += x;
+  }
+  std::vector<int32_t> out(v->size());
+  for (int32_t k : *v) out[(size_t)cnt[(size_t)(wmax - W[k])]++] = k;
+  v->swap(out);
+}
+
 gc_status classify_c_units(int32_t n, const int32_t* d_rp, const int32_t* d_ci, bool ranked, PrepBuffers* p,
                            cudaStream_t s) {
   const int32_t nu = p->n_units;
-  cudaError_t e = cudaMallocAsync(&p->cunits, sizeof(int32_t) * (nu > 0 ? nu : 1), s);
+  cudaError_t e = pool_alloc(&p->cunits, sizeof(int32_t) * (nu > 0 ? nu : 1), s);
   if (e != cudaSuccess) return cuda_fail(e, "alloc cunits");
   p->n_cheavy = 0;
   p->n_chash = 0;
@@ -415,10 +438,10 @@ gc_status classify_c_units(int32_t n, const int32_t* d_rp, const int32_t* d_ci, 
   std::vector<long long> W(nu);
   std::vector<int32_t> NX(nu), U(nu), out;
   out.reserve(nu);
-  e = cudaMallocAsync(&dW, sizeof(long long) * nu, s);
-  if (e == cudaSuccess) e = cudaMallocAsync(&dNX, sizeof(int32_t) * nu, s);
+  e = pool_alloc(&dW, sizeof(long long) * nu, s);
+  if (e == cudaSuccess) e = pool_alloc(&dNX, sizeof(int32_t) * nu, s);
   if (e == cudaSuccess) {
-    k_cwork<<<grid_for((int64_t)nu * 32, 256), 256, 0, s>>>(nu, p->units, d_rp, d_ci, dW, dNX);
+    k_cwork<<<grid_for((int64_t)nu * 32, 256), 256, 0, s>>>(nu, p->units, d_rp, d_ci, p->rev, dW, dNX);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaMemcpyAsync(W.data(), dW, sizeof(long long) * nu, cudaMemcpyDeviceToHost, s);
@@ -458,7 +481,7 @@ gc_status classify_c_units(int32_t n, const int32_t* d_rp, const int32_t* d_ci, 
   std::vector<int32_t> hashed;
   for (int32_t k = 0; k < nu; ++k)
     if (!is_heavy[k] && W[k] > 0 && W[k] <= kHashMaxW) hashed.push_back(k);
-  std::sort(hashed.begin(), hashed.end(), [&](int32_t a, int32_t b) { return W[a] > W[b]; });
+  sort_by_wedges_desc(&hashed, W, kHashMaxW);
   std::vector<int32_t> hw;
   hw.reserve(hashed.size());
   for (int32_t k : hashed) {
@@ -471,7 +494,7 @@ gc_status classify_c_units(int32_t n, const int32_t* d_rp, const int32_t* d_ci, 
   std::vector<int32_t> hashed2;
   for (int32_t k = 0; k < nu; ++k)
     if (fits_hash2(k)) hashed2.push_back(k);
-  std::sort(hashed2.begin(), hashed2.end(), [&](int32_t a, int32_t b) { return W[a] > W[b]; });
+  sort_by_wedges_desc(&hashed2, W, kHash2MaxW);
   std::vector<char> is_hashed2(nu, 0);
   for (int32_t k : hashed2) {
     out.push_back(U[k]);
@@ -522,13 +545,13 @@ gc_status classify_c_units(int32_t n, const int32_t* d_rp, const int32_t* d_ci, 
   }
   p->n_cjobs = (int32_t)jobs.size();
   if (!jobs.empty()) {
-    e = cudaMallocAsync(&p->cjobs, sizeof(int4) * jobs.size(), s);
+    e = pool_alloc(&p->cjobs, sizeof(int4) * jobs.size(), s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(p->cjobs, jobs.data(), sizeof(int4) * jobs.size(), cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return cuda_fail(e, "hub jobs");
   }
   if (!out.empty()) e = cudaMemcpyAsync(p->cunits, out.data(), sizeof(int32_t) * out.size(), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess && !hw.empty()) {
-    e = cudaMallocAsync(&p->chash_w, sizeof(int32_t) * hw.size(), s);
+    e = pool_alloc(&p->chash_w, sizeof(int32_t) * hw.size(), s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(p->chash_w, hw.data(), sizeof(int32_t) * hw.size(), cudaMemcpyHostToDevice, s);
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -539,7 +562,7 @@ gc_status first_unreversed_slot(int64_t nnz, const int32_t* d_rev, int32_t* out,
   *out = -1;
   if (nnz <= 0) return GC_OK;
   int32_t* d = nullptr;
-  cudaError_t e = cudaMallocAsync(&d, sizeof(int32_t), s);
+  cudaError_t e = pool_alloc(&d, sizeof(int32_t), s);
   const int32_t init = 0x7fffffff;
   int32_t h = init;
   if (e == cudaSuccess) e = cudaMemcpyAsync(d, &init, sizeof(int32_t), cudaMemcpyHostToDevice, s);
@@ -592,24 +615,24 @@ gc_status prepare_graph(int32_t n, int32_t m, const int32_t* d_rp, const int32_t
       goto fail;                           \
     }                                      \
   } while (0)
-  GC_TRY(cudaMallocAsync(&P.deg, sizeof(int32_t) * (n > 0 ? n : 1), s), "alloc deg");
-  if (!P.eid) GC_TRY(cudaMallocAsync(&P.eid, sizeof(int32_t) * (nnz > 0 ? nnz : 1), s), "alloc eid");
-  GC_TRY(cudaMallocAsync(&P.rev, sizeof(int32_t) * (nnz > 0 ? nnz : 1), s), "alloc rev");
-  GC_TRY(cudaMallocAsync(&P.uv, sizeof(int32_t) * (nnz > 0 ? nnz : 1), s), "alloc uv");
-  GC_TRY(cudaMallocAsync(&P.out_ptr, sizeof(int32_t) * ((int64_t)n + 1), s), "alloc out_ptr");
-  GC_TRY(cudaMallocAsync(&P.out_idx, sizeof(int32_t) * (m > 0 ? m : 1), s), "alloc out_idx");
-  GC_TRY(cudaMallocAsync(&P.units, sizeof(int32_t) * (n > 0 ? n : 1), s), "alloc units");
-  GC_TRY(cudaMallocAsync(&P.ocsr, sizeof(int32_t) * (m > 0 ? m : 1), s), "alloc ocsr");
-  GC_TRY(cudaMallocAsync(&P.e2o, sizeof(int32_t) * (m > 0 ? m : 1), s), "alloc e2o");
+  GC_TRY(pool_alloc(&P.deg, sizeof(int32_t) * (n > 0 ? n : 1), s), "alloc deg");
+  if (!P.eid) GC_TRY(pool_alloc(&P.eid, sizeof(int32_t) * (nnz > 0 ? nnz : 1), s), "alloc eid");
+  GC_TRY(pool_alloc(&P.rev, sizeof(int32_t) * (nnz > 0 ? nnz : 1), s), "alloc rev");
+  GC_TRY(pool_alloc(&P.uv, sizeof(int32_t) * (nnz > 0 ? nnz : 1), s), "alloc uv");
+  GC_TRY(pool_alloc(&P.out_ptr, sizeof(int32_t) * ((int64_t)n + 1), s), "alloc out_ptr");
+  GC_TRY(pool_alloc(&P.out_idx, sizeof(int32_t) * (m > 0 ? m : 1), s), "alloc out_idx");
+  GC_TRY(pool_alloc(&P.units, sizeof(int32_t) * (n > 0 ? n : 1), s), "alloc units");
+  GC_TRY(pool_alloc(&P.ocsr, sizeof(int32_t) * (m > 0 ? m : 1), s), "alloc ocsr");
+  GC_TRY(pool_alloc(&P.e2o, sizeof(int32_t) * (m > 0 ? m : 1), s), "alloc e2o");
   GC_TRY(cudaMemsetAsync(P.e2o, 0, sizeof(int32_t) * (m > 0 ? m : 1), s), "memset e2o");  // in range whatever the input
-  GC_TRY(cudaMallocAsync(&P.kunits, sizeof(int32_t) * (n > 0 ? n : 1), s), "alloc kunits");
-  GC_TRY(cudaMallocAsync(&up, sizeof(int32_t) * (n > 0 ? n : 1), s), "alloc up");
-  GC_TRY(cudaMallocAsync(&upoff, sizeof(int32_t) * ((int64_t)n + 1), s), "alloc upoff");
-  GC_TRY(cudaMallocAsync(&out_cnt, sizeof(int32_t) * (n > 0 ? n : 1), s), "alloc out_cnt");
-  GC_TRY(cudaMallocAsync(&P.S, sizeof(long long) * (n > 0 ? n : 1), s), "alloc S");
+  GC_TRY(pool_alloc(&P.kunits, sizeof(int32_t) * (n > 0 ? n : 1), s), "alloc kunits");
+  GC_TRY(pool_alloc(&up, sizeof(int32_t) * (n > 0 ? n : 1), s), "alloc up");
+  GC_TRY(pool_alloc(&upoff, sizeof(int32_t) * ((int64_t)n + 1), s), "alloc upoff");
+  GC_TRY(pool_alloc(&out_cnt, sizeof(int32_t) * (n > 0 ? n : 1), s), "alloc out_cnt");
+  GC_TRY(pool_alloc(&P.S, sizeof(long long) * (n > 0 ? n : 1), s), "alloc S");
   S = P.S;
   // [0] max degree, [1..64] v-group bins, [65] max out-degree, [66..97] pass-K bins
-  GC_TRY(cudaMallocAsync(&dmax, sizeof(int32_t) * 98, s), "alloc dmax");
+  GC_TRY(pool_alloc(&dmax, sizeof(int32_t) * 98, s), "alloc dmax");
   hist = dmax + 1;
   GC_TRY(cudaMemsetAsync(dmax, 0, sizeof(int32_t) * 98, s), "memset");
   if (n > 0) {

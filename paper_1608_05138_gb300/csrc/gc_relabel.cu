@@ -206,9 +206,9 @@ gc_status relabel_on_device(int32_t n, int32_t m, const int32_t* d_rp0, const in
     k_sort_long<<<n_long, kLongThreads, 0, s>>>(d_long_rows, d_long_off, d_rp, d_ci, d_tmp);
     RL_TRY(cudaGetLastError(), "k_sort_long");
   }
-  RL_TRY(cudaMallocAsync(&first_up, sizeof(int32_t) * (size_t)n, s), "alloc relabel");
-  RL_TRY(cudaMallocAsync(&up_cnt, sizeof(int32_t) * (size_t)n, s), "alloc relabel");
-  RL_TRY(cudaMallocAsync(&up_off, sizeof(int32_t) * ((size_t)n + 1), s), "alloc relabel");
+  RL_TRY(pool_alloc(&first_up, sizeof(int32_t) * (size_t)n, s), "alloc relabel");
+  RL_TRY(pool_alloc(&up_cnt, sizeof(int32_t) * (size_t)n, s), "alloc relabel");
+  RL_TRY(pool_alloc(&up_off, sizeof(int32_t) * ((size_t)n + 1), s), "alloc relabel");
   k_upper<<<blocks_for(n, 256), 256, 0, s>>>(n, d_rp0, d_ci0, first_up, up_cnt);
   RL_TRY(cudaGetLastError(), "k_upper");
   if ((st = exclusive_scan(n, up_cnt, up_off, s)) != GC_OK) goto out;

@@ -63,26 +63,26 @@ gc_status scratch_init(Scratch* sc, int32_t m, int32_t table_n, int32_t kmax, in
     if (e != cudaSuccess) return cuda_fail(e, "scratch alloc"); \
   } while (0)
   const size_t m1 = (size_t)(m > 0 ? m : 1);
-  GS_TRY(cudaMallocAsync(&sc->trio, sizeof(int32_t) * m1, s));
-  GS_TRY(cudaMallocAsync(&sc->P, sizeof(unsigned long long) * 2 * m1, s));
-  GS_TRY(cudaMallocAsync(&sc->xc, sizeof(unsigned long long) * 2 * m1, s));
-  GS_TRY(cudaMallocAsync(&sc->misc, sizeof(int32_t) * 16, s));
-  GS_TRY(cudaMallocAsync(&sc->work, sizeof(unsigned long long) * kNumWork, s));
+  GS_TRY(pool_alloc(&sc->trio, sizeof(int32_t) * m1, s));
+  GS_TRY(pool_alloc(&sc->P, sizeof(unsigned long long) * 2 * m1, s));
+  GS_TRY(pool_alloc(&sc->xc, sizeof(unsigned long long) * 2 * m1, s));
+  GS_TRY(pool_alloc(&sc->misc, sizeof(int32_t) * 16, s));
+  GS_TRY(pool_alloc(&sc->work, sizeof(unsigned long long) * kNumWork, s));
   if (table_n > kSmemTableMax) {
     sc->tables_n = (size_t)count_grid_size() * (size_t)table_n;
-    GS_TRY(cudaMallocAsync(&sc->tables, sizeof(uint32_t) * sc->tables_n, s));
+    GS_TRY(pool_alloc(&sc->tables, sizeof(uint32_t) * sc->tables_n, s));
     GS_TRY(cudaMemsetAsync(sc->tables, 0, sizeof(uint32_t) * sc->tables_n, s));
   }
   if (cnx_max > 0) {
     sc->cbuf_nx = cnx_max;
-    GS_TRY(cudaMallocAsync(&sc->cbuf, sizeof(int32_t) * 3 * (size_t)cnx_max * (size_t)(count_grid_size() / kCtasPerSm), s));
+    GS_TRY(pool_alloc(&sc->cbuf, sizeof(int32_t) * 3 * (size_t)cnx_max * (size_t)(count_grid_size() / kCtasPerSm), s));
   }
   {  // pass K: each CTA records the edges of its current H_a (at most C(kmax, 2))
     const long long full = (long long)kmax * (kmax - 1) / 2;
     const long long cap = k_list_cap();
     sc->hitcap = (int32_t)(full < cap ? (full > 0 ? full : 1) : cap);
     sc->hitbuf_ctas = 4 * (count_grid_size() / kCtasPerSm);  // up to four CTAs per SM in any tier
-    GS_TRY(cudaMallocAsync(&sc->hitbuf, sizeof(int32_t) * 2 * (size_t)sc->hitcap * (size_t)sc->hitbuf_ctas, s));
+    GS_TRY(pool_alloc(&sc->hitbuf, sizeof(int32_t) * 2 * (size_t)sc->hitcap * (size_t)sc->hitbuf_ctas, s));
   }
   if (kmax > kTierCap[kTier1024]) {
     sc->kbuf_cap = kmax;
@@ -92,7 +92,7 @@ gc_status scratch_init(Scratch* sc, int32_t m, int32_t table_n, int32_t kmax, in
     if (ctas > sms) ctas = sms;
     if (ctas < 1) ctas = 1;
     sc->kbuf_ctas = (int32_t)ctas;
-    GS_TRY(cudaMallocAsync(&sc->kbuf, sc->kbuf_stride * ctas, s));
+    GS_TRY(pool_alloc(&sc->kbuf, sc->kbuf_stride * ctas, s));
   }
 #undef GS_TRY
   return GC_OK;
@@ -160,17 +160,17 @@ gc_status run_count(const DevGraph& g, const int32_t* units, int32_t n_units, co
         sc->tlist = nullptr;
         sc->tlist_cap = 0;
         const long long cap = need;
-        if (cudaMallocAsync(&sc->tlist, sizeof(int2) * (size_t)cap, s) == cudaSuccess) sc->tlist_cap = cap;
+        if (pool_alloc(&sc->tlist, sizeof(int2) * (size_t)cap, s) == cudaSuccess) sc->tlist_cap = cap;
         else cudaGetLastError();  // no list: pass K scans
       }
       if (nku > sc->tl_units) {
         for (void* p : {(void*)sc->tl_off, (void*)sc->tl_cnt})
           if (p) cudaFreeAsync(p, s);
-        GR_TRY(cudaMallocAsync(&sc->tl_off, sizeof(long long) * (size_t)nku, s), "alloc list index");
-        GR_TRY(cudaMallocAsync(&sc->tl_cnt, sizeof(int32_t) * (size_t)nku, s), "alloc list index");
+        GR_TRY(pool_alloc(&sc->tl_off, sizeof(long long) * (size_t)nku, s), "alloc list index");
+        GR_TRY(pool_alloc(&sc->tl_cnt, sizeof(int32_t) * (size_t)nku, s), "alloc list index");
         sc->tl_units = nku;
       }
-      if (!sc->tl_fill) GR_TRY(cudaMallocAsync(&sc->tl_fill, sizeof(unsigned long long), s), "alloc list fill");
+      if (!sc->tl_fill) GR_TRY(pool_alloc(&sc->tl_fill, sizeof(unsigned long long), s), "alloc list fill");
     }
   }
   a.tlist = sc->tlist_cap > 0 ? sc->tlist : nullptr;
@@ -184,9 +184,9 @@ gc_status run_count(const DevGraph& g, const int32_t* units, int32_t n_units, co
   a.dsum = nullptr;
   const bool want_induced = induced != nullptr && g.m > 0;
   if (want_induced) {  // scratch of the per-edge induced counts, kept with the graph
-    if (!sc->dsum) GR_TRY(cudaMallocAsync(&sc->dsum, sizeof(unsigned long long) * (size_t)g.m, s), "alloc dsum");
+    if (!sc->dsum) GR_TRY(pool_alloc(&sc->dsum, sizeof(unsigned long long) * (size_t)g.m, s), "alloc dsum");
     if (!sc->vsum)
-      GR_TRY(cudaMallocAsync(&sc->vsum, sizeof(unsigned long long) * 2 * (size_t)(g.n > 0 ? g.n : 1), s),
+      GR_TRY(pool_alloc(&sc->vsum, sizeof(unsigned long long) * 2 * (size_t)(g.n > 0 ? g.n : 1), s),
              "alloc vsum");
     GR_TRY(cudaMemsetAsync(sc->dsum, 0, sizeof(unsigned long long) * (size_t)g.m, s), "zero dsum");
     a.dsum = sc->dsum;

@@ -772,3 +772,23 @@ def test_batch_submit_many_rejects_a_malformed_graph():
             assert x is not None and x.shape == (0, 17, 2)
         finally:
             gcb.gc_batch_destroy(b)
+
+
+def test_memory_pool_keeps_blocks_until_released():
+    # a freed graph's blocks stay in the library pool (not zeroed) and serve
+    # the next graph, whose counts must not depend on their old contents;
+    # gc_release_cached_memory hands them back to the device
+    import torch
+    torch.cuda.synchronize()
+    gcb.gc_release_cached_memory()
+    free0, _ = torch.cuda.mem_get_info()
+    rp, ci = graphgen.rmat(16, 16, 0.57, 0.19, 0.19, 3)
+    with gcb.Graph(rp, ci) as g:
+        g.count(np.zeros((g.m, 13), np.uint64))
+    free1, _ = torch.cuda.mem_get_info()
+    assert free0 - free1 > 50 << 20  # kept by the pool
+    rp2, ci2 = graphgen.chung_lu(60000, 400000, 2.1, 8e5, 3000.0, 5)
+    assert_parity(rp2, ci2)          # counted in reused blocks
+    gcb.gc_release_cached_memory()
+    free2, _ = torch.cuda.mem_get_info()
+    assert free2 > free1 and free0 - free2 < 64 << 20
