@@ -91,7 +91,7 @@ __global__ void k_edges(int32_t n, int32_t m, const int32_t* __restrict__ rp, co
                         const int32_t* __restrict__ upoff, const int32_t* __restrict__ out_ptr,
                         int32_t* __restrict__ eid, int32_t* __restrict__ uv,
                         int32_t* __restrict__ out_idx, int32_t* __restrict__ ocsr, int32_t* __restrict__ rev,
-                        int32_t* __restrict__ e2o, bool write_ids) {
+                        int32_t* __restrict__ e2o, bool write_ids, const int32_t* __restrict__ perm) {
   const int lane = threadIdx.x & 31;
   const int warps = (gridDim.x * blockDim.x) >> 5;
   for (int32_t x = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < n; x += warps) {
@@ -103,10 +103,19 @@ __global__ void k_edges(int32_t n, int32_t m, const int32_t* __restrict__ rp, co
       bool valid = p < e;
       int32_t y = valid ? ci[p] : 0;
       bool is_out = valid && rank_less(deg, x, y);
-      if (valid) {  // the slot of (y, x)
+      int32_t qr = -1;  // ids given: the reverse slot, once found
+      if (valid && write_ids) {  // the slot of (y, x); the ids below take the same search
         const int32_t yb = rp[y], ye = rp[y + 1];
         const int32_t q = lower_bound_i32(ci, yb, ye, x);
         rev[p] = (q < ye && ci[q] == x) ? q : p;  // p itself only for invalid input
+      } else if (valid && y > x) {  // ids given: one search per edge, from its lower end, sets both
+        const int32_t yb = rp[y], ye = rp[y + 1];
+        const int32_t q = lower_bound_i32(ci, yb, ye, x);
+        if (q < ye && ci[q] == x) {
+          rev[p] = q;
+          rev[q] = p;
+          qr = q;
+        }  // else both keep rev = self (k_rev_init): no reverse, invalid input
       }
       int32_t id = 0;
       if (valid && write_ids) {
@@ -126,12 +135,31 @@ __global__ void k_edges(int32_t n, int32_t m, const int32_t* __restrict__ rp, co
         const int32_t os = o + __popc(mask & ((1u << lane) - 1u));
         out_idx[os] = y;
         ocsr[os] = p;
-        const int32_t ide = write_ids ? id : eid[p];
+        // ids given (ids are ranks, so an out-slot is the slot searched from):
+        // the relabel wrote the id of the slot whose caller labels ascend;
+        // the other slot of the edge takes it here
+        int32_t ide = id;
+        if (!write_ids) {
+          if (qr >= 0 && perm[x] > perm[y]) {
+            ide = eid[qr];
+            eid[p] = ide;
+          } else {
+            ide = eid[p];
+            if (qr >= 0) eid[qr] = ide;
+          }
+        }
         if ((uint32_t)ide < (uint32_t)m) e2o[ide] = os;  // out of range only for invalid input
       }
       o += __popc(mask);
     }
   }
+}
+
+// rev[p] = p for every slot, before k_edges searches each edge once: a slot
+// that no search reaches keeps it (it has no reverse).
+__global__ void k_rev_init(int64_t nnz, int32_t* __restrict__ rev) {
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nnz; p += (int64_t)gridDim.x * blockDim.x)
+    rev[p] = (int32_t)p;
 }
 
 // Edge list in the caller's labels when the graph was relabelled.
@@ -642,9 +670,13 @@ gc_status prepare_graph(int32_t n, int32_t m, const int32_t* d_rp, const int32_t
     k_out_cnt<<<grid_for((int64_t)n * 32, 256), 256, 0, s>>>(n, d_rp, d_ci, P.deg, out_cnt, S, dmax, dmax + 65);
     GC_TRY(cudaGetLastError(), "k_out_cnt");
     if ((st = exclusive_scan(n, out_cnt, P.out_ptr, s)) != GC_OK) goto fail;
+    if (d_eid_given) {
+      k_rev_init<<<grid_for(nnz, 256), 256, 0, s>>>(nnz, P.rev);
+      GC_TRY(cudaGetLastError(), "k_rev_init");
+    }
     k_edges<<<grid_for((int64_t)n * 32, 256), 256, 0, s>>>(n, m, d_rp, d_ci, P.deg, up, upoff,
                                                             P.out_ptr, P.eid, P.uv, P.out_idx, P.ocsr, P.rev,
-                                                            P.e2o, d_eid_given == nullptr);
+                                                            P.e2o, d_eid_given == nullptr, d_perm);
     GC_TRY(cudaGetLastError(), "k_edges");
     if (d_eid_given) {
       k_uv_perm<<<grid_for((int64_t)n * 32, 256), 256, 0, s>>>(n, d_rp, d_ci, P.eid, d_perm, P.uv);

@@ -10,9 +10,10 @@
 //     rows of up to 32 entries, a CTA in shared memory up to 4096, and for
 //     longer rows a CTA over a padded copy in global memory whose strides
 //     below 4096 are done tile by tile in shared memory,
-//   * finds the caller's edge id of every internal slot: the rank of (u, v),
-//     u < v, in the caller's row-major upper triangle, from a binary search of
-//     v in the caller's row u.
+//   * finds the caller's edge id of every internal slot (u, v) with u < v in
+//     the caller's labels: its rank in the caller's row-major upper triangle,
+//     from a binary search of v in the caller's row u (the reverse slot takes
+//     the same id in the preparation, which finds every slot's reverse).
 #include <cuda_runtime.h>
 
 #include "gc_internal.h"
@@ -161,9 +162,11 @@ __global__ void k_slot_eid(int32_t n, int32_t m, const int32_t* __restrict__ rp,
     const int32_t x = perm[i];
     for (int32_t s = rp[i] + lane; s < rp[i + 1]; s += 32) {
       const int32_t y = perm[ci[s]];
-      const int32_t u = min(x, y), v = max(x, y);
-      const int32_t q = lower_bound_dev(ci0, first_up[u], rp0[u + 1], v);
-      int32_t id = (q < rp0[u + 1] && ci0[q] == v) ? up_off[u] + (q - first_up[u]) : 0;  // 0 only without symmetry
+      int32_t id = 0;  // the slot of (y, x), x > y, takes its id from its reverse in k_edges
+      if (x < y) {
+        const int32_t q = lower_bound_dev(ci0, first_up[x], rp0[x + 1], y);
+        id = (q < rp0[x + 1] && ci0[q] == y) ? up_off[x] + (q - first_up[x]) : 0;
+      }
       eid[s] = (id >= 0 && id < m) ? id : 0;
     }
   }
