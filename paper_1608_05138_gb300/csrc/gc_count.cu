@@ -688,6 +688,7 @@ __global__ void __launch_bounds__(kHeavyBlock, 1) k_pass_c_heavy(DevGraph g, Cou
 // and rows ascend).
 constexpr int kHashBlock = 512;
 constexpr int kHashSlots = 2 * kHashMaxW;
+constexpr int kHashSmallBlock = 128;
 
 __device__ __forceinline__ uint32_t o_hash(int32_t o, int bits) {
   return ((uint32_t)o * 0x9E3779B1u) >> (32 - bits);  // Fibonacci hashing
@@ -718,26 +719,34 @@ __device__ __forceinline__ int32_t hash_find(const int32_t* keys, int32_t o, uin
   return -1;
 }
 
-__global__ void __launch_bounds__(kHashBlock, kCtasPerSm) k_pass_c_hash(DevGraph g, CountArgs a) {
-  extern __shared__ int32_t hkeys[];                                  // [kHashSlots] o, or -1
-  uint32_t* hcnt = reinterpret_cast<uint32_t*>(hkeys + kHashSlots);   // [kHashSlots / 2] two counts
+// Two instances: 512-thread CTAs, two an SM, with the table for kHashMaxW
+// wedges; and, for the many units of at most kHashSmallW wedges (on R-MAT
+// scale 22, 87 % of the hashed units and 10 % of their wedges), 128-thread
+// CTAs with a table for kHashSmallW, sixteen an SM, so that a unit's barriers
+// and latency chains no longer hold a large CTA. Units [k0, k1) of the
+// hashed list (heaviest first), taken from *cursor.
+template <int kThreads, int kMaxW>
+__global__ void __launch_bounds__(kThreads, kThreads == kHashBlock ? kCtasPerSm : 2048 / kThreads)
+    k_pass_c_hash(DevGraph g, CountArgs a, int32_t k0, int32_t k1, int32_t* cursor) {
+  extern __shared__ int32_t hkeys[];                                  // [2 kMaxW] o, or -1
+  uint32_t* hcnt = reinterpret_cast<uint32_t*>(hkeys + 2 * kMaxW);    // [kMaxW] two counts
   __shared__ int32_t s_unit, s_next[2];
   const int lane = threadIdx.x & 31;
   long long w_wedge = 0;  // lane 0
   for (;;) {
     __syncthreads();
-    if (threadIdx.x == 0) s_unit = atomicAdd(a.cursor + 9, 1);
+    if (threadIdx.x == 0) s_unit = k0 + atomicAdd(cursor, 1);
     __syncthreads();
     const int32_t k = s_unit;
-    if (k >= a.n_chash) break;
+    if (k >= k1) break;
     const int32_t h = a.cunits[a.n_cheavy + k];
-    const int32_t wk = min(a.chash_w[k], (int32_t)kHashMaxW);
+    const int32_t wk = min(a.chash_w[k], (int32_t)kMaxW);
     int bits = 6;
     while ((1 << bits) < 2 * wk) ++bits;  // at most log2(kHashSlots)
     const uint32_t mask = (1u << bits) - 1u;
     const int32_t hb = g.rp[h], he = g.rp[h + 1];
-    for (int32_t i = threadIdx.x; i <= (int32_t)mask; i += kHashBlock) hkeys[i] = -1;
-    for (int32_t i = threadIdx.x; i <= (int32_t)(mask >> 1); i += kHashBlock) hcnt[i] = 0u;
+    for (int32_t i = threadIdx.x; i <= (int32_t)mask; i += kThreads) hkeys[i] = -1;
+    for (int32_t i = threadIdx.x; i <= (int32_t)(mask >> 1); i += kThreads) hcnt[i] = 0u;
     if (threadIdx.x < 2) s_next[threadIdx.x] = hb;
     __syncthreads();
     // pass 0 counts cnt_h(o); pass 1 attributes cnt_h(o) - 1 to the slots
@@ -1004,16 +1013,29 @@ gc_status run_pass_c_heavy(const DevGraph& g, const CountArgs& a, cudaStream_t s
   return e == cudaSuccess ? GC_OK : cuda_fail(e, "k_pass_c_heavy");
 }
 
-gc_status run_pass_c_hash(const DevGraph& g, const CountArgs& a, cudaStream_t s) {
-  if (a.n_chash <= 0) return GC_OK;
-  const size_t smem = sizeof(int32_t) * kHashSlots + sizeof(uint32_t) * (kHashSlots / 2);
-  cudaError_t e = cudaFuncSetAttribute(k_pass_c_hash, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+template <int kThreads, int kMaxW>
+static gc_status launch_hash(const DevGraph& g, const CountArgs& a, int32_t k0, int32_t k1, int32_t* cursor,
+                             cudaStream_t s) {
+  if (k1 <= k0) return GC_OK;
+  auto kern = k_pass_c_hash<kThreads, kMaxW>;
+  const size_t smem = sizeof(int32_t) * 2 * kMaxW + sizeof(uint32_t) * kMaxW;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return cuda_fail(e, "k_pass_c_hash");
-  int grid = count_grid_size();
-  if (grid > a.n_chash) grid = a.n_chash;
-  k_pass_c_hash<<<grid, kHashBlock, smem, s>>>(g, a);
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
+  if (e != cudaSuccess) return cuda_fail(e, "k_pass_c_hash occupancy");
+  int grid = (per_sm > 0 ? per_sm : 1) * (count_grid_size() / kCtasPerSm);
+  if (grid > k1 - k0) grid = k1 - k0;
+  kern<<<grid, kThreads, smem, s>>>(g, a, k0, k1, cursor);
   e = cudaGetLastError();
   return e == cudaSuccess ? GC_OK : cuda_fail(e, "k_pass_c_hash");
+}
+
+gc_status run_pass_c_hash(const DevGraph& g, const CountArgs& a, cudaStream_t s) {
+  if (a.n_chash <= 0) return GC_OK;
+  gc_status st = launch_hash<kHashBlock, kHashMaxW>(g, a, 0, a.n_chash_big, a.cursor + 9, s);
+  if (st != GC_OK) return st;
+  return launch_hash<kHashSmallBlock, kHashSmallW>(g, a, a.n_chash_big, a.n_chash, a.cursor + 7, s);
 }
 
 gc_status run_pass_c_hash2(const DevGraph& g, const CountArgs& a, cudaStream_t s) {

@@ -53,6 +53,7 @@ struct CountArgs {
   int32_t n_cheavy;        // hub units of pass C (cunits[0 .. n_cheavy))
   const int32_t* chash_w;  // wedges of the hashed units cunits[n_cheavy .. n_cheavy + n_chash + n_chash2)
   int32_t n_chash;
+  int32_t n_chash_big;     // hashed units of more than kHashSmallW wedges (the first of them)
   int32_t n_chash2;        // units of the packed-key hash tier, after the hashed units
   const int4* cjobs;       // pass C hub kernel: jobs (hub index into cunits, first o-range block, blocks),
                            // heaviest first
@@ -180,6 +181,7 @@ struct KUnits {
   int32_t n_cjobs;
   const int32_t* chash_w;
   int32_t n_chash;
+  int32_t n_chash_big;
   int32_t n_chash2;
   int32_t n_cunits;        // pass C units in all (units without wedges are left out)
 };
@@ -244,6 +246,7 @@ struct PrepBuffers {
   int32_t n_cjobs = 0;
   int32_t* chash_w = nullptr;  // wedges of each hashed unit (both hash tiers)
   int32_t n_chash = 0;
+  int32_t n_chash_big = 0;     // hashed units of more than kHashSmallW wedges
   int32_t n_chash2 = 0;        // units of the packed-key hash tier
   int32_t n_cunits = 0;
   int32_t cnx_max = 0;      // most lower neighbours of a hub unit
@@ -323,6 +326,7 @@ __host__ __device__ __forceinline__ int hub_cpw(int64_t nx) { return nx < 1023 ?
 // hash of 2 kHashMaxW keys (at most half full: a unit has no more distinct
 // o than wedges).
 constexpr int kHashMaxW = 8192;
+constexpr int kHashSmallW = 512;  // hashed units up to this many wedges run in small CTAs
 gc_status run_pass_c_hash(const DevGraph& g, const CountArgs& a, cudaStream_t s);
 // Units of more than kHashMaxW and at most kHash2MaxW wedges, with fewer than
 // kHash2MaxNx lower neighbours, in graphs of at most 2^22 vertices: a

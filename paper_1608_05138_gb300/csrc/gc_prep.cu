@@ -454,6 +454,7 @@ gc_status classify_c_units(int32_t n, const int32_t* d_rp, const int32_t* d_ci, 
   if (e != cudaSuccess) return cuda_fail(e, "alloc cunits");
   p->n_cheavy = 0;
   p->n_chash = 0;
+  p->n_chash_big = 0;
   p->n_chash2 = 0;
   p->n_cunits = nu;
   p->cnx_max = 0;
@@ -533,6 +534,8 @@ gc_status classify_c_units(int32_t n, const int32_t* d_rp, const int32_t* d_ci, 
     if (!is_heavy[k] && !is_hashed2[k] && W[k] > kHashMaxW) out.push_back(U[k]);
   p->n_cheavy = (int32_t)heavy.size();
   p->n_chash = (int32_t)hashed.size();
+  p->n_chash_big = 0;  // hashed is heaviest first
+  while (p->n_chash_big < p->n_chash && W[hashed[(size_t)p->n_chash_big]] > kHashSmallW) ++p->n_chash_big;
   p->n_chash2 = (int32_t)hashed2.size();
   p->n_cunits = (int32_t)out.size();
   // Hub units cut into jobs of consecutive o-range blocks (the finer

@@ -127,13 +127,14 @@ gc_status run_count(const DevGraph& g, const int32_t* units, int32_t n_units, co
   a.n_cjobs = ku.n_cjobs;
   a.chash_w = ku.chash_w;
   a.n_chash = ku.n_chash;
+  a.n_chash_big = ku.n_chash_big;
   a.n_chash2 = ku.n_chash2;
   a.cbuf = sc->cbuf;
   a.cbuf_nx = sc->cbuf_nx;
   a.hub_tab = hub_tab_words();
   for (int t = 0; t <= kNumTiers; ++t) a.ktier_off[t] = ku.tier_off[t];
   a.cursor = sc->misc;  // [0] pass C, [2 + tier] pass K, [8] pass C hubs, [9] pass C hashed, [10 + tier] pass T,
-                        // [15] pass C packed-key hash
+                        // [15] pass C packed-key hash, [7] pass C hashed small units
   a.status = sc->misc + 1;
   a.tables = g.table_n > kSmemTableMax ? sc->tables : nullptr;
   a.trio = sc->trio;
