@@ -438,12 +438,14 @@ gc_status gc_graph_upload(int32_t n, const int32_t* row_ptr, const int32_t* col_
   gc_status st = GC_OK;
   RelabelPlan R;
   int32_t *d_eid = nullptr, *d_perm = nullptr, *d_newid = nullptr, *d_rp0 = nullptr, *d_ci0 = nullptr;
-  int32_t *d_lists = nullptr, *d_tmp = nullptr;
+  int32_t* d_lists = nullptr;
+  long long* d_tmp = nullptr;
   int64_t* d_loff = nullptr;
   auto drop_temps = [&] {
     for (void* p : {(void*)d_newid, (void*)d_rp0, (void*)d_ci0, (void*)d_lists, (void*)d_tmp, (void*)d_loff})
       if (p) cudaFreeAsync(p, s);
-    d_newid = d_rp0 = d_ci0 = d_lists = d_tmp = nullptr;
+    d_newid = d_rp0 = d_ci0 = d_lists = nullptr;
+    d_tmp = nullptr;
     d_loff = nullptr;
   };
   // On a failure the symmetry check is awaited first: an invalid input is
@@ -489,7 +491,7 @@ gc_status gc_graph_upload(int32_t n, const int32_t* row_ptr, const int32_t* col_
   GC_CHECK(pool_alloc(&d_lists, sizeof(int32_t) * (n_lists > 0 ? n_lists : 1), s), "alloc row lists");
   GC_CHECK(pool_alloc(&d_loff, sizeof(int64_t) * (R.long_off.size() > 0 ? R.long_off.size() : 1), s),
            "alloc row lists");
-  GC_CHECK(pool_alloc(&d_tmp, sizeof(int32_t) * (size_t)(R.tmp_len > 0 ? R.tmp_len : 1), s), "alloc sort buffer");
+  GC_CHECK(pool_alloc(&d_tmp, sizeof(long long) * (size_t)(R.tmp_len > 0 ? R.tmp_len : 1), s), "alloc sort buffer");
   GC_CHECK(cudaMemcpyAsync(d_rp0, row_ptr, sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyHostToDevice, s),
            "copy row_ptr");
   if (nnz > 0)

@@ -220,7 +220,7 @@ inline cudaError_t pool_alloc(T** p, size_t bytes, cudaStream_t s) {
 gc_status relabel_on_device(int32_t n, int32_t m, const int32_t* d_rp0, const int32_t* d_ci0,
                             const int32_t* d_perm, const int32_t* d_newid, const int32_t* d_rp, int32_t* d_ci,
                             int32_t* d_eid, const int32_t* d_mid_rows, int32_t n_mid, const int32_t* d_long_rows,
-                            const int64_t* d_long_off, int32_t n_long, int32_t* d_tmp, cudaStream_t s);
+                            const int64_t* d_long_off, int32_t n_long, long long* d_tmp, cudaStream_t s);
 
 // ---- preprocessing (gc_prep.cu) ----
 struct PrepBuffers {

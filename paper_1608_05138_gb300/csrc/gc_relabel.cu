@@ -4,16 +4,18 @@
 //
 // The host computes the permutation (a counting sort of n degrees) and the
 // internal row pointers; the device
-//   * writes every internal row i (caller vertex perm[i]) as the internal ids
-//     of its caller row,
+//   * writes every internal row i (caller vertex perm[i]) as 64-bit keys:
+//     the internal id of each caller entry above, its position in the caller
+//     row below (ids are distinct within a row, so the order is the ids'),
 //   * sorts each row ascending -- bitonic networks: a warp in registers for
 //     rows of up to 32 entries, a CTA in shared memory up to 4096, and for
 //     longer rows a CTA over a padded copy in global memory whose strides
 //     below 4096 are done tile by tile in shared memory,
-//   * finds the caller's edge id of every internal slot (u, v) with u < v in
-//     the caller's labels: its rank in the caller's row-major upper triangle,
-//     from a binary search of v in the caller's row u (the reverse slot takes
-//     the same id in the preparation, which finds every slot's reverse).
+//   * splits the keys: the internal ids become the row, and the caller
+//     position gives, for every internal slot (u, v) with u < v in the
+//     caller's labels, the caller's edge id (its rank in the caller's
+//     row-major upper triangle) without a search; the reverse slot takes the
+//     same id in the preparation, which finds every slot's reverse.
 #include <cuda_runtime.h>
 
 #include "gc_internal.h"
@@ -25,8 +27,10 @@ constexpr int32_t kTile = 4096;   // entries of a shared-memory tile
 constexpr int kMidThreads = 256;
 constexpr int kLongThreads = 1024;
 
-__device__ __forceinline__ void cmpswap(int32_t* a, int32_t i, int32_t l, bool asc) {
-  const int32_t x = a[i], y = a[l];
+constexpr long long kKeyPad = 0x7fffffffffffffffLL;  // sorts after every key
+
+__device__ __forceinline__ void cmpswap(long long* a, int32_t i, int32_t l, bool asc) {
+  const long long x = a[i], y = a[l];
   if ((x > y) == asc) {
     a[i] = y;
     a[l] = x;
@@ -42,30 +46,31 @@ __device__ __forceinline__ int32_t lower_bound_dev(const int32_t* a, int32_t lo,
   return lo;
 }
 
-// Warp per internal row: the internal ids of the caller row, unsorted.
+// Warp per internal row: the keys (internal id, caller position) of the
+// caller row, unsorted.
 __global__ void k_fill_rows(int32_t n, const int32_t* __restrict__ rp0, const int32_t* __restrict__ ci0,
                             const int32_t* __restrict__ perm, const int32_t* __restrict__ newid,
-                            const int32_t* __restrict__ rp, int32_t* __restrict__ ci) {
+                            const int32_t* __restrict__ rp, long long* __restrict__ kv) {
   const int lane = threadIdx.x & 31;
   const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += warps) {
     const int32_t x = perm[i];
     const int32_t b0 = rp0[x], len = rp0[x + 1] - b0, b = rp[i];
-    for (int32_t k = lane; k < len; k += 32) ci[b + k] = newid[ci0[b0 + k]];
+    for (int32_t k = lane; k < len; k += 32) kv[b + k] = ((long long)newid[ci0[b0 + k]] << 32) | k;
   }
 }
 
 // Rows of 2..32 entries: one warp each, one entry per lane.
-__global__ void k_sort_short(int32_t n, const int32_t* __restrict__ rp, int32_t* __restrict__ ci) {
+__global__ void k_sort_short(int32_t n, const int32_t* __restrict__ rp, long long* __restrict__ ci) {
   const int lane = threadIdx.x & 31;
   const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += warps) {
     const int32_t b = rp[i], len = rp[i + 1] - b;
     if (len < 2 || len > 32) continue;  // warp-uniform
-    int32_t v = lane < len ? ci[b + lane] : 0x7fffffff;
+    long long v = lane < len ? ci[b + lane] : kKeyPad;
     for (int k = 2; k <= 32; k <<= 1)
       for (int j = k >> 1; j > 0; j >>= 1) {
-        const int32_t w = __shfl_xor_sync(0xffffffffu, v, j);
+        const long long w = __shfl_xor_sync(0xffffffffu, v, j);
         const bool asc = (lane & k) == 0, lower = (lane & j) == 0;
         v = (asc == lower) ? min(v, w) : max(v, w);
       }
@@ -75,13 +80,13 @@ __global__ void k_sort_short(int32_t n, const int32_t* __restrict__ rp, int32_t*
 
 // Rows of 33..4096 entries (listed): one CTA each, in shared memory.
 __global__ void __launch_bounds__(kMidThreads) k_sort_mid(const int32_t* __restrict__ rows, const int32_t* __restrict__ rp,
-                                                          int32_t* __restrict__ ci) {
-  __shared__ int32_t sh[kTile];
+                                                          long long* __restrict__ ci) {
+  __shared__ long long sh[kTile];
   const int32_t r = rows[blockIdx.x];
   const int32_t b = rp[r], len = rp[r + 1] - b;
   int32_t P = 64;
   while (P < len) P <<= 1;
-  for (int32_t i = threadIdx.x; i < P; i += kMidThreads) sh[i] = i < len ? ci[b + i] : 0x7fffffff;
+  for (int32_t i = threadIdx.x; i < P; i += kMidThreads) sh[i] = i < len ? ci[b + i] : kKeyPad;
   __syncthreads();
   for (int32_t k = 2; k <= P; k <<= 1)
     for (int32_t j = k >> 1; j > 0; j >>= 1) {
@@ -96,7 +101,7 @@ __global__ void __launch_bounds__(kMidThreads) k_sort_mid(const int32_t* __restr
 
 // Steps (k, j) of the bitonic network on one aligned tile of kTile entries of
 // a, for j from j0 down to 1 (all pairs lie inside the tile when j0 < kTile).
-__device__ __forceinline__ void tile_steps(int32_t* sh, int32_t* a, int32_t c0, int32_t k_lo, int32_t k_hi,
+__device__ __forceinline__ void tile_steps(long long* sh, long long* a, int32_t c0, int32_t k_lo, int32_t k_hi,
                                            int32_t j0) {
   for (int32_t i = threadIdx.x; i < kTile; i += kLongThreads) sh[i] = a[c0 + i];
   __syncthreads();
@@ -116,15 +121,15 @@ __device__ __forceinline__ void tile_steps(int32_t* sh, int32_t* a, int32_t c0, 
 // (power-of-two length P) at tmp + toff[row].
 __global__ void __launch_bounds__(kLongThreads) k_sort_long(const int32_t* __restrict__ rows,
                                                             const int64_t* __restrict__ toff,
-                                                            const int32_t* __restrict__ rp, int32_t* __restrict__ ci,
-                                                            int32_t* __restrict__ tmp) {
-  __shared__ int32_t sh[kTile];
+                                                            const int32_t* __restrict__ rp, long long* __restrict__ ci,
+                                                            long long* __restrict__ tmp) {
+  __shared__ long long sh[kTile];
   const int32_t r = rows[blockIdx.x];
   const int32_t b = rp[r], len = rp[r + 1] - b;
   int32_t P = kTile;
   while (P < len) P <<= 1;
-  int32_t* a = tmp + toff[blockIdx.x];
-  for (int32_t i = threadIdx.x; i < P; i += kLongThreads) a[i] = i < len ? ci[b + i] : 0x7fffffff;
+  long long* a = tmp + toff[blockIdx.x];
+  for (int32_t i = threadIdx.x; i < P; i += kLongThreads) a[i] = i < len ? ci[b + i] : kKeyPad;
   __syncthreads();
   for (int32_t c0 = 0; c0 < P; c0 += kTile) tile_steps(sh, a, c0, 2, kTile, 1);  // k <= kTile: inside tiles
   for (int32_t k = 2 * kTile; k <= P; k <<= 1) {
@@ -151,22 +156,25 @@ __global__ void k_upper(int32_t n, const int32_t* __restrict__ rp0, const int32_
   }
 }
 
-// Warp per internal row: the caller's edge id of every slot.
-__global__ void k_slot_eid(int32_t n, int32_t m, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                           const int32_t* __restrict__ perm, const int32_t* __restrict__ rp0,
-                           const int32_t* __restrict__ ci0, const int32_t* __restrict__ first_up,
-                           const int32_t* __restrict__ up_off, int32_t* __restrict__ eid) {
+// Warp per internal row i (caller vertex x = perm[i]): the sorted keys split
+// into the row's internal ids and, for every slot whose caller labels ascend
+// (x < y), the caller's edge id from the caller position; the other slots get
+// 0 here and their reverse's id in the preparation.
+__global__ void k_split_eid(int32_t n, int32_t m, const int32_t* __restrict__ rp, const long long* __restrict__ kv,
+                            const int32_t* __restrict__ perm, const int32_t* __restrict__ rp0,
+                            const int32_t* __restrict__ first_up, const int32_t* __restrict__ up_off,
+                            int32_t* __restrict__ ci, int32_t* __restrict__ eid) {
   const int lane = threadIdx.x & 31;
   const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += warps) {
     const int32_t x = perm[i];
     for (int32_t s = rp[i] + lane; s < rp[i + 1]; s += 32) {
-      const int32_t y = perm[ci[s]];
-      int32_t id = 0;  // the slot of (y, x), x > y, takes its id from its reverse in k_edges
-      if (x < y) {
-        const int32_t q = lower_bound_dev(ci0, first_up[x], rp0[x + 1], y);
-        id = (q < rp0[x + 1] && ci0[q] == y) ? up_off[x] + (q - first_up[x]) : 0;
-      }
+      const long long key = kv[s];
+      const int32_t j = (int32_t)(key >> 32), pos = (int32_t)(key & 0xffffffffLL);
+      ci[s] = j;
+      const int32_t y = perm[j];
+      int32_t id = 0;
+      if (x < y) id = up_off[x] + (rp0[x] + pos - first_up[x]);
       eid[s] = (id >= 0 && id < m) ? id : 0;
     }
   }
@@ -184,10 +192,12 @@ int blocks_for(int64_t threads, int block) {
 gc_status relabel_on_device(int32_t n, int32_t m, const int32_t* d_rp0, const int32_t* d_ci0,
                             const int32_t* d_perm, const int32_t* d_newid, const int32_t* d_rp, int32_t* d_ci,
                             int32_t* d_eid, const int32_t* d_mid_rows, int32_t n_mid, const int32_t* d_long_rows,
-                            const int64_t* d_long_off, int32_t n_long, int32_t* d_tmp, cudaStream_t s) {
+                            const int64_t* d_long_off, int32_t n_long, long long* d_tmp, cudaStream_t s) {
   if (n <= 0) return GC_OK;
   cudaError_t e = cudaSuccess;
   int32_t *first_up = nullptr, *up_cnt = nullptr, *up_off = nullptr;
+  long long* kv = nullptr;
+  const int64_t nnz = 2 * (int64_t)m;
   gc_status st = GC_OK;
 #define RL_TRY(call, what)               \
   do {                                   \
@@ -197,16 +207,17 @@ gc_status relabel_on_device(int32_t n, int32_t m, const int32_t* d_rp0, const in
       goto out;                          \
     }                                    \
   } while (0)
-  k_fill_rows<<<blocks_for((int64_t)n * 32, 256), 256, 0, s>>>(n, d_rp0, d_ci0, d_perm, d_newid, d_rp, d_ci);
+  RL_TRY(pool_alloc(&kv, sizeof(long long) * (size_t)(nnz > 0 ? nnz : 1), s), "alloc relabel keys");
+  k_fill_rows<<<blocks_for((int64_t)n * 32, 256), 256, 0, s>>>(n, d_rp0, d_ci0, d_perm, d_newid, d_rp, kv);
   RL_TRY(cudaGetLastError(), "k_fill_rows");
-  k_sort_short<<<blocks_for((int64_t)n * 32, 256), 256, 0, s>>>(n, d_rp, d_ci);
+  k_sort_short<<<blocks_for((int64_t)n * 32, 256), 256, 0, s>>>(n, d_rp, kv);
   RL_TRY(cudaGetLastError(), "k_sort_short");
   if (n_mid > 0) {
-    k_sort_mid<<<n_mid, kMidThreads, 0, s>>>(d_mid_rows, d_rp, d_ci);
+    k_sort_mid<<<n_mid, kMidThreads, 0, s>>>(d_mid_rows, d_rp, kv);
     RL_TRY(cudaGetLastError(), "k_sort_mid");
   }
   if (n_long > 0) {
-    k_sort_long<<<n_long, kLongThreads, 0, s>>>(d_long_rows, d_long_off, d_rp, d_ci, d_tmp);
+    k_sort_long<<<n_long, kLongThreads, 0, s>>>(d_long_rows, d_long_off, d_rp, kv, d_tmp);
     RL_TRY(cudaGetLastError(), "k_sort_long");
   }
   RL_TRY(pool_alloc(&first_up, sizeof(int32_t) * (size_t)n, s), "alloc relabel");
@@ -215,12 +226,12 @@ gc_status relabel_on_device(int32_t n, int32_t m, const int32_t* d_rp0, const in
   k_upper<<<blocks_for(n, 256), 256, 0, s>>>(n, d_rp0, d_ci0, first_up, up_cnt);
   RL_TRY(cudaGetLastError(), "k_upper");
   if ((st = exclusive_scan(n, up_cnt, up_off, s)) != GC_OK) goto out;
-  k_slot_eid<<<blocks_for((int64_t)n * 32, 256), 256, 0, s>>>(n, m, d_rp, d_ci, d_perm, d_rp0, d_ci0, first_up,
-                                                             up_off, d_eid);
-  RL_TRY(cudaGetLastError(), "k_slot_eid");
+  k_split_eid<<<blocks_for((int64_t)n * 32, 256), 256, 0, s>>>(n, m, d_rp, kv, d_perm, d_rp0, first_up, up_off,
+                                                              d_ci, d_eid);
+  RL_TRY(cudaGetLastError(), "k_split_eid");
 out:
 #undef RL_TRY
-  for (void* p : {(void*)first_up, (void*)up_cnt, (void*)up_off})
+  for (void* p : {(void*)first_up, (void*)up_cnt, (void*)up_off, (void*)kv})
     if (p) cudaFreeAsync(p, s);
   return st;
 }
