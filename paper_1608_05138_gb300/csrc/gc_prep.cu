@@ -466,7 +466,6 @@ gc_status classify_c_units(int32_t n, const int32_t* d_rp, const int32_t* d_ci, 
   int32_t* dNX = nullptr;
   std::vector<long long> W(nu);
   std::vector<int32_t> NX(nu), U(nu), out;
-  out.reserve(nu);
   e = pool_alloc(&dW, sizeof(long long) * nu, s);
   if (e == cudaSuccess) e = pool_alloc(&dNX, sizeof(int32_t) * nu, s);
   if (e == cudaSuccess) {
@@ -485,53 +484,55 @@ gc_status classify_c_units(int32_t n, const int32_t* d_rp, const int32_t* d_ci, 
   // a CTA's worth of lower neighbours), against roughly 10 ns per wedge on an
   // SM for a wedge that goes through the vertex-indexed table in DRAM; the
   // hub kernel is taken when the wedges exceed blocks x max(1024, nx), about
-  // three times the break-even point. Units that fit the packed-key hash
-  // (below) stay there.
-  auto fits_hash2 = [&](int32_t k) {
-    return W[k] > kHashMaxW && W[k] <= kHash2MaxW && NX[k] < kHash2MaxNx && n <= kHash2MaxN;
-  };
-  std::vector<int32_t> heavy;
+  // three times the break-even point. One pass over the units, in unit
+  // order: the packed-key hash takes every unit it fits; the hub rule is
+  // tested (with its division) only from 16384 wedges; units without wedges
+  // add nothing to P and are left out.
+  std::vector<int32_t> heavy, hashed, hashed2, rest;
+  const long long tab = hub_tab_words();
   for (int32_t k = 0; k < nu; ++k) {
-    if (fits_hash2(k)) continue;
-    const long long span = (long long)hub_cpw(NX[k]) * hub_tab_words();
-    const long long blocks = ((long long)U[k] + span - 1) / span;
-    const long long per_block = NX[k] > 1024 ? NX[k] : 1024;
-    if (W[k] >= 16384 && W[k] >= blocks * per_block && NX[k] < (1 << 26)) heavy.push_back(k);
+    const long long w = W[k];
+    if (w <= 0) continue;
+    if (w <= kHashMaxW) {
+      hashed.push_back(k);
+      continue;
+    }
+    if (w <= kHash2MaxW && NX[k] < kHash2MaxNx && n <= kHash2MaxN) {
+      hashed2.push_back(k);
+      continue;
+    }
+    if (w >= 16384 && NX[k] < (1 << 26)) {
+      const long long span = (long long)hub_cpw(NX[k]) * tab;
+      const long long blocks = ((long long)U[k] + span - 1) / span;
+      const long long per_block = NX[k] > 1024 ? NX[k] : 1024;
+      if (w >= blocks * per_block) {
+        heavy.push_back(k);
+        continue;
+      }
+    }
+    rest.push_back(k);
   }
+  // hub units heaviest first, then the hashed units heaviest first, the
+  // packed-key hash units heaviest first, and the rest in unit order
   std::sort(heavy.begin(), heavy.end(), [&](int32_t a, int32_t b) { return W[a] > W[b]; });
-  std::vector<char> is_heavy(nu, 0);
+  sort_by_wedges_desc(&hashed, W, kHashMaxW);
+  sort_by_wedges_desc(&hashed2, W, kHash2MaxW);
+  out.reserve(heavy.size() + hashed.size() + hashed2.size() + rest.size());
+  std::vector<int32_t> hw;
+  hw.reserve(hashed.size() + hashed2.size());
   for (int32_t k : heavy) {
     out.push_back(U[k]);
-    is_heavy[k] = 1;
     if (NX[k] > p->cnx_max) p->cnx_max = NX[k];
   }
-  // Units of at most kHashMaxW wedges: the hashed kernel, heaviest first.
-  // Units without wedges add nothing to P and are left out.
-  std::vector<int32_t> hashed;
-  for (int32_t k = 0; k < nu; ++k)
-    if (!is_heavy[k] && W[k] > 0 && W[k] <= kHashMaxW) hashed.push_back(k);
-  sort_by_wedges_desc(&hashed, W, kHashMaxW);
-  std::vector<int32_t> hw;
-  hw.reserve(hashed.size());
   for (int32_t k : hashed) {
     out.push_back(U[k]);
     hw.push_back((int32_t)W[k]);
   }
-  // Units above it, with fewer than kHash2MaxNx lower neighbours (counts fit
-  // 10 bits) in a graph whose ids fit 22 bits: the packed-key hash, heaviest
-  // first. The rest stay on the vertex-indexed tables.
-  std::vector<int32_t> hashed2;
-  for (int32_t k = 0; k < nu; ++k)
-    if (fits_hash2(k)) hashed2.push_back(k);
-  sort_by_wedges_desc(&hashed2, W, kHash2MaxW);
-  std::vector<char> is_hashed2(nu, 0);
   for (int32_t k : hashed2) {
     out.push_back(U[k]);
     hw.push_back((int32_t)W[k]);
-    is_hashed2[k] = 1;
   }
-  for (int32_t k = 0; k < nu; ++k)
-    if (!is_heavy[k] && !is_hashed2[k] && W[k] > kHashMaxW) out.push_back(U[k]);
+  for (int32_t k : rest) out.push_back(U[k]);
   p->n_cheavy = (int32_t)heavy.size();
   p->n_chash = (int32_t)hashed.size();
   p->n_chash_big = 0;  // hashed is heaviest first
