@@ -105,3 +105,72 @@ def test_noalloc_wrapper_rejects_bad_tensors_before_the_call():
     for args, words in cases:
         with pytest.raises(ValueError, match=re.escape(words)):
             gcb.gc_edge_triangles_noalloc(*args)
+
+
+def _first_violation(rp, ci):
+    """The code and message of the first entry (in row order) that breaks a
+    linear check, range, self-loop, duplicate, order in that priority, the
+    contract of include/gc.h (numpy)."""
+    n = len(rp) - 1
+    rows = np.repeat(np.arange(n), np.diff(rp))
+    ci64 = ci.astype(np.int64)
+    start = np.zeros(len(ci), bool)
+    start[rp[:-1][np.diff(rp) > 0]] = True
+    prev = np.concatenate([[0], ci64[:-1]])
+    rng = (ci64 < 0) | (ci64 >= n)
+    loop = ci64 == rows
+    dup = ~start & (prev == ci64)
+    desc = ~start & (prev > ci64)
+    bad = np.flatnonzero(rng | loop | dup | desc)
+    if len(bad) == 0:
+        return None
+    p = bad[0]
+    x, y = int(rows[p]), int(ci[p])
+    if rng[p]:
+        return -6, f"column {y} out of range in row {x}"
+    if loop[p]:
+        return -4, f"self-loop at vertex {x}"
+    if dup[p]:
+        return -3, f"duplicate neighbour {y} in row {x}"
+    return -2, f"row {x} not ascending"
+
+
+def test_validation_of_corrupted_large_graphs(lib):
+    # more than 2^20 entries (the checks run in threads, with a branch-free
+    # pass per row and the entry-by-entry checks on a failing row): random
+    # corruptions, one or two rows at a time, give the first failure in row
+    # order with its code and message
+    import graphgen
+    rp0, ci0 = graphgen.er(20000, 0.003, 5)
+    assert len(ci0) > (1 << 20)
+    n = len(rp0) - 1
+    rng = np.random.default_rng(11)
+    deg = np.diff(rp0)
+    rows_ok = np.flatnonzero(deg >= 3)
+
+    def corrupt(ci, kind):
+        x = int(rng.choice(rows_ok))
+        b, e = int(rp0[x]), int(rp0[x + 1])
+        p = int(rng.integers(b + 1, e - 1))
+        if kind == 0:
+            ci[p] = n + int(rng.integers(0, 5))
+        elif kind == 1:
+            ci[p] = -1 - int(rng.integers(0, 5))
+        elif kind == 2:
+            ci[p] = x
+        elif kind == 3:
+            ci[p] = ci[p - 1]
+        else:
+            ci[p], ci[p + 1] = ci[p + 1], ci[p]
+
+    for trial in range(24):
+        ci = ci0.copy()
+        corrupt(ci, trial % 5)
+        if trial % 3 == 0:
+            corrupt(ci, int(rng.integers(0, 5)))
+        want = _first_violation(rp0, ci)
+        assert want is not None
+        with pytest.raises(gcb.GcError) as ei:
+            gcb.gc_graph_upload(rp0, ci)
+        assert ei.value.status == want[0], (trial, str(ei.value), want)
+        assert str(ei.value).endswith(want[1]), (trial, str(ei.value), want)
