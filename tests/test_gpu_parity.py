@@ -792,3 +792,42 @@ def test_memory_pool_keeps_blocks_until_released():
     gcb.gc_release_cached_memory()
     free2, _ = torch.cuda.mem_get_info()
     assert free2 > free1 and free0 - free2 < 64 << 20
+
+
+def test_batch_submit_many_randomized_corruptions():
+    # one graph of a bulk submission corrupted at random (range, self-loop,
+    # duplicate, order): refused with the code and message of its first
+    # failing entry in row order, naming that graph; nothing is admitted
+    from tests.test_abi import _first_violation
+    rng = np.random.default_rng(21)
+    gs = [graphgen.er(int(rng.integers(40, 400)), 0.1, 300 + i) for i in range(12)]
+    for trial in range(10):
+        k = int(rng.integers(0, len(gs)))
+        rp, ci = gs[k][0], gs[k][1].copy()
+        n = len(rp) - 1
+        x = int(rng.choice(np.flatnonzero(np.diff(rp) >= 3)))
+        p = int(rng.integers(rp[x] + 1, rp[x + 1] - 1))
+        kind = trial % 4
+        if kind == 0:
+            ci[p] = n + 2
+        elif kind == 1:
+            ci[p] = x
+        elif kind == 2:
+            ci[p] = ci[p - 1]
+        else:
+            ci[p], ci[p + 1] = ci[p + 1], ci[p]
+        code, msg = _first_violation(rp, ci)
+        parts = [(r, c) for r, c in gs]
+        parts[k] = (rp, ci)
+        nvert = np.array([len(r) - 1 for r, _ in parts], np.int32)
+        voff = np.concatenate([[0], np.cumsum([len(r) for r, _ in parts])]).astype(np.int64)
+        eoff = np.concatenate([[0], np.cumsum([len(c) for _, c in parts])]).astype(np.int64)
+        b = gcb.gc_batch_create(1 << 30, gcb.GC_BATCH_MANUAL)
+        try:
+            with pytest.raises(gcb.GcError) as ei:
+                gcb.gc_batch_submit_many(b, nvert, voff, eoff, np.concatenate([r for r, _ in parts]),
+                                         np.concatenate([c for _, c in parts]))
+            assert ei.value.status == code and str(ei.value).endswith(f"graph {k}: {msg}"), (str(ei.value), code, msg)
+            assert gcb.gc_batch_poll_many(b, np.zeros(0, np.uint64), timeout_us=0).shape == (0, 17, 2)
+        finally:
+            gcb.gc_batch_destroy(b)
