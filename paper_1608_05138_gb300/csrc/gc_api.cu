@@ -658,6 +658,8 @@ static gc_status count_graph(gc_graph g, uint64_t* per_edge_out, uint64_t* induc
   ku.n_chash = g->prep.n_chash;
   ku.n_chash2 = g->prep.n_chash2;
   ku.n_chash_big = g->prep.n_chash_big;
+  ku.n_chash_mid = g->prep.n_chash_mid;
+  ku.n_chash2_big = g->prep.n_chash2_big;
   ku.n_cunits = g->prep.n_cunits;
   for (int t = 0; t <= kNumTiers; ++t) ku.tier_off[t] = g->prep.ktier_off[t];
   if ((st = run_count(dg, g->prep.units, g->prep.n_units, ku, pe_dev, g->d_csum, g->d_x, &g->sc, s, g->ev, pe_host,

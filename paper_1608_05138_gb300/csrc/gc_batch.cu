@@ -264,6 +264,8 @@ gc_status run_union(std::vector<PendingGraph*>& graphs, cudaStream_t s, Launch* 
     ku.n_chash = prep.n_chash;
     ku.n_chash2 = prep.n_chash2;
     ku.n_chash_big = prep.n_chash_big;
+    ku.n_chash_mid = prep.n_chash_mid;
+    ku.n_chash2_big = prep.n_chash2_big;
     ku.n_cunits = prep.n_cunits;
     for (int t = 0; t <= kNumTiers; ++t) ku.tier_off[t] = prep.ktier_off[t];
     if ((st = run_count(dg, prep.units, prep.n_units, ku, nullptr, d_csum, d_x, &sc, s, nullptr)) != GC_OK) {

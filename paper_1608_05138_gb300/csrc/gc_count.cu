@@ -689,6 +689,7 @@ __global__ void __launch_bounds__(kHeavyBlock, 1) k_pass_c_heavy(DevGraph g, Cou
 constexpr int kHashBlock = 512;
 constexpr int kHashSlots = 2 * kHashMaxW;
 constexpr int kHashSmallBlock = 128;
+constexpr int kHashMidBlock = 256;
 
 __device__ __forceinline__ uint32_t o_hash(int32_t o, int bits) {
   return ((uint32_t)o * 0x9E3779B1u) >> (32 - bits);  // Fibonacci hashing
@@ -719,12 +720,13 @@ __device__ __forceinline__ int32_t hash_find(const int32_t* keys, int32_t o, uin
   return -1;
 }
 
-// Two instances: 512-thread CTAs, two an SM, with the table for kHashMaxW
-// wedges; and, for the many units of at most kHashSmallW wedges (on R-MAT
-// scale 22, 87 % of the hashed units and 10 % of their wedges), 128-thread
-// CTAs with a table for kHashSmallW, sixteen an SM, so that a unit's barriers
-// and latency chains no longer hold a large CTA. Units [k0, k1) of the
-// hashed list (heaviest first), taken from *cursor.
+// Three instances: 512-thread CTAs, two an SM, with the table for kHashMaxW
+// wedges; 256-thread CTAs, eight an SM, for units of at most kHashMidW; and,
+// for the many units of at most kHashSmallW wedges (on R-MAT scale 22, 87 %
+// of the hashed units and 10 % of their wedges), 128-thread CTAs with a table
+// for kHashSmallW, sixteen an SM, so that a unit's barriers and latency
+// chains no longer hold a large CTA. Units [k0, k1) of the hashed list
+// (heaviest first), taken from *cursor.
 template <int kThreads, int kMaxW>
 __global__ void __launch_bounds__(kThreads, kThreads == kHashBlock ? kCtasPerSm : 2048 / kThreads)
     k_pass_c_hash(DevGraph g, CountArgs a, int32_t k0, int32_t k1, int32_t* cursor) {
@@ -845,23 +847,29 @@ __device__ __forceinline__ uint32_t h2_count(const uint32_t* tab, int32_t o, uin
   return 0u;
 }
 
-__global__ void __launch_bounds__(kHash2Block, 1) k_pass_c_hash2(DevGraph g, CountArgs a) {
-  extern __shared__ uint32_t htab[];  // kHash2Slots packed (o, count) words
+// Two instances: 1024-thread CTAs with the whole table, one an SM; and
+// 512-thread CTAs with half of it, two an SM, for the units of at most
+// kHash2HalfMaxW wedges. Units [k0, k1) of the packed-key list (heaviest
+// first), taken from *cursor.
+template <int kThreads, int kSlots>
+__global__ void __launch_bounds__(kThreads, kThreads == kHash2Block ? 1 : 2)
+    k_pass_c_hash2(DevGraph g, CountArgs a, int32_t k0, int32_t k1, int32_t* cursor) {
+  extern __shared__ uint32_t htab[];  // kSlots packed (o, count) words
   __shared__ int32_t s_unit, s_next[2];
   const int lane = threadIdx.x & 31;
   long long w_wedge = 0;  // lane 0
   const int32_t first = a.n_cheavy + a.n_chash;
   for (;;) {
     __syncthreads();
-    if (threadIdx.x == 0) s_unit = atomicAdd(a.cursor + 15, 1);
+    if (threadIdx.x == 0) s_unit = k0 + atomicAdd(cursor, 1);
     __syncthreads();
     const int32_t k = s_unit;
-    if (k >= a.n_chash2) break;
+    if (k >= k1) break;
     const int32_t h = a.cunits[first + k];
     const int32_t wk = min(a.chash_w[a.n_chash + k], (int32_t)kHash2MaxW);
-    const uint32_t size = min((uint32_t)kHash2Slots, (uint32_t)(((long long)wk * 25 + 17) / 18) + 32u);
+    const uint32_t size = min((uint32_t)kSlots, (uint32_t)(((long long)wk * 25 + 17) / 18) + 32u);
     const int32_t hb = g.rp[h], he = g.rp[h + 1];
-    for (uint32_t i = threadIdx.x; i < size; i += kHash2Block) htab[i] = kHash2Empty;
+    for (uint32_t i = threadIdx.x; i < size; i += kThreads) htab[i] = kHash2Empty;
     if (threadIdx.x < 2) s_next[threadIdx.x] = hb;
     __syncthreads();
     // pass 0 counts cnt_h(o); pass 1 attributes cnt_h(o) - 1 to the slots
@@ -1033,21 +1041,36 @@ static gc_status launch_hash(const DevGraph& g, const CountArgs& a, int32_t k0, 
 
 gc_status run_pass_c_hash(const DevGraph& g, const CountArgs& a, cudaStream_t s) {
   if (a.n_chash <= 0) return GC_OK;
-  gc_status st = launch_hash<kHashBlock, kHashMaxW>(g, a, 0, a.n_chash_big, a.cursor + 9, s);
+  gc_status st = launch_hash<kHashBlock, kHashMaxW>(g, a, 0, a.n_chash_mid, a.cursor + 9, s);
+  if (st != GC_OK) return st;
+  st = launch_hash<kHashMidBlock, kHashMidW>(g, a, a.n_chash_mid, a.n_chash_big, a.cursor + 16, s);
   if (st != GC_OK) return st;
   return launch_hash<kHashSmallBlock, kHashSmallW>(g, a, a.n_chash_big, a.n_chash, a.cursor + 7, s);
 }
 
-gc_status run_pass_c_hash2(const DevGraph& g, const CountArgs& a, cudaStream_t s) {
-  if (a.n_chash2 <= 0) return GC_OK;
-  const size_t smem = sizeof(uint32_t) * kHash2Slots;
-  cudaError_t e = cudaFuncSetAttribute(k_pass_c_hash2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+template <int kThreads, int kSlots>
+static gc_status launch_hash2(const DevGraph& g, const CountArgs& a, int32_t k0, int32_t k1, int32_t* cursor,
+                              cudaStream_t s) {
+  if (k1 <= k0) return GC_OK;
+  auto kern = k_pass_c_hash2<kThreads, kSlots>;
+  const size_t smem = sizeof(uint32_t) * kSlots;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return cuda_fail(e, "k_pass_c_hash2");
-  int grid = count_grid_size() / kCtasPerSm;
-  if (grid > a.n_chash2) grid = a.n_chash2;
-  k_pass_c_hash2<<<grid, kHash2Block, smem, s>>>(g, a);
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
+  if (e != cudaSuccess) return cuda_fail(e, "k_pass_c_hash2 occupancy");
+  int grid = (per_sm > 0 ? per_sm : 1) * (count_grid_size() / kCtasPerSm);
+  if (grid > k1 - k0) grid = k1 - k0;
+  kern<<<grid, kThreads, smem, s>>>(g, a, k0, k1, cursor);
   e = cudaGetLastError();
   return e == cudaSuccess ? GC_OK : cuda_fail(e, "k_pass_c_hash2");
+}
+
+gc_status run_pass_c_hash2(const DevGraph& g, const CountArgs& a, cudaStream_t s) {
+  if (a.n_chash2 <= 0) return GC_OK;
+  gc_status st = launch_hash2<kHash2Block, kHash2Slots>(g, a, 0, a.n_chash2_big, a.cursor + 15, s);
+  if (st != GC_OK) return st;
+  return launch_hash2<kHash2Block / 2, kHash2HalfSlots>(g, a, a.n_chash2_big, a.n_chash2, a.cursor + 17, s);
 }
 
 gc_status run_finish(const DevGraph& g, const CountArgs& a, cudaStream_t s) {

@@ -53,8 +53,10 @@ struct CountArgs {
   int32_t n_cheavy;        // hub units of pass C (cunits[0 .. n_cheavy))
   const int32_t* chash_w;  // wedges of the hashed units cunits[n_cheavy .. n_cheavy + n_chash + n_chash2)
   int32_t n_chash;
+  int32_t n_chash_mid;     // hashed units of more than kHashMidW wedges (the first of them)
   int32_t n_chash_big;     // hashed units of more than kHashSmallW wedges (the first of them)
   int32_t n_chash2;        // units of the packed-key hash tier, after the hashed units
+  int32_t n_chash2_big;    // of them, units of more than kHash2HalfMaxW wedges (the first)
   const int4* cjobs;       // pass C hub kernel: jobs (hub index into cunits, first o-range block, blocks),
                            // heaviest first
   int32_t n_cjobs;
@@ -138,7 +140,7 @@ struct Scratch {
   int32_t* trio = nullptr;           // [m]
   unsigned long long* P = nullptr;   // [2m]
   unsigned long long* xc = nullptr;  // [m][2]
-  int32_t* misc = nullptr;           // [16] cursors, status
+  int32_t* misc = nullptr;           // [32] cursors, status
   int32_t* cbuf = nullptr;           // pass C hub cursors
   int32_t cbuf_nx = 0;
   uint32_t* tables = nullptr;        // count_grid_size() x table_n
@@ -181,8 +183,10 @@ struct KUnits {
   int32_t n_cjobs;
   const int32_t* chash_w;
   int32_t n_chash;
+  int32_t n_chash_mid;
   int32_t n_chash_big;
   int32_t n_chash2;
+  int32_t n_chash2_big;
   int32_t n_cunits;        // pass C units in all (units without wedges are left out)
 };
 // induced (optional): [m][10] rows of the per-edge induced counts of H_7..H_16
@@ -246,8 +250,10 @@ struct PrepBuffers {
   int32_t n_cjobs = 0;
   int32_t* chash_w = nullptr;  // wedges of each hashed unit (both hash tiers)
   int32_t n_chash = 0;
+  int32_t n_chash_mid = 0;     // hashed units of more than kHashMidW wedges
   int32_t n_chash_big = 0;     // hashed units of more than kHashSmallW wedges
   int32_t n_chash2 = 0;        // units of the packed-key hash tier
+  int32_t n_chash2_big = 0;    // of them, units of more than kHash2HalfMaxW wedges
   int32_t n_cunits = 0;
   int32_t cnx_max = 0;      // most lower neighbours of a hub unit
 };
@@ -327,6 +333,7 @@ __host__ __device__ __forceinline__ int hub_cpw(int64_t nx) { return nx < 1023 ?
 // o than wedges).
 constexpr int kHashMaxW = 8192;
 constexpr int kHashSmallW = 512;  // hashed units up to this many wedges run in small CTAs
+constexpr int kHashMidW = 2048;   // and up to this many in middle-sized CTAs
 gc_status run_pass_c_hash(const DevGraph& g, const CountArgs& a, cudaStream_t s);
 // Units of more than kHashMaxW and at most kHash2MaxW wedges, with fewer than
 // kHash2MaxNx lower neighbours, in graphs of at most 2^22 vertices: a
@@ -335,6 +342,10 @@ gc_status run_pass_c_hash(const DevGraph& g, const CountArgs& a, cudaStream_t s)
 constexpr int kHash2Slots = 57344;
 constexpr int kHash2MaxW = 41287;
 constexpr int kHash2MaxNx = 1023;
+// Packed-key units of at most kHash2HalfMaxW wedges fit half the table and
+// run in 512-thread CTAs, two an SM.
+constexpr int kHash2HalfSlots = 28672;
+constexpr int kHash2HalfMaxW = 20620;  // (kHash2HalfSlots - 32) * 18 / 25
 constexpr int32_t kHash2MaxN = 1 << 22;
 gc_status run_pass_c_hash2(const DevGraph& g, const CountArgs& a, cudaStream_t s);
 gc_status run_derive(const DevGraph& g, const unsigned long long* csum, unsigned long long* x,

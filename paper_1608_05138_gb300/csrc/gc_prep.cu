@@ -455,7 +455,9 @@ gc_status classify_c_units(int32_t n, const int32_t* d_rp, const int32_t* d_ci, 
   p->n_cheavy = 0;
   p->n_chash = 0;
   p->n_chash_big = 0;
+  p->n_chash_mid = 0;
   p->n_chash2 = 0;
+  p->n_chash2_big = 0;
   p->n_cunits = nu;
   p->cnx_max = 0;
   if (!ranked || n <= kSmemTableMax || nu == 0) {
@@ -537,7 +539,11 @@ gc_status classify_c_units(int32_t n, const int32_t* d_rp, const int32_t* d_ci, 
   p->n_chash = (int32_t)hashed.size();
   p->n_chash_big = 0;  // hashed is heaviest first
   while (p->n_chash_big < p->n_chash && W[hashed[(size_t)p->n_chash_big]] > kHashSmallW) ++p->n_chash_big;
+  p->n_chash_mid = 0;
+  while (p->n_chash_mid < p->n_chash_big && W[hashed[(size_t)p->n_chash_mid]] > kHashMidW) ++p->n_chash_mid;
   p->n_chash2 = (int32_t)hashed2.size();
+  p->n_chash2_big = 0;  // heaviest first too
+  while (p->n_chash2_big < p->n_chash2 && W[hashed2[(size_t)p->n_chash2_big]] > kHash2HalfMaxW) ++p->n_chash2_big;
   p->n_cunits = (int32_t)out.size();
   // Hub units cut into jobs of consecutive o-range blocks (the finer
   // granularity of Sec. 4.4: one hub's work spread over several CTAs), so

@@ -66,7 +66,7 @@ gc_status scratch_init(Scratch* sc, int32_t m, int32_t table_n, int32_t kmax, in
   GS_TRY(pool_alloc(&sc->trio, sizeof(int32_t) * m1, s));
   GS_TRY(pool_alloc(&sc->P, sizeof(unsigned long long) * 2 * m1, s));
   GS_TRY(pool_alloc(&sc->xc, sizeof(unsigned long long) * 2 * m1, s));
-  GS_TRY(pool_alloc(&sc->misc, sizeof(int32_t) * 16, s));
+  GS_TRY(pool_alloc(&sc->misc, sizeof(int32_t) * 32, s));
   GS_TRY(pool_alloc(&sc->work, sizeof(unsigned long long) * kNumWork, s));
   if (table_n > kSmemTableMax) {
     sc->tables_n = (size_t)count_grid_size() * (size_t)table_n;
@@ -128,13 +128,16 @@ gc_status run_count(const DevGraph& g, const int32_t* units, int32_t n_units, co
   a.chash_w = ku.chash_w;
   a.n_chash = ku.n_chash;
   a.n_chash_big = ku.n_chash_big;
+  a.n_chash_mid = ku.n_chash_mid;
+  a.n_chash2_big = ku.n_chash2_big;
   a.n_chash2 = ku.n_chash2;
   a.cbuf = sc->cbuf;
   a.cbuf_nx = sc->cbuf_nx;
   a.hub_tab = hub_tab_words();
   for (int t = 0; t <= kNumTiers; ++t) a.ktier_off[t] = ku.tier_off[t];
   a.cursor = sc->misc;  // [0] pass C, [2 + tier] pass K, [8] pass C hubs, [9] pass C hashed, [10 + tier] pass T,
-                        // [15] pass C packed-key hash, [7] pass C hashed small units
+                        // [15] pass C packed-key hash, [7] pass C hashed small units,
+                        // [16] pass C hashed middle units, [17] pass C packed-key hash, half tables
   a.status = sc->misc + 1;
   a.tables = g.table_n > kSmemTableMax ? sc->tables : nullptr;
   a.trio = sc->trio;
@@ -195,7 +198,7 @@ gc_status run_count(const DevGraph& g, const int32_t* units, int32_t n_units, co
   a.csum = csum;
   a.work = sc->work;
   const size_t m1 = (size_t)(g.m > 0 ? g.m : 1);
-  GR_TRY(cudaMemsetAsync(sc->misc, 0, sizeof(int32_t) * 16, s), "memset misc");
+  GR_TRY(cudaMemsetAsync(sc->misc, 0, sizeof(int32_t) * 32, s), "memset misc");
   GR_TRY(cudaMemsetAsync(sc->work, 0, sizeof(unsigned long long) * kNumWork, s), "memset work");
   GR_TRY(cudaMemsetAsync(csum, 0, sizeof(unsigned long long) * 26 * (size_t)g.G, s), "memset sums");
   GR_TRY(cudaMemsetAsync(sc->P, 0, sizeof(unsigned long long) * 2 * m1, s), "zero P");
