@@ -435,6 +435,129 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
+// The counts of one chunk's runs: lane l's run is [st, st + L) of Gamma(x)
+// for its x (L = 0 for none); runs of 32 or more entries are taken by the
+// whole warp one at a time, the shorter ones dealt to the lanes end to end.
+template <int kCpw>
+__device__ __forceinline__ void count_chunk(const DevGraph& g, uint32_t* tab, int32_t* comp, int32_t st, int32_t L,
+                                            int32_t lo_id, int lane) {
+  // runs of 32 or more entries (most of the wedges): the whole warp,
+  // one run at a time, consecutive entries over the lanes
+  unsigned lm = __ballot_sync(0xffffffffu, L >= 32);
+  while (lm) {
+    const int src = __ffs(lm) - 1;
+    lm &= lm - 1;
+    const int32_t s0 = __shfl_sync(0xffffffffu, st, src);
+    const int32_t n0 = __shfl_sync(0xffffffffu, L, src);
+    for (int32_t k0 = 0; k0 < n0; k0 += 256) {  // eight windows of loads in flight
+      int32_t o[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int32_t kk = k0 + 32 * j + lane;
+        o[j] = kk < n0 ? g.ci[s0 + kk] : -1;
+      }
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        if (o[j] >= 0) add_count<kCpw>(tab, o[j] - lo_id);
+    }
+  }
+  // shorter runs dealt to the lanes end to end
+  const int32_t Ls = L < 32 ? L : 0;
+  const Deal d = deal_setup(Ls, comp, lane);
+  const int32_t sb = st - d.excl;  // slot of position kk of this lane's run: sb + kk
+  int before = 0;
+  for (int32_t k0 = 0; k0 < d.total; k0 += 128) {
+    int32_t q[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int ol = deal_owner(d, Ls, k0 + 32 * j, comp, lane, before);
+      const int32_t kk = k0 + 32 * j + lane;
+      const int32_t bj = __shfl_sync(0xffffffffu, sb, ol);
+      q[j] = kk < d.total ? bj + kk : -1;
+    }
+    int32_t o[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) o[j] = q[j] >= 0 ? g.ci[q[j]] : lo_id;
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (q[j] >= 0) add_count<kCpw>(tab, o[j] - lo_id);
+  }
+}
+
+// The attribution of one chunk's wedges (runs as in count_chunk; lane l's x
+// is the i-th lower neighbour, i < nx): cnt_h(o) - 1 to the slot (x, o) of
+// each wedge, and the sum over the run to the slot (h, x).
+template <int kCpw>
+__device__ __forceinline__ void attr_chunk(const DevGraph& g, const CountArgs& a, uint32_t* tab,
+                                           unsigned long long* sx, uint32_t* sx32, int32_t* comp, int32_t st,
+                                           int32_t L, int32_t i, int32_t nx, int32_t hb, int32_t lo_id, int lane) {
+  sx[lane] = 0ull;  // per x of the chunk: sum of its wedges' counts
+  sx32[lane] = 0u;
+  __syncwarp();
+  // runs of 32 or more entries: the whole warp, one run at a time
+  unsigned lm = __ballot_sync(0xffffffffu, L >= 32);
+  while (lm) {
+    const int src = __ffs(lm) - 1;
+    lm &= lm - 1;
+    const int32_t s0 = __shfl_sync(0xffffffffu, st, src);
+    const int32_t n0 = __shfl_sync(0xffffffffu, L, src);
+    unsigned long long acc = 0ull;
+    for (int32_t k0 = 0; k0 < n0; k0 += 256) {  // eight windows of loads in flight
+      int32_t o[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int32_t kk = k0 + 32 * j + lane;
+        o[j] = kk < n0 ? g.ci[s0 + kk] : -1;
+      }
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        if (o[j] < 0) continue;
+        const uint32_t cnt = read_count<kCpw>(tab, o[j] - lo_id) - 1u;
+        if (cnt) {
+          atomicAdd(&a.P[s0 + k0 + 32 * j + lane], (unsigned long long)cnt);  // slot (x, o)
+          acc += cnt;
+        }
+      }
+    }
+    for (int off = 16; off; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if (lane == src) sx[lane] += acc;
+  }
+  __syncwarp();
+  // shorter runs dealt to the lanes end to end
+  const int32_t Ls = L < 32 ? L : 0;
+  const Deal d = deal_setup(Ls, comp, lane);
+  const int32_t sb = st - d.excl;  // slot of position kk of this lane's run: sb + kk
+  int before = 0;
+  for (int32_t k0 = 0; k0 < d.total; k0 += 128) {
+    int32_t q[4], ol[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      ol[j] = deal_owner(d, Ls, k0 + 32 * j, comp, lane, before);
+      const int32_t kk = k0 + 32 * j + lane;
+      const int32_t bj = __shfl_sync(0xffffffffu, sb, ol[j]);
+      q[j] = kk < d.total ? bj + kk : -1;
+    }
+    int32_t o[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) o[j] = q[j] >= 0 ? g.ci[q[j]] : lo_id;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (q[j] >= 0) {
+        const uint32_t cnt = read_count<kCpw>(tab, o[j] - lo_id) - 1u;
+        if (cnt) {
+          atomicAdd(&a.P[q[j]], (unsigned long long)cnt);  // slot (x, o)
+          atomicAdd(&sx32[ol[j]], cnt);                    // the owner's sum
+        }
+      }
+    }
+  }
+  __syncwarp();
+  if (i < nx) {
+    const unsigned long long sum = sx[lane] + sx32[lane];
+    if (sum) atomicAdd(&a.P[hb + i], sum);  // slot (h, x)
+  }
+}
+
 // One block [lo_id, r1) of a hub job: the counts of the block from each
 // x's run in it (found by galloping search from the x's cursor), then the
 // attribution of the block's wedges. Called by the whole CTA after the
@@ -463,47 +586,7 @@ __device__ __forceinline__ void hub_block(const DevGraph& g, const CountArgs& a,
       beg[i] = st;
       cur[i] = en;
     }
-    // runs of 32 or more entries (most of the wedges): the whole warp,
-    // one run at a time, consecutive entries over the lanes
-    unsigned lm = __ballot_sync(0xffffffffu, L >= 32);
-    while (lm) {
-      const int src = __ffs(lm) - 1;
-      lm &= lm - 1;
-      const int32_t s0 = __shfl_sync(0xffffffffu, st, src);
-      const int32_t n0 = __shfl_sync(0xffffffffu, L, src);
-      for (int32_t k0 = 0; k0 < n0; k0 += 256) {  // eight windows of loads in flight
-        int32_t o[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const int32_t kk = k0 + 32 * j + lane;
-          o[j] = kk < n0 ? g.ci[s0 + kk] : -1;
-        }
-#pragma unroll
-        for (int j = 0; j < 8; ++j)
-          if (o[j] >= 0) add_count<kCpw>(tab, o[j] - lo_id);
-      }
-    }
-    // shorter runs dealt to the lanes end to end
-    const int32_t Ls = L < 32 ? L : 0;
-    const Deal d = deal_setup(Ls, comp, lane);
-    const int32_t sb = st - d.excl;  // slot of position kk of this lane's run: sb + kk
-    int before = 0;
-    for (int32_t k0 = 0; k0 < d.total; k0 += 128) {
-      int32_t q[4];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int ol = deal_owner(d, Ls, k0 + 32 * j, comp, lane, before);
-        const int32_t kk = k0 + 32 * j + lane;
-        const int32_t bj = __shfl_sync(0xffffffffu, sb, ol);
-        q[j] = kk < d.total ? bj + kk : -1;
-      }
-      int32_t o[4];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) o[j] = q[j] >= 0 ? g.ci[q[j]] : lo_id;
-#pragma unroll
-      for (int j = 0; j < 4; ++j)
-        if (q[j] >= 0) add_count<kCpw>(tab, o[j] - lo_id);
-    }
+    count_chunk<kCpw>(g, tab, comp, st, L, lo_id, lane);
     __syncwarp();
   }
   __syncthreads();
@@ -519,73 +602,32 @@ __device__ __forceinline__ void hub_block(const DevGraph& g, const CountArgs& a,
       st = beg[i];
       L = cur[i] - st;
     }
-    sx[lane] = 0ull;  // per x of the chunk: sum of its wedges' counts
-    sx32[lane] = 0u;
-    __syncwarp();
-    // runs of 32 or more entries: the whole warp, one run at a time
-    unsigned lm = __ballot_sync(0xffffffffu, L >= 32);
-    while (lm) {
-      const int src = __ffs(lm) - 1;
-      lm &= lm - 1;
-      const int32_t s0 = __shfl_sync(0xffffffffu, st, src);
-      const int32_t n0 = __shfl_sync(0xffffffffu, L, src);
-      unsigned long long acc = 0ull;
-      for (int32_t k0 = 0; k0 < n0; k0 += 256) {  // eight windows of loads in flight
-        int32_t o[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const int32_t kk = k0 + 32 * j + lane;
-          o[j] = kk < n0 ? g.ci[s0 + kk] : -1;
-        }
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          if (o[j] < 0) continue;
-          const uint32_t cnt = read_count<kCpw>(tab, o[j] - lo_id) - 1u;
-          if (cnt) {
-            atomicAdd(&a.P[s0 + k0 + 32 * j + lane], (unsigned long long)cnt);  // slot (x, o)
-            acc += cnt;
-          }
-        }
-      }
-      for (int off = 16; off; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-      if (lane == src) sx[lane] += acc;
-    }
-    __syncwarp();
-    // shorter runs dealt to the lanes end to end
-    const int32_t Ls = L < 32 ? L : 0;
-    const Deal d = deal_setup(Ls, comp, lane);
-    const int32_t sb = st - d.excl;  // slot of position kk of this lane's run: sb + kk
-    int before = 0;
-    for (int32_t k0 = 0; k0 < d.total; k0 += 128) {
-      int32_t q[4], ol[4];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        ol[j] = deal_owner(d, Ls, k0 + 32 * j, comp, lane, before);
-        const int32_t kk = k0 + 32 * j + lane;
-        const int32_t bj = __shfl_sync(0xffffffffu, sb, ol[j]);
-        q[j] = kk < d.total ? bj + kk : -1;
-      }
-      int32_t o[4];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) o[j] = q[j] >= 0 ? g.ci[q[j]] : lo_id;
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        if (q[j] >= 0) {
-          const uint32_t cnt = read_count<kCpw>(tab, o[j] - lo_id) - 1u;
-          if (cnt) {
-            atomicAdd(&a.P[q[j]], (unsigned long long)cnt);  // slot (x, o)
-            atomicAdd(&sx32[ol[j]], cnt);                    // the owner's sum
-          }
-        }
-      }
-    }
-    __syncwarp();
-    if (i < nx) {
-      const unsigned long long sum = sx[lane] + sx32[lane];
-      if (sum) atomicAdd(&a.P[hb + i], sum);  // slot (h, x)
-    }
+    attr_chunk<kCpw>(g, a, tab, sx, sx32, comp, st, L, i, nx, hb, lo_id, lane);
     __syncwarp();
   }
+}
+
+// One block of a hub of at most 1024 lower neighbours: warp w always takes
+// the chunk x = w, w + 32, ..., so each thread keeps its x's cursor (cur) and
+// run in registers across the two phases and the blocks of the job. Called
+// by the whole CTA after the table is zeroed (and a barrier).
+template <int kCpw>
+__device__ __forceinline__ void hub_block_small(const DevGraph& g, const CountArgs& a, uint32_t* tab,
+                                                unsigned long long* sx, uint32_t* sx32, int32_t* comp,
+                                                int32_t& cur, int32_t endx, int32_t i, int32_t nx, int32_t hb,
+                                                int32_t lo_id, int32_t r1, int lane) {
+  int32_t st = 0, L = 0, en = cur;
+  if (i < nx) {
+    st = cur;
+    en = gallop_lower_bound(g.ci, st, endx, r1);
+    L = en - st;
+  }
+  count_chunk<kCpw>(g, tab, comp, st, L, lo_id, lane);
+  __syncwarp();
+  __syncthreads();
+  attr_chunk<kCpw>(g, a, tab, sx, sx32, comp, st, L, i, nx, hb, lo_id, lane);
+  __syncwarp();
+  cur = en;
 }
 
 __global__ void __launch_bounds__(kHeavyBlock, 1) k_pass_c_heavy(DevGraph g, CountArgs a) {
@@ -631,13 +673,28 @@ __global__ void __launch_bounds__(kHeavyBlock, 1) k_pass_c_heavy(DevGraph g, Cou
     const int32_t span = cpw * a.hub_tab;
     const int64_t job_lo = (int64_t)job.y * span;                       // the job's o-range
     const int64_t job_hi = min((int64_t)h, job_lo + (int64_t)job.z * span);
-    for (int32_t i = threadIdx.x; i < nx; i += kHeavyBlock) {
-      const int32_t x = g.ci[hb + i];
-      const int32_t xb = g.rp[x];
-      const int32_t lo = min(max(g.rev[hb + i], xb), g.rp[x + 1]);  // Gamma(x) below the slot of (x, h) is < h
-      cur[i] = job.y == 0 ? xb : gallop_lower_bound(g.ci, xb, lo, (int32_t)job_lo);
-      endp[i] = lo;
-      if (job.y == 0) w_wedge += lo - xb;  // the hub's wedges, counted by its first job
+    // at most 1024 lower neighbours: this thread's x (chunk = warp) and its
+    // cursor in registers; otherwise the cursors of all x in the CTA's buffers
+    const bool small = nchunks == kHeavyWarps;
+    const int32_t ix = warp + kHeavyWarps * lane;
+    int32_t rcur = 0, rend = 0;
+    if (small) {
+      if (ix < nx) {
+        const int32_t x = g.ci[hb + ix];
+        const int32_t xb = g.rp[x];
+        rend = min(max(g.rev[hb + ix], xb), g.rp[x + 1]);  // Gamma(x) below the slot of (x, h) is < h
+        rcur = job.y == 0 ? xb : gallop_lower_bound(g.ci, xb, rend, (int32_t)job_lo);
+        if (job.y == 0) w_wedge += rend - xb;  // the hub's wedges, counted by its first job
+      }
+    } else {
+      for (int32_t i = threadIdx.x; i < nx; i += kHeavyBlock) {
+        const int32_t x = g.ci[hb + i];
+        const int32_t xb = g.rp[x];
+        const int32_t lo = min(max(g.rev[hb + i], xb), g.rp[x + 1]);  // Gamma(x) below the slot of (x, h) is < h
+        cur[i] = job.y == 0 ? xb : gallop_lower_bound(g.ci, xb, lo, (int32_t)job_lo);
+        endp[i] = lo;
+        if (job.y == 0) w_wedge += lo - xb;  // the hub's wedges, counted by its first job
+      }
     }
     if (threadIdx.x == 0) ++w_jobs;
     for (int64_t lo64 = job_lo; lo64 < job_hi; lo64 += span) {
@@ -651,7 +708,12 @@ __global__ void __launch_bounds__(kHeavyBlock, 1) k_pass_c_heavy(DevGraph g, Cou
         s_chunk[1] = 0;
       }
       __syncthreads();
-      if (cpw == 3)
+      if (small) {
+        if (cpw == 3)
+          hub_block_small<3>(g, a, tab, s_sx[warp], s_sx32[warp], comp, rcur, rend, ix, nx, hb, lo_id, r1, lane);
+        else
+          hub_block_small<2>(g, a, tab, s_sx[warp], s_sx32[warp], comp, rcur, rend, ix, nx, hb, lo_id, r1, lane);
+      } else if (cpw == 3)
         hub_block<3>(g, a, tab, s_chunk, s_sx[warp], s_sx32[warp], comp, beg, cur, endp, nx, nchunks, hb, lo_id, r1,
                      lane);
       else if (cpw == 2)
