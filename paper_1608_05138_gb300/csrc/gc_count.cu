@@ -338,10 +338,11 @@ __global__ void __launch_bounds__(kBlock) k_pass_c(DevGraph g, CountArgs a) {
 // memory from each x's run of o in the block (a per-x cursor walks Gamma(x)
 // once over all blocks; the end of the run is found by galloping search),
 // then the wedges of the block are attributed with the block's counts.
-// In both phases a warp takes a chunk of up to 32 x's at a time (from a
-// shared counter; heaviest first, or interleaved for a hub of at most 1024
-// x's, so that the warps carry equal work): runs of 32 or more entries are
-// taken by the whole warp one
+// In both phases a warp works on a chunk of up to 32 x's: for a hub of more
+// than 1024 x's it takes chunks from a shared counter, heaviest first; for a
+// smaller hub each warp keeps one chunk, x = w, w + 32, ..., with its cursors
+// in registers, so that the warps carry equal work. Runs of 32 or more
+// entries are taken by the whole warp one
 // at a time, the shorter ones are dealt to its lanes end to end, so that run
 // lengths, however skewed, do not leave lanes idle, and the P atomics of
 // consecutive lanes hit consecutive slots. The per-x sums of the attribution
@@ -560,12 +561,11 @@ __device__ __forceinline__ void attr_chunk(const DevGraph& g, const CountArgs& a
 
 // One block [lo_id, r1) of a hub job: the counts of the block from each
 // x's run in it (found by galloping search from the x's cursor), then the
-// attribution of the block's wedges. Called by the whole CTA after the
-// table is zeroed and the chunk counters reset (and a barrier). A hub of
-// more than 1024 lower neighbours has chunks of 32 consecutive x's, taken
-// heaviest first (X ascends by degree); a smaller one has one chunk per
-// warp, chunk c holding x = c, c + 32, ..., so that every warp gets the same
-// mix of light and heavy x's.
+// attribution of the block's wedges, for a hub of more than 1024 lower
+// neighbours: chunks of 32 consecutive x's taken heaviest first (X ascends
+// by degree), their cursors in the CTA's buffers (a smaller hub runs
+// hub_block_small). Called by the whole CTA after the table is zeroed and
+// the chunk counters reset (and a barrier).
 template <int kCpw>
 __device__ __forceinline__ void hub_block(const DevGraph& g, const CountArgs& a, uint32_t* tab, int32_t* s_chunk,
                                           unsigned long long* sx, uint32_t* sx32, int32_t* comp, int32_t* beg,
@@ -577,7 +577,7 @@ __device__ __forceinline__ void hub_block(const DevGraph& g, const CountArgs& a,
     if (lane == 0) c = atomicAdd(&s_chunk[0], 1);
     c = __shfl_sync(0xffffffffu, c, 0);
     if (c >= nchunks) break;
-    const int32_t i = nchunks == kHeavyWarps ? c + kHeavyWarps * lane : (nchunks - 1 - c) * 32 + lane;
+    const int32_t i = (nchunks - 1 - c) * 32 + lane;
     int32_t st = 0, L = 0;
     if (i < nx) {
       st = cur[i];
@@ -596,7 +596,7 @@ __device__ __forceinline__ void hub_block(const DevGraph& g, const CountArgs& a,
     if (lane == 0) c = atomicAdd(&s_chunk[1], 1);
     c = __shfl_sync(0xffffffffu, c, 0);
     if (c >= nchunks) break;
-    const int32_t i = nchunks == kHeavyWarps ? c + kHeavyWarps * lane : (nchunks - 1 - c) * 32 + lane;
+    const int32_t i = (nchunks - 1 - c) * 32 + lane;
     int32_t st = 0, L = 0;
     if (i < nx) {
       st = beg[i];
