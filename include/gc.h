@@ -241,7 +241,10 @@ gc_status gc_batch_submit(gc_batch b, int32_t n, const int32_t* row_ptr, const i
  * col_idx[eoff[g] .. eoff[g + 1]). All graphs are validated (in parallel)
  * and admitted together, or none is: the first invalid graph's error is
  * returned (message names its index), GC_ERR_BUSY if they do not fit in the
- * budget now. tickets_out receives G tickets. Host pointers; copied. */
+ * budget now. tickets_out receives G tickets. Host pointers; copied into a
+ * host buffer that the batch keeps for reuse once the graphs retire (at most
+ * four such buffers, the smallest given back first; all freed by
+ * gc_batch_destroy once no graph holds them). */
 gc_status gc_batch_submit_many(gc_batch b, int64_t G, const int32_t* nvert, const int64_t* voff, const int64_t* eoff,
                                const int32_t* row_ptr, const int32_t* col_idx, uint64_t* tickets_out);
 gc_status gc_batch_flush(gc_batch b);

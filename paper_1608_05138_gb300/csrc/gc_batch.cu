@@ -48,11 +48,62 @@ __global__ void k_globalize(int32_t n, const int32_t* __restrict__ rp, const int
   }
 }
 
+// Host buffers for the library's copies of bulk submissions, kept for reuse:
+// a submission takes the smallest kept buffer that holds it, whose pages are
+// already mapped, instead of a fresh allocation that every submission would
+// fault in again. Buffers are not initialised (the copy that fills a buffer
+// writes every entry it reads). At most kKeep buffers are kept, the smallest
+// dropped first; the cache lives until the batch and its last buffer are gone.
+struct HostCache {
+  static constexpr int kKeep = 4;
+  std::mutex mu;
+  std::vector<std::pair<size_t, int32_t*>> free;  // (entries, buffer)
+  ~HostCache() {
+    for (auto& f : free) delete[] f.second;
+  }
+};
+
+// A buffer of at least `entries` int32 from the cache (or new); it returns to
+// the cache when its last reference goes. Throws std::bad_alloc.
+std::shared_ptr<int32_t> host_buffer(const std::shared_ptr<HostCache>& cache, size_t entries) {
+  if (entries == 0) entries = 1;
+  int32_t* p = nullptr;
+  size_t cap = 0;
+  {
+    std::lock_guard<std::mutex> lk(cache->mu);
+    int best = -1;
+    for (int i = 0; i < (int)cache->free.size(); ++i)
+      if (cache->free[i].first >= entries && (best < 0 || cache->free[i].first < cache->free[best].first)) best = i;
+    if (best >= 0) {
+      cap = cache->free[best].first;
+      p = cache->free[best].second;
+      cache->free.erase(cache->free.begin() + best);
+    }
+  }
+  if (!p) {
+    p = new int32_t[entries];
+    cap = entries;
+  }
+  std::shared_ptr<HostCache> keep = cache;
+  return std::shared_ptr<int32_t>(p, [keep, cap](int32_t* q) {
+    std::lock_guard<std::mutex> lk(keep->mu);
+    keep->free.emplace_back(cap, q);
+    if ((int)keep->free.size() > HostCache::kKeep) {
+      auto it = std::min_element(keep->free.begin(), keep->free.end(),
+                                 [](const std::pair<size_t, int32_t*>& a, const std::pair<size_t, int32_t*>& b) {
+                                   return a.first < b.first;
+                                 });
+      delete[] it->second;
+      keep->free.erase(it);
+    }
+  });
+}
+
 // A graph waiting for a launch. Its CSR is the library's own copy: rp (n + 1
 // entries starting at 0) and ci (2m entries) point into `owner` -- a copy of
 // one graph (gc_batch_submit), or one shared copy of a whole bulk submission
-// (gc_batch_submit_many: one allocation and two bulk copies instead of one
-// pair per graph).
+// (gc_batch_submit_many: one buffer from the batch's host cache and one bulk
+// copy per graph, made while validating).
 struct PendingGraph {
   uint64_t ticket;
   int32_t n;
@@ -60,7 +111,7 @@ struct PendingGraph {
   int64_t bytes;
   const int32_t* rp = nullptr;
   const int32_t* ci = nullptr;
-  std::shared_ptr<std::vector<int32_t>> owner;
+  std::shared_ptr<int32_t> owner;
 };
 
 struct Result {
@@ -148,6 +199,7 @@ struct gc_batch_s {
   cudaStream_t streams[kMaxInflight] = {};
   int next_stream = 0;                  // manual mode: round-robin over the slots
   int device = 0;
+  std::shared_ptr<HostCache> host = std::make_shared<HostCache>();  // bulk-submission copies
 };
 
 namespace {
@@ -721,15 +773,15 @@ gc_status gc_batch_submit(gc_batch b, int32_t n, const int32_t* row_ptr, const i
   pg.m = m;
   pg.bytes = bytes;
   try {
-    pg.owner = std::make_shared<std::vector<int32_t>>((size_t)n + 1 + 2 * (size_t)m);
+    pg.owner = std::shared_ptr<int32_t>(new int32_t[(size_t)n + 1 + 2 * (size_t)m], std::default_delete<int32_t[]>());
   } catch (...) {
     set_error("host allocation failed");
     return GC_ERR_NOMEM;
   }
-  std::memcpy(pg.owner->data(), row_ptr, sizeof(int32_t) * ((size_t)n + 1));
-  if (m > 0) std::memcpy(pg.owner->data() + n + 1, col_idx, sizeof(int32_t) * 2 * (size_t)m);
-  pg.rp = pg.owner->data();
-  pg.ci = pg.owner->data() + n + 1;
+  std::memcpy(pg.owner.get(), row_ptr, sizeof(int32_t) * ((size_t)n + 1));
+  if (m > 0) std::memcpy(pg.owner.get() + n + 1, col_idx, sizeof(int32_t) * 2 * (size_t)m);
+  pg.rp = pg.owner.get();
+  pg.ci = pg.owner.get() + n + 1;
   {
     std::lock_guard<std::mutex> lk(b->mu);
     if (b->in_use + bytes > b->budget) {
@@ -766,15 +818,15 @@ gc_status gc_batch_submit_many(gc_batch b, int64_t G, const int32_t* nvert, cons
     own_v[g + 1] = own_v[g] + n + 1;
     own_e[g + 1] = own_e[g] + (eoff[g + 1] - eoff[g]);
   }
-  std::shared_ptr<std::vector<int32_t>> owner;
+  std::shared_ptr<int32_t> owner;
   try {
-    owner = std::make_shared<std::vector<int32_t>>((size_t)(own_v[G] + own_e[G]));
+    owner = host_buffer(b->host, (size_t)(own_v[G] + own_e[G]));
   } catch (...) {
     set_error("host allocation failed");
     return GC_ERR_NOMEM;
   }
-  int32_t* own_rp = owner->data();
-  int32_t* own_ci = owner->data() + own_v[G];
+  int32_t* own_rp = owner.get();
+  int32_t* own_ci = owner.get() + own_v[G];
   std::vector<PendingGraph> pgs((size_t)G);
   unsigned hw = std::thread::hardware_concurrency();
   const int nt = (int)std::min<int64_t>(std::max(1u, std::min(hw, 32u)), G);
