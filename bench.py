@@ -122,8 +122,8 @@ def measured_traffic(phase: str, workload: str, scale: int):
     """DRAM bytes per count of a phase from the committed ncu counters
     (profiles/roofline_traffic_rmat20.txt, R-MAT scale 20), or None when the
     workload differs or the kernel sources changed since the counters were
-    taken. The bytes per wedge grow with the scale (1.36 at 19, 4.82 at 20
-    for the hub kernel), so they are not scaled to another size."""
+    taken. The bytes per wedge grow with the scale (about 1.4 at 19 and 5 at
+    20 for the hub kernel), so they are not scaled to another size."""
     path = os.path.join(ROOT, TRAFFIC_FILE)
     if workload != "rmat22" or scale != TRAFFIC_SCALE or not os.path.exists(path):
         return None
