@@ -88,6 +88,21 @@ const char* gc_last_error(void);
 gc_status gc_graph_upload(int32_t n, const int32_t* row_ptr, const int32_t* col_idx,
                           uint32_t flags, void* stream, gc_graph* out);
 
+/*
+ * The host checks of gc_graph_upload alone, with no device work: row_ptr[0]
+ * == 0, row_ptr ascending, row_ptr[n] even, every column in [0, n), rows
+ * strictly ascending without self-loops, and every entry (x, y) matched by
+ * (y, x). Host pointers, read only. Graphs of fewer than 2^20 entries get the
+ * single-threaded checks that every graph of gc_batch_submit_many gets, larger
+ * ones the multi-threaded checks of gc_graph_upload; both return the same
+ * code and message for the same graph. The message names the first failing
+ * entry in row order -- for GC_ERR_ASYMMETRIC, the first entry (x, y) whose
+ * reverse (y, x) is absent.
+ * Errors: GC_ERR_ARG, GC_ERR_RANGE, GC_ERR_UNSORTED, GC_ERR_DUPLICATE,
+ * GC_ERR_SELF_LOOP, GC_ERR_ASYMMETRIC.
+ */
+gc_status gc_validate_csr(int32_t n, const int32_t* row_ptr, const int32_t* col_idx);
+
 /* n and the number of undirected edges m = row_ptr[n] / 2. Either pointer may be NULL. */
 gc_status gc_graph_info(gc_graph g, int64_t* n, int64_t* m);
 

@@ -44,7 +44,8 @@ EXPORTED = ["gc_last_error", "gc_graph_upload", "gc_graph_info", "gc_graph_edges
             "gc_graph_phase_ms", "gc_graph_free", "gc_batch_create", "gc_batch_submit",
             "gc_batch_flush", "gc_batch_poll", "gc_batch_destroy", "gc_edge_triangles_noalloc",
             "gc_graph_work_counts", "gc_batch_submit_many", "gc_count_edge_induced", "gc_batch_set_param",
-            "gc_batch_get_param", "gc_batch_last_stats", "gc_batch_poll_many", "gc_release_cached_memory"]
+            "gc_batch_get_param", "gc_batch_last_stats", "gc_batch_poll_many", "gc_release_cached_memory",
+            "gc_validate_csr"]
 WORK_NAMES = ["t_members", "c_wedges", "k_members", "k_scan", "k_local_edges", "k_words", "finish_edges", "launches",
               "c_heavy_wedges", "c_heavy_sweeps", "t_scan", "t_triangles", "c_hash_wedges", "c_hub_jobs",
               "c_hub_ctas", "c_hub_busy_sum_ns", "c_hub_busy_max_ns", "c_hash2_wedges"]
@@ -99,7 +100,7 @@ def lib():
                          "gc_batch_submit", "gc_batch_flush", "gc_batch_poll", "gc_batch_destroy",
                          "gc_edge_triangles_noalloc", "gc_graph_work_counts", "gc_batch_submit_many",
                          "gc_batch_set_param", "gc_batch_get_param", "gc_batch_last_stats", "gc_batch_poll_many",
-                         "gc_release_cached_memory"):
+                         "gc_release_cached_memory", "gc_validate_csr"):
                 getattr(L, name).restype = C.c_int
             _lib = L
     return _lib
@@ -146,6 +147,13 @@ def _join(lo, hi):
 
 def gc_last_error() -> str:
     return lib().gc_last_error().decode(errors="replace")
+
+
+def gc_validate_csr(row_ptr, col_idx):
+    """The host checks of gc_graph_upload alone (no device work); raises
+    GcError with the code and message of the first failing entry."""
+    rp, ci = _host_i32(row_ptr), _host_i32(col_idx)
+    _check(lib().gc_validate_csr(len(rp) - 1, _ptr(rp), _ptr(ci) if len(ci) else None), "gc_validate_csr")
 
 
 def gc_graph_upload(row_ptr, col_idx, flags: int = 0, stream=None):

@@ -94,6 +94,32 @@ void run_threads(int nt, F f) {
   for (auto& x : th) x.join();
 }
 
+// For a graph that passed the linear checks (columns in range, rows
+// ascending) and failed a symmetry check: the message naming the first entry
+// (x, y) in row order whose reverse (y, x) is absent, found by a binary
+// search in row y per entry (rows in chunks over the host threads). A walk's
+// first mismatch need not be that entry -- an extra entry x0 in row y makes
+// the next (x1, y) mismatch although (y, x1) exists -- so the failure path
+// looks it up directly.
+std::string first_without_reverse(int32_t n, const int32_t* rp, const int32_t* ci) {
+  const int nt = rp[n] < (1 << 20) ? 1 : host_threads();
+  const std::vector<int32_t> b = nnz_chunks(n, rp, nt);
+  std::vector<std::pair<int32_t, int32_t>> hit((size_t)nt, {-1, -1});
+  run_threads(nt, [&](int t) {
+    for (int32_t x = b[t]; x < b[t + 1]; ++x)
+      for (int32_t p = rp[x]; p < rp[x + 1]; ++p) {
+        const int32_t y = ci[p];
+        if (!std::binary_search(ci + rp[y], ci + rp[y + 1], x)) {
+          hit[(size_t)t] = {x, y};
+          return;
+        }
+      }
+  });
+  for (const auto& h : hit)
+    if (h.first >= 0) return "edge (" + std::to_string(h.first) + "," + std::to_string(h.second) + ") has no reverse";
+  return "asymmetric graph";  // not reached after a failed symmetry check
+}
+
 // First error of a multi-threaded check, by thread (thread order = row order).
 struct Checks {
   std::vector<gc_status> st;
@@ -173,7 +199,8 @@ gc_status csr_linear_checks(int32_t n, const int32_t* rp, const int32_t* ci) {
 // row) gives the slot where x must stand in row y, and the entry there is
 // compared with x. Every entry is checked against a slot of row y, so a
 // missing reverse always fails, and a symmetric graph always passes. The
-// message of a failure is returned in *msg (the calling thread sets it).
+// message of a failure, naming the first entry in row order without a
+// reverse, is returned in *msg (the calling thread sets it).
 gc_status csr_symmetry(int32_t n, const int32_t* rp, const int32_t* ci, std::string* msg) {
   const int64_t nnz = rp[n];
   int nt = nnz < (1 << 20) ? 1 : host_threads();
@@ -182,7 +209,6 @@ gc_status csr_symmetry(int32_t n, const int32_t* rp, const int32_t* ci, std::str
   nt = (int)std::max<int64_t>(1, std::min<int64_t>(nt, (int64_t(1) << 30) / per));
   const std::vector<int32_t> b = nnz_chunks(n, rp, nt);
   std::vector<gc_status> st((size_t)nt, GC_OK);
-  std::vector<std::string> ms((size_t)nt);
   run_threads(nt, [&](int t) {
     std::vector<int32_t> fill((size_t)(n > 0 ? n : 1), -1);
     const int32_t x0 = b[t];
@@ -196,14 +222,13 @@ gc_status csr_symmetry(int32_t n, const int32_t* rp, const int32_t* ci, std::str
         const int32_t q = yb + f;
         if (q >= ye || ci[q] != x) {
           st[t] = GC_ERR_ASYMMETRIC;
-          ms[t] = "edge (" + std::to_string(x) + "," + std::to_string(y) + ") has no reverse";
           return;
         }
       }
   });
   for (int t = 0; t < nt; ++t)
     if (st[t] != GC_OK) {
-      *msg = ms[t];
+      *msg = first_without_reverse(n, rp, ci);
       return st[t];
     }
   return GC_OK;
@@ -237,8 +262,8 @@ gc_status validate_csr_small(int32_t n, const int32_t* rp, const int32_t* ci, st
   // (x, y), y > x, taken in row order, is matched with the next unmatched
   // entry of row y, which must be x; at the end every lower part must be
   // matched to its end. One random access per edge instead of one per entry;
-  // on a failure, the walk over every entry below names the first entry in
-  // row order without a reverse, as for a large graph.
+  // a failure names the first entry in row order without a reverse, as for a
+  // large graph.
   if ((int64_t)fill->size() < 2 * (int64_t)n) fill->resize(2 * (size_t)n);
   int32_t* f = fill->data();      // next unmatched entry of row y
   int32_t* lend = f + n;          // end of row x's lower part
@@ -260,17 +285,7 @@ gc_status validate_csr_small(int32_t n, const int32_t* rp, const int32_t* ci, st
   }
   for (int32_t y = 0; y < n && sym; ++y) sym = f[y] == lend[y];
   if (sym) return GC_OK;
-  for (int32_t y = 0; y < n; ++y) f[y] = rp[y];
-  for (int32_t x = 0; x < n; ++x)
-    for (int32_t p = rp[x]; p < rp[x + 1]; ++p) {
-      const int32_t y = ci[p];
-      const int32_t q = f[y]++;
-      if (q >= rp[y + 1] || ci[q] != x) {
-        set_error("edge (" + std::to_string(x) + "," + std::to_string(y) + ") has no reverse");
-        return GC_ERR_ASYMMETRIC;
-      }
-    }
-  set_error("asymmetric graph");  // not reached: the full walk finds the entry
+  set_error(first_without_reverse(n, rp, ci));
   return GC_ERR_ASYMMETRIC;
 }
 
@@ -416,6 +431,19 @@ struct gc_graph_s {
 extern "C" {
 
 const char* gc_last_error(void) { return t_err.c_str(); }
+
+gc_status gc_validate_csr(int32_t n, const int32_t* row_ptr, const int32_t* col_idx) {
+  if (n < 0 || !row_ptr || (!col_idx && n > 0 && row_ptr[n] > 0)) {
+    set_error("bad arguments to gc_validate_csr");
+    return GC_ERR_ARG;
+  }
+  if (row_ptr[n] >= 0 && row_ptr[n] < (1 << 20)) {
+    // the single-threaded checks each graph of a bulk submission gets
+    std::vector<int32_t> fill;
+    return validate_csr_small(n, row_ptr, col_idx, &fill);
+  }
+  return validate_csr(n, row_ptr, col_idx);
+}
 
 static void graph_release(gc_graph g) {
   if (!g) return;

@@ -174,3 +174,97 @@ def test_validation_of_corrupted_large_graphs(lib):
             gcb.gc_graph_upload(rp0, ci)
         assert ei.value.status == want[0], (trial, str(ei.value), want)
         assert str(ei.value).endswith(want[1]), (trial, str(ei.value), want)
+
+
+def _first_without_reverse(rp, ci):
+    """The first entry (x, y) in row order whose reverse (y, x) is absent, or
+    None (numpy, on a graph that passes the linear checks)."""
+    n = len(rp) - 1
+    rows = np.repeat(np.arange(n, dtype=np.int64), np.diff(rp))
+    key = rows * n + ci.astype(np.int64)           # (x, y), ascending in row order
+    rev = ci.astype(np.int64) * n + rows           # (y, x)
+    pos = np.searchsorted(key, rev)
+    present = (pos < len(key)) & (key[np.minimum(pos, len(key) - 1)] == rev)
+    bad = np.flatnonzero(~present)
+    return None if len(bad) == 0 else (int(rows[bad[0]]), int(ci[bad[0]]))
+
+
+@pytest.mark.parametrize("n,p,seed", [(300, 0.1, 1), (20000, 0.003, 5)])
+def test_validate_csr_names_the_first_failing_entry(lib, n, p, seed):
+    # gc_validate_csr on corrupted graphs below 2^20 entries (the checks of a
+    # bulk submission's graphs) and above (the threaded checks of an upload):
+    # the code and message of the first failing entry in row order; for an
+    # asymmetric graph, the first entry whose reverse is absent -- also where
+    # an extra entry of another row shifts a walk's alignment
+    import graphgen
+    rp0, ci0 = graphgen.er(n, p, seed)
+    assert (len(ci0) < (1 << 20)) == (n == 300)
+    gcb.gc_validate_csr(rp0, ci0)
+    rng = np.random.default_rng(seed)
+    deg = np.diff(rp0)
+    rows_ok = np.flatnonzero(deg >= 3)
+
+    def drop(rp, ci, x, k):
+        """row x without its entry k (row pointers shifted)."""
+        ci = np.delete(ci, rp[x] + k)
+        rp = rp.copy()
+        rp[x + 1:] -= 1
+        return rp, ci
+
+    for trial in range(30):
+        rp, ci = rp0.copy(), ci0.copy()
+        kind = trial % 3
+        if kind == 0:    # two entries dropped: their reverses left alone
+            for _ in range(2):
+                x = int(rng.choice(rows_ok))
+                rp, ci = drop(rp, ci, x, int(rng.integers(0, rp[x + 1] - rp[x])))
+        elif kind == 1:  # an entry moved to an absent column between its neighbours
+            x = int(rng.choice(rows_ok))
+            b, e = int(rp[x]), int(rp[x + 1])
+            k = int(rng.integers(b + 1, e - 1))
+            free = [y for y in range(int(ci[k - 1]) + 1, int(ci[k + 1])) if y != x and y != ci[k]]
+            if not free:
+                continue
+            ci[k] = int(rng.choice(free))
+        else:            # a linear violation (range, self-loop, duplicate, order)
+            x = int(rng.choice(rows_ok))
+            k = int(rng.integers(rp[x] + 1, rp[x + 1] - 1))
+            v = trial % 4
+            if v == 0:
+                ci[k] = n + 3
+            elif v == 1:
+                ci[k] = x
+            elif v == 2:
+                ci[k] = ci[k - 1]
+            else:
+                ci[k], ci[k + 1] = ci[k + 1], ci[k]
+        want = _first_violation(rp, ci)
+        if want is None and rp[-1] % 2:
+            want = (-5, "row_ptr[n] is odd: the graph cannot be symmetric")
+        if want is None:
+            e = _first_without_reverse(rp, ci)
+            want = None if e is None else (-5, f"edge ({e[0]},{e[1]}) has no reverse")
+        if want is None:
+            gcb.gc_validate_csr(rp, ci)
+            continue
+        with pytest.raises(gcb.GcError) as ei:
+            gcb.gc_validate_csr(rp, ci)
+        assert ei.value.status == want[0], (trial, str(ei.value), want)
+        assert str(ei.value).endswith(want[1]), (trial, str(ei.value), want)
+
+
+def test_validate_csr_extra_entry_names_the_entry_without_reverse(lib):
+    # rows 0:{1,3} 1:{0,2} 2:{0,1} 3:{0,1}: (2,0) and (3,1) have no reverse,
+    # (2,0) first in row order. Matching row 2's lower part in order, (1,2)
+    # meets the slot of the extra entry 0 first, though (2,1) exists: the
+    # message names the entry that really lacks its reverse.
+    rp = np.array([0, 2, 4, 6, 8], np.int32)
+    ci = np.array([1, 3, 0, 2, 0, 1, 0, 1], np.int32)
+    assert _first_without_reverse(rp, ci) == (2, 0)
+    with pytest.raises(gcb.GcError) as ei:
+        gcb.gc_validate_csr(rp, ci)
+    assert ei.value.status == -5 and str(ei.value).endswith("edge (2,0) has no reverse")
+    # an odd number of entries is refused before any walk
+    with pytest.raises(gcb.GcError) as ei:
+        gcb.gc_validate_csr(np.array([0, 1, 2, 3], np.int32), np.array([1, 2, 1], np.int32))
+    assert ei.value.status == -5 and str(ei.value).endswith("row_ptr[n] is odd: the graph cannot be symmetric")
